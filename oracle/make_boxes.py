@@ -1,0 +1,53 @@
+"""Write the stored boxes of the synthetic workloads (paper_2107_01745_b300/data/boxes.json).
+
+Reading of "box constraints on x and u at 80 % of the unconstrained-LQ range": for
+every state (input) component k, the bound is 0.8 max |x_k^i| (0.8 max |u_k^i|) over
+the nodes of the unconstrained solution x(0) of the instance, computed here by the
+FP64 oracle (Algorithm 3 at y = 0).  The box is symmetric; the root state is fixed
+to x0 and is not boxed.
+
+Usage: python oracle/make_boxes.py [workload ...]
+"""
+import json
+import os
+import sys
+
+import numpy as np
+
+_ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+if _ROOT not in sys.path:
+    sys.path.insert(0, _ROOT)
+
+from paper_2107_01745_b300 import workloads as W  # noqa: E402
+from oracle.oracle import LQOracle  # noqa: E402
+
+RECIPES = {
+    "paper_scale": lambda: W.paper_scale_unboxed(2),
+}
+
+
+def box_of(p, frac=0.8):
+    o = LQOracle(p)
+    x, u = o.solve(np.zeros(o.m))
+    xmax = frac * np.max(np.abs(x[1:]), axis=0)
+    umax = frac * np.max(np.abs(u), axis=0)
+    return xmax, umax
+
+
+def main(names):
+    path = os.path.join(_ROOT, "paper_2107_01745_b300", "data", "boxes.json")
+    boxes = {}
+    if os.path.exists(path):
+        with open(path) as f:
+            boxes = json.load(f)
+    for name in names:
+        xmax, umax = box_of(RECIPES[name]())
+        boxes[name] = {"xmax": [float(v) for v in xmax], "umax": [float(v) for v in umax],
+                       "recipe": "0.8 * max over nodes of |x_k|, |u_k| of the oracle's x(0)"}
+        print(name, "xmax range", xmax.min(), xmax.max(), "umax range", umax.min(), umax.max())
+    with open(path, "w") as f:
+        json.dump(boxes, f, indent=1)
+
+
+if __name__ == "__main__":
+    main(sys.argv[1:] or list(RECIPES))

@@ -1,0 +1,405 @@
+"""FP64 CPU oracle for dual MINFBE / NAMA on scenario trees.
+
+TEST INFRASTRUCTURE ONLY: imported by the tests, by the smoke check and by the
+benchmark's CPU-baseline leg, never by the library.  It shares no code with
+the CUDA path; both take their inputs from ``paper_2107_01745_b300.workloads``.
+
+The heavy lifting (offline factor, Algorithms 3 and 4) is in
+``stotree_oracle.c``; everything else here is plain numpy in FP64 and follows
+the paper's definitions directly:
+
+* Section II-D: prox, forward-backward map T_lambda, residual R_lambda = z - Hx,
+  x(y) = grad f*(-H'y), z_lambda(y) = prox_{g/lambda}(y/lambda + Hx(y)).
+  The sign of T_lambda follows the algorithms' own update, T(y) = y + lambda(Hx - z).
+* Section III-A: the forward-backward envelope (FBE) phi_lambda, evaluated both
+  by its definition and by the equivalent augmented-Lagrangian expression
+  -[f(x) + <y, Hx - z> + lambda/2 ||Hx - z||^2].
+* Section III-B, Algorithm 1: dual MINFBE with L-BFGS directions.
+* Section III-C, Algorithm 2: NAMA.  The extrapolation is read as
+  w = y + tau d + (1 - tau)(T(y) - y), so tau = 0 is the plain forward-backward step,
+  and the dual update as y+ = T(w).
+* Section III-E: diagonal preconditioning ybar^i = y^i / sqrt(pi^i); the solvers
+  iterate on ybar (equivalently on S H and the box S Y with S = diag(sqrt(pi))).
+  The termination test uses the unscaled residual ||z - Hx||_inf.
+
+Line searches evaluate phi_lambda(w) with a full solve at every trial point
+(no affine shortcut), so the oracle is slow but obviously follows the text.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import subprocess
+import time
+
+import numpy as np
+
+from paper_2107_01745_b300.workloads import Problem, dual_offsets
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_SRC = os.path.join(_HERE, "stotree_oracle.c")
+_BUILD = os.path.join(_HERE, "_build")
+_SO = os.path.join(_BUILD, "liboracle.so")
+
+
+def build_oracle(force: bool = False) -> str:
+    """Compile the C oracle (gcc, -O2, OpenMP) into oracle/_build/liboracle.so."""
+    os.makedirs(_BUILD, exist_ok=True)
+    if force or not os.path.exists(_SO) or os.path.getmtime(_SO) < os.path.getmtime(_SRC):
+        tmp = _SO + f".{os.getpid()}.tmp"
+        subprocess.check_call(["gcc", "-O2", "-fopenmp", "-fPIC", "-shared", "-std=c11",
+                               _SRC, "-o", tmp, "-lm"])
+        os.replace(tmp, _SO)
+    return _SO
+
+
+class _OrcProblem(ctypes.Structure):
+    _fields_ = [("Nn", ctypes.c_int), ("Np", ctypes.c_int), ("N", ctypes.c_int),
+                ("nx", ctypes.c_int), ("nu", ctypes.c_int),
+                ("parent", ctypes.c_void_p), ("cbeg", ctypes.c_void_p), ("ccnt", ctypes.c_void_p),
+                ("soff", ctypes.c_void_p), ("prob", ctypes.c_void_p),
+                ("A", ctypes.c_void_p), ("B", ctypes.c_void_p), ("c", ctypes.c_void_p),
+                ("Q", ctypes.c_void_p), ("R", ctypes.c_void_p), ("PN", ctypes.c_void_p),
+                ("q", ctypes.c_void_p), ("r", ctypes.c_void_p), ("pN", ctypes.c_void_p)]
+
+
+_lib_handle = None
+
+
+def _lib():
+    global _lib_handle
+    if _lib_handle is None:
+        lib = ctypes.CDLL(build_oracle())
+        lib.orc_factor.restype = ctypes.c_int
+        lib.orc_solve.restype = ctypes.c_int
+        lib.orc_num_threads.restype = ctypes.c_int
+        _lib_handle = lib
+    return _lib_handle
+
+
+def num_threads() -> int:
+    return int(_lib().orc_num_threads())
+
+
+def _ptr(a: np.ndarray):
+    return ctypes.c_void_p(a.ctypes.data)
+
+
+class LQOracle:
+    """Factor once, then evaluate x(y) (Algorithm 3) and x_lin(r) (Algorithm 4)."""
+
+    def __init__(self, p: Problem):
+        self.p = p
+        t = p.tree
+        self.nx, self.nu = p.nx, p.nu
+        self.Nn, self.Np, self.N = t.num_nodes, t.num_nonleaf, t.horizon
+        self._keep = {}
+        self._keep["parent"] = np.ascontiguousarray(t.parent, dtype=np.int32)
+        self._keep["cbeg"] = np.ascontiguousarray(t.child_begin, dtype=np.int32)
+        self._keep["ccnt"] = np.ascontiguousarray(t.child_count, dtype=np.int32)
+        soff = np.zeros(self.N + 2, dtype=np.int32)
+        for s in range(self.N + 1):
+            soff[s] = int(np.searchsorted(t.stage, s))
+        soff[self.N + 1] = self.Nn
+        self._keep["soff"] = soff
+        for name in ("A", "B", "c", "Q", "R", "PN", "q", "r", "pN"):
+            self._keep[name] = np.ascontiguousarray(getattr(p, name), dtype=np.float64)
+        self._keep["prob"] = np.ascontiguousarray(t.prob, dtype=np.float64)
+        k = self._keep
+        self._cp = _OrcProblem(self.Nn, self.Np, self.N, self.nx, self.nu,
+                               _ptr(k["parent"]), _ptr(k["cbeg"]), _ptr(k["ccnt"]), _ptr(k["soff"]),
+                               _ptr(k["prob"]), _ptr(k["A"]), _ptr(k["B"]), _ptr(k["c"]),
+                               _ptr(k["Q"]), _ptr(k["R"]), _ptr(k["PN"]),
+                               _ptr(k["q"]), _ptr(k["r"]), _ptr(k["pN"]))
+        nx, nu = self.nx, self.nu
+        self.P = np.zeros((self.Nn, nx, nx))
+        self.K = np.zeros((self.Np, nu, nx))
+        self.Lc = np.zeros((self.Np, nu, nu))
+        self.gu = np.zeros((self.Np, nu))
+        self.gx = np.zeros((self.Np, nx))
+        st = _lib().orc_factor(ctypes.byref(self._cp), _ptr(self.P), _ptr(self.K), _ptr(self.Lc),
+                               _ptr(self.gu), _ptr(self.gx))
+        if st != 0:
+            raise np.linalg.LinAlgError(f"Rbar not positive definite at node {-st - 1}")
+        self._s = np.zeros((self.Nn, nx))
+        self._ubar = np.zeros((self.Np, nu))
+        self.off = dual_offsets(t, nx, nu)
+        self.m = int(self.off[-1])
+        self.solve_calls = 0
+        # per dual element: sqrt(pi) of its node, unscaled box (root state block unbounded)
+        node_of = np.repeat(np.arange(self.Nn), np.diff(self.off))
+        self.node_of = node_of
+        self.sq = np.sqrt(t.prob[node_of])
+        lo = np.empty(self.m)
+        hi = np.empty(self.m)
+        for i in range(self.Nn):
+            o = self.off[i]
+            lo[o:o + nx], hi[o:o + nx] = p.xlo, p.xhi
+            if i < self.Np:
+                lo[o + nx:o + nx + nu], hi[o + nx:o + nx + nu] = p.ulo, p.uhi
+        lo[:nx], hi[:nx] = -np.inf, np.inf
+        self.lo, self.hi = lo, hi
+
+    @property
+    def Rbar(self) -> np.ndarray:
+        return np.einsum("iab,icb->iac", self.Lc, self.Lc)
+
+    def solve(self, y: np.ndarray, homogeneous: bool = False):
+        """x(y) by Algorithm 3 (or Algorithm 4 if homogeneous).  y is unscaled, dual-sized."""
+        y = np.ascontiguousarray(y, dtype=np.float64)
+        assert y.shape == (self.m,)
+        x = np.zeros((self.Nn, self.nx))
+        u = np.zeros((self.Np, self.nu))
+        x0 = np.ascontiguousarray(self.p.x0, dtype=np.float64)
+        _lib().orc_solve(ctypes.byref(self._cp), _ptr(self.K), _ptr(self.Lc), _ptr(self.gu), _ptr(self.gx),
+                         _ptr(y), _ptr(x0), ctypes.c_int(1 if homogeneous else 0),
+                         _ptr(x), _ptr(u), _ptr(self._s), _ptr(self._ubar))
+        self.solve_calls += 1
+        return x, u
+
+    def stack(self, x: np.ndarray, u: np.ndarray) -> np.ndarray:
+        """Hx laid out like y: nonleaf [x^i; u^i], leaf x^l."""
+        npl, nx, nu = self.Np, self.nx, self.nu
+        h = np.empty(self.m)
+        h[:npl * (nx + nu)] = np.concatenate([x[:npl], u], axis=1).reshape(-1)
+        h[npl * (nx + nu):] = x[npl:].reshape(-1)
+        return h
+
+    def unstack(self, h: np.ndarray):
+        npl, nx, nu = self.Np, self.nx, self.nu
+        blk = h[:npl * (nx + nu)].reshape(npl, nx + nu)
+        x = np.concatenate([blk[:, :nx], h[npl * (nx + nu):].reshape(-1, nx)], axis=0)
+        return x, blk[:, nx:].copy()
+
+    def hx(self, y: np.ndarray, homogeneous: bool = False) -> np.ndarray:
+        return self.stack(*self.solve(y, homogeneous))
+
+    def cost(self, x: np.ndarray, u: np.ndarray) -> float:
+        """f(x) of eq. (f-definition) with the quadratic costs of Section II-B (no 1/2).
+        The root's state term pi^0 (p'Qp + q'p) is a constant and is included."""
+        p, pr = self.p, self.p.tree.prob
+        npl = self.Np
+        xn, xl = x[:npl], x[npl:]
+        f = np.sum(pr[:npl] * (xn ** 2 @ p.Q + u ** 2 @ p.R + xn @ p.q + u @ p.r))
+        f += np.sum(pr[npl:] * (xl ** 2 @ p.PN + xl @ p.pN))
+        return float(f)
+
+
+# --------------------------------------------------------------------------------------
+# Scaled dual quantities (Sections II-D, III-A, III-E).  ybar is the scaled dual.
+# --------------------------------------------------------------------------------------
+
+def hbar(o: LQOracle, yb: np.ndarray):
+    """S Hx(S ybar) and the primal (x, u)."""
+    x, u = o.solve(o.sq * yb)
+    return o.sq * o.stack(x, u), x, u
+
+
+def hbar_lin(o: LQOracle, r: np.ndarray) -> np.ndarray:
+    """S H x_lin(S r) = -grad^2 fhat(ybar) r (Algorithm 4)."""
+    return o.sq * o.hx(o.sq * r, homogeneous=True)
+
+
+def proj_box(o: LQOracle, v: np.ndarray) -> np.ndarray:
+    """Projection on the scaled box S Y (prox of the indicator, Section II-D)."""
+    return np.minimum(np.maximum(v, o.sq * o.lo), o.sq * o.hi)
+
+
+def g_conj(o: LQOracle, v: np.ndarray) -> float:
+    """Support function of S Y: sum_k max(lo_k v_k, hi_k v_k); +inf off its domain."""
+    lo, hi = o.sq * o.lo, o.sq * o.hi
+    out = 0.0
+    pos, neg = v > 0, v < 0
+    if np.any(np.isinf(hi[pos])) or np.any(np.isinf(lo[neg])):
+        return np.inf
+    out += float(np.sum(hi[pos] * v[pos])) + float(np.sum(lo[neg] * v[neg]))
+    return out
+
+
+def prox_g_conj(o: LQOracle, v: np.ndarray, lam: float) -> np.ndarray:
+    """prox_{lam g*}(v) = v - lam proj(v / lam) (Moreau decomposition)."""
+    return v - lam * proj_box(o, v / lam)
+
+
+def prox_g_conj_closed(o: LQOracle, v: np.ndarray, lam: float) -> np.ndarray:
+    """Two-sided shrink: v - lam hi if v > lam hi, v - lam lo if v < lam lo, else 0."""
+    lo, hi = o.sq * o.lo, o.sq * o.hi
+    out = np.zeros_like(v)
+    up, dn = v > lam * hi, v < lam * lo
+    out[up] = v[up] - lam * hi[up]
+    out[dn] = v[dn] - lam * lo[dn]
+    return out
+
+
+def fb_point(o: LQOracle, yb: np.ndarray, lam: float) -> dict:
+    """Everything the algorithms need at one dual point (full solve)."""
+    h, x, u = hbar(o, yb)
+    z = proj_box(o, h + yb / lam)
+    r = z - h
+    f = o.cost(x, u)
+    phi = -(f + float(np.dot(yb, h - z)) + 0.5 * lam * float(np.dot(h - z, h - z)))
+    return dict(y=yb, h=h, x=x, u=u, z=z, r=r, f=f, phi=phi, T=yb - lam * r,
+                res_inf=float(np.max(np.abs(r / o.sq))) if r.size else 0.0)
+
+
+def fhat(o: LQOracle, yb: np.ndarray) -> float:
+    """fhat(ybar) = f*(-Hbar' ybar) = -(f(x(ybar)) + <ybar, Hbar x(ybar)>)."""
+    h, x, u = hbar(o, yb)
+    return -(o.cost(x, u) + float(np.dot(yb, h)))
+
+
+def fbe_literal(o: LQOracle, yb: np.ndarray, lam: float) -> float:
+    """phi_lambda(y) = fhat(y) + g*(T(y)) - lam <grad fhat(y), R(y)> + lam/2 ||R(y)||^2 (Section III-A)."""
+    pt = fb_point(o, yb, lam)
+    grad = -pt["h"]
+    fh = -(pt["f"] + float(np.dot(yb, pt["h"])))
+    return fh + g_conj(o, pt["T"]) - lam * float(np.dot(grad, pt["r"])) + 0.5 * lam * float(np.dot(pt["r"], pt["r"]))
+
+
+def fbe_grad(o: LQOracle, yb: np.ndarray, lam: float, pt: dict | None = None) -> np.ndarray:
+    """grad phi = (I - lam grad^2 fhat) R = R + lam Hbar x_lin(R)."""
+    if pt is None:
+        pt = fb_point(o, yb, lam)
+    return pt["r"] + lam * hbar_lin(o, pt["r"])
+
+
+# --------------------------------------------------------------------------------------
+# L-BFGS (two-loop recursion, Nocedal & Wright Alg. 7.4), FIFO memory.
+# --------------------------------------------------------------------------------------
+
+class LBFGS:
+    """H0 = gamma I with gamma = <s,q>/<q,q> of the newest pair; lam I while empty."""
+
+    def __init__(self, mem: int, lam: float):
+        self.mem, self.lam = mem, lam
+        self.S, self.Y = [], []
+
+    def push(self, s: np.ndarray, q: np.ndarray):
+        self.S.append(s.copy())
+        self.Y.append(q.copy())
+        if len(self.S) > self.mem:
+            self.S.pop(0)
+            self.Y.pop(0)
+
+    def clear(self):
+        self.S, self.Y = [], []
+
+    def apply(self, g: np.ndarray) -> np.ndarray:
+        """B g, with B the L-BFGS inverse-Hessian approximation."""
+        if not self.S:
+            return self.lam * g
+        qv = g.copy()
+        alphas = []
+        rhos = [1.0 / float(np.dot(s, y)) for s, y in zip(self.S, self.Y)]
+        for s, y, rho in zip(reversed(self.S), reversed(self.Y), reversed(rhos)):
+            a = rho * float(np.dot(s, qv))
+            alphas.append(a)
+            qv -= a * y
+        s_new, y_new = self.S[-1], self.Y[-1]
+        gamma = float(np.dot(s_new, y_new)) / float(np.dot(y_new, y_new))
+        rvec = gamma * qv
+        for (s, y, rho), a in zip(zip(self.S, self.Y, rhos), reversed(alphas)):
+            b = rho * float(np.dot(y, rvec))
+            rvec += (a - b) * s
+        return rvec
+
+
+def power_lambda(o: LQOracle, r0: np.ndarray, iters: int = 50, safety: float = 0.9):
+    """Estimate L = ||grad^2 fhat|| by power iteration on r -> -Hbar x_lin(r), lam = safety / L."""
+    r = r0 / np.linalg.norm(r0)
+    L = 0.0
+    for _ in range(iters):
+        v = -hbar_lin(o, r)
+        L = float(np.dot(r, v))
+        nv = np.linalg.norm(v)
+        if nv == 0.0:
+            break
+        r = v / nv
+    return safety / L, L
+
+
+# --------------------------------------------------------------------------------------
+# Algorithms 1 and 2.
+# --------------------------------------------------------------------------------------
+
+def _result(o, pt, k, hist, status, t0):
+    return dict(y=o.sq * pt["y"], ybar=pt["y"], x=pt["x"], u=pt["u"], z=pt["z"] / o.sq,
+                h=pt["h"] / o.sq, res_inf=pt["res_inf"], iters=k, status=status,
+                solve_calls=o.solve_calls, phi=hist["phi"], tau=hist["tau"], res=hist["res"],
+                seconds=time.perf_counter() - t0)
+
+
+def nama(o: LQOracle, lam: float, y0: np.ndarray | None = None, tol: float = 1e-8, mem: int = 5,
+         max_iter: int = 1000, max_ls: int = 30, eps_curv: float = 1e-12) -> dict:
+    """Algorithm 2 on the preconditioned dual.  y0 is unscaled."""
+    t0 = time.perf_counter()
+    o.solve_calls = 0
+    yb = np.zeros(o.m) if y0 is None else np.asarray(y0, dtype=np.float64) / o.sq
+    lb = LBFGS(mem, lam)
+    pt = fb_point(o, yb, lam)
+    hist = dict(phi=[pt["phi"]], tau=[], res=[pt["res_inf"]])
+    k = 0
+    while pt["res_inf"] > tol:
+        if k >= max_iter:
+            return _result(o, pt, k, hist, "not_converged", t0)
+        r = pt["r"]
+        d = -lb.apply(r)
+        fb_dir = pt["T"] - pt["y"]
+        tau, wp = 1.0, None
+        for _ in range(max_ls + 1):
+            cand = fb_point(o, pt["y"] + tau * d + (1.0 - tau) * fb_dir, lam)
+            if cand["phi"] <= pt["phi"]:
+                wp = cand
+                break
+            tau *= 0.5
+        if wp is None:
+            tau, wp = 0.0, fb_point(o, pt["T"].copy(), lam)
+        new = fb_point(o, wp["T"], lam)
+        s = new["y"] - pt["y"]
+        qv = new["r"] - r
+        if float(np.dot(s, qv)) > eps_curv * float(np.dot(s, s)) * float(np.dot(r, r)):
+            lb.push(s, qv)
+        pt = new
+        k += 1
+        hist["phi"].append(pt["phi"])
+        hist["tau"].append(tau)
+        hist["res"].append(pt["res_inf"])
+    return _result(o, pt, k, hist, "converged", t0)
+
+
+def minfbe(o: LQOracle, lam: float, y0: np.ndarray | None = None, tol: float = 1e-8, mem: int = 5,
+           max_iter: int = 1000, max_ls: int = 30, eps_curv: float = 1e-12) -> dict:
+    """Algorithm 1 on the preconditioned dual.  y0 is unscaled."""
+    t0 = time.perf_counter()
+    o.solve_calls = 0
+    yb = np.zeros(o.m) if y0 is None else np.asarray(y0, dtype=np.float64) / o.sq
+    lb = LBFGS(mem, lam)
+    pt = fb_point(o, yb, lam)
+    g = fbe_grad(o, yb, lam, pt)
+    hist = dict(phi=[pt["phi"]], tau=[], res=[pt["res_inf"]])
+    k = 0
+    while pt["res_inf"] > tol:
+        if k >= max_iter:
+            return _result(o, pt, k, hist, "not_converged", t0)
+        d = -lb.apply(g)
+        tau, wp = 1.0, None
+        for _ in range(max_ls + 1):
+            cand = fb_point(o, pt["y"] + tau * d, lam)
+            if cand["phi"] <= pt["phi"]:
+                wp = cand
+                break
+            tau *= 0.5
+        if wp is None:
+            tau, wp = 0.0, pt
+        new = fb_point(o, wp["T"], lam)
+        g_new = fbe_grad(o, new["y"], lam, new)
+        s = new["y"] - pt["y"]
+        qv = g_new - g
+        if float(np.dot(s, qv)) > eps_curv * float(np.dot(s, s)) * float(np.dot(g, g)):
+            lb.push(s, qv)
+        pt, g = new, g_new
+        k += 1
+        hist["phi"].append(pt["phi"])
+        hist["tau"].append(tau)
+        hist["res"].append(pt["res_inf"])
+    return _result(o, pt, k, hist, "converged", t0)

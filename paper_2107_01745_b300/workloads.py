@@ -1,0 +1,298 @@
+"""Seeded synthetic scenario trees and problem data.
+
+This module only draws inputs: tree shapes, probabilities, dynamics, costs,
+boxes and initial states.  It holds none of the method's arithmetic (no
+factorisation, no solve, no prox), so both the CPU oracle and the CUDA path
+can take their inputs from it.
+
+Tree conventions (Section II-A, scenario trees):
+  * nodes are numbered stage by stage (breadth first), the root is node 0;
+  * the children of a node occupy a contiguous index range;
+  * every leaf sits at stage N, so nodes 0..Np-1 are the non-leaf nodes and
+    Np..Nn-1 the leaves;
+  * node probabilities satisfy pi^0 = 1, sum over a stage = 1 and
+    sum over child(i) = pi^i.
+
+Problem data (Section II-B/C, eq. system_dynamics_tree and the quadratic
+stage cost): per node j >= 1 the edge data A^j (nx x nx), B^j (nx x nu) and
+c^j (nx) lives on the child; the costs Q, R, P_N are diagonal and shared by
+all nodes, the linear terms q, r, p_N are shared vectors, and the box
+constraints on x and u are shared vectors.
+"""
+from __future__ import annotations
+
+import json
+import os
+from dataclasses import dataclass, field
+
+import numpy as np
+
+_DATA_DIR = os.path.join(os.path.dirname(os.path.abspath(__file__)), "data")
+
+
+@dataclass
+class Tree:
+    horizon: int
+    parent: np.ndarray      # int32 [Nn], parent[0] = -1
+    stage: np.ndarray       # int32 [Nn]
+    prob: np.ndarray        # float64 [Nn]
+    child_begin: np.ndarray  # int32 [Nn]
+    child_count: np.ndarray  # int32 [Nn]
+
+    @property
+    def num_nodes(self) -> int:
+        return int(self.parent.shape[0])
+
+    @property
+    def num_nonleaf(self) -> int:
+        return int(np.count_nonzero(self.child_count > 0))
+
+    @property
+    def num_leaves(self) -> int:
+        return self.num_nodes - self.num_nonleaf
+
+    def stage_nodes(self, t: int) -> np.ndarray:
+        return np.nonzero(self.stage == t)[0]
+
+    def stage_ranges(self):
+        """(first, count) of every stage; stages are contiguous by construction."""
+        out = []
+        for t in range(self.horizon + 1):
+            idx = self.stage_nodes(t)
+            out.append((int(idx[0]), int(idx.size)))
+        return out
+
+
+def tree_from_branching(branching, cond_probs=None) -> Tree:
+    """Build a tree from a per-node child count.
+
+    ``branching`` is either a list with one entry per stage 0..N-1 (every node
+    of that stage gets that many children) or a list of per-stage lists with
+    one child count per node of the stage (ragged trees).  ``cond_probs``
+    optionally gives, per non-leaf node in index order, the conditional
+    probabilities pi^[i] of its children; the default is uniform.
+    """
+    parent = [-1]
+    stage = [0]
+    prob = [1.0]
+    frontier = [0]
+    child_begin = {}
+    child_count = {}
+    t = 0
+    cp_iter = iter(cond_probs) if cond_probs is not None else None
+    for spec in branching:
+        nxt = []
+        counts = spec if isinstance(spec, (list, tuple, np.ndarray)) else [spec] * len(frontier)
+        if len(counts) != len(frontier):
+            raise ValueError("per-stage branching list has the wrong length")
+        for node, b in zip(frontier, counts):
+            b = int(b)
+            if b < 1:
+                raise ValueError("every non-leaf node needs at least one child")
+            child_begin[node] = len(parent)
+            child_count[node] = b
+            w = np.full(b, 1.0 / b) if cp_iter is None else np.asarray(next(cp_iter), dtype=np.float64)
+            for k in range(b):
+                parent.append(node)
+                stage.append(t + 1)
+                prob.append(prob[node] * float(w[k]))
+                nxt.append(len(parent) - 1)
+        frontier = nxt
+        t += 1
+    nn = len(parent)
+    cb = np.array([child_begin.get(i, 0) for i in range(nn)], dtype=np.int32)
+    cc = np.array([child_count.get(i, 0) for i in range(nn)], dtype=np.int32)
+    return Tree(horizon=t, parent=np.array(parent, dtype=np.int32),
+                stage=np.array(stage, dtype=np.int32), prob=np.array(prob, dtype=np.float64),
+                child_begin=cb, child_count=cc)
+
+
+def random_tree(rng: np.random.Generator, horizon: int, max_branch: int = 3,
+                p_branch: float = 0.6, random_probs: bool = True) -> Tree:
+    """Ragged tree: each node of each stage draws 1..max_branch children."""
+    counts_per_stage = []
+    width = 1
+    for _ in range(horizon):
+        counts = [int(rng.integers(1, max_branch + 1)) if rng.random() < p_branch else 1
+                  for _ in range(width)]
+        counts_per_stage.append(counts)
+        width = sum(counts)
+    cond = None
+    if random_probs:
+        cond = []
+        for counts in counts_per_stage:
+            for b in counts:
+                w = rng.uniform(0.2, 1.0, size=b)
+                cond.append(w / w.sum())
+    return tree_from_branching(counts_per_stage, cond)
+
+
+@dataclass
+class Problem:
+    """One scenario-tree LQ problem with box constraints (FP64 host arrays)."""
+    tree: Tree
+    nx: int
+    nu: int
+    A: np.ndarray       # [Nn, nx, nx]; row 0 unused (zeros)
+    B: np.ndarray       # [Nn, nx, nu]
+    c: np.ndarray       # [Nn, nx]
+    Q: np.ndarray       # [nx] diagonal
+    R: np.ndarray       # [nu] diagonal
+    PN: np.ndarray      # [nx] diagonal
+    q: np.ndarray       # [nx]
+    r: np.ndarray       # [nu]
+    pN: np.ndarray      # [nx]
+    xlo: np.ndarray     # [nx]
+    xhi: np.ndarray     # [nx]
+    ulo: np.ndarray     # [nu]
+    uhi: np.ndarray     # [nu]
+    x0: np.ndarray      # [nx]
+    name: str = "problem"
+    meta: dict = field(default_factory=dict)
+
+    @property
+    def num_dual(self) -> int:
+        t = self.tree
+        return t.num_nonleaf * (self.nx + self.nu) + t.num_leaves * self.nx
+
+    @property
+    def num_primal(self) -> int:
+        t = self.tree
+        return t.num_nonleaf * self.nu + (t.num_nodes - 1) * self.nx
+
+
+def dual_offsets(tree: Tree, nx: int, nu: int) -> np.ndarray:
+    """Start of node i's block in a dual-sized vector: nonleaf [x; u], leaf [x]."""
+    nn, npl = tree.num_nodes, tree.num_nonleaf
+    off = np.empty(nn + 1, dtype=np.int64)
+    idx = np.arange(nn, dtype=np.int64)
+    off[:nn] = np.where(idx < npl, idx * (nx + nu), npl * (nx + nu) + (idx - npl) * nx)
+    off[nn] = npl * (nx + nu) + (nn - npl) * nx
+    return off
+
+
+def spectral_rescale(M: np.ndarray, rho: float) -> np.ndarray:
+    ev = np.linalg.eigvals(M)
+    return M * (rho / np.max(np.abs(ev)))
+
+
+# --------------------------------------------------------------------------------------
+# Workload recipes.  Draw order per recipe: A, per-node perturbations, B, Q, w (= c), x0.
+# --------------------------------------------------------------------------------------
+
+def tiny_fp64(seed: int = 0) -> Problem:
+    """Horizon 3, binary tree (15 nodes), nx=4, nu=2, shared A (rho 0.95) and B."""
+    rng = np.random.default_rng(seed)
+    nx, nu = 4, 2
+    tree = tree_from_branching([2, 2, 2])
+    nn = tree.num_nodes
+    A0 = spectral_rescale(rng.standard_normal((nx, nx)), 0.95)
+    B0 = rng.standard_normal((nx, nu))
+    A = np.broadcast_to(A0, (nn, nx, nx)).copy()
+    B = np.broadcast_to(B0, (nn, nx, nu)).copy()
+    c = 0.1 * rng.standard_normal((nn, nx))
+    A[0] = 0.0
+    B[0] = 0.0
+    c[0] = 0.0
+    x0 = rng.uniform(-3.0, 3.0, size=nx)
+    return Problem(tree=tree, nx=nx, nu=nu, A=A, B=B, c=c,
+                   Q=np.ones(nx), R=0.1 * np.ones(nu), PN=np.ones(nx),
+                   q=np.zeros(nx), r=np.zeros(nu), pN=np.zeros(nx),
+                   xlo=-5.0 * np.ones(nx), xhi=5.0 * np.ones(nx),
+                   ulo=-np.ones(nu), uhi=np.ones(nu), x0=x0, name="tiny_fp64")
+
+
+def paper_scale_tree() -> Tree:
+    """Horizon 20: binary for the first 10 stages, then one child (1024 scenarios)."""
+    return tree_from_branching([2] * 10 + [1] * 10)
+
+
+def paper_scale_unboxed(seed: int = 2, nx: int = 100, nu: int = 50, tree: Tree | None = None) -> Problem:
+    """Paper-scale instance before its box is set: per-node A_j = A + 0.05 N(0,1),
+    A at spectral radius 0.98, B_j ~ N(0, 1/nx), w ~ N(0, 0.05^2), Q = diag(U[0.5, 2]),
+    R = 0.1 I, P_N = I, x0 ~ U[-3, 3].  Boxes are infinite here."""
+    rng = np.random.default_rng(seed)
+    tree = paper_scale_tree() if tree is None else tree
+    nn = tree.num_nodes
+    A0 = spectral_rescale(rng.standard_normal((nx, nx)), 0.98)
+    A = np.empty((nn, nx, nx))
+    A[0] = 0.0
+    A[1:] = A0[None] + 0.05 * rng.standard_normal((nn - 1, nx, nx))
+    B = np.empty((nn, nx, nu))
+    B[0] = 0.0
+    B[1:] = rng.standard_normal((nn - 1, nx, nu)) * (1.0 / np.sqrt(nx))
+    Qd = rng.uniform(0.5, 2.0, size=nx)
+    c = np.empty((nn, nx))
+    c[0] = 0.0
+    c[1:] = 0.05 * rng.standard_normal((nn - 1, nx))
+    x0 = rng.uniform(-3.0, 3.0, size=nx)
+    inf = np.inf
+    return Problem(tree=tree, nx=nx, nu=nu, A=A, B=B, c=c,
+                   Q=Qd, R=0.1 * np.ones(nu), PN=np.ones(nx),
+                   q=np.zeros(nx), r=np.zeros(nu), pN=np.zeros(nx),
+                   xlo=-inf * np.ones(nx), xhi=inf * np.ones(nx),
+                   ulo=-inf * np.ones(nu), uhi=inf * np.ones(nu), x0=x0, name="paper_scale")
+
+
+def load_box(name: str):
+    path = os.path.join(_DATA_DIR, "boxes.json")
+    with open(path) as f:
+        boxes = json.load(f)
+    if name not in boxes:
+        raise KeyError(f"no stored box for workload {name!r}; run oracle/make_boxes.py")
+    b = boxes[name]
+    return np.asarray(b["xmax"], dtype=np.float64), np.asarray(b["umax"], dtype=np.float64)
+
+
+def with_box(p: Problem, xmax: np.ndarray, umax: np.ndarray) -> Problem:
+    p.xlo, p.xhi = -np.asarray(xmax, dtype=np.float64), np.asarray(xmax, dtype=np.float64)
+    p.ulo, p.uhi = -np.asarray(umax, dtype=np.float64), np.asarray(umax, dtype=np.float64)
+    return p
+
+
+def paper_scale(seed: int = 2) -> Problem:
+    """The paper-scale instance (N=20, 1024 scenarios, nx=100, nu=50) with its stored box:
+    per component 80 % of the largest |x_k| (|u_k|) of the unconstrained solution x(0)."""
+    p = paper_scale_unboxed(seed)
+    xmax, umax = load_box("paper_scale")
+    p.name = "paper_scale"
+    return with_box(p, xmax, umax)
+
+
+def random_problem(seed: int, horizon: int = 3, nx: int = 3, nu: int = 2, max_branch: int = 3,
+                   box_scale: float = 1.0, linear_terms: bool = True, p_branch: float = 0.6) -> Problem:
+    """Small ragged problem with per-node dynamics, for parity cases and pins."""
+    rng = np.random.default_rng(seed)
+    tree = random_tree(rng, horizon, max_branch=max_branch, p_branch=p_branch)
+    nn = tree.num_nodes
+    A0 = spectral_rescale(rng.standard_normal((nx, nx)), 0.95)
+    A = np.empty((nn, nx, nx))
+    A[0] = 0.0
+    A[1:] = A0[None] + 0.1 * rng.standard_normal((nn - 1, nx, nx))
+    B = np.empty((nn, nx, nu))
+    B[0] = 0.0
+    B[1:] = rng.standard_normal((nn - 1, nx, nu))
+    c = np.empty((nn, nx))
+    c[0] = 0.0
+    c[1:] = 0.1 * rng.standard_normal((nn - 1, nx))
+    Qd = rng.uniform(0.5, 2.0, size=nx)
+    Rd = rng.uniform(0.05, 0.5, size=nu)
+    PNd = rng.uniform(0.5, 2.0, size=nx)
+    if linear_terms:
+        q, r, pN = (0.1 * rng.standard_normal(nx), 0.1 * rng.standard_normal(nu),
+                    0.1 * rng.standard_normal(nx))
+    else:
+        q, r, pN = np.zeros(nx), np.zeros(nu), np.zeros(nx)
+    x0 = rng.uniform(-3.0, 3.0, size=nx)
+    xmax = box_scale * rng.uniform(1.0, 3.0, size=nx)
+    umax = box_scale * rng.uniform(0.3, 1.0, size=nu)
+    return Problem(tree=tree, nx=nx, nu=nu, A=A, B=B, c=c, Q=Qd, R=Rd, PN=PNd, q=q, r=r, pN=pN,
+                   xlo=-xmax, xhi=xmax, ulo=-umax, uhi=umax, x0=x0, name=f"random{seed}")
+
+
+def random_dual(p: Problem, seed: int, scale: float = 1.0) -> np.ndarray:
+    """A seeded dual vector (unscaled), zero on the root's state block."""
+    rng = np.random.default_rng(seed)
+    y = scale * rng.standard_normal(p.num_dual)
+    y[:p.nx] = 0.0
+    return y
