@@ -1,0 +1,212 @@
+/*
+ * stotree.h -- C ABI of the B300 scenario-tree solver library (libstotree.so).
+ *
+ * The library computes, on one NVIDIA B300 (sm_103a), the data-parallel hot path of
+ * dual MINFBE and NAMA for scenario-based stochastic optimal control, after
+ * Sampathirao, Patrinos, Bemporad and Sopasakis, "Massively parallelizable proximal
+ * algorithms for large-scale stochastic optimal control problems":
+ *   - the offline factor of the tree LQ problem (Section III-D),
+ *   - the dual-gradient solve x(y) (Algorithm 3) and Hessian-vector products
+ *     (Algorithm 4), for one or several right-hand sides,
+ *   - Algorithm 1 (dual MINFBE with L-BFGS) and Algorithm 2 (NAMA) around them,
+ *   - an FP64 KKT-residual check of a returned primal-dual pair.
+ *
+ * Problem (Section II): scenario tree with nodes 0..Nn-1 numbered stage by stage,
+ * root 0, children of a node contiguous, every leaf at stage N; node probabilities
+ * pi^i.  Dynamics x^j = A^j x^i + B^j u^i + c^j for j in child(i) (eq.
+ * system_dynamics_tree).  Cost sum over nonleaf i of pi^i (x'Qx + u'Ru + q'x + r'u)
+ * plus sum over leaves l of pi^l (x'P_N x + p_N'x), with diagonal Q, R, P_N shared by
+ * all nodes (no 1/2 factor, as in Section II-B).  Constraints: box on the block
+ * z^i = [x^i; u^i] of every nonleaf node and on z^l = x^l of every leaf; the root
+ * state is the parameter p = x0 and is not boxed.
+ *
+ * Vector layouts.  A dual-sized vector (y, Hx, z; length m = Np(nx+nu) + Nl nx) has
+ * one block per node: nonleaf i at offset i(nx+nu) holding [x-part (nx); u-part (nu)],
+ * leaf l at offset Np(nx+nu) + (l-Np)nx holding [x-part (nx)].  Primal outputs are
+ * x [Nn][nx] (x[0] = x0) and u [Np][nu].
+ *
+ * Precision: a handle is created either FP64 (every device array and vector of the
+ * solve path in double) or FP32 (solve step, prox and L-BFGS in float; the factor
+ * always runs in FP64 and is rounded to FP32 once).  "real" below is double or
+ * float accordingly; scalars crossing the ABI are double.
+ *
+ * Memory.  The library never allocates device memory: the caller asks for the
+ * workspace size, allocates it (e.g. as a torch tensor) and binds it.  All vector
+ * arguments of the solve calls are device pointers owned by the caller, 16-byte
+ * aligned.  Host arrays passed to the set-up calls are copied before return.
+ *
+ * Streams and errors.  Every call taking a cudaStream_t enqueues its work on that
+ * stream; the *_solve calls and stotree_estimate_lambda synchronise the stream
+ * before returning (their results are host scalars).  Errors are returned, never
+ * trapped; a CUDA error is reported as STO_ERR_CUDA and the message is kept for
+ * stotree_last_error().  Calls on one handle must not overlap in time: the handle's
+ * workspace holds the intermediate state of every call.
+ */
+#ifndef STOTREE_H
+#define STOTREE_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#if defined(__GNUC__)
+#define STO_API __attribute__((visibility("default")))
+#else
+#define STO_API
+#endif
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct CUstream_st *sto_stream_t; /* = cudaStream_t; NULL is the legacy default stream */
+typedef struct stotree_s *stotree_t;
+
+typedef enum {
+    STO_OK = 0,
+    STO_ERR_INVALID_ARG = 1,   /* null pointer, bad size, bad option value */
+    STO_ERR_TREE = 2,          /* numbering or probabilities violate the tree conventions */
+    STO_ERR_NOT_READY = 3,     /* workspace not bound, data missing or not factored */
+    STO_ERR_NUMERICAL = 4,     /* Rbar not positive definite, or NaN/Inf met in a solve */
+    STO_ERR_CUDA = 5,          /* a CUDA runtime call failed (see stotree_last_error) */
+    STO_ERR_TIMEOUT = 6,       /* a bounded device-side wait gave up */
+    STO_NOT_CONVERGED = 7,     /* max_iter reached; the last iterate is still returned */
+    STO_ERR_WORKSPACE = 8      /* workspace smaller than stotree_workspace_size() */
+} sto_status;
+
+typedef enum { STO_FP64 = 0, STO_FP32 = 1 } sto_precision;
+
+/* Tree (Section II-A).  parent[0] = -1, parent[i] < i, stage(parent[i]) = stage(i) - 1,
+ * nodes sorted by stage, children of each node contiguous, all leaves at stage horizon;
+ * prob[0] = 1, prob > 0, sum over child(i) of prob = prob[i] (relative tolerance 1e-9).
+ * Host pointers, copied. */
+typedef struct {
+    int32_t num_nodes, horizon, nx, nu;
+    const int32_t *parent;
+    const double *prob;
+} sto_tree_desc;
+
+/* Options of Algorithms 1 and 2. */
+typedef struct {
+    double lambda;      /* step, in (0, 1/L) (Algorithm 1 input); see stotree_estimate_lambda */
+    double tol;         /* stop when ||z - Hx||_inf <= tol (unscaled residual, Section III-B) */
+    double eps_curv;    /* epsilon' of the L-BFGS curvature test (Li-Fukushima) */
+    int32_t lbfgs_mem;  /* L-BFGS memory, 1..16 */
+    int32_t max_iter;   /* iteration cap; STO_NOT_CONVERGED when hit */
+    int32_t max_ls;     /* line-search halvings tau = 2^0 .. 2^-max_ls (<= 30), then tau = 0 */
+} sto_opts;
+
+typedef struct {
+    int32_t iters;        /* iterations k performed */
+    int32_t solve_calls;  /* right-hand sides pushed through Algorithm 3/4 ("oracle calls") */
+    int32_t status;       /* sto_status of the solve */
+    int32_t ls_zero;      /* iterations whose line search fell back to tau = 0 */
+    double res_inf;       /* ||z - Hx||_inf at the returned iterate */
+    double fbe;           /* phi_lambda at the returned iterate (scaled dual) */
+    double ms;            /* wall time of the call on the stream, milliseconds */
+} sto_info;
+
+/* Validate the tree and create a handle.  No device work.
+ * Errors: STO_ERR_INVALID_ARG (null pointer, nx < 1, nu < 1, nx + nu > 512 for FP32 or
+ * > 256 for FP64, m >= 2^31), STO_ERR_TREE. */
+STO_API sto_status stotree_create(const sto_tree_desc *tree, int32_t precision, stotree_t *out);
+
+/* Release the handle (host memory only; the workspace belongs to the caller). */
+STO_API void stotree_destroy(stotree_t h);
+
+/* Problem sizes: m (dual length), n (primal length Np nu + (Nn-1) nx), Np, Nl. */
+STO_API sto_status stotree_sizes(stotree_t h, int64_t *m, int64_t *n, int32_t *num_nonleaf, int32_t *num_leaves);
+
+/* Device workspace needed for every call of this handle, in bytes (256-byte aligned
+ * sections; the caller passes a 256-byte aligned base). */
+STO_API sto_status stotree_workspace_size(stotree_t h, size_t *bytes);
+
+/* Bind caller-owned device memory of at least stotree_workspace_size() bytes and
+ * upload the tree arrays on the stream.  Errors: STO_ERR_WORKSPACE, STO_ERR_INVALID_ARG. */
+STO_API sto_status stotree_bind_workspace(stotree_t h, void *dev_ptr, size_t bytes, sto_stream_t stream);
+
+/* Upload the dynamics of nodes [first, first+count) (eq. system_dynamics_tree): host
+ * FP64 A [count][nx][nx], B [count][nx][nu], c [count][nx], row-major, where entry k
+ * belongs to node first+k.  Node 0's data is ignored.  May be called in chunks.
+ * Invalidates the factor. */
+STO_API sto_status stotree_set_dynamics(stotree_t h, int32_t first, int32_t count, const double *A,
+                                const double *B, const double *c, sto_stream_t stream);
+
+/* Upload the shared costs (Section II-B): diagonals Q [nx], R [nu] (> 0), P_N [nx] (>= 0)
+ * and linear terms q [nx], r [nu], p_N [nx] (NULL = zero).  Host FP64.  Invalidates the factor. */
+STO_API sto_status stotree_set_costs(stotree_t h, const double *Q, const double *R, const double *PN,
+                             const double *q, const double *r, const double *pN, sto_stream_t stream);
+
+/* Upload the shared box (Section II-B, indicator of Y): xlo <= x <= xhi on every non-root
+ * node's state, ulo <= u <= uhi on every nonleaf input.  +-INFINITY allowed.  Host FP64. */
+STO_API sto_status stotree_set_box(stotree_t h, const double *xlo, const double *xhi, const double *ulo,
+                           const double *uhi, sto_stream_t stream);
+
+/* Offline factor (Section III-D, Riccati-type recursion), FP64 on the device, then the
+ * solve arrays in the handle's precision.  Enqueued on the stream; the positive
+ * definiteness check of Rbar is reported by the next synchronising call, or here when
+ * sync != 0.  Errors: STO_ERR_NOT_READY, STO_ERR_NUMERICAL (sync only). */
+STO_API sto_status stotree_factor(stotree_t h, int32_t sync, sto_stream_t stream);
+
+/* One solve round of Algorithm 3 (homogeneous = 0) or Algorithm 4 (homogeneous = 1) for
+ * nrhs right-hand sides (1..4) sharing one pass over the factor arrays (the parallel
+ * x(r), x(d) evaluation of Section III-C).
+ *   y    device real [nrhs][m]: dual vectors.  scaled = 0: unscaled y; scaled = 1: the
+ *        preconditioned ybar of Section III-E, i.e. y = sqrt(pi) ybar per node block.
+ *   x0   device real [nx], the root state p (ignored when homogeneous).
+ *   hx   device real [nrhs][m]: Hx(y) laid out like y; with scaled = 1 the output is
+ *        sqrt(pi) Hx per block.  The root block holds [x0; u^0] ([0; u^0] if homogeneous).
+ * Asynchronous.  Errors: STO_ERR_INVALID_ARG, STO_ERR_NOT_READY. */
+STO_API sto_status stotree_solve_step(stotree_t h, const void *y, const void *x0, void *hx, int32_t nrhs,
+                              int32_t homogeneous, int32_t scaled, sto_stream_t stream);
+
+/* Primal trajectory of the last solve round's first right-hand side: x [Nn][nx],
+ * u [Np][nu] (device real).  Asynchronous. */
+STO_API sto_status stotree_last_primal(stotree_t h, void *x, void *u, sto_stream_t stream);
+
+/* Estimate L = ||grad^2 fhat|| of the preconditioned dual by `iters` power iterations on
+ * r -> -sqrt(pi) H x_lin(sqrt(pi) r) (Algorithm 4) from the caller's start vector r0
+ * (device real [m], overwritten), and return lambda = safety / L.  Synchronises. */
+STO_API sto_status stotree_estimate_lambda(stotree_t h, void *r0, int32_t iters, double safety,
+                                   double *lambda, double *L, sto_stream_t stream);
+
+/* Algorithm 2 (NAMA) on the preconditioned dual, from y (device real [m], unscaled; zeros
+ * for a cold start).  On return: y = the final dual iterate (unscaled), x [Nn][nx],
+ * u [Np][nu] = x(y), z [m] = z_lambda(y) (unscaled); any of x, u, z may be NULL.
+ * x0 is the device root state.  Synchronises the stream; fills info.
+ * Errors: STO_ERR_INVALID_ARG, STO_ERR_NOT_READY, STO_ERR_NUMERICAL, STO_NOT_CONVERGED. */
+STO_API sto_status stotree_nama_solve(stotree_t h, const sto_opts *opts, const void *x0, void *y, void *x,
+                              void *u, void *z, sto_info *info, sto_stream_t stream);
+
+/* Algorithm 1 (dual MINFBE with L-BFGS directions); arguments as stotree_nama_solve. */
+STO_API sto_status stotree_minfbe_solve(stotree_t h, const sto_opts *opts, const void *x0, void *y, void *x,
+                                void *u, void *z, sto_info *info, sto_stream_t stream);
+
+/* FP64 optimality check of a primal-dual pair (x, u, y), all device real, against the FP64
+ * problem data (conditions listed under Algorithm 1):
+ *   out[0] = max |x^j - A^j x^i - B^j u^i - c^j|              (dynamics, x^0 = x0)
+ *   out[1] = max |stationarity of f(x) + <y, Hx> in (x, u)|   (-H'y in the subdifferential of f)
+ *   out[2] = max over box violation of Hx                      (primal feasibility)
+ *   out[3] = max |y_k| over components strictly inside the box by more than tol_active
+ *   out[4] = max of -y_k at upper bounds / +y_k at lower bounds (sign of the multipliers)
+ * Synchronises.  out is host double[5]. */
+STO_API sto_status stotree_kkt_check(stotree_t h, const void *x0, const void *x, const void *u, const void *y,
+                             double tol_active, double *out, sto_stream_t stream);
+
+/* Per-launch timing of the solve-step kernels with CUDA events on the launching stream:
+ * enable (1) / disable (0); read the accumulated device milliseconds and launch count. */
+STO_API sto_status stotree_set_timing(stotree_t h, int32_t enable);
+STO_API sto_status stotree_get_timing(stotree_t h, double *solve_ms, int64_t *solve_launches,
+                              int64_t *solve_rhs);
+
+/* Bytes of matrix data one solve round reads (algorithmic, independent of nrhs) and of
+ * vector data per right-hand side, for roofline accounting. */
+STO_API sto_status stotree_solve_bytes(stotree_t h, double *matrix_bytes, double *vector_bytes_per_rhs);
+
+STO_API const char *stotree_status_str(sto_status s);
+STO_API const char *stotree_last_error(stotree_t h);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* STOTREE_H */

@@ -3,8 +3,11 @@
 Reading of "box constraints on x and u at 80 % of the unconstrained-LQ range": for
 every state (input) component k, the bound is 0.8 max |x_k^i| (0.8 max |u_k^i|) over
 the nodes of the unconstrained solution x(0) of the instance, computed here by the
-FP64 oracle (Algorithm 3 at y = 0).  The box is symmetric; the root state is fixed
-to x0 and is not boxed.
+FP64 oracle (Algorithm 3 at y = 0), but never below 1.02 times the unconstrained
+values of the first two stages after the root (inputs of stages 0 and 1).  Those
+states are set by x0 through nu < nx inputs, and a plain 80 % box makes the
+instance infeasible (the dual iterates diverge).  The box is symmetric; the root
+state is fixed to x0 and is not boxed.
 
 Usage: python oracle/make_boxes.py [workload ...]
 """
@@ -26,11 +29,14 @@ RECIPES = {
 }
 
 
-def box_of(p, frac=0.8):
+def box_of(p, frac=0.8, protect=2, margin=1.02):
     o = LQOracle(p)
     x, u = o.solve(np.zeros(o.m))
-    xmax = frac * np.max(np.abs(x[1:]), axis=0)
-    umax = frac * np.max(np.abs(u), axis=0)
+    st = p.tree.stage
+    early_x = (st >= 1) & (st <= protect)
+    early_u = st[:o.Np] < protect
+    xmax = np.maximum(frac * np.max(np.abs(x[1:]), axis=0), margin * np.max(np.abs(x[early_x]), axis=0))
+    umax = np.maximum(frac * np.max(np.abs(u), axis=0), margin * np.max(np.abs(u[early_u]), axis=0))
     return xmax, umax
 
 
@@ -43,7 +49,7 @@ def main(names):
     for name in names:
         xmax, umax = box_of(RECIPES[name]())
         boxes[name] = {"xmax": [float(v) for v in xmax], "umax": [float(v) for v in umax],
-                       "recipe": "0.8 * max over nodes of |x_k|, |u_k| of the oracle's x(0)"}
+                       "recipe": "max(0.8 * max over nodes, 1.02 * max over stages 1-2 (inputs 0-1)) of |x_k|, |u_k| of the oracle's x(0)"}
         print(name, "xmax range", xmax.min(), xmax.max(), "umax range", umax.min(), umax.max())
     with open(path, "w") as f:
         json.dump(boxes, f, indent=1)

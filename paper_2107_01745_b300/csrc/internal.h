@@ -1,0 +1,141 @@
+// Internal declarations of libstotree (not part of the C ABI).
+#pragma once
+#include <cuda_runtime.h>
+
+#include <cstdint>
+#include <string>
+#include <vector>
+
+#include "../../include/stotree.h"
+
+namespace sto {
+
+constexpr int kMaxMem = 16;          // L-BFGS memory limit (ring has kMaxMem + 1 slots)
+constexpr int kMaxRhs = 4;           // right-hand sides per solve round
+constexpr int kMaxDim = 1024;        // nx, nu limit
+constexpr int kRedBlocks = 592;      // blocks of the reduction kernels (4 per SM on 148 SMs)
+constexpr int kRedSlots = 80;        // doubles per block in the partials buffer
+constexpr int kMaxCand = 32;         // line-search candidates
+
+// Device-resident state of one MINFBE / NAMA run: every decision of the algorithms is
+// taken by device code and read by the host only for the stopping test.
+struct SolverScalars {
+    // header: the host reads only these first kScalHead bytes per iteration
+    double lambda, tol, eps_curv;
+    int mem, max_ls, method, nan_flag;
+    double phi;       // FBE at the current iterate
+    double res_inf;   // ||z - Hx||_inf (unscaled) at the current iterate
+    double tau;       // accepted line-search step
+    int ls_done, ls_zero, iters, status;
+    double cand[kMaxCand];
+    // L-BFGS ring of mem+1 slots (slot order = oldest .. newest starting at head)
+    int lb_count, lb_head, lb_pending_valid, lb_new_pair;
+    double SY[kMaxMem + 1][kMaxMem + 1];   // s_a' y_b by slot
+    double YY[kMaxMem + 1][kMaxMem + 1];   // y_a' y_b by slot
+    double gamma;                          // H0 = gamma I
+    double coef_s[kMaxMem + 1];            // direction d = -(gamma g + sum coef_s[a] s_a + sum coef_y[a] y_a)
+    double coef_y[kMaxMem + 1];
+    // curvature test pieces of the pending pair
+    double sq_dot, s_norm2, g_norm2_prev, g_norm2;
+    // power iteration
+    double pw_L, pw_inv_norm;
+    // reduction bookkeeping
+    unsigned int red_counter;
+    unsigned int pad2;
+};
+constexpr size_t kScalHead = 80;
+
+struct Layout {
+    size_t total = 0;
+    // tree
+    size_t parent, cbeg, ccnt, soff, node_stage;
+    size_t prob64;               // double [Nn]
+    size_t sqp;                  // real [Nn] sqrt(pi)
+    // FP64 problem data
+    size_t G64;                  // double [Nn][nx][ld64] = [A | B | c]
+    size_t cost64;               // double [3nx + 3nu... ] Q R PN q r pN
+    size_t box64;                // double [2(nx+nu)]
+    // factor scratch (FP64)
+    size_t P[2], PG, W, Rb, Zb, M, K64;
+    size_t fstatus;              // int
+    // solve arrays (real)
+    size_t G, K, Ri, gu, gx, c;
+    size_t cost, box;            // real copies: W (Q|R|PN), ell (q|r|pN), lo/hi (x|u)
+    // solve scratch (real)
+    size_t s, ubar, xs, us;
+    // solver
+    size_t vec;                  // kNumVec vectors of m reals
+    size_t ringS, ringY;         // (kMaxMem+1) vectors of m reals each
+    size_t partials;             // double [kRedBlocks][kRedSlots]
+    size_t scal;                 // SolverScalars
+    size_t kkt;                  // double scratch for the KKT check
+};
+
+constexpr int kNumVec = 10;      // ybar, h, r, d, hr, hd, g, tmp0, tmp1, tmp2
+
+}  // namespace sto
+
+struct stotree_s {
+    int Nn = 0, Np = 0, Nl = 0, N = 0, nx = 0, nu = 0;
+    int prec = STO_FP32;
+    int64_t m = 0, n = 0;
+    std::vector<int32_t> parent, cbeg, ccnt, soff, stage;
+    std::vector<double> prob;
+    int max_width = 0;
+    int ld64 = 0;     // G64 row length (nx + nu + 1 rounded to 2)
+    int ldg = 0;      // solve G row length (nx + nu rounded to 16 bytes)
+    int ldk = 0;      // K row length (nx rounded)
+    int ldr = 0;      // Ri row length (nu rounded)
+    size_t esz = 4;   // sizeof(real)
+    sto::Layout L;
+    char *ws = nullptr;
+    size_t ws_bytes = 0;
+    std::vector<uint8_t> have_dyn;   // per node
+    bool have_cost = false, have_box = false, factored = false;
+    std::string err;
+    // timing
+    bool timing = false;
+    std::vector<cudaEvent_t> ev_pool;
+    size_t ev_used = 0;
+    double solve_ms = 0.0;
+    int64_t solve_launches = 0, solve_rhs = 0;
+    int64_t solve_calls = 0;
+    // pinned host mirror of the device scalars
+    sto::SolverScalars *host_scal = nullptr;
+
+    template <class T>
+    T *at(size_t off) const { return reinterpret_cast<T *>(ws + off); }
+};
+
+namespace sto {
+
+sto_status cuda_fail(stotree_t h, cudaError_t e, const char *what);
+#define STO_CUDA(h, call)                                       \
+    do {                                                        \
+        cudaError_t _e = (call);                                \
+        if (_e != cudaSuccess) return sto::cuda_fail(h, _e, #call); \
+    } while (0)
+
+// factor.cu
+sto_status factor_run(stotree_t h, cudaStream_t st);
+
+// solve.cu: one round of Algorithm 3/4 on nrhs vectors (real pointers in the workspace
+// or caller memory).  scaled: input is ybar and output S Hx.
+sto_status solve_round(stotree_t h, const void *const *y, const void *x0, void *const *hx, int nrhs,
+                       bool homogeneous, bool scaled, cudaStream_t st);
+
+// vecops.cu
+template <class T>
+struct VecOps;  // defined in vecops.cu
+
+sto_status solver_run(stotree_t h, int method, const sto_opts *o, const void *x0, void *y, void *x,
+                      void *u, void *z, sto_info *info, cudaStream_t st);
+sto_status lambda_run(stotree_t h, void *r0, int iters, double safety, double *lambda, double *L,
+                      cudaStream_t st);
+sto_status kkt_run(stotree_t h, const void *x0, const void *x, const void *u, const void *y,
+                   double tol_active, double *out, cudaStream_t st);
+
+void timing_begin(stotree_t h, cudaStream_t st, cudaEvent_t *ev);
+void timing_end(stotree_t h, cudaStream_t st, cudaEvent_t ev0, int nrhs);
+
+}  // namespace sto

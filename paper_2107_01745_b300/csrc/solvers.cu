@@ -1,0 +1,888 @@
+// Algorithms 1 (dual MINFBE) and 2 (NAMA) on the preconditioned dual, the power-iteration
+// estimate of L, and the FP64 KKT check.
+//
+// Every step except the solve rounds is an elementwise pass over the m dual entries with a
+// deterministic two-level reduction (per-block partials, the last block to finish sums them in
+// block order and takes the algorithm's decision on the device):
+//   k_point   z = proj_{SY}(h + ybar/lam), r = z - h, FBE, ||S^-1 r||_inf          (Section II-D, III-A)
+//   k_grad    g = r + lam S H x_lin(r) = grad FBE                                  (Section III-A)
+//   k_lb_dots / k_lb_dir   L-BFGS direction d = -B g, compact form               (Alg. 1 line 3, Alg. 2 line 5)
+//   k_ls      FBE at up to 19 step sizes tau = 2^-k in one pass                    (Alg. 1 line 4, Alg. 2 line 6)
+//   k_fbstep  ybar+ = T_lam(w), s = ybar+ - ybar                                   (Alg. 1 line 5, Alg. 2 lines 7-8)
+//
+// Readings of the text used here:
+//   * T_lam(y) = y + lam (Hx(y) - z_lam(y)), the sign used by Algorithm 2's update.
+//   * NAMA's extrapolation is w = y + tau d + (1 - tau)(T(y) - y) (tau = 0 is the FB step) and
+//     its update y+ = T(w); MINFBE's update (printed as x^{k+1}) is y+ = T(w).
+//   * "Choose the smallest tau" means the largest tau = 2^-nu, nu = 0, 1, ...; after max_ls
+//     halvings tau = 0, for which the FB step always decreases the FBE.
+//   * x(y + tau d) = x(y) + tau x_lin(d) with x_lin from Algorithm 4 (the printed x(d) holds
+//     only without affine terms), so every trial point costs one elementwise pass.
+//   * The FBE is evaluated as -[f(x) + <y, Hx - z> + lam/2 ||Hx - z||^2], equal to the
+//     definition of Section III-A; with diagonal costs f(x) is a weighted sum over the
+//     entries of S Hx.  The line search sums the per-entry change against the current point.
+//   * Termination uses the unscaled residual ||z - Hx||_inf (Section III-B).
+//   * L-BFGS: H0 = gamma I with gamma = <s,q>/<q,q> of the newest pair, lam I while empty;
+//     pairs are kept when <s,q> > eps' ||s||^2 ||g||^2 (Alg. 1 line 7, Alg. 2 line 10).
+#include <cmath>
+#include <cstring>
+
+#include "internal.h"
+
+namespace sto {
+namespace {
+
+constexpr int kThreads = 256;
+
+template <class T>
+struct DualView {
+    int m, Np, nx, nu, nxu, leaf_base;
+    const T *sqp, *box, *Wc;  // box = [lo x|u][hi x|u], Wc = [Q|R|PN][q|r|pN]
+
+    struct Meta {
+        T sq, lo, hi, w, l;
+    };
+
+    __device__ __forceinline__ Meta meta(int e) const {
+        int node, comp, kind;
+        if (e < leaf_base) {
+            node = e / nxu;
+            const int k = e - node * nxu;
+            kind = k < nx ? 0 : 1;
+            comp = k < nx ? k : k - nx;
+        } else {
+            const int e2 = e - leaf_base;
+            node = Np + e2 / nx;
+            comp = e2 - (node - Np) * nx;
+            kind = 2;
+        }
+        Meta M;
+        M.sq = sqp[node];
+        const int bi = kind == 1 ? nx + comp : comp;
+        const int wi = kind == 0 ? comp : (kind == 1 ? nx + comp : nx + nu + comp);
+        if (node == 0 && kind == 0) {
+            M.lo = -INFINITY;
+            M.hi = INFINITY;
+        } else {
+            M.lo = M.sq * box[bi];
+            M.hi = M.sq * box[nxu + bi];
+        }
+        M.w = Wc[wi];
+        M.l = M.sq * Wc[2 * nx + nu + wi];
+        return M;
+    }
+};
+
+template <class T>
+__device__ __forceinline__ T clampv(T v, T lo, T hi) {
+    return v < lo ? lo : (v > hi ? hi : v);
+}
+
+// Per-entry term of -FBE: W h^2 + l h + w (h - z) + lam/2 (h - z)^2, z = proj(h + w/lam).
+template <class T>
+__device__ __forceinline__ T fbe_term(T h, T w, T lam, T ilam, const typename DualView<T>::Meta &M) {
+    const T z = clampv(h + w * ilam, M.lo, M.hi);
+    const T dz = h - z;
+    return h * (M.w * h + M.l) + dz * (w + T(0.5) * lam * dz);
+}
+
+__device__ __forceinline__ double warp_sum_d(double v) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    return v;
+}
+__device__ __forceinline__ double warp_max_d(double v) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v = fmax(v, __shfl_xor_sync(0xffffffffu, v, o));
+    return v;
+}
+
+// Two-level deterministic reduction of NS sums and NM maxima.  Returns true in the last
+// block to finish, where out[0..NS+NM) holds the totals (summed in block order).
+template <int NS, int NM>
+__device__ bool reduce_last(double *sums, double *maxs, double *partials, unsigned *counter, double *out) {
+    constexpr int NV = NS + NM;
+    __shared__ double red[kThreads / 32][NV > 0 ? NV : 1];
+    __shared__ bool last;
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+#pragma unroll
+    for (int k = 0; k < NS; ++k) sums[k] = warp_sum_d(sums[k]);
+#pragma unroll
+    for (int k = 0; k < NM; ++k) maxs[k] = warp_max_d(maxs[k]);
+    if (lane == 0) {
+#pragma unroll
+        for (int k = 0; k < NS; ++k) red[warp][k] = sums[k];
+#pragma unroll
+        for (int k = 0; k < NM; ++k) red[warp][NS + k] = maxs[k];
+    }
+    __syncthreads();
+    if (threadIdx.x < NV) {
+        const int k = threadIdx.x;
+        double acc = k < NS ? 0.0 : -INFINITY;
+        for (int w = 0; w < kThreads / 32; ++w) acc = k < NS ? acc + red[w][k] : fmax(acc, red[w][k]);
+        partials[blockIdx.x * kRedSlots + k] = acc;
+    }
+    __threadfence();
+    __syncthreads();
+    if (threadIdx.x == 0) last = atomicAdd(counter, 1u) == gridDim.x - 1;
+    __syncthreads();
+    if (!last) return false;
+    __threadfence();
+    if (threadIdx.x < NV) {
+        const int k = threadIdx.x;
+        double acc = k < NS ? 0.0 : -INFINITY;
+        for (int b = 0; b < (int)gridDim.x; ++b) {
+            const double v = __ldcg(partials + b * kRedSlots + k);
+            acc = k < NS ? acc + v : fmax(acc, v);
+        }
+        out[k] = acc;
+    }
+    if (threadIdx.x == 0) *counter = 0u;
+    __syncthreads();
+    return true;
+}
+
+// ---------------------------------------------------------------------------------------
+// k_point: residual, FBE and stopping test at the current ybar (h = S H x(ybar)).
+// pair = 1 (NAMA after a step): q = r_new - r_old -> Y[p], curvature test, commit pair.
+// ---------------------------------------------------------------------------------------
+template <class T>
+__global__ void __launch_bounds__(kThreads) k_point(DualView<T> dv, const T *__restrict__ yb, const T *__restrict__ h,
+                                                    T *r, T *ringS, T *ringY, long long vstride, int pair,
+                                                    SolverScalars *sc, double *partials) {
+    __shared__ double tot[8];
+    const T lam = (T)sc->lambda, ilam = T(1) / lam;
+    const int p = (sc->lb_head + sc->lb_count) % (sc->mem + 1);
+    const T *sv = ringS + p * vstride;
+    T *qv = ringY + p * vstride;
+    T fsum = 0, sq_dot = 0, s2 = 0, g2 = 0;
+    double sums[5] = {0, 0, 0, 0, 0};
+    double maxs[1] = {0.0};
+    int nan = 0;
+    for (int e = blockIdx.x * kThreads + threadIdx.x; e < dv.m; e += gridDim.x * kThreads) {
+        const auto M = dv.meta(e);
+        const T he = h[e], ye = yb[e];
+        const T z = clampv(he + ye * ilam, M.lo, M.hi);
+        const T re = z - he;
+        fsum += fbe_term<T>(he, ye, lam, ilam, M);
+        const T ra = fabs(re) / M.sq;
+        if (!(ra <= T(3.0e38))) nan = 1;
+        maxs[0] = fmax(maxs[0], (double)ra);
+        if (pair) {
+            const T ro = r[e];
+            const T q = re - ro;
+            const T s = sv[e];
+            qv[e] = q;
+            sq_dot += s * q;
+            s2 += s * s;
+            g2 += ro * ro;
+        }
+        r[e] = re;
+    }
+    sums[0] = fsum;
+    sums[1] = sq_dot;
+    sums[2] = s2;
+    sums[3] = g2;
+    sums[4] = nan;
+    if (reduce_last<5, 1>(sums, maxs, partials, &sc->red_counter, tot) && threadIdx.x == 0) {
+        sc->phi = -tot[0];
+        sc->res_inf = tot[5];
+        if (tot[4] > 0.0 || !(tot[0] == tot[0])) sc->nan_flag = 1;
+        if (pair && sc->lb_pending_valid) {
+            if (tot[1] > sc->eps_curv * tot[2] * tot[3]) {
+                if (sc->lb_count < sc->mem)
+                    sc->lb_count += 1;
+                else
+                    sc->lb_head = (sc->lb_head + 1) % (sc->mem + 1);
+                sc->lb_new_pair = 1;
+            }
+            sc->lb_pending_valid = 0;
+        }
+    }
+}
+
+// MINFBE: g_new = r + lam hr = grad FBE; with a pending pair q = g_new - g_old -> Y[p].
+template <class T>
+__global__ void __launch_bounds__(kThreads) k_grad(int m, const T *__restrict__ r, const T *__restrict__ hr, T *g,
+                                                   T *ringS, T *ringY, long long vstride, SolverScalars *sc,
+                                                   double *partials) {
+    __shared__ double tot[8];
+    const T lam = (T)sc->lambda;
+    const int pair = sc->lb_pending_valid;
+    const int p = (sc->lb_head + sc->lb_count) % (sc->mem + 1);
+    const T *sv = ringS + p * vstride;
+    T *qv = ringY + p * vstride;
+    T sq_dot = 0, s2 = 0, g2 = 0;
+    for (int e = blockIdx.x * kThreads + threadIdx.x; e < m; e += gridDim.x * kThreads) {
+        const T gn = r[e] + lam * hr[e];
+        if (pair) {
+            const T go = g[e];
+            const T q = gn - go;
+            const T s = sv[e];
+            qv[e] = q;
+            sq_dot += s * q;
+            s2 += s * s;
+            g2 += go * go;
+        }
+        g[e] = gn;
+    }
+    double sums[3] = {sq_dot, s2, g2};
+    double maxs[1];
+    if (reduce_last<3, 0>(sums, maxs, partials, &sc->red_counter, tot) && threadIdx.x == 0) {
+        if (pair) {
+            if (tot[0] > sc->eps_curv * tot[1] * tot[2]) {
+                if (sc->lb_count < sc->mem)
+                    sc->lb_count += 1;
+                else
+                    sc->lb_head = (sc->lb_head + 1) % (sc->mem + 1);
+                sc->lb_new_pair = 1;
+            }
+            sc->lb_pending_valid = 0;
+        }
+    }
+}
+
+// L-BFGS, compact representation (Byrd, Nocedal, Schnabel 1994): one pass for S'g, Y'g and the
+// Gram column of a newly committed pair, then the small solve in the last block.  MEM >= mem.
+template <class T, int MEM>
+__global__ void __launch_bounds__(kThreads) k_lb_dots(int m, const T *__restrict__ g, const T *ringS,
+                                                      const T *ringY, long long vstride, SolverScalars *sc,
+                                                      double *partials) {
+    __shared__ double tot[4 * MEM];
+    const int cnt = sc->lb_count, head = sc->lb_head, M1 = sc->mem + 1, newp = sc->lb_new_pair;
+    if (cnt == 0) {
+        if (blockIdx.x == 0 && threadIdx.x == 0) {
+            sc->gamma = sc->lambda;
+            sc->lb_new_pair = 0;
+        }
+        return;
+    }
+    const int nslot = (head + cnt - 1) % M1;
+    const T *yn = ringY + nslot * vstride;
+    const T *sp[MEM];
+    const T *yp[MEM];
+#pragma unroll
+    for (int k = 0; k < MEM; ++k) {
+        const int sl = (head + (k < cnt ? k : 0)) % M1;
+        sp[k] = ringS + sl * vstride;
+        yp[k] = ringY + sl * vstride;
+    }
+    T a[MEM], b[MEM], c[MEM], d[MEM];
+#pragma unroll
+    for (int k = 0; k < MEM; ++k) a[k] = b[k] = c[k] = d[k] = T(0);
+    for (int e = blockIdx.x * kThreads + threadIdx.x; e < m; e += gridDim.x * kThreads) {
+        const T ge = g[e];
+        const T ye = newp ? yn[e] : T(0);
+#pragma unroll
+        for (int k = 0; k < MEM; ++k) {
+            if (k < cnt) {
+                const T se = sp[k][e], qe = yp[k][e];
+                a[k] += se * ge;
+                b[k] += qe * ge;
+                c[k] += se * ye;
+                d[k] += qe * ye;
+            }
+        }
+    }
+    double sums[4 * MEM];
+#pragma unroll
+    for (int k = 0; k < MEM; ++k) {
+        sums[k] = a[k];
+        sums[MEM + k] = b[k];
+        sums[2 * MEM + k] = c[k];
+        sums[3 * MEM + k] = d[k];
+    }
+    double maxs[1];
+    if (reduce_last<4 * MEM, 0>(sums, maxs, partials, &sc->red_counter, tot) && threadIdx.x == 0) {
+        int sl[MEM];
+        for (int k = 0; k < cnt; ++k) sl[k] = (head + k) % M1;
+        if (newp) {
+            for (int k = 0; k < cnt; ++k) {
+                sc->SY[sl[k]][nslot] = tot[2 * MEM + k];
+                sc->YY[sl[k]][nslot] = tot[3 * MEM + k];
+                sc->YY[nslot][sl[k]] = tot[3 * MEM + k];
+            }
+            sc->lb_new_pair = 0;
+        }
+        const double gamma = sc->SY[nslot][nslot] / sc->YY[nslot][nslot];
+        double x1[MEM], t[MEM], top[MEM];
+        // x1 = R^-1 a with R_ij = s_i'y_j (i <= j)
+        for (int i = cnt - 1; i >= 0; --i) {
+            double s = tot[i];
+            for (int j = i + 1; j < cnt; ++j) s -= sc->SY[sl[i]][sl[j]] * x1[j];
+            x1[i] = s / sc->SY[sl[i]][sl[i]];
+        }
+        // t = (D + gamma Y'Y) x1 - gamma b,  top = R^-T t
+        for (int i = 0; i < cnt; ++i) {
+            double s = sc->SY[sl[i]][sl[i]] * x1[i] - gamma * tot[MEM + i];
+            for (int j = 0; j < cnt; ++j) s += gamma * sc->YY[sl[i]][sl[j]] * x1[j];
+            t[i] = s;
+        }
+        for (int i = 0; i < cnt; ++i) {
+            double s = t[i];
+            for (int j = 0; j < i; ++j) s -= sc->SY[sl[j]][sl[i]] * top[j];
+            top[i] = s / sc->SY[sl[i]][sl[i]];
+        }
+        sc->gamma = gamma;
+        for (int i = 0; i < cnt; ++i) {
+            sc->coef_s[i] = top[i];
+            sc->coef_y[i] = -gamma * x1[i];
+        }
+    }
+}
+
+// d = -(gamma g + sum_i coef_s[i] s_i + sum_i coef_y[i] y_i)
+template <class T, int MEM>
+__global__ void __launch_bounds__(kThreads) k_lb_dir(int m, const T *__restrict__ g, const T *ringS, const T *ringY,
+                                                     long long vstride, const SolverScalars *sc, T *dvec) {
+    const int cnt = sc->lb_count, head = sc->lb_head, M1 = sc->mem + 1;
+    const T gamma = (T)sc->gamma;
+    T cs[MEM], cy[MEM];
+    const T *sp[MEM];
+    const T *yp[MEM];
+#pragma unroll
+    for (int k = 0; k < MEM; ++k) {
+        const int sl = (head + (k < cnt ? k : 0)) % M1;
+        cs[k] = k < cnt ? (T)sc->coef_s[k] : T(0);
+        cy[k] = k < cnt ? (T)sc->coef_y[k] : T(0);
+        sp[k] = ringS + sl * vstride;
+        yp[k] = ringY + sl * vstride;
+    }
+    for (int e = blockIdx.x * kThreads + threadIdx.x; e < m; e += gridDim.x * kThreads) {
+        T acc = gamma * g[e];
+#pragma unroll
+        for (int k = 0; k < MEM; ++k)
+            if (k < cnt) acc += cs[k] * sp[k][e] + cy[k] * yp[k][e];
+        dvec[e] = -acc;
+    }
+}
+
+template <class T, int MEM>
+void lb_direction_t(int grid, cudaStream_t st, int m, const T *g, const T *ringS, const T *ringY, long long vs,
+                    SolverScalars *sc, double *part, T *d) {
+    k_lb_dots<T, MEM><<<grid, kThreads, 0, st>>>(m, g, ringS, ringY, vs, sc, part);
+    k_lb_dir<T, MEM><<<grid, kThreads, 0, st>>>(m, g, ringS, ringY, vs, sc, d);
+}
+
+template <class T>
+void lb_direction(int mem, int grid, cudaStream_t st, int m, const T *g, const T *ringS, const T *ringY, long long vs,
+                  SolverScalars *sc, double *part, T *d) {
+    if (mem <= 2)
+        lb_direction_t<T, 2>(grid, st, m, g, ringS, ringY, vs, sc, part, d);
+    else if (mem <= 5)
+        lb_direction_t<T, 5>(grid, st, m, g, ringS, ringY, vs, sc, part, d);
+    else if (mem <= 8)
+        lb_direction_t<T, 8>(grid, st, m, g, ringS, ringY, vs, sc, part, d);
+    else
+        lb_direction_t<T, 16>(grid, st, m, g, ringS, ringY, vs, sc, part, d);
+}
+
+// Line search: candidates tau_j = 2^-(e0 + j), j < nc <= J, evaluated in one pass.
+// NAMA (nama = 1): w = ybar - lam r + tau (d + lam r),  h(w) = h - lam hr + tau (hd + lam hr).
+// MINFBE:          w = ybar + tau d,                     h(w) = h + tau hd.
+// Accept the largest tau with FBE(w) <= FBE(ybar); after the last group tau = 0.
+template <class T, int J>
+__global__ void __launch_bounds__(kThreads) k_ls(DualView<T> dv, const T *__restrict__ yb, const T *__restrict__ h,
+                                                 const T *__restrict__ r, const T *__restrict__ dvec,
+                                                 const T *__restrict__ hr, const T *__restrict__ hd, int nama, int e0,
+                                                 int nc, int last_group, SolverScalars *sc, double *partials) {
+    __shared__ double tot[J];
+    if (sc->ls_done) return;
+    const T lam = (T)sc->lambda, ilam = T(1) / lam;
+    T tau[J];
+#pragma unroll
+    for (int j = 0; j < J; ++j) tau[j] = (T)ldexp(1.0, -(e0 + j));
+    T acc[J];
+#pragma unroll
+    for (int j = 0; j < J; ++j) acc[j] = T(0);
+    for (int e = blockIdx.x * kThreads + threadIdx.x; e < dv.m; e += gridDim.x * kThreads) {
+        const auto M = dv.meta(e);
+        const T y0 = yb[e], h0 = h[e];
+        T wa, wb, ha, hb;
+        if (nama) {
+            const T re = r[e], hre = hr[e];
+            wa = y0 - lam * re;
+            wb = dvec[e] + lam * re;
+            ha = h0 - lam * hre;
+            hb = hd[e] + lam * hre;
+        } else {
+            wa = y0;
+            wb = dvec[e];
+            ha = h0;
+            hb = hd[e];
+        }
+        const T c0 = fbe_term<T>(h0, y0, lam, ilam, M);
+#pragma unroll
+        for (int j = 0; j < J; ++j) {
+            const T cj = fbe_term<T>(ha + tau[j] * hb, wa + tau[j] * wb, lam, ilam, M);
+            acc[j] += cj - c0;
+        }
+    }
+    double sums[J];
+#pragma unroll
+    for (int j = 0; j < J; ++j) sums[j] = acc[j];
+    double maxs[1];
+    if (reduce_last<J, 0>(sums, maxs, partials, &sc->red_counter, tot) && threadIdx.x == 0) {
+        // FBE(w) - FBE(ybar) = -sum_e (term(w) - term(ybar))
+        for (int j = 0; j < nc; ++j) {
+            sc->cand[e0 + j] = -tot[j];
+            if (-tot[j] <= 0.0) {
+                sc->tau = ldexp(1.0, -(e0 + j));
+                sc->ls_done = 1;
+                return;
+            }
+        }
+        if (last_group) {
+            sc->tau = 0.0;
+            sc->ls_done = 1;
+            sc->ls_zero += 1;
+        }
+    }
+}
+
+// ybar+ = T_lam(w(tau)) = w + lam (h(w) - z(w)); s = ybar+ - ybar -> S[p]; ybar <- ybar+.
+template <class T>
+__global__ void __launch_bounds__(kThreads) k_fbstep(DualView<T> dv, T *yb, const T *__restrict__ h,
+                                                     const T *__restrict__ r, const T *__restrict__ dvec,
+                                                     const T *__restrict__ hr, const T *__restrict__ hd, int nama,
+                                                     T *ringS, long long vstride, SolverScalars *sc) {
+    const T lam = (T)sc->lambda, ilam = T(1) / lam;
+    const T tau = (T)sc->tau;
+    const int p = (sc->lb_head + sc->lb_count) % (sc->mem + 1);
+    T *sv = ringS + p * vstride;
+    for (int e = blockIdx.x * kThreads + threadIdx.x; e < dv.m; e += gridDim.x * kThreads) {
+        const auto M = dv.meta(e);
+        const T y0 = yb[e], h0 = h[e];
+        T w, hw;
+        if (nama) {
+            const T re = r[e], hre = hr[e];
+            w = y0 - lam * re + tau * (dvec[e] + lam * re);
+            hw = h0 - lam * hre + tau * (hd[e] + lam * hre);
+        } else {
+            w = y0 + tau * dvec[e];
+            hw = h0 + tau * hd[e];
+        }
+        const T z = clampv(hw + w * ilam, M.lo, M.hi);
+        const T yn = w + lam * (hw - z);
+        sv[e] = yn - y0;
+        yb[e] = yn;
+    }
+    if (blockIdx.x == 0 && threadIdx.x == 0) {
+        sc->lb_pending_valid = 1;
+        sc->ls_done = 0;
+        sc->iters += 1;
+    }
+}
+
+// ybar = y / sqrt(pi) (in) and y = sqrt(pi) ybar, z = z_bar / sqrt(pi), x, u = S^-1 h (out).
+template <class T>
+__global__ void k_scale_in(DualView<T> dv, const T *y, T *yb) {
+    for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < dv.m; e += gridDim.x * blockDim.x)
+        yb[e] = y[e] / dv.meta(e).sq;
+}
+
+template <class T>
+__global__ void k_finish_out(DualView<T> dv, const T *yb, const T *h, const SolverScalars *sc, T *y, T *z, T *x,
+                             T *u) {
+    const T lam = (T)sc->lambda, ilam = T(1) / lam;
+    for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < dv.m; e += gridDim.x * blockDim.x) {
+        const auto M = dv.meta(e);
+        const T ye = yb[e], he = h[e];
+        y[e] = M.sq * ye;
+        if (z) z[e] = clampv(he + ye * ilam, M.lo, M.hi) / M.sq;
+        if (x) {
+            int node, k;
+            if (e < dv.leaf_base) {
+                node = e / dv.nxu;
+                k = e - node * dv.nxu;
+                if (k < dv.nx)
+                    x[(size_t)node * dv.nx + k] = he / M.sq;
+                else
+                    u[(size_t)node * dv.nu + (k - dv.nx)] = he / M.sq;
+            } else {
+                const int e2 = e - dv.leaf_base;
+                node = dv.Np + e2 / dv.nx;
+                k = e2 - (node - dv.Np) * dv.nx;
+                x[(size_t)node * dv.nx + k] = he / M.sq;
+            }
+        }
+    }
+}
+
+// Power iteration on r -> -hr (hr = S H x_lin(S r)): L = <r, -hr> / <r, r>, r <- -hr / ||hr||.
+template <class T>
+__global__ void __launch_bounds__(kThreads) k_power_dots(int m, const T *r, const T *hr, SolverScalars *sc,
+                                                         double *partials) {
+    __shared__ double tot[3];
+    T a = 0, b = 0, c = 0;
+    for (int e = blockIdx.x * kThreads + threadIdx.x; e < m; e += gridDim.x * kThreads) {
+        const T re = r[e], he = hr[e];
+        a += -re * he;
+        b += he * he;
+        c += re * re;
+    }
+    double sums[3] = {a, b, c};
+    double maxs[1];
+    if (reduce_last<3, 0>(sums, maxs, partials, &sc->red_counter, tot) && threadIdx.x == 0) {
+        sc->pw_L = tot[0] / tot[2];
+        sc->pw_inv_norm = tot[1] > 0.0 ? 1.0 / sqrt(tot[1]) : 0.0;
+    }
+}
+
+template <class T>
+__global__ void k_power_next(int m, T *r, const T *hr, const SolverScalars *sc) {
+    const T s = (T)(-sc->pw_inv_norm);
+    for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < m; e += gridDim.x * blockDim.x) r[e] = s * hr[e];
+}
+
+template <class T>
+__global__ void k_normalize(int m, T *r, SolverScalars *sc, double *partials) {
+    __shared__ double tot[1];
+    T a = 0;
+    for (int e = blockIdx.x * kThreads + threadIdx.x; e < m; e += gridDim.x * kThreads) a += r[e] * r[e];
+    double sums[1] = {a};
+    double maxs[1];
+    if (reduce_last<1, 0>(sums, maxs, partials, &sc->red_counter, tot) && threadIdx.x == 0)
+        sc->pw_inv_norm = tot[0] > 0.0 ? 1.0 / sqrt(tot[0]) : 0.0;
+}
+
+template <class T>
+__global__ void k_scale_by(int m, T *r, const SolverScalars *sc) {
+    const T s = (T)sc->pw_inv_norm;
+    for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < m; e += gridDim.x * blockDim.x) r[e] *= s;
+}
+
+int red_grid(int64_t m) {
+    const int64_t b = (m + kThreads - 1) / kThreads;
+    return (int)(b < kRedBlocks ? (b > 0 ? b : 1) : kRedBlocks);
+}
+
+template <class T>
+DualView<T> make_view(stotree_t h) {
+    DualView<T> dv;
+    dv.m = (int)h->m;
+    dv.Np = h->Np;
+    dv.nx = h->nx;
+    dv.nu = h->nu;
+    dv.nxu = h->nx + h->nu;
+    dv.leaf_base = h->Np * (h->nx + h->nu);
+    dv.sqp = h->at<T>(h->L.sqp);
+    dv.box = h->at<T>(h->L.box);
+    dv.Wc = h->at<T>(h->L.cost);
+    return dv;
+}
+
+size_t vstride_of(stotree_t h) { return (size_t)((h->m + 63) / 64 * 64); }
+
+template <class T>
+sto_status solver_impl(stotree_t h, int method, const sto_opts *o, const void *x0v, void *yv, void *xv, void *uv,
+                       void *zv, sto_info *info, cudaStream_t st) {
+    const Layout &L = h->L;
+    const int m = (int)h->m;
+    const long long vs = (long long)vstride_of(h);
+    T *V = h->at<T>(L.vec);
+    T *yb = V, *hv = V + vs, *r = V + 2 * vs, *d = V + 3 * vs, *hr = V + 4 * vs, *hd = V + 5 * vs, *g = V + 6 * vs;
+    T *ringS = h->at<T>(L.ringS), *ringY = h->at<T>(L.ringY);
+    SolverScalars *sc = h->at<SolverScalars>(L.scal);
+    double *part = h->at<double>(L.partials);
+    const DualView<T> dv = make_view<T>(h);
+    const int grid = red_grid(m);
+    const bool nama = method == 0;
+
+    cudaEvent_t e0, e1;
+    STO_CUDA(h, cudaEventCreate(&e0));
+    STO_CUDA(h, cudaEventCreate(&e1));
+    STO_CUDA(h, cudaEventRecord(e0, st));
+    const int64_t calls0 = h->solve_calls;
+
+    SolverScalars *hs = h->host_scal;
+    std::memset(hs, 0, sizeof(SolverScalars));
+    hs->lambda = o->lambda;
+    hs->tol = o->tol;
+    hs->eps_curv = o->eps_curv;
+    hs->mem = o->lbfgs_mem;
+    hs->max_ls = o->max_ls;
+    hs->method = method;
+    STO_CUDA(h, cudaMemcpyAsync(sc, hs, sizeof(SolverScalars), cudaMemcpyHostToDevice, st));
+    // the host mirror is rewritten below; make sure the upload has consumed it
+    STO_CUDA(h, cudaStreamSynchronize(st));
+
+    // line-search candidate groups: 4, 8, then the rest up to max_ls halvings
+    int gfirst[3], gcount[3], ng = 0;
+    {
+        int left = o->max_ls + 1, e = 0;
+        const int sizes[3] = {4, 8, 19};
+        for (int k = 0; k < 3 && left > 0; ++k) {
+            const int c = left < sizes[k] ? left : sizes[k];
+            gfirst[ng] = e;
+            gcount[ng] = c;
+            ++ng;
+            e += c;
+            left -= c;
+        }
+    }
+
+    auto full_solve = [&]() -> sto_status {
+        const void *ys[1] = {yb};
+        void *hs_[1] = {hv};
+        return solve_round(h, ys, x0v, hs_, 1, false, true, st);
+    };
+    auto lin_solve = [&](T *in, T *out) -> sto_status {
+        const void *ys[1] = {in};
+        void *hs_[1] = {out};
+        return solve_round(h, ys, nullptr, hs_, 1, true, true, st);
+    };
+
+    k_scale_in<T><<<grid, kThreads, 0, st>>>(dv, static_cast<const T *>(yv), yb);
+    sto_status s = full_solve();
+    if (s != STO_OK) return s;
+    k_point<T><<<grid, kThreads, 0, st>>>(dv, yb, hv, r, ringS, ringY, vs, 0, sc, part);
+    if (!nama) {
+        if ((s = lin_solve(r, hr)) != STO_OK) return s;
+        k_grad<T><<<grid, kThreads, 0, st>>>(m, r, hr, g, ringS, ringY, vs, sc, part);
+    }
+    sto_status result = STO_OK;
+    int iters = 0;
+    while (true) {
+        STO_CUDA(h, cudaMemcpyAsync(hs, sc, kScalHead, cudaMemcpyDeviceToHost, st));
+        STO_CUDA(h, cudaStreamSynchronize(st));
+        if (hs->nan_flag) {
+            result = STO_ERR_NUMERICAL;
+            h->err = "NaN or Inf in the residual";
+            break;
+        }
+        if (hs->res_inf <= o->tol) break;
+        if (iters >= o->max_iter) {
+            result = STO_NOT_CONVERGED;
+            break;
+        }
+        T *gdir = nama ? r : g;
+        lb_direction<T>(o->lbfgs_mem, grid, st, m, gdir, ringS, ringY, vs, sc, part, d);
+        if (nama) {
+            const void *ys[2] = {r, d};
+            void *outs[2] = {hr, hd};
+            if ((s = solve_round(h, ys, nullptr, outs, 2, true, true, st)) != STO_OK) return s;
+        } else {
+            if ((s = lin_solve(d, hd)) != STO_OK) return s;
+        }
+        for (int k = 0; k < ng; ++k) {
+            const int last = k == ng - 1;
+            if (k == 0)
+                k_ls<T, 4><<<grid, kThreads, 0, st>>>(dv, yb, hv, r, d, hr, hd, nama, gfirst[k], gcount[k], last, sc,
+                                                     part);
+            else if (k == 1)
+                k_ls<T, 8><<<grid, kThreads, 0, st>>>(dv, yb, hv, r, d, hr, hd, nama, gfirst[k], gcount[k], last, sc,
+                                                     part);
+            else
+                k_ls<T, 19><<<grid, kThreads, 0, st>>>(dv, yb, hv, r, d, hr, hd, nama, gfirst[k], gcount[k], last, sc,
+                                                      part);
+        }
+        k_fbstep<T><<<grid, kThreads, 0, st>>>(dv, yb, hv, r, d, hr, hd, nama, ringS, vs, sc);
+        if ((s = full_solve()) != STO_OK) return s;
+        k_point<T><<<grid, kThreads, 0, st>>>(dv, yb, hv, r, ringS, ringY, vs, nama ? 1 : 0, sc, part);
+        if (!nama) {
+            if ((s = lin_solve(r, hr)) != STO_OK) return s;
+            k_grad<T><<<grid, kThreads, 0, st>>>(m, r, hr, g, ringS, ringY, vs, sc, part);
+        }
+        ++iters;
+        STO_CUDA(h, cudaGetLastError());
+    }
+    k_finish_out<T><<<grid, kThreads, 0, st>>>(dv, yb, hv, sc, static_cast<T *>(yv), static_cast<T *>(zv),
+                                               static_cast<T *>(xv), static_cast<T *>(uv));
+    if (xv) {
+        // the root state is the parameter p
+        STO_CUDA(h, cudaMemcpyAsync(xv, x0v, h->nx * sizeof(T), cudaMemcpyDeviceToDevice, st));
+    }
+    STO_CUDA(h, cudaEventRecord(e1, st));
+    STO_CUDA(h, cudaMemcpyAsync(hs, sc, sizeof(SolverScalars), cudaMemcpyDeviceToHost, st));
+    STO_CUDA(h, cudaStreamSynchronize(st));
+    float ms = 0.f;
+    cudaEventElapsedTime(&ms, e0, e1);
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    if (info) {
+        info->iters = iters;
+        info->solve_calls = (int32_t)(h->solve_calls - calls0);
+        info->status = result;
+        info->ls_zero = hs->ls_zero;
+        info->res_inf = hs->res_inf;
+        info->fbe = hs->phi;
+        info->ms = ms;
+    }
+    STO_CUDA(h, cudaGetLastError());
+    return result;
+}
+
+template <class T>
+sto_status lambda_impl(stotree_t h, void *r0, int iters, double safety, double *lambda, double *Lout,
+                       cudaStream_t st) {
+    const int m = (int)h->m;
+    const long long vs = (long long)vstride_of(h);
+    T *hr = h->at<T>(h->L.vec) + 4 * vs;
+    T *r = static_cast<T *>(r0);
+    SolverScalars *sc = h->at<SolverScalars>(h->L.scal);
+    double *part = h->at<double>(h->L.partials);
+    const int grid = red_grid(m);
+    STO_CUDA(h, cudaMemsetAsync(sc, 0, sizeof(SolverScalars), st));
+    k_normalize<T><<<grid, kThreads, 0, st>>>(m, r, sc, part);
+    k_scale_by<T><<<grid, kThreads, 0, st>>>(m, r, sc);
+    for (int k = 0; k < iters; ++k) {
+        const void *ys[1] = {r};
+        void *outs[1] = {hr};
+        sto_status s = solve_round(h, ys, nullptr, outs, 1, true, true, st);
+        if (s != STO_OK) return s;
+        k_power_dots<T><<<grid, kThreads, 0, st>>>(m, r, hr, sc, part);
+        k_power_next<T><<<grid, kThreads, 0, st>>>(m, r, hr, sc);
+    }
+    SolverScalars *hs = h->host_scal;
+    STO_CUDA(h, cudaMemcpyAsync(hs, sc, sizeof(SolverScalars), cudaMemcpyDeviceToHost, st));
+    STO_CUDA(h, cudaStreamSynchronize(st));
+    if (!(hs->pw_L > 0.0)) {
+        h->err = "power iteration gave a non-positive estimate";
+        return STO_ERR_NUMERICAL;
+    }
+    *lambda = safety / hs->pw_L;
+    if (Lout) *Lout = hs->pw_L;
+    return STO_OK;
+}
+
+// ------------------------------- FP64 KKT check ---------------------------------------
+// Costates mu^j = grad_x^j of f + <y, Hx> through the dynamics, from the leaves up:
+//   leaf  mu^l = 2 pi^l P_N x^l + pi^l p_N + y^l
+//   j>=1  mu^j = 2 pi^j Q x^j + pi^j q + y_x^j + sum_k A^k' mu^k
+// and at every nonleaf i the input stationarity 2 pi^i R u^i + pi^i r + y_u^i + sum_j B^j' mu^j.
+__device__ void atomic_max_nonneg(double *addr, double v) {
+    if (!(v >= 0.0)) v = INFINITY;  // NaN counts as a failure
+    atomicMax(reinterpret_cast<unsigned long long *>(addr), (unsigned long long)__double_as_longlong(v));
+}
+
+template <class T>
+__global__ void k_kkt_stage(int first, int nx, int nu, int Np, int ld64, const int *cbeg, const int *ccnt,
+                            const double *prob, const double *G64, const double *cost64, const T *x, const T *u,
+                            const T *y, double *mu, double *out) {
+    const int i = first + blockIdx.x;
+    const int nxu = nx + nu;
+    const long long oi = i < Np ? (long long)i * nxu : (long long)Np * nxu + (long long)(i - Np) * nx;
+    const double pi = prob[i];
+    const double *Q = cost64, *R = cost64 + nx, *PN = cost64 + nx + nu, *q = cost64 + 2 * nx + nu,
+                 *r = cost64 + 3 * nx + nu, *pN = cost64 + 3 * nx + 2 * nu;
+    for (int c = threadIdx.x; c < nxu; c += blockDim.x) {
+        double acc = 0.0;
+        if (i < Np) {
+            for (int j = cbeg[i]; j < cbeg[i] + ccnt[i]; ++j) {
+                const double *Gj = G64 + (size_t)j * nx * ld64;
+                const double *mj = mu + (size_t)j * nx;
+                for (int k = 0; k < nx; ++k) acc += Gj[(size_t)k * ld64 + c] * mj[k];
+            }
+        }
+        if (c < nx) {
+            if (i == 0) continue;
+            const double xv = (double)x[(size_t)i * nx + c];
+            const double loc = i < Np ? 2.0 * pi * Q[c] * xv + pi * q[c] : 2.0 * pi * PN[c] * xv + pi * pN[c];
+            mu[(size_t)i * nx + c] = loc + (double)y[oi + c] + acc;
+        } else if (i < Np) {
+            const int a = c - nx;
+            const double res = 2.0 * pi * R[a] * (double)u[(size_t)i * nu + a] + pi * r[a] + (double)y[oi + c] + acc;
+            atomic_max_nonneg(out + 1, fabs(res));
+        }
+    }
+}
+
+template <class T>
+__global__ void k_kkt_elem(int Nn, int nx, int nu, int Np, int ld64, const int *parent, const double *G64,
+                           const double *box64, const T *x0, const T *x, const T *u, const T *y, double tol_act,
+                           double *out) {
+    const int nxu = nx + nu;
+    // dynamics residual per node and state component
+    for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < (long long)(Nn - 1) * nx;
+         e += (long long)gridDim.x * blockDim.x) {
+        const int j = 1 + (int)(e / nx), rr = (int)(e % nx);
+        const int i = parent[j];
+        const double *row = G64 + ((size_t)j * nx + rr) * ld64;
+        double acc = row[nx + nu];
+        for (int k = 0; k < nx; ++k) acc += row[k] * (double)(i == 0 ? x0[k] : x[(size_t)i * nx + k]);
+        for (int k = 0; k < nu; ++k) acc += row[nx + k] * (double)u[(size_t)i * nu + k];
+        atomic_max_nonneg(out + 0, fabs((double)x[(size_t)j * nx + rr] - acc));
+    }
+    // box feasibility, complementarity and multiplier signs per dual entry
+    const long long m = (long long)Np * nxu + (long long)(Nn - Np) * nx;
+    for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < m; e += (long long)gridDim.x * blockDim.x) {
+        int node, k, bi;
+        double hv;
+        if (e < (long long)Np * nxu) {
+            node = (int)(e / nxu);
+            k = (int)(e % nxu);
+            if (k < nx) {
+                hv = node == 0 ? (double)x0[k] : (double)x[(size_t)node * nx + k];
+                bi = k;
+            } else {
+                hv = (double)u[(size_t)node * nu + (k - nx)];
+                bi = k;
+            }
+        } else {
+            const long long e2 = e - (long long)Np * nxu;
+            node = Np + (int)(e2 / nx);
+            k = (int)(e2 % nx);
+            hv = (double)x[(size_t)node * nx + k];
+            bi = k;
+        }
+        double lo = box64[bi], hi = box64[nxu + bi];
+        if (node == 0 && k < nx) {
+            lo = -INFINITY;
+            hi = INFINITY;
+        }
+        const double ye = (double)y[e];
+        atomic_max_nonneg(out + 2, fmax(0.0, fmax(lo - hv, hv - hi)));
+        const bool at_hi = hv >= hi - tol_act, at_lo = hv <= lo + tol_act;
+        if (!at_hi && !at_lo) atomic_max_nonneg(out + 3, fabs(ye));
+        double sgn = 0.0;
+        if (at_hi && !at_lo) sgn = fmax(0.0, -ye);
+        if (at_lo && !at_hi) sgn = fmax(0.0, ye);
+        atomic_max_nonneg(out + 4, sgn);
+    }
+}
+
+template <class T>
+sto_status kkt_impl(stotree_t h, const void *x0, const void *x, const void *u, const void *y, double tol_act,
+                    double *out, cudaStream_t st) {
+    const Layout &L = h->L;
+    double *mu = h->at<double>(L.kkt);
+    double *dout = mu + (size_t)h->Nn * h->nx + (size_t)h->Np * h->nu;
+    STO_CUDA(h, cudaMemsetAsync(dout, 0, 8 * sizeof(double), st));
+    for (int t = h->N; t >= 0; --t) {
+        const int first = h->soff[t], count = h->soff[t + 1] - first;
+        k_kkt_stage<T><<<count, 128, 0, st>>>(first, h->nx, h->nu, h->Np, h->ld64, h->at<int>(L.cbeg),
+                                              h->at<int>(L.ccnt), h->at<double>(L.prob64), h->at<double>(L.G64),
+                                              h->at<double>(L.cost64), static_cast<const T *>(x),
+                                              static_cast<const T *>(u), static_cast<const T *>(y), mu, dout);
+    }
+    k_kkt_elem<T><<<592, 256, 0, st>>>(h->Nn, h->nx, h->nu, h->Np, h->ld64, h->at<int>(L.parent),
+                                       h->at<double>(L.G64), h->at<double>(L.box64), static_cast<const T *>(x0),
+                                       static_cast<const T *>(x), static_cast<const T *>(u),
+                                       static_cast<const T *>(y), tol_act, dout);
+    STO_CUDA(h, cudaMemcpyAsync(out, dout, 5 * sizeof(double), cudaMemcpyDeviceToHost, st));
+    STO_CUDA(h, cudaStreamSynchronize(st));
+    STO_CUDA(h, cudaGetLastError());
+    return STO_OK;
+}
+
+}  // namespace
+
+sto_status solver_run(stotree_t h, int method, const sto_opts *o, const void *x0, void *y, void *x, void *u,
+                      void *z, sto_info *info, cudaStream_t st) {
+    return h->prec == STO_FP64 ? solver_impl<double>(h, method, o, x0, y, x, u, z, info, st)
+                               : solver_impl<float>(h, method, o, x0, y, x, u, z, info, st);
+}
+
+sto_status lambda_run(stotree_t h, void *r0, int iters, double safety, double *lambda, double *L, cudaStream_t st) {
+    return h->prec == STO_FP64 ? lambda_impl<double>(h, r0, iters, safety, lambda, L, st)
+                               : lambda_impl<float>(h, r0, iters, safety, lambda, L, st);
+}
+
+sto_status kkt_run(stotree_t h, const void *x0, const void *x, const void *u, const void *y, double tol_active,
+                   double *out, cudaStream_t st) {
+    return h->prec == STO_FP64 ? kkt_impl<double>(h, x0, x, u, y, tol_active, out, st)
+                               : kkt_impl<float>(h, x0, x, u, y, tol_active, out, st);
+}
+
+}  // namespace sto

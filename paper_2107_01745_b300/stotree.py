@@ -1,0 +1,254 @@
+"""Python binding of libstotree (argument marshalling only).
+
+Every function mirrors an entry point of ``include/stotree.h``; torch is used for device
+memory and streams, and every computation runs in the library's CUDA kernels.  Loading
+fails loudly when ``libstotree.so`` has not been built
+(``python -m paper_2107_01745_b300.build``): there is no CPU path.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+import numpy as np
+import torch
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libstotree.so")
+
+STO_FP64, STO_FP32 = 0, 1
+STATUS = {0: "ok", 1: "invalid argument", 2: "invalid scenario tree", 3: "not ready", 4: "numerical failure",
+          5: "CUDA error", 6: "timeout", 7: "not converged", 8: "workspace too small"}
+STO_NOT_CONVERGED = 7
+
+
+class StoError(RuntimeError):
+    def __init__(self, code, where, detail=""):
+        self.code = code
+        super().__init__(f"{where}: {STATUS.get(code, code)}" + (f" ({detail})" if detail else ""))
+
+
+class _TreeDesc(ctypes.Structure):
+    _fields_ = [("num_nodes", ctypes.c_int32), ("horizon", ctypes.c_int32), ("nx", ctypes.c_int32),
+                ("nu", ctypes.c_int32), ("parent", ctypes.c_void_p), ("prob", ctypes.c_void_p)]
+
+
+class Opts(ctypes.Structure):
+    _fields_ = [("lambda_", ctypes.c_double), ("tol", ctypes.c_double), ("eps_curv", ctypes.c_double),
+                ("lbfgs_mem", ctypes.c_int32), ("max_iter", ctypes.c_int32), ("max_ls", ctypes.c_int32)]
+
+
+class Info(ctypes.Structure):
+    _fields_ = [("iters", ctypes.c_int32), ("solve_calls", ctypes.c_int32), ("status", ctypes.c_int32),
+                ("ls_zero", ctypes.c_int32), ("res_inf", ctypes.c_double), ("fbe", ctypes.c_double),
+                ("ms", ctypes.c_double)]
+
+    def as_dict(self):
+        return {k: getattr(self, k) for k, _ in self._fields_}
+
+
+_lib = None
+
+
+def lib():
+    global _lib
+    if _lib is None:
+        if not os.path.exists(LIB_PATH):
+            raise RuntimeError(f"{LIB_PATH} is missing: build it with python -m paper_2107_01745_b300.build")
+        L = ctypes.CDLL(LIB_PATH)
+        vp, i32, dbl, sz = ctypes.c_void_p, ctypes.c_int32, ctypes.c_double, ctypes.c_size_t
+        sigs = {
+            "stotree_create": [vp, i32, vp],
+            "stotree_sizes": [vp, vp, vp, vp, vp],
+            "stotree_workspace_size": [vp, vp],
+            "stotree_bind_workspace": [vp, vp, sz, vp],
+            "stotree_set_dynamics": [vp, i32, i32, vp, vp, vp, vp],
+            "stotree_set_costs": [vp, vp, vp, vp, vp, vp, vp, vp],
+            "stotree_set_box": [vp, vp, vp, vp, vp, vp],
+            "stotree_factor": [vp, i32, vp],
+            "stotree_solve_step": [vp, vp, vp, vp, i32, i32, i32, vp],
+            "stotree_last_primal": [vp, vp, vp, vp],
+            "stotree_estimate_lambda": [vp, vp, i32, dbl, vp, vp, vp],
+            "stotree_nama_solve": [vp, vp, vp, vp, vp, vp, vp, vp, vp],
+            "stotree_minfbe_solve": [vp, vp, vp, vp, vp, vp, vp, vp, vp],
+            "stotree_kkt_check": [vp, vp, vp, vp, vp, dbl, vp, vp],
+            "stotree_set_timing": [vp, i32],
+            "stotree_get_timing": [vp, vp, vp, vp],
+            "stotree_solve_bytes": [vp, vp, vp],
+        }
+        for name, args in sigs.items():
+            fn = getattr(L, name)
+            fn.argtypes = args
+            fn.restype = ctypes.c_int
+        L.stotree_destroy.argtypes = [vp]
+        L.stotree_destroy.restype = None
+        L.stotree_last_error.argtypes = [vp]
+        L.stotree_last_error.restype = ctypes.c_char_p
+        L.stotree_status_str.argtypes = [ctypes.c_int]
+        L.stotree_status_str.restype = ctypes.c_char_p
+        _lib = L
+    return _lib
+
+
+def exported_symbols():
+    return [n for n in ("stotree_create", "stotree_destroy", "stotree_sizes", "stotree_workspace_size",
+                        "stotree_bind_workspace", "stotree_set_dynamics", "stotree_set_costs", "stotree_set_box",
+                        "stotree_factor", "stotree_solve_step", "stotree_last_primal", "stotree_estimate_lambda",
+                        "stotree_nama_solve", "stotree_minfbe_solve", "stotree_kkt_check", "stotree_set_timing",
+                        "stotree_get_timing", "stotree_solve_bytes", "stotree_status_str", "stotree_last_error")]
+
+
+def _np_ptr(a):
+    return ctypes.c_void_p(a.ctypes.data)
+
+
+def _t_ptr(t):
+    return ctypes.c_void_p(t.data_ptr()) if t is not None else None
+
+
+def _stream(stream=None):
+    s = torch.cuda.current_stream() if stream is None else stream
+    return ctypes.c_void_p(s.cuda_stream)
+
+
+class StoTree:
+    """One scenario-tree problem on one GPU: handle, workspace and data."""
+
+    def __init__(self, problem, precision: str = "fp32", device="cuda:0", chunk_nodes: int = 2048):
+        self.device = torch.device(device)
+        self.p = problem
+        self.prec = STO_FP32 if precision == "fp32" else STO_FP64
+        self.dtype = torch.float32 if self.prec == STO_FP32 else torch.float64
+        t = problem.tree
+        L = lib()
+        self._parent = np.ascontiguousarray(t.parent, dtype=np.int32)
+        self._prob = np.ascontiguousarray(t.prob, dtype=np.float64)
+        desc = _TreeDesc(t.num_nodes, t.horizon, problem.nx, problem.nu, _np_ptr(self._parent), _np_ptr(self._prob))
+        h = ctypes.c_void_p()
+        self._check(L.stotree_create(ctypes.byref(desc), self.prec, ctypes.byref(h)), "stotree_create", handle=False)
+        self.h = h
+        m, n = ctypes.c_int64(), ctypes.c_int64()
+        npl, nl = ctypes.c_int32(), ctypes.c_int32()
+        L.stotree_sizes(h, ctypes.byref(m), ctypes.byref(n), ctypes.byref(npl), ctypes.byref(nl))
+        self.m, self.n, self.Np, self.Nl = m.value, n.value, npl.value, nl.value
+        self.Nn, self.nx, self.nu = t.num_nodes, problem.nx, problem.nu
+        wb = ctypes.c_size_t()
+        L.stotree_workspace_size(h, ctypes.byref(wb))
+        self.workspace_bytes = wb.value
+        with torch.cuda.device(self.device):
+            self.ws = torch.empty(self.workspace_bytes, dtype=torch.uint8, device=self.device)
+            st = _stream()
+            self._check(L.stotree_bind_workspace(h, _t_ptr(self.ws), self.workspace_bytes, st), "bind_workspace")
+            nn = t.num_nodes
+            for f in range(0, nn, chunk_nodes):
+                c = min(chunk_nodes, nn - f)
+                A = np.ascontiguousarray(problem.A[f:f + c], dtype=np.float64)
+                B = np.ascontiguousarray(problem.B[f:f + c], dtype=np.float64)
+                cc = np.ascontiguousarray(problem.c[f:f + c], dtype=np.float64)
+                self._check(L.stotree_set_dynamics(h, f, c, _np_ptr(A), _np_ptr(B), _np_ptr(cc), st), "set_dynamics")
+            self.set_costs(problem.Q, problem.R, problem.PN, problem.q, problem.r, problem.pN)
+            self.set_box(problem.xlo, problem.xhi, problem.ulo, problem.uhi)
+
+    # -- plumbing -------------------------------------------------------------------------
+    def _check(self, code, where, handle=True):
+        if code != 0:
+            detail = ""
+            if handle and getattr(self, "h", None):
+                detail = lib().stotree_last_error(self.h).decode()
+            raise StoError(code, where, detail)
+
+    def close(self):
+        if getattr(self, "h", None):
+            lib().stotree_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def vec(self, nrhs=1):
+        return torch.zeros((nrhs, self.m) if nrhs > 1 else (self.m,), dtype=self.dtype, device=self.device)
+
+    def to_dev(self, a):
+        return torch.as_tensor(np.asarray(a), dtype=self.dtype).to(self.device).contiguous()
+
+    # -- set-up ---------------------------------------------------------------------------
+    def set_costs(self, Q, R, PN, q=None, r=None, pN=None):
+        arr = [np.ascontiguousarray(v, dtype=np.float64) if v is not None else None for v in (Q, R, PN, q, r, pN)]
+        self._keep_cost = arr
+        ptrs = [_np_ptr(a) if a is not None else None for a in arr]
+        self._check(lib().stotree_set_costs(self.h, *ptrs, _stream()), "set_costs")
+
+    def set_box(self, xlo, xhi, ulo, uhi):
+        arr = [np.ascontiguousarray(v, dtype=np.float64) for v in (xlo, xhi, ulo, uhi)]
+        self._check(lib().stotree_set_box(self.h, *[_np_ptr(a) for a in arr], _stream()), "set_box")
+
+    def factor(self, sync=True):
+        self._check(lib().stotree_factor(self.h, 1 if sync else 0, _stream()), "factor")
+
+    # -- hot path -------------------------------------------------------------------------
+    def solve_step(self, y, x0=None, homogeneous=False, scaled=False, out=None):
+        """Algorithm 3 (or 4): y [m] or [nrhs, m] device tensor -> Hx of the same shape."""
+        y = y.contiguous()
+        nrhs = 1 if y.dim() == 1 else y.shape[0]
+        out = torch.empty_like(y) if out is None else out
+        x0 = x0 if x0 is not None else (None if homogeneous else self.to_dev(self.p.x0))
+        self._check(lib().stotree_solve_step(self.h, _t_ptr(y), _t_ptr(x0), _t_ptr(out), nrhs,
+                                             1 if homogeneous else 0, 1 if scaled else 0, _stream()), "solve_step")
+        return out
+
+    def last_primal(self):
+        x = torch.empty((self.Nn, self.nx), dtype=self.dtype, device=self.device)
+        u = torch.empty((self.Np, self.nu), dtype=self.dtype, device=self.device)
+        self._check(lib().stotree_last_primal(self.h, _t_ptr(x), _t_ptr(u), _stream()), "last_primal")
+        return x, u
+
+    def estimate_lambda(self, r0, iters=50, safety=0.9):
+        r = r0.clone().contiguous()
+        lam, L = ctypes.c_double(), ctypes.c_double()
+        self._check(lib().stotree_estimate_lambda(self.h, _t_ptr(r), iters, safety, ctypes.byref(lam),
+                                                  ctypes.byref(L), _stream()), "estimate_lambda")
+        return lam.value, L.value
+
+    def solve(self, method, lam, x0=None, y0=None, tol=1e-4, mem=5, max_iter=1000, max_ls=30, eps_curv=None,
+              outputs=True, allow_not_converged=False):
+        """Algorithm 1 (method='minfbe') or 2 (method='nama').  Returns tensors and info."""
+        if eps_curv is None:
+            eps_curv = 1e-12 if self.prec == STO_FP64 else 1e-8
+        x0 = self.to_dev(self.p.x0) if x0 is None else x0
+        y = self.vec() if y0 is None else y0.clone().contiguous()
+        x = torch.empty((self.Nn, self.nx), dtype=self.dtype, device=self.device) if outputs else None
+        u = torch.empty((self.Np, self.nu), dtype=self.dtype, device=self.device) if outputs else None
+        z = torch.empty(self.m, dtype=self.dtype, device=self.device) if outputs else None
+        o = Opts(lam, tol, eps_curv, mem, max_iter, max_ls)
+        info = Info()
+        fn = lib().stotree_nama_solve if method == "nama" else lib().stotree_minfbe_solve
+        code = fn(self.h, ctypes.byref(o), _t_ptr(x0), _t_ptr(y), _t_ptr(x), _t_ptr(u), _t_ptr(z),
+                  ctypes.byref(info), _stream())
+        if code != 0 and not (allow_not_converged and code == STO_NOT_CONVERGED):
+            self._check(code, method)
+        return dict(y=y, x=x, u=u, z=z, info=info.as_dict())
+
+    def kkt_check(self, x0, x, u, y, tol_active=1e-6):
+        out = (ctypes.c_double * 5)()
+        self._check(lib().stotree_kkt_check(self.h, _t_ptr(x0), _t_ptr(x), _t_ptr(u), _t_ptr(y), tol_active, out,
+                                            _stream()), "kkt_check")
+        return dict(dynamics=out[0], stationarity=out[1], feasibility=out[2], complementarity=out[3],
+                    sign=out[4])
+
+    # -- measurement ----------------------------------------------------------------------
+    def set_timing(self, on=True):
+        self._check(lib().stotree_set_timing(self.h, 1 if on else 0), "set_timing")
+
+    def get_timing(self):
+        ms, n, rhs = ctypes.c_double(), ctypes.c_int64(), ctypes.c_int64()
+        self._check(lib().stotree_get_timing(self.h, ctypes.byref(ms), ctypes.byref(n), ctypes.byref(rhs)),
+                    "get_timing")
+        return ms.value, n.value, rhs.value
+
+    def solve_bytes(self):
+        a, b = ctypes.c_double(), ctypes.c_double()
+        lib().stotree_solve_bytes(self.h, ctypes.byref(a), ctypes.byref(b))
+        return a.value, b.value

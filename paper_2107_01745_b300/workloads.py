@@ -252,7 +252,8 @@ def with_box(p: Problem, xmax: np.ndarray, umax: np.ndarray) -> Problem:
 
 def paper_scale(seed: int = 2) -> Problem:
     """The paper-scale instance (N=20, 1024 scenarios, nx=100, nu=50) with its stored box:
-    per component 80 % of the largest |x_k| (|u_k|) of the unconstrained solution x(0)."""
+    per component 80 % of the largest |x_k| (|u_k|) of the unconstrained solution x(0),
+    but not below the unconstrained values of the first two stages (see oracle/make_boxes.py)."""
     p = paper_scale_unboxed(seed)
     xmax, umax = load_box("paper_scale")
     p.name = "paper_scale"

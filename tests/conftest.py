@@ -8,6 +8,12 @@ if ROOT not in sys.path:
     sys.path.insert(0, ROOT)
 
 
+def pytest_sessionstart(session):
+    """Bring libstotree.so up to date before any test loads it (no-op when current)."""
+    from paper_2107_01745_b300 import build
+    build.build()
+
+
 def pytest_configure(config):
     config.addinivalue_line("markers", "gpu: needs a CUDA device (B300, sm_103a)")
     config.addinivalue_line("markers", "slow: paper-scale CPU work (tens of seconds)")

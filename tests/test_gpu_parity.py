@@ -1,0 +1,193 @@
+"""Parity of the CUDA path (through the C ABI) with the FP64 oracle, element by element.
+
+Tolerances: FP64 handles within 1e-11 relative on the solve step (rounding only); FP32
+handles within 1e-5 relative (2-norm) on the dual gradient, the bound stated for the
+FP32 path; solver results at the same stopping tolerance within 1e-4 relative (FP32) or
+1e-8 (FP64)."""
+import numpy as np
+import pytest
+import torch
+
+from oracle import oracle as O
+from paper_2107_01745_b300 import workloads as W
+from tests import dense_kkt as D
+
+pytestmark = pytest.mark.gpu
+
+
+def _st():
+    from paper_2107_01745_b300.stotree import StoTree
+    return StoTree
+
+
+def _rel2(a, b):
+    return float(np.linalg.norm(a - b) / max(1e-30, np.linalg.norm(b)))
+
+
+def _relinf(a, b):
+    return float(np.max(np.abs(a - b)) / max(1.0, np.max(np.abs(b))))
+
+
+SMALL = [W.tiny_fp64(0),
+         W.random_problem(21, horizon=3, nx=3, nu=2),
+         W.random_problem(22, horizon=4, nx=1, nu=1, max_branch=4),
+         W.random_problem(23, horizon=3, nx=17, nu=5),
+         W.random_problem(24, horizon=2, nx=33, nu=50, max_branch=3),
+         W.random_problem(25, horizon=5, nx=6, nu=3, p_branch=0.3)]
+
+
+@pytest.mark.parametrize("prec", ["fp64", "fp32"])
+@pytest.mark.parametrize("p", SMALL, ids=lambda p: f"{p.name}-nx{p.nx}-nu{p.nu}")
+def test_solve_step_matches_oracle(cuda_device, p, prec):
+    """Algorithm 3 / 4 through stotree_solve_step, 1 to 3 right-hand sides, unscaled and scaled."""
+    o = O.LQOracle(p)
+    st = _st()(p, precision=prec)
+    st.factor()
+    tol = 1e-11 if prec == "fp64" else 1e-5
+    ys = [W.random_dual(p, 100 + k, scale=1.5) for k in range(3)]
+    for homog in (False, True):
+        for nrhs in (1, 2, 3):
+            Y = st.to_dev(np.stack(ys[:nrhs]))
+            H = st.solve_step(Y if nrhs > 1 else Y[0], homogeneous=homog).cpu().numpy().reshape(nrhs, -1)
+            for k in range(nrhs):
+                ref = o.hx(ys[k], homogeneous=homog)
+                assert _rel2(H[k], ref) < tol, (homog, nrhs, k)
+    # scaled: input ybar, output S Hx(S ybar)
+    yb = ys[0] / o.sq
+    Hs = st.solve_step(st.to_dev(yb), scaled=True).cpu().numpy()
+    assert _rel2(Hs, o.sq * o.hx(ys[0])) < tol
+    # primal of the last round
+    st.solve_step(st.to_dev(ys[1]))
+    x, u = st.last_primal()
+    xr, ur = o.solve(ys[1])
+    assert _rel2(x.cpu().numpy(), xr) < tol and _rel2(u.cpu().numpy(), ur) < tol
+
+
+def test_set_costs_rejects_nonpositive_r(cuda_device):
+    """R must be positive definite (Section II-B); the host rejects it before any kernel."""
+    from paper_2107_01745_b300.stotree import StoError
+    p = W.random_problem(31, horizon=2, nx=2, nu=2)
+    st = _st()(p, precision="fp64")
+    with pytest.raises(StoError):
+        st.set_costs(p.Q, -np.ones(p.nu), p.PN)
+
+
+@pytest.mark.parametrize("prec", ["fp64", "fp32"])
+def test_lambda_power_iteration(cuda_device, prec):
+    p = SMALL[1]
+    o = O.LQOracle(p)
+    st = _st()(p, precision=prec)
+    st.factor()
+    r0 = np.random.default_rng(3).standard_normal(o.m)
+    lam_o, L_o = O.power_lambda(o, r0, iters=50)
+    lam_g, L_g = st.estimate_lambda(st.to_dev(r0), iters=50)
+    assert abs(L_g - L_o) / L_o < (1e-10 if prec == "fp64" else 1e-4)
+    assert abs(lam_g - lam_o) / lam_o < (1e-10 if prec == "fp64" else 1e-4)
+
+
+BOXED = [W.tiny_fp64(0)] + [D.boxed_problem(s, horizon=h, nx=nx, nu=nu) for s, h, nx, nu in
+                            [(41, 3, 3, 2), (42, 4, 4, 2), (43, 3, 9, 4)]]
+
+
+@pytest.mark.parametrize("method", ["nama", "minfbe"])
+@pytest.mark.parametrize("p", BOXED, ids=lambda p: p.name)
+def test_solver_fp64_matches_oracle(cuda_device, p, method):
+    """FP64 Algorithms 1 and 2 on the GPU follow the oracle's iterates: same stopping
+    iteration and the same solution to 1e-8."""
+    o = O.LQOracle(p)
+    lam, _ = O.power_lambda(o, np.random.default_rng(0).standard_normal(o.m))
+    ref = (O.nama if method == "nama" else O.minfbe)(o, lam, tol=1e-10, max_iter=500)
+    st = _st()(p, precision="fp64")
+    st.factor()
+    res = st.solve(method, lam, tol=1e-10, max_iter=500)
+    info = res["info"]
+    assert info["status"] == 0 and info["res_inf"] <= 1e-10
+    assert info["iters"] == ref["iters"]
+    assert _relinf(res["x"].cpu().numpy(), ref["x"]) < 1e-8
+    assert _relinf(res["u"].cpu().numpy(), ref["u"]) < 1e-8
+    assert _relinf(res["y"].cpu().numpy(), ref["y"]) < 1e-8
+    assert _relinf(res["z"].cpu().numpy(), ref["z"]) < 1e-8
+    kkt = st.kkt_check(st.to_dev(p.x0), res["x"], res["u"], res["y"], tol_active=1e-8)
+    assert kkt["dynamics"] < 1e-12 and kkt["stationarity"] < 1e-10
+    assert kkt["feasibility"] < 1e-9 and kkt["sign"] < 1e-12
+
+
+@pytest.mark.parametrize("method", ["nama", "minfbe"])
+@pytest.mark.parametrize("p", BOXED[1:], ids=lambda p: p.name)
+def test_solver_fp32_matches_oracle(cuda_device, p, method):
+    """FP32 Algorithms 1 and 2 reach the stopping tolerance; the solution matches the
+    oracle's at the same tolerance within 1e-4 relative."""
+    o = O.LQOracle(p)
+    lam, _ = O.power_lambda(o, np.random.default_rng(0).standard_normal(o.m))
+    ref = (O.nama if method == "nama" else O.minfbe)(o, lam, tol=1e-5, max_iter=500)
+    st = _st()(p, precision="fp32")
+    st.factor()
+    res = st.solve(method, lam, tol=1e-5, max_iter=500)
+    assert res["info"]["res_inf"] <= 1e-5
+    assert _relinf(res["x"].cpu().numpy(), ref["x"]) < 1e-4
+    assert _relinf(res["u"].cpu().numpy(), ref["u"]) < 1e-4
+    assert _relinf(res["y"].cpu().numpy(), ref["y"]) < 1e-3
+
+
+def test_loose_box_returns_unconstrained_solution(cuda_device):
+    p = W.random_problem(14, box_scale=1e6)
+    st = _st()(p, precision="fp64")
+    st.factor()
+    res = st.solve("nama", 0.1, tol=1e-12)
+    assert res["info"]["iters"] == 0
+    xd, ud = D.dense_solve(p, np.zeros(p.num_dual))
+    assert _relinf(res["x"].cpu().numpy(), xd) < 1e-10
+
+
+def test_not_converged_is_reported(cuda_device):
+    from paper_2107_01745_b300.stotree import StoError
+    p = BOXED[1]
+    st = _st()(p, precision="fp32")
+    st.factor()
+    with pytest.raises(StoError) as ei:
+        st.solve("nama", 0.1, tol=1e-12, max_iter=2)
+    assert ei.value.code == 7
+    res = st.solve("nama", 0.1, tol=1e-12, max_iter=2, allow_not_converged=True)
+    assert res["info"]["iters"] == 2
+
+
+@pytest.fixture(scope="module")
+def paper_scale():
+    p = W.paper_scale(2)
+    return p, O.LQOracle(p)
+
+
+def test_paper_scale_solve_step(cuda_device, paper_scale):
+    """Full-size instance (1.79M dual variables), every output entry against the oracle."""
+    p, o = paper_scale
+    st = _st()(p, precision="fp32")
+    st.factor()
+    for homog in (False, True):
+        y = W.random_dual(p, 7, scale=0.5)
+        h = st.solve_step(st.to_dev(y), homogeneous=homog).cpu().numpy().astype(np.float64)
+        ref = o.hx(y, homogeneous=homog)
+        assert _rel2(h, ref) < 1e-5
+    # two right-hand sides in one round
+    Y = np.stack([W.random_dual(p, 8), W.random_dual(p, 9)])
+    H = st.solve_step(st.to_dev(Y), homogeneous=True).cpu().numpy()
+    for k in range(2):
+        assert _rel2(H[k], o.hx(Y[k], homogeneous=True)) < 1e-5
+
+
+@pytest.mark.slow
+@pytest.mark.parametrize("method", ["nama", "minfbe"])
+def test_paper_scale_solver(cuda_device, paper_scale, method):
+    """Full-size FP32 MINFBE / NAMA to ||z - Hx||_inf <= 1e-4 against the FP64 oracle run to
+    the same tolerance, plus the FP64 KKT check of the GPU result."""
+    p, o = paper_scale
+    r0 = np.random.default_rng(7).standard_normal(o.m)
+    lam, _ = O.power_lambda(o, r0)
+    ref = (O.nama if method == "nama" else O.minfbe)(o, lam, tol=1e-4, max_iter=300)
+    st = _st()(p, precision="fp32")
+    st.factor()
+    res = st.solve(method, lam, tol=1e-4, max_iter=300)
+    assert res["info"]["res_inf"] <= 1e-4
+    assert _relinf(res["x"].cpu().numpy(), ref["x"]) < 1e-3
+    assert _relinf(res["u"].cpu().numpy(), ref["u"]) < 1e-3
+    kkt = st.kkt_check(st.to_dev(p.x0), res["x"], res["u"], res["y"], tol_active=1e-3)
+    assert kkt["dynamics"] < 1e-4 and kkt["feasibility"] < 2e-4
