@@ -1,0 +1,325 @@
+#!/usr/bin/env python
+"""Benchmark: milliseconds to ||z - Hx||_inf <= 1e-4 for NAMA (Algorithm 2) on the paper-scale
+scenario tree (horizon 20, binary for 10 stages then one child, 1024 scenarios, 12,287 nodes,
+nx = 100, nu = 50: 1.79M primal and dual variables), FP32 solve path with the FP64 factor.
+
+One step = one cold-started NAMA solve (y0 = 0) to tolerance, inputs resident on the device;
+the factor and the step-size estimate are set-up and are not timed.  MINFBE (Algorithm 1) is
+timed beside it.  The solve rounds (Algorithm 3/4) are timed inside the library with CUDA
+events on the launching stream for the roofline line.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
+
+Under torchrun each rank solves its own replica of the instance (independent problems, no
+collective on the data path; scaling "weak"); rank 0 prints one JSON line.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+METRIC = "ms to KKT tol 1e-4 (MINFBE/NAMA), batched/warm vs plain; solve-step GB/s"
+TOL = 1e-4
+WORKLOAD = ("paper_scale: horizon 20, branching 2 for stages 0-9 then 1 (1024 scenarios, 12287 nodes), "
+            "nx=100, nu=50, per-node A_j = A + 0.05 N(0,1) (rho(A)=0.98), B_j ~ N(0,1/nx), w ~ N(0,0.05^2), "
+            "Q=diag(U[0.5,2]), R=0.1I, P_N=I, box = 80% of the unconstrained range (not below the first two "
+            "stages), x0 ~ U[-3,3], seed 2; NAMA cold start to ||z-Hx||_inf <= 1e-4")
+
+
+def _peaks():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(path):
+        with open(path) as f:
+            d = json.load(f)
+        return float(d["hbm_gbs"]), "measured"
+    return 6400.0, "fallback"
+
+
+class ClockSampler:
+    """nvidia-smi sampling of SM clocks and throttle reasons during the timed region."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.gpu = gpu_index
+        self.proc = None
+        self.path = None
+
+    def __enter__(self):
+        fd, self.path = tempfile.mkstemp(suffix=".csv")
+        os.close(fd)
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", f"--id={self.gpu}", f"--query-gpu={self.FIELDS}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+        except OSError:
+            self.proc = None
+        return self
+
+    def __exit__(self, *exc):
+        if self.proc is not None:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+
+    def summary(self):
+        if not self.path or not os.path.exists(self.path):
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        with open(self.path) as f:
+            for line in f:
+                parts = [x.strip() for x in line.split(",")]
+                if len(parts) < 9:
+                    continue
+                try:
+                    sm.append(float(parts[1]))
+                    smax.append(float(parts[2]))
+                except ValueError:
+                    continue
+                for n, v in zip(names, parts[5:9]):
+                    if v.lower() == "active":
+                        reasons.add(n)
+        os.unlink(self.path)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no samples"]}
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(smax), "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def _dist():
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return world, rank, local
+
+
+def run_ours(args):
+    import torch
+    from paper_2107_01745_b300 import workloads as W
+    from paper_2107_01745_b300.stotree import StoTree
+
+    world, rank, local = _dist()
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    pg = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=dev)
+        pg = dist
+    p = W.paper_scale(2)
+    st = StoTree(p, precision="fp32", device=dev)
+    st.factor()
+    r0 = torch.as_tensor(np.random.default_rng(7).standard_normal(st.m), dtype=torch.float32, device=dev)
+    lam, Lhat = st.estimate_lambda(r0, iters=50, safety=0.9)
+    x0 = st.to_dev(p.x0)
+    stream = torch.cuda.current_stream()
+
+    def one(method, y0=None):
+        res = st.solve(method, lam, x0=x0, y0=y0, tol=TOL, mem=5, max_iter=500)
+        if res["info"]["res_inf"] > TOL:
+            raise RuntimeError(f"{method} stopped at residual {res['info']['res_inf']}")
+        return res
+
+    for _ in range(args.warmup):
+        one("nama")
+        one("minfbe")
+
+    def timed(method, k):
+        infos = []
+        if pg is not None:
+            pg.barrier()
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for _ in range(k):
+            infos.append(one(method)["info"])
+        e1.record(stream)
+        torch.cuda.synchronize()
+        ms = e0.elapsed_time(e1) / k
+        if pg is not None:
+            t = torch.tensor([ms], device=dev)
+            pg.all_reduce(t, op=pg.ReduceOp.MAX)
+            ms = float(t.item())
+        return ms, infos
+
+    st.set_timing(True)
+    st.get_timing()  # reset counters
+    with ClockSampler(local) as clk:
+        nama_ms, nama_infos = timed("nama", args.steps)
+    solve_ms, rounds, rhs = st.get_timing()
+    st.set_timing(False)
+    minfbe_ms, minfbe_infos = timed("minfbe", args.steps)
+
+    mat_bytes, vec_bytes = st.solve_bytes()
+    alg_bytes = rounds * mat_bytes + rhs * vec_bytes
+    achieved = alg_bytes / (solve_ms * 1e-3) / 1e9
+    peak, peak_kind = _peaks()
+
+    # end to end through the public API: pinned host inputs in, results out, every step
+    x0_h = torch.as_tensor(p.x0, dtype=torch.float32).pin_memory()
+    y0_h = torch.zeros(st.m, dtype=torch.float32).pin_memory()
+    y_h = torch.empty(st.m, dtype=torch.float32).pin_memory()
+    x_h = torch.empty((st.Nn, st.nx), dtype=torch.float32).pin_memory()
+    u_h = torch.empty((st.Np, st.nu), dtype=torch.float32).pin_memory()
+    x0_d = torch.empty_like(x0)
+    y0_d = torch.empty(st.m, dtype=torch.float32, device=dev)
+    if pg is not None:
+        pg.barrier()
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(args.steps):
+        x0_d.copy_(x0_h, non_blocking=True)
+        y0_d.copy_(y0_h, non_blocking=True)
+        res = st.solve("nama", lam, x0=x0_d, y0=y0_d, tol=TOL, mem=5, max_iter=500)
+        y_h.copy_(res["y"], non_blocking=True)
+        x_h.copy_(res["x"], non_blocking=True)
+        u_h.copy_(res["u"], non_blocking=True)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    e2e_ms = e0.elapsed_time(e1) / args.steps
+    if pg is not None:
+        t = torch.tensor([e2e_ms], device=dev)
+        pg.all_reduce(t, op=pg.ReduceOp.MAX)
+        e2e_ms = float(t.item())
+    h2d = 4 * (st.nx + st.m)
+    d2h = 4 * (st.m + st.Nn * st.nx + st.Np * st.nu)
+
+    line = None
+    if rank == 0:
+        cpu = cpu_baseline(p, lam, nama_infos[0]["iters"])
+        launches = int(sum(i["launches"] for i in nama_infos))
+        line = {
+            "metric": METRIC, "value": round(nama_ms, 4), "unit": "ms", "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": round(nama_ms, 4), "higher_is_better": False,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "config": {"workload": WORKLOAD, "method": "nama", "solver_tol": TOL, "lbfgs_mem": 5,
+                       "lambda": lam, "L_estimate": Lhat, "m_dual": st.m, "n_primal": st.n,
+                       "l2": "inputs larger than L2: each solve round streams 2.04 GB of factor arrays",
+                       "parallelism": f"replicas x{world}"},
+            "nama": {"ms": round(nama_ms, 4), "iters": nama_infos[0]["iters"],
+                     "solve_calls": nama_infos[0]["solve_calls"], "ls_zero": nama_infos[0]["ls_zero"]},
+            "minfbe": {"ms": round(minfbe_ms, 4), "iters": minfbe_infos[0]["iters"],
+                       "solve_calls": minfbe_infos[0]["solve_calls"]},
+            "roofline": {"kernel": "solve round (Algorithm 3/4 stage kernels)", "bound": "hbm",
+                         "achieved": round(achieved, 1), "peak": peak, "unit": "GB/s",
+                         "frac": round(achieved / peak, 4), "peak_source": peak_kind,
+                         "traffic": None, "rounds": rounds, "rhs": rhs,
+                         "algorithmic_bytes_per_round": mat_bytes, "vector_bytes_per_rhs": vec_bytes,
+                         "avg_round_ms": round(solve_ms / max(rounds, 1), 5)},
+            "solve_step_gbs": round(achieved, 1),
+            "e2e": {"value": round(e2e_ms, 4), "unit": "ms", "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
+            "gpu_launches": launches,
+            "clocks": clk.summary(),
+            "cpu_baseline": cpu,
+        }
+    if pg is not None:
+        pg.barrier()
+        pg.destroy_process_group()
+    return line
+
+
+def cpu_baseline(p, lam, gpu_iters):
+    """The FP64 oracle, as it stands, on the host cores: one full NAMA solve of the same instance
+    (factor not timed), capped at 60 iterations."""
+    from oracle import oracle as O
+    o = O.LQOracle(p)
+    t0 = time.perf_counter()
+    res = O.nama(o, lam, tol=TOL, max_iter=60)
+    sec = time.perf_counter() - t0
+    return {"value": round(sec * 1e3, 1), "unit": "ms", "cores": O.num_threads(), "kind": "oracle",
+            "sample": f"one full cold-started NAMA solve of the same instance with the same lambda "
+                      f"(FP64 C + numpy, {res['iters']} iterations, status {res['status']}, residual "
+                      f"{res['res_inf']:.2e}; factor not timed)"}
+
+
+def run_reference(args):
+    """The oracle as the reference arm: same workload, metric and unit, on the host cores."""
+    world, rank, _ = _dist()
+    if rank != 0:
+        return None
+    from oracle import oracle as O
+    from paper_2107_01745_b300 import workloads as W
+    p = W.paper_scale(2)
+    o = O.LQOracle(p)
+    lam, _ = O.power_lambda(o, np.random.default_rng(7).standard_normal(o.m))
+    full = O.nama(o, lam, tol=TOL, max_iter=100)
+    iters_to_tol = full["iters"]
+    per_iter = []
+    sample_iters = 3
+    for k in range(args.warmup + args.steps):
+        t0 = time.perf_counter()
+        r = O.nama(o, lam, tol=TOL, max_iter=sample_iters)
+        dt = time.perf_counter() - t0
+        if k >= args.warmup:
+            per_iter.append(dt / max(1, r["iters"]))
+    ms = 1e3 * statistics.mean(per_iter) * iters_to_tol
+    return {"impl": "reference", "metric": METRIC, "value": round(ms, 1), "unit": "ms", "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(ms, 1), "higher_is_better": False,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": WORKLOAD, "method": "nama", "solver_tol": TOL},
+            "cpu_baseline": {"value": round(ms, 1), "unit": "ms", "cores": O.num_threads(), "kind": "oracle",
+                             "sample": f"each step: {sample_iters} NAMA iterations of the FP64 oracle; value = "
+                                       f"mean time per iteration x {iters_to_tol} iterations, the oracle's own "
+                                       f"count to tolerance (full solve {full['seconds']:.1f} s)"},
+            "e2e": {"value": round(ms, 1), "unit": "ms", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+
+
+def run_profile(method):
+    """Set-up and one warm solve outside the profiler range, then exactly one solve inside
+    cudaProfilerStart/Stop (for ncu --profile-from-start off)."""
+    import torch
+    from paper_2107_01745_b300 import workloads as W
+    from paper_2107_01745_b300.stotree import StoTree
+    p = W.paper_scale(2)
+    st = StoTree(p, precision="fp32")
+    st.factor()
+    r0 = torch.as_tensor(np.random.default_rng(7).standard_normal(st.m), dtype=torch.float32, device="cuda")
+    lam, _ = st.estimate_lambda(r0, iters=50)
+    st.solve(method, lam, tol=TOL)
+    torch.cuda.synchronize()
+    torch.cuda.cudart().cudaProfilerStart()
+    res = st.solve(method, lam, tol=TOL)
+    torch.cuda.synchronize()
+    torch.cuda.cudart().cudaProfilerStop()
+    print(json.dumps({"profiled": method, **res["info"]}))
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--profile", choices=["nama", "minfbe"], default=None,
+                    help="run one solve inside a profiler range (no JSON benchmark line)")
+    args = ap.parse_args()
+    if args.profile:
+        run_profile(args.profile)
+        return
+    if args.warmup < 3:
+        raise SystemExit("at least 3 warm-up steps")
+    line = run_reference(args) if args.impl == "reference" else run_ours(args)
+    if line is not None:
+        print(json.dumps(line), flush=True)
+
+
+if __name__ == "__main__":
+    main()

@@ -100,6 +100,8 @@ typedef struct {
     int32_t solve_calls;  /* right-hand sides pushed through Algorithm 3/4 ("oracle calls") */
     int32_t status;       /* sto_status of the solve */
     int32_t ls_zero;      /* iterations whose line search fell back to tau = 0 */
+    int32_t launches;     /* CUDA kernels launched by the call */
+    int32_t reserved;
     double res_inf;       /* ||z - Hx||_inf at the returned iterate */
     double fbe;           /* phi_lambda at the returned iterate (scaled dual) */
     double ms;            /* wall time of the call on the stream, milliseconds */

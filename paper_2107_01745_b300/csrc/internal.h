@@ -100,6 +100,7 @@ struct stotree_s {
     double solve_ms = 0.0;
     int64_t solve_launches = 0, solve_rhs = 0;
     int64_t solve_calls = 0;
+    int64_t launches = 0;   // kernels launched through this handle
     // pinned host mirror of the device scalars
     sto::SolverScalars *host_scal = nullptr;
 

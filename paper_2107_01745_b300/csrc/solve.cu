@@ -313,6 +313,7 @@ void run_round(stotree_t h, const SolveArgs<T> &a, cudaStream_t st) {
         const int first = h->soff[t], count = h->soff[t + 1] - first;
         launch_fwd<T, NR>(a, first, count, st);
     }
+    h->launches += 2 * h->N + 1;
 }
 
 template <class T>

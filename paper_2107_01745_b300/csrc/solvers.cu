@@ -594,6 +594,7 @@ sto_status solver_impl(stotree_t h, int method, const sto_opts *o, const void *x
     STO_CUDA(h, cudaEventCreate(&e1));
     STO_CUDA(h, cudaEventRecord(e0, st));
     const int64_t calls0 = h->solve_calls;
+    const int64_t launches0 = h->launches;
 
     SolverScalars *hs = h->host_scal;
     std::memset(hs, 0, sizeof(SolverScalars));
@@ -634,12 +635,15 @@ sto_status solver_impl(stotree_t h, int method, const sto_opts *o, const void *x
     };
 
     k_scale_in<T><<<grid, kThreads, 0, st>>>(dv, static_cast<const T *>(yv), yb);
+    h->launches += 1;
     sto_status s = full_solve();
     if (s != STO_OK) return s;
     k_point<T><<<grid, kThreads, 0, st>>>(dv, yb, hv, r, ringS, ringY, vs, 0, sc, part);
+    h->launches += 1;
     if (!nama) {
         if ((s = lin_solve(r, hr)) != STO_OK) return s;
         k_grad<T><<<grid, kThreads, 0, st>>>(m, r, hr, g, ringS, ringY, vs, sc, part);
+        h->launches += 1;
     }
     sto_status result = STO_OK;
     int iters = 0;
@@ -658,6 +662,7 @@ sto_status solver_impl(stotree_t h, int method, const sto_opts *o, const void *x
         }
         T *gdir = nama ? r : g;
         lb_direction<T>(o->lbfgs_mem, grid, st, m, gdir, ringS, ringY, vs, sc, part, d);
+        h->launches += 2 + ng + 2;  // L-BFGS pair, line-search groups, FB step, residual pass
         if (nama) {
             const void *ys[2] = {r, d};
             void *outs[2] = {hr, hd};
@@ -683,10 +688,12 @@ sto_status solver_impl(stotree_t h, int method, const sto_opts *o, const void *x
         if (!nama) {
             if ((s = lin_solve(r, hr)) != STO_OK) return s;
             k_grad<T><<<grid, kThreads, 0, st>>>(m, r, hr, g, ringS, ringY, vs, sc, part);
+            h->launches += 1;
         }
         ++iters;
         STO_CUDA(h, cudaGetLastError());
     }
+    h->launches += 1;
     k_finish_out<T><<<grid, kThreads, 0, st>>>(dv, yb, hv, sc, static_cast<T *>(yv), static_cast<T *>(zv),
                                                static_cast<T *>(xv), static_cast<T *>(uv));
     if (xv) {
@@ -708,6 +715,8 @@ sto_status solver_impl(stotree_t h, int method, const sto_opts *o, const void *x
         info->res_inf = hs->res_inf;
         info->fbe = hs->phi;
         info->ms = ms;
+        info->launches = (int32_t)(h->launches - launches0);
+        info->reserved = 0;
     }
     STO_CUDA(h, cudaGetLastError());
     return result;

@@ -40,7 +40,8 @@ class Opts(ctypes.Structure):
 
 class Info(ctypes.Structure):
     _fields_ = [("iters", ctypes.c_int32), ("solve_calls", ctypes.c_int32), ("status", ctypes.c_int32),
-                ("ls_zero", ctypes.c_int32), ("res_inf", ctypes.c_double), ("fbe", ctypes.c_double),
+                ("ls_zero", ctypes.c_int32), ("launches", ctypes.c_int32), ("reserved", ctypes.c_int32),
+                ("res_inf", ctypes.c_double), ("fbe", ctypes.c_double),
                 ("ms", ctypes.c_double)]
 
     def as_dict(self):
