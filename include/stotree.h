@@ -161,6 +161,23 @@ STO_API sto_status stotree_factor(stotree_t h, int32_t sync, sto_stream_t stream
 STO_API sto_status stotree_solve_step(stotree_t h, const void *y, const void *x0, void *hx, int32_t nrhs,
                               int32_t homogeneous, int32_t scaled, sto_stream_t stream);
 
+/* stotree_solve_step for one right-hand side without any allocation (the paper has no
+ * counterpart).  For callers that cannot call cudaMalloc, or any allocator, while they run a
+ * solve: e.g. a controller whose device-memory plan is frozen after start-up.  The handle must
+ * be set up and factored beforehand; a call then touches only y, hx, the factor arrays in the
+ * bound workspace and a fixed 32 MiB scratch array compiled into the library, which every GPU
+ * that loads the library holds until the process exits.
+ *   y, x0, hx, homogeneous, scaled: as stotree_solve_step with nrhs = 1.
+ * Limit: the round needs 2 (Nn nx + Np nu) reals of scratch (each part 256-byte aligned); larger
+ * problems get STO_ERR_INVALID_ARG and a message in stotree_last_error.  The first call on a
+ * device looks the array's address up (cudaGetSymbolAddress) with that device current; make
+ * that first call before any stream capture.  All calls share the one array: calls that
+ * overlap on the GPU (other streams, other handles) race and give wrong results.  The
+ * primal trajectory stays in the array, so stotree_last_primal does not report it.
+ * Asynchronous.  Errors: STO_ERR_INVALID_ARG, STO_ERR_NOT_READY, STO_ERR_CUDA. */
+STO_API sto_status stotree_solve_step_noalloc(stotree_t h, const void *y, const void *x0, void *hx,
+                                              int32_t homogeneous, int32_t scaled, sto_stream_t stream);
+
 /* Primal trajectory of the last solve round's first right-hand side: x [Nn][nx],
  * u [Np][nu] (device real).  Asynchronous. */
 STO_API sto_status stotree_last_primal(stotree_t h, void *x, void *u, sto_stream_t stream);

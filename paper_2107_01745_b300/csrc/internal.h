@@ -121,9 +121,13 @@ sto_status cuda_fail(stotree_t h, cudaError_t e, const char *what);
 sto_status factor_run(stotree_t h, cudaStream_t st);
 
 // solve.cu: one round of Algorithm 3/4 on nrhs vectors (real pointers in the workspace
-// or caller memory).  scaled: input is ybar and output S Hx.
+// or caller memory).  scaled: input is ybar and output S Hx.  With `scratch`, the round
+// (one right-hand side) keeps its intermediate vectors there instead of in the workspace.
+struct SolveScratch {
+    void *s, *ubar, *xs, *us;  // real [Nn][nx], [Np][nu], [Nn][nx], [Np][nu]
+};
 sto_status solve_round(stotree_t h, const void *const *y, const void *x0, void *const *hx, int nrhs,
-                       bool homogeneous, bool scaled, cudaStream_t st);
+                       bool homogeneous, bool scaled, cudaStream_t st, const SolveScratch *scratch = nullptr);
 
 // vecops.cu
 template <class T>

@@ -318,7 +318,7 @@ void run_round(stotree_t h, const SolveArgs<T> &a, cudaStream_t st) {
 
 template <class T>
 sto_status solve_impl(stotree_t h, const void *const *y, const void *x0, void *const *hx, int nrhs, bool homog,
-                      bool scaled, cudaStream_t st) {
+                      bool scaled, cudaStream_t st, const SolveScratch *scratch) {
     const Layout &L = h->L;
     SolveArgs<T> a;
     a.nx = h->nx;
@@ -345,10 +345,17 @@ sto_status solve_impl(stotree_t h, const void *const *y, const void *x0, void *c
         a.h[k] = static_cast<T *>(hx[k < nrhs ? k : 0]);
     }
     a.x0 = static_cast<const T *>(x0);
-    a.s = h->at<T>(L.s);
-    a.ubar = h->at<T>(L.ubar);
-    a.xs = h->at<T>(L.xs);
-    a.us = h->at<T>(L.us);
+    if (scratch) {  // caller-supplied scratch for one right-hand side
+        a.s = static_cast<T *>(scratch->s);
+        a.ubar = static_cast<T *>(scratch->ubar);
+        a.xs = static_cast<T *>(scratch->xs);
+        a.us = static_cast<T *>(scratch->us);
+    } else {
+        a.s = h->at<T>(L.s);
+        a.ubar = h->at<T>(L.ubar);
+        a.xs = h->at<T>(L.xs);
+        a.us = h->at<T>(L.us);
+    }
     a.s_stride = (long long)h->Nn * h->nx;
     a.u_stride = (long long)h->Np * h->nu;
     a.homog = homog ? 1 : 0;
@@ -370,9 +377,10 @@ sto_status solve_impl(stotree_t h, const void *const *y, const void *x0, void *c
 }  // namespace
 
 sto_status solve_round(stotree_t h, const void *const *y, const void *x0, void *const *hx, int nrhs, bool homog,
-                       bool scaled, cudaStream_t st) {
-    return h->prec == STO_FP64 ? solve_impl<double>(h, y, x0, hx, nrhs, homog, scaled, st)
-                               : solve_impl<float>(h, y, x0, hx, nrhs, homog, scaled, st);
+                       bool scaled, cudaStream_t st, const SolveScratch *scratch) {
+    if (scratch && nrhs != 1) return STO_ERR_INVALID_ARG;
+    return h->prec == STO_FP64 ? solve_impl<double>(h, y, x0, hx, nrhs, homog, scaled, st, scratch)
+                               : solve_impl<float>(h, y, x0, hx, nrhs, homog, scaled, st, scratch);
 }
 
 }  // namespace sto

@@ -68,6 +68,7 @@ def lib():
             "stotree_set_box": [vp, vp, vp, vp, vp, vp],
             "stotree_factor": [vp, i32, vp],
             "stotree_solve_step": [vp, vp, vp, vp, i32, i32, i32, vp],
+            "stotree_solve_step_noalloc": [vp, vp, vp, vp, i32, i32, vp],
             "stotree_last_primal": [vp, vp, vp, vp],
             "stotree_estimate_lambda": [vp, vp, i32, dbl, vp, vp, vp],
             "stotree_nama_solve": [vp, vp, vp, vp, vp, vp, vp, vp, vp],
@@ -94,7 +95,7 @@ def lib():
 def exported_symbols():
     return [n for n in ("stotree_create", "stotree_destroy", "stotree_sizes", "stotree_workspace_size",
                         "stotree_bind_workspace", "stotree_set_dynamics", "stotree_set_costs", "stotree_set_box",
-                        "stotree_factor", "stotree_solve_step", "stotree_last_primal", "stotree_estimate_lambda",
+                        "stotree_factor", "stotree_solve_step", "stotree_solve_step_noalloc", "stotree_last_primal", "stotree_estimate_lambda",
                         "stotree_nama_solve", "stotree_minfbe_solve", "stotree_kkt_check", "stotree_set_timing",
                         "stotree_get_timing", "stotree_solve_bytes", "stotree_status_str", "stotree_last_error")]
 
@@ -198,6 +199,16 @@ class StoTree:
         x0 = x0 if x0 is not None else (None if homogeneous else self.to_dev(self.p.x0))
         self._check(lib().stotree_solve_step(self.h, _t_ptr(y), _t_ptr(x0), _t_ptr(out), nrhs,
                                              1 if homogeneous else 0, 1 if scaled else 0, _stream()), "solve_step")
+        return out
+
+    def solve_step_noalloc(self, y, x0=None, homogeneous=False, scaled=False, out=None):
+        """stotree_solve_step_noalloc: one right-hand side, scratch in the library's static array."""
+        y = y.contiguous()
+        out = torch.empty_like(y) if out is None else out
+        x0 = x0 if x0 is not None else (None if homogeneous else self.to_dev(self.p.x0))
+        self._check(lib().stotree_solve_step_noalloc(self.h, _t_ptr(y), _t_ptr(x0), _t_ptr(out),
+                                                     1 if homogeneous else 0, 1 if scaled else 0, _stream()),
+                    "solve_step_noalloc")
         return out
 
     def last_primal(self):
