@@ -19,6 +19,59 @@ sto_status cuda_fail(stotree_t h, cudaError_t e, const char *what) {
 
 static size_t round_up(size_t v, size_t a) { return (v + a - 1) / a * a; }
 
+// Work items of a solve round: maximal paths of at most kSegMax nodes along which every node
+// has one child, so that a CTA keeps the recursion's vector in shared memory along the path.
+// Backward: over nonleaf nodes, lowest node first; a node joins its only child's segment when
+// that child is nonleaf and the segment is not full.  Segments are ordered by lowest node
+// descending, so every segment's children segments come earlier (tickets are handed out in
+// this order and a segment only waits on earlier ones).  Forward: over all nodes, top node
+// first; a node joins its parent's segment when it is the parent's only child.  Ordered by top
+// node ascending, so the parent's segment always comes earlier.
+static void build_segments(stotree_t h) {
+    const int Nn = h->Nn, Np = h->Np;
+    std::vector<std::vector<int>> segs;
+    std::vector<int> seg_of(Nn, -1);
+    for (int i = Np - 1; i >= 0; --i) {
+        if (h->ccnt[i] == 1 && h->cbeg[i] < Np) {
+            const int c = h->cbeg[i], sc = seg_of[c];
+            if ((int)segs[sc].size() < kSegMax && segs[sc].back() == c) {
+                segs[sc].push_back(i);
+                seg_of[i] = sc;
+                continue;
+            }
+        }
+        seg_of[i] = (int)segs.size();
+        segs.push_back({i});
+    }
+    h->bstart.assign(1, 0);
+    h->bnodes.clear();
+    for (auto &s : segs) {
+        for (int v : s) h->bnodes.push_back(v);
+        h->bstart.push_back((int)h->bnodes.size());
+    }
+    segs.clear();
+    std::fill(seg_of.begin(), seg_of.end(), -1);
+    for (int j = 0; j < Nn; ++j) {
+        const int p = h->parent[j];
+        if (p >= 0 && h->ccnt[p] == 1) {
+            const int sp = seg_of[p];
+            if ((int)segs[sp].size() < kSegMax && segs[sp].back() == p) {
+                segs[sp].push_back(j);
+                seg_of[j] = sp;
+                continue;
+            }
+        }
+        seg_of[j] = (int)segs.size();
+        segs.push_back({j});
+    }
+    h->fstart.assign(1, 0);
+    h->fnodes.clear();
+    for (auto &s : segs) {
+        for (int v : s) h->fnodes.push_back(v);
+        h->fstart.push_back((int)h->fnodes.size());
+    }
+}
+
 static void compute_layout(stotree_t h) {
     Layout &L = h->L;
     size_t total = 0;
@@ -67,6 +120,12 @@ static void compute_layout(stotree_t h) {
     L.partials = add((size_t)kRedBlocks * kRedSlots * 8);
     L.scal = add(sizeof(SolverScalars));
     L.kkt = add((Nn * nx + Np * nu) * 8 + 64 * 8);
+    L.bstart = add(h->bstart.size() * 4);
+    L.bnodes = add(h->bnodes.size() * 4);
+    L.fstart = add(h->fstart.size() * 4);
+    L.fnodes = add(h->fnodes.size() * 4);
+    L.flags = add(2 * Nn * 4);
+    L.ticket = add(64);
     L.total = round_up(total, 256);
 }
 
@@ -190,6 +249,7 @@ sto_status stotree_create(const sto_tree_desc *t, int32_t precision, stotree_t *
     }
     h->have_dyn.assign(Nn, 0);
     h->have_dyn[0] = 1;
+    build_segments(h);
     compute_layout(h);
     if (cudaMallocHost(&h->host_scal, sizeof(SolverScalars)) != cudaSuccess) {
         h->host_scal = new SolverScalars();
@@ -237,6 +297,12 @@ sto_status stotree_bind_workspace(stotree_t h, void *dev, size_t bytes, sto_stre
     STO_CUDA(h, cudaMemcpyAsync(h->ws + L.soff, h->soff.data(), (h->N + 2) * 4, cudaMemcpyHostToDevice, st));
     STO_CUDA(h, cudaMemcpyAsync(h->ws + L.node_stage, h->stage.data(), h->Nn * 4, cudaMemcpyHostToDevice, st));
     STO_CUDA(h, cudaMemcpyAsync(h->ws + L.prob64, h->prob.data(), h->Nn * 8, cudaMemcpyHostToDevice, st));
+    STO_CUDA(h, cudaMemcpyAsync(h->ws + L.bstart, h->bstart.data(), h->bstart.size() * 4, cudaMemcpyHostToDevice, st));
+    STO_CUDA(h, cudaMemcpyAsync(h->ws + L.bnodes, h->bnodes.data(), h->bnodes.size() * 4, cudaMemcpyHostToDevice, st));
+    STO_CUDA(h, cudaMemcpyAsync(h->ws + L.fstart, h->fstart.data(), h->fstart.size() * 4, cudaMemcpyHostToDevice, st));
+    STO_CUDA(h, cudaMemcpyAsync(h->ws + L.fnodes, h->fnodes.data(), h->fnodes.size() * 4, cudaMemcpyHostToDevice, st));
+    h->epoch = 0;          // flags and ticket counter start at zero (memset above)
+    h->ticket_base = 0;
     if (h->prec == STO_FP64) {
         std::vector<double> sq(h->Nn);
         for (int i = 0; i < h->Nn; ++i) sq[i] = std::sqrt(h->prob[i]);

@@ -69,7 +69,13 @@ struct Layout {
     size_t partials;             // double [kRedBlocks][kRedSlots]
     size_t scal;                 // SolverScalars
     size_t kkt;                  // double scratch for the KKT check
+    // solve-round work items (path segments) and their dependency flags
+    size_t bstart, bnodes, fstart, fnodes;  // int: segment offsets and node lists
+    size_t flags;                // unsigned [2][Nn]: backward / forward completion epochs
+    size_t ticket;               // unsigned long long: work-item counter
 };
+
+constexpr int kSegMax = 4;       // nodes per path segment (work item) of a solve round
 
 constexpr int kNumVec = 10;      // ybar, h, r, d, hr, hd, g, tmp0, tmp1, tmp2
 
@@ -101,6 +107,12 @@ struct stotree_s {
     int64_t solve_launches = 0, solve_rhs = 0;
     int64_t solve_calls = 0;
     int64_t launches = 0;   // kernels launched through this handle
+    // solve-round work items: backward segments (lowest node first, ordered by lowest node
+    // descending) and forward segments (top node first, ordered by top node ascending)
+    std::vector<int32_t> bstart, bnodes, fstart, fnodes;
+    unsigned epoch = 0;                 // last epoch written to the flags
+    unsigned long long ticket_base = 0;  // value of the ticket counter before the next round
+    int grid_ctas[5] = {0, 0, 0, 0, 0};  // CTAs of the persistent solve kernel, per nrhs
     // pinned host mirror of the device scalars
     sto::SolverScalars *host_scal = nullptr;
 
@@ -125,13 +137,13 @@ sto_status factor_run(stotree_t h, cudaStream_t st);
 // (one right-hand side) keeps its intermediate vectors there instead of in the workspace.
 struct SolveScratch {
     void *s, *ubar, *xs, *us;  // real [Nn][nx], [Np][nu], [Nn][nx], [Np][nu]
+    void *flags;               // unsigned [2][Nn] (cleared by the round)
+    void *ticket;              // unsigned long long (cleared by the round)
 };
 sto_status solve_round(stotree_t h, const void *const *y, const void *x0, void *const *hx, int nrhs,
                        bool homogeneous, bool scaled, cudaStream_t st, const SolveScratch *scratch = nullptr);
 
-// vecops.cu
-template <class T>
-struct VecOps;  // defined in vecops.cu
+sto_status check_round_error(stotree_t h, cudaStream_t st);
 
 sto_status solver_run(stotree_t h, int method, const sto_opts *o, const void *x0, void *y, void *x,
                       void *u, void *z, sto_info *info, cudaStream_t st);

@@ -50,10 +50,12 @@ extern "C" STO_API sto_status stotree_solve_step_noalloc(stotree_t h, const void
                                                          int32_t homogeneous, int32_t scaled, sto_stream_t stream) {
     if (!h || !y || !hx) return STO_ERR_INVALID_ARG;
     if (!homogeneous && !x0) return STO_ERR_INVALID_ARG;
-    // s [Nn][nx], ubar [Np][nu], x [Nn][nx], u [Np][nu] of one right-hand side
+    // s [Nn][nx], ubar [Np][nu], x [Nn][nx], u [Np][nu] of one right-hand side, then the
+    // round's dependency flags [2][Nn] and its work-item counter
     const size_t bx = align256((size_t)h->Nn * h->nx * h->esz);
     const size_t bu = align256((size_t)h->Np * h->nu * h->esz);
-    const size_t need = 2 * (bx + bu);
+    const size_t bf = align256((size_t)2 * h->Nn * sizeof(unsigned));
+    const size_t need = 2 * (bx + bu) + bf + 256;
     if (need > kScratchBytes) {
         h->err = "stotree_solve_step_noalloc: the problem needs " + std::to_string(need) +
                  " bytes of scratch, more than the fixed " + std::to_string(kScratchBytes) + " bytes";
@@ -64,9 +66,10 @@ extern "C" STO_API sto_status stotree_solve_step_noalloc(stotree_t h, const void
     cudaError_t e = scratch_address(&base);
     if (e != cudaSuccess) return sto::cuda_fail(h, e, "cudaGetSymbolAddress(g_scratch)");
     char *b = static_cast<char *>(base);
-    // Every entry of s, ubar, x and u is written before it is read within one round, so the
-    // contents left by the previous call need no clearing.
-    sto::SolveScratch sc{b, b + bx, b + bx + bu, b + 2 * bx + bu};
+    // Every entry of s, ubar, x and u is written before it is read within one round; the flags
+    // and the counter must start at zero and are cleared by the round (cudaMemsetAsync on the
+    // caller's stream, no allocation).
+    sto::SolveScratch sc{b, b + bx, b + bx + bu, b + 2 * bx + bu, b + 2 * (bx + bu), b + 2 * (bx + bu) + bf};
     const void *ys[1] = {y};
     void *hs[1] = {hx};
     return sto::solve_round(h, ys, x0, hs, 1, homogeneous != 0, scaled != 0, reinterpret_cast<cudaStream_t>(stream),

@@ -1,24 +1,60 @@
-// Algorithm 3 (dual gradient x(y)) and Algorithm 4 (Hessian-vector products) on the device.
+// Algorithm 3 (dual gradient x(y)) and Algorithm 4 (Hessian-vector products) on the device:
+// one persistent kernel per solve round.
 //
 // With the factor of Section III-D (see factor.cu), one solve round is
-//   backward, stages t = N-1 .. 0, every parent i of the stage in parallel:
+//   backward, children before parents:
 //     s^l    = y^l / 2 + pi^l p_N / 2                    (leaf children, formed on the fly)
 //     acc    = sum_{j in child(i)} G^j' s^j   with G^j = [A^j | B^j]  -> [A's ; B's]
 //     v^i    = y_u^i / 2 + acc_B + gu^i
 //     ubar^i = -Rbar^-1 v^i,     s^i = y_x^i / 2 + acc_A + K^i' v^i + gx^i
-//   forward, stages t = 0 .. N:
+//   forward, parents before children:
 //     x^0 = p,   x^j = G^j [x^i; u^i] + c^j,   u^j = K^j x^j + ubar^j
 // and Algorithm 4 is the same with c, gu, gx, the leaf term and p set to zero.  Algorithm 3
 // overwrites u^i, q^i in its child loop where Algorithm 4 accumulates; both accumulate here.
 // Several right-hand sides share every matrix load (the parallel x(r), x(d) of Section III-C).
 //
-// Layout: G^j is nx rows of ldg reals (16-byte padded), row-major, node-major; the backward
-// pass reads it in axpy form (warps over rows, lanes over 16-byte column groups) and the
-// forward pass in dot form (one warp per row, shuffle reduction), both coalesced.
+// Scheduling.  "For k = N-1..0, in parallel over nodes(k)" needs a grid-wide barrier per
+// stage; instead the round is a dataflow over work items, each a path segment of up to
+// kSegMax nodes (api.cu: build_segments).  A ticket counter hands the items out in an order in
+// which every item depends only on earlier ones; an item waits (bounded) on per-node epoch
+// flags of the segments it depends on, so a CTA holding a ticket never waits on a later one
+// and all CTAs are resident (grid = occupancy): no deadlock.  Inside a segment the recursion's
+// vector stays in shared memory.
+//
+// Data movement.  The node matrices are independent of the solve, so one producer warp per
+// CTA streams the matrices of its items with cp.async.bulk (TMA bulk copies) into a ring of
+// shared-memory slots, running ahead of the eight consumer warps by up to the ring depth; the
+// consumers read the slots (backward: axpy form, warps over rows, lanes over 16-byte column
+// groups; forward: dot form, one warp per row, shuffle reduction) and release them through
+// mbarriers.  Every wait is bounded: on expiry the kernel raises an error flag, stops waiting
+// and runs to its end, and the host reports STO_ERR_TIMEOUT.
+#include <cstdint>
+
 #include "internal.h"
 
 namespace sto {
 namespace {
+
+constexpr int kCW = 8;               // consumer warps
+constexpr int kThreadsT = (kCW + 1) * 32;
+constexpr int kSlots = 4;            // ring depth
+constexpr int kChunk = 16384;        // bytes per ring slot
+constexpr unsigned long long kWaitNs = 1500000000ull;  // bounded waits: 1.5 s of wall time
+
+enum : int { KIND_END = 0, KIND_BG = 1, KIND_BR = 2, KIND_BK = 3, KIND_FG = 4, KIND_FK = 5 };
+enum : int {
+    F_FIRST = 1,        // first chunk of this (kind, node) run
+    F_LAST = 2,         // last chunk of this run
+    F_FIRST_CHILD = 4,  // backward G: first child of the parent
+    F_INSEG = 8,        // the child (backward) / parent (forward) is the previous node of the segment
+    F_END_NODE = 16,    // last chunk of the node's step
+    F_END_ITEM = 32,    // last chunk of the work item (segment)
+    F_ROOT = 64         // forward root step
+};
+
+struct Meta {
+    int kind, node, aux, row0, nrows, flags, pad0, pad1;
+};
 
 template <class T>
 struct V16;
@@ -49,14 +85,14 @@ __device__ __forceinline__ void v_fma<double>(double s, const double2 &g, double
 }
 
 template <class T>
-__device__ __forceinline__ T v_dot(const typename V16<T>::type &g, const T *x);
+__device__ __forceinline__ T v_dot(const typename V16<T>::type &g, const typename V16<T>::type &x);
 template <>
-__device__ __forceinline__ float v_dot<float>(const float4 &g, const float *x) {
-    return fmaf(g.x, x[0], fmaf(g.y, x[1], fmaf(g.z, x[2], g.w * x[3])));
+__device__ __forceinline__ float v_dot<float>(const float4 &g, const float4 &x) {
+    return fmaf(g.x, x.x, fmaf(g.y, x.y, fmaf(g.z, x.z, g.w * x.w)));
 }
 template <>
-__device__ __forceinline__ double v_dot<double>(const double2 &g, const double *x) {
-    return fma(g.x, x[0], g.y * x[1]);
+__device__ __forceinline__ double v_dot<double>(const double2 &g, const double2 &x) {
+    return fma(g.x, x.x, g.y * x.y);
 }
 
 template <class T>
@@ -66,268 +102,600 @@ __device__ __forceinline__ T warp_sum(T v) {
     return v;
 }
 
+// ---- PTX: mbarrier, bulk copy, flags ------------------------------------------------------
+__device__ __forceinline__ unsigned sm_addr(const void *p) { return (unsigned)__cvta_generic_to_shared(p); }
+
+__device__ __forceinline__ void mbar_init(uint64_t *b, unsigned count) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(sm_addr(b)), "r"(count) : "memory");
+}
+__device__ __forceinline__ void mbar_expect_tx(uint64_t *b, unsigned bytes) {
+    asm volatile("{ .reg .b64 st; mbarrier.arrive.expect_tx.shared::cta.b64 st, [%0], %1; }" ::"r"(sm_addr(b)),
+                 "r"(bytes)
+                 : "memory");
+}
+__device__ __forceinline__ void mbar_arrive(uint64_t *b) {
+    asm volatile("{ .reg .b64 st; mbarrier.arrive.shared::cta.b64 st, [%0]; }" ::"r"(sm_addr(b)) : "memory");
+}
+__device__ __forceinline__ bool mbar_try(uint64_t *b, unsigned parity) {
+    unsigned ok;
+    asm volatile(
+        "{ .reg .pred p; mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2; selp.u32 %0, 1, 0, p; }"
+        : "=r"(ok)
+        : "r"(sm_addr(b)), "r"(parity)
+        : "memory");
+    return ok != 0;
+}
+__device__ __forceinline__ unsigned long long now_ns() {
+    unsigned long long t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return t;
+}
+// Bounded wait for a phase; on expiry the error flag is raised and the wait gives up.
+__device__ __forceinline__ bool mbar_wait(uint64_t *b, unsigned parity, int *err) {
+    if (mbar_try(b, parity)) return true;
+    const unsigned long long t0 = now_ns();
+    for (;;) {
+        for (int it = 0; it < 64; ++it)
+            if (mbar_try(b, parity)) return true;
+        if (now_ns() - t0 > kWaitNs) break;
+    }
+    atomicExch(err, 2);
+    return false;
+}
+__device__ __forceinline__ void bulk_load(void *dst, const void *src, unsigned bytes, uint64_t *bar) {
+    asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+                     sm_addr(dst)),
+                 "l"(src), "r"(bytes), "r"(sm_addr(bar))
+                 : "memory");
+}
+__device__ __forceinline__ unsigned ld_acquire(const unsigned *p) {
+    unsigned v;
+    asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+    return v;
+}
+__device__ __forceinline__ void st_release(unsigned *p, unsigned v) {
+    asm volatile("st.release.gpu.global.u32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
+}
+// Bounded wait until *f == epoch.  Gives up at once when the error flag is already raised.
+__device__ __forceinline__ void wait_flag(const unsigned *f, unsigned epoch, int *err) {
+    if (ld_acquire(f) == epoch) return;
+    const unsigned long long t0 = now_ns();
+    for (;;) {
+        for (int it = 0; it < 32; ++it) {
+            if (ld_acquire(f) == epoch) return;
+            __nanosleep(32);
+        }
+        if (*(volatile int *)err) return;
+        if (now_ns() - t0 > kWaitNs) break;
+    }
+    atomicExch(err, 1);
+}
+__device__ __forceinline__ void cbar() { asm volatile("bar.sync 1, %0;" ::"n"(kCW * 32) : "memory"); }
+
 template <class T>
-struct SolveArgs {
-    int nx, nu, ldg, ldk, ldr, Np, nxu;
+struct TreeArgs {
+    int nx, nu, ldg, ldk, ldr, Np, Nn, nxu;
+    int Tb, Tf;
+    const int *bstart, *bnodes, *fstart, *fnodes;
+    const int *cbeg, *ccnt, *parent;
     const T *G, *K, *Ri, *gu, *gx, *c, *sqp, *pN;
     const double *prob;
-    const int *cbeg, *ccnt, *parent;
     const T *y[kMaxRhs];
     T *h[kMaxRhs];
     const T *x0;
     T *s, *ubar, *xs, *us;  // scratch, [kMaxRhs][Nn][nx] and [kMaxRhs][Np][nu]
     long long s_stride, u_stride;
+    unsigned *flags;        // [2][Nn]
+    unsigned long long *ticket;
+    int *err;
     int homog, scaled;
+    int rpcG, rpcR, rpcK;   // rows per ring slot
 };
 
 __device__ __forceinline__ long long dual_off(int i, int Np, int nxu, int nx) {
     return i < Np ? (long long)i * nxu : (long long)Np * nxu + (long long)(i - Np) * nx;
 }
 
-constexpr int kWarps = 8;
+// ---- producer ----------------------------------------------------------------------------
+template <class T>
+struct Producer {
+    const TreeArgs<T> &a;
+    unsigned char *ring;
+    Meta *meta;
+    uint64_t *full, *empty;
+    unsigned long long n = 0;
 
-// Backward pass over one stage: one CTA per parent node.
-template <class T, int NR, int KV>
-__global__ void __launch_bounds__(256) k_bwd(SolveArgs<T> a, int first) {
-    using VT = typename V16<T>::type;
-    constexpr int VN = V16<T>::n;
-    extern __shared__ __align__(16) unsigned char smem_raw[];
-    T *sm = reinterpret_cast<T *>(smem_raw);
-    const int nx = a.nx, nu = a.nu, ldg = a.ldg;
-    T *s_in = sm;                              // [NR][nx]
-    T *part = s_in + NR * nx;                  // [kWarps][NR][ldg]
-    T *accs = part + kWarps * NR * ldg;        // [NR][ldg]
-    T *v = accs + NR * ldg;                    // [NR][nu]
-    const int i = first + blockIdx.x;
-    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const int nvec = ldg / VN;
-    const T sci = a.scaled ? a.sqp[i] : T(1);
+    __device__ Producer(const TreeArgs<T> &a_, unsigned char *r, Meta *m, uint64_t *f, uint64_t *e)
+        : a(a_), ring(r), meta(m), full(f), empty(e) {}
 
-    T acc[NR][KV][VN];
-#pragma unroll
-    for (int k = 0; k < NR; ++k)
-#pragma unroll
-        for (int q = 0; q < KV; ++q)
-#pragma unroll
-            for (int e = 0; e < VN; ++e) acc[k][q][e] = T(0);
+    // false when a slot never came free (the error flag is then raised): stop issuing copies
+    __device__ bool slot_acquire(int &slot) {
+        slot = (int)(n % kSlots);
+        const unsigned long long round = n / kSlots;
+        if (round > 0) return mbar_wait(&empty[slot], (unsigned)((round - 1) & 1), a.err);
+        return true;
+    }
+    bool dead = false;
+    __device__ void emit(int kind, int node, int aux, int row0, int nrows, int flags, const T *src, int ld) {
+        int slot;
+        if (dead || !slot_acquire(slot)) {
+            dead = true;
+            return;
+        }
+        Meta md;
+        md.kind = kind;
+        md.node = node;
+        md.aux = aux;
+        md.row0 = row0;
+        md.nrows = nrows;
+        md.flags = flags;
+        md.pad0 = md.pad1 = 0;
+        meta[slot] = md;
+        const unsigned bytes = (unsigned)(nrows * ld * sizeof(T));
+        mbar_expect_tx(&full[slot], bytes);
+        bulk_load(ring + (size_t)slot * kChunk, src + (size_t)row0 * ld, bytes, &full[slot]);
+        ++n;
+    }
+    __device__ void emit_end() {
+        int slot;
+        if (dead || !slot_acquire(slot)) return;
+        Meta md = {KIND_END, -1, -1, 0, 0, 0, 0, 0};
+        meta[slot] = md;
+        mbar_arrive(&full[slot]);
+        ++n;
+    }
+    // the chunks of one matrix: rows [0, rows) in runs of rpc rows
+    __device__ void matrix(int kind, int node, int aux, const T *base, int rows, int ld, int rpc, int flags_first,
+                           int flags_last) {
+        for (int r0 = 0; r0 < rows; r0 += rpc) {
+            const int nr = min(rpc, rows - r0);
+            int f = 0;
+            if (r0 == 0) f |= F_FIRST | flags_first;
+            if (r0 + nr == rows) f |= F_LAST | flags_last;
+            emit(kind, node, aux, r0, nr, f, base);
+        }
+    }
+    __device__ void emit(int kind, int node, int aux, int row0, int nrows, int flags, const T *base) {
+        const int ld = kind == KIND_BR ? a.ldr : ((kind == KIND_BK || kind == KIND_FK) ? a.ldk : a.ldg);
+        emit(kind, node, aux, row0, nrows, flags, base, ld);
+    }
 
-    const int jb = a.cbeg[i], je = jb + a.ccnt[i];
-    for (int j = jb; j < je; ++j) {
-        if (j >= a.Np) {  // leaf: s^l = y^l / 2 + pi^l p_N / 2
-            const long long o = dual_off(j, a.Np, a.nxu, nx);
-            const T scj = a.scaled ? a.sqp[j] : T(1);
-            const T cj = a.homog ? T(0) : T(0.5 * a.prob[j]);
-            for (int e = threadIdx.x; e < NR * nx; e += blockDim.x) {
-                const int k = e / nx, r = e - k * nx;
-                s_in[e] = T(0.5) * scj * a.y[k][o + r] + cj * a.pN[r];
-            }
-        } else {
-            for (int e = threadIdx.x; e < NR * nx; e += blockDim.x) {
-                const int k = e / nx, r = e - k * nx;
-                s_in[e] = a.s[k * a.s_stride + (long long)j * nx + r];
+    __device__ void run(unsigned long long tbase) {
+        const int nx = a.nx, nu = a.nu;
+        const int total = a.Tb + a.Tf;
+        for (;;) {
+            if (dead) return;
+            const unsigned long long tk = atomicAdd(a.ticket, 1ull) - tbase;
+            if (tk >= (unsigned long long)total) break;
+            const int item = (int)tk;
+            if (item < a.Tb) {
+                const int b0 = a.bstart[item], b1 = a.bstart[item + 1];
+                for (int k = b0; k < b1; ++k) {
+                    const int i = a.bnodes[k];
+                    const bool last_node = k == b1 - 1;
+                    const int jb = k == b0 ? a.cbeg[i] : a.bnodes[k - 1];
+                    const int je = k == b0 ? a.cbeg[i] + a.ccnt[i] : jb + 1;
+                    for (int j = jb; j < je; ++j) {
+                        int ff = (j == jb ? F_FIRST_CHILD : 0) | (k > b0 ? F_INSEG : 0);
+                        matrix(KIND_BG, j, i, a.G + (size_t)j * nx * a.ldg, nx, a.ldg, a.rpcG, ff, 0);
+                    }
+                    matrix(KIND_BR, i, -1, a.Ri + (size_t)i * nu * a.ldr, nu, a.ldr, a.rpcR, 0, 0);
+                    matrix(KIND_BK, i, -1, a.K + (size_t)i * nu * a.ldk, nu, a.ldk, a.rpcK, 0,
+                           F_END_NODE | (last_node ? F_END_ITEM : 0));
+                }
+            } else {
+                const int it = item - a.Tb;
+                const int f0 = a.fstart[it], f1 = a.fstart[it + 1];
+                for (int k = f0; k < f1; ++k) {
+                    const int j = a.fnodes[k];
+                    const bool last_node = k == f1 - 1;
+                    const int endf = F_END_NODE | (last_node ? F_END_ITEM : 0);
+                    const bool nonleaf = j < a.Np;
+                    if (j != 0)
+                        matrix(KIND_FG, j, -1, a.G + (size_t)j * nx * a.ldg, nx, a.ldg, a.rpcG, k > f0 ? F_INSEG : 0,
+                               nonleaf ? 0 : endf);
+                    if (nonleaf)
+                        matrix(KIND_FK, j, -1, a.K + (size_t)j * nu * a.ldk, nu, a.ldk, a.rpcK, j == 0 ? F_ROOT : 0,
+                               endf);
+                }
             }
         }
-        __syncthreads();
-        const VT *Gj = reinterpret_cast<const VT *>(a.G + (size_t)j * nx * ldg);
-        for (int r = warp; r < nx; r += kWarps) {
-            T sr[NR];
+        emit_end();
+    }
+};
+
+// ---- consumers ---------------------------------------------------------------------------
+template <class T, int NR, int KV>
+struct Consumer {
+    using VT = typename V16<T>::type;
+    static constexpr int VN = V16<T>::n;
+    const TreeArgs<T> &a;
+    unsigned char *ring;
+    const Meta *meta;
+    uint64_t *full, *empty;
+    unsigned epoch;
+    int warp, lane, tid;
+    int *abort_flag;  // shared
+    // shared vectors
+    T *s_in, *s_out, *part, *accs, *v, *xu, *xj, *uj;
+    T acc[NR][KV][VN];
+
+    __device__ void zero_acc() {
 #pragma unroll
-            for (int k = 0; k < NR; ++k) sr[k] = s_in[k * nx + r];
-            const VT *row = Gj + (size_t)r * nvec;
+        for (int k = 0; k < NR; ++k)
+#pragma unroll
+            for (int q = 0; q < KV; ++q)
+#pragma unroll
+                for (int e = 0; e < VN; ++e) acc[k][q][e] = T(0);
+    }
+    // part[warp] <- acc over the first `width` columns; cbar; dst[k][c] = sum_w part[w][k][c]
+    __device__ void reduce_acc(int width, T *dst, int dst_stride) {
+        const int nvec = width / VN;
+#pragma unroll
+        for (int k = 0; k < NR; ++k)
+#pragma unroll
+            for (int q = 0; q < KV; ++q) {
+                const int cv = lane + 32 * q;
+                if (cv < nvec)
+                    *reinterpret_cast<VT *>(part + ((size_t)warp * NR + k) * a.ldg + cv * VN) =
+                        *reinterpret_cast<const VT *>(acc[k][q]);
+            }
+        cbar();
+        for (int e = tid; e < NR * width; e += kCW * 32) {
+            const int k = e / width, c = e - k * width;
+            T sum = T(0);
+#pragma unroll
+            for (int w = 0; w < kCW; ++w) sum += part[((size_t)w * NR + k) * a.ldg + c];
+            dst[k * dst_stride + c] = sum;
+        }
+        cbar();
+    }
+    // acc[k] += coef[k][row0 + r] * M[r][:] over the rows of the slot
+    __device__ void axpy_rows(const T *M, int ld, int nrows, const T *coef, int cstride, int row0) {
+        const int nvec = ld / VN;
+        for (int r = warp; r < nrows; r += kCW) {
+            T cr[NR];
+#pragma unroll
+            for (int k = 0; k < NR; ++k) cr[k] = coef[k * cstride + row0 + r];
+            const VT *row = reinterpret_cast<const VT *>(M + (size_t)r * ld);
 #pragma unroll
             for (int q = 0; q < KV; ++q) {
                 const int cv = lane + 32 * q;
                 if (cv < nvec) {
-                    const VT g = __ldg(row + cv);
+                    const VT g = row[cv];
 #pragma unroll
-                    for (int k = 0; k < NR; ++k) v_fma<T>(sr[k], g, acc[k][q]);
+                    for (int k = 0; k < NR; ++k) v_fma<T>(cr[k], g, acc[k][q]);
                 }
             }
         }
-        __syncthreads();
     }
-    // cross-warp reduction of the column sums
+    // out[k][row0 + r] = M[r] . x[k] + add[row0 + r]   (add may be null)
+    __device__ void dot_rows(const T *M, int ld, int nrows, const T *x, int xstride, T *out, int ostride, int row0,
+                             const T *add, long long add_kstride) {
+        const int nvec = ld / VN;
+        for (int r = warp; r < nrows; r += kCW) {
+            const VT *row = reinterpret_cast<const VT *>(M + (size_t)r * ld);
+            T sum[NR];
 #pragma unroll
-    for (int k = 0; k < NR; ++k)
+            for (int k = 0; k < NR; ++k) sum[k] = T(0);
+            for (int cv = lane; cv < nvec; cv += 32) {
+                const VT g = row[cv];
 #pragma unroll
-        for (int q = 0; q < KV; ++q) {
-            const int cv = lane + 32 * q;
-            if (cv < nvec) {
+                for (int k = 0; k < NR; ++k)
+                    sum[k] += v_dot<T>(g, *reinterpret_cast<const VT *>(x + k * xstride + cv * VN));
+            }
 #pragma unroll
-                for (int e = 0; e < VN; ++e) part[(warp * NR + k) * ldg + cv * VN + e] = acc[k][q][e];
+            for (int k = 0; k < NR; ++k) {
+                const T tot = warp_sum(sum[k]);
+                if (lane == 0)
+                    out[k * ostride + row0 + r] = tot + (add ? __ldcg(add + k * add_kstride + row0 + r) : T(0));
             }
         }
-    __syncthreads();
-    for (int e = threadIdx.x; e < NR * ldg; e += blockDim.x) {
-        const int k = e / ldg, c = e - k * ldg;
-        T sum = T(0);
-#pragma unroll
-        for (int w = 0; w < kWarps; ++w) sum += part[(w * NR + k) * ldg + c];
-        accs[e] = sum;
     }
-    __syncthreads();
-    const long long oi = (long long)i * a.nxu;
-    for (int e = threadIdx.x; e < NR * nu; e += blockDim.x) {
-        const int k = e / nu, c = e - k * nu;
-        v[e] = T(0.5) * sci * a.y[k][oi + nx + c] + accs[k * ldg + nx + c] +
-               (a.homog ? T(0) : a.gu[(size_t)i * nu + c]);
-    }
-    __syncthreads();
-    // ubar = -Rbar^-1 v (Ri holds -Rbar^-1, symmetric) and s = y_x/2 + A's + K'v + gx
-    const T *Ri = a.Ri + (size_t)i * nu * a.ldr;
-    const T *Ki = a.K + (size_t)i * nu * a.ldk;
-    for (int e = threadIdx.x; e < NR * (nu + nx); e += blockDim.x) {
-        const int k = e / (nu + nx), c = e - k * (nu + nx);
-        const T *vk = v + k * nu;
-        if (c < nu) {
-            T sum = T(0);
-            for (int r = 0; r < nu; ++r) sum += vk[r] * Ri[(size_t)r * a.ldr + c];
-            a.ubar[k * a.u_stride + (long long)i * nu + c] = sum;
-        } else {
-            const int cx = c - nu;
-            T sum = T(0);
-            for (int r = 0; r < nu; ++r) sum += vk[r] * Ki[(size_t)r * a.ldk + cx];
-            a.s[k * a.s_stride + (long long)i * nx + cx] = T(0.5) * sci * a.y[k][oi + cx] + accs[k * ldg + cx] + sum +
-                                                           (a.homog ? T(0) : a.gx[(size_t)i * nx + cx]);
+
+    __device__ void run() {
+        const int nx = a.nx, nu = a.nu;
+        unsigned long long n = 0;
+        zero_acc();
+        for (;;) {
+            const int slot = (int)(n % kSlots);
+            // a copy that never lands leaves nothing sensible to do: every consumer warp leaves
+            // the loop together (the decision is shared before anyone can reach a named barrier)
+            if (!mbar_wait(&full[slot], (unsigned)((n / kSlots) & 1), a.err)) *abort_flag = 1;
+            cbar();
+            if (*(volatile int *)abort_flag) break;
+            const Meta md = meta[slot];
+            if (md.kind == KIND_END) break;
+            const T *M = reinterpret_cast<const T *>(ring + (size_t)slot * kChunk);
+            const int f = md.flags;
+            if (md.kind == KIND_BG) {
+                // child md.node of parent md.aux: s of the child into s_in
+                if (f & F_FIRST) {
+                    const int j = md.node;
+                    cbar();  // every warp is done with the previous s_in
+                    if (f & F_FIRST_CHILD) zero_acc();
+                    if (f & F_INSEG) {
+                        for (int e = tid; e < NR * nx; e += kCW * 32) s_in[e] = s_out[e];
+                    } else if (j >= a.Np) {
+                        const long long o = dual_off(j, a.Np, a.nxu, nx);
+                        const T scj = a.scaled ? a.sqp[j] : T(1);
+                        const T cj = a.homog ? T(0) : T(0.5 * a.prob[j]);
+                        for (int e = tid; e < NR * nx; e += kCW * 32) {
+                            const int k = e / nx, r = e - k * nx;
+                            s_in[e] = T(0.5) * scj * a.y[k][o + r] + cj * a.pN[r];
+                        }
+                    } else {
+                        if (tid == 0) wait_flag(a.flags + j, epoch, a.err);
+                        cbar();
+                        for (int e = tid; e < NR * nx; e += kCW * 32) {
+                            const int k = e / nx, r = e - k * nx;
+                            s_in[e] = __ldcg(a.s + k * a.s_stride + (long long)j * nx + r);
+                        }
+                    }
+                    cbar();
+                }
+                axpy_rows(M, a.ldg, md.nrows, s_in, nx, md.row0);
+                __syncwarp();
+                if (lane == 0) mbar_arrive(&empty[slot]);
+            } else if (md.kind == KIND_BR) {
+                const int i = md.node;
+                if (f & F_FIRST) {
+                    // all children done: accs = sum over warps, v = y_u/2 + acc_B + gu
+                    reduce_acc(a.ldg, accs, a.ldg);
+                    const long long oi = (long long)i * a.nxu;
+                    const T sci = a.scaled ? a.sqp[i] : T(1);
+                    for (int e = tid; e < NR * nu; e += kCW * 32) {
+                        const int k = e / nu, cc = e - k * nu;
+                        v[e] = T(0.5) * sci * a.y[k][oi + nx + cc] + accs[k * a.ldg + nx + cc] +
+                               (a.homog ? T(0) : a.gu[(size_t)i * nu + cc]);
+                    }
+                    zero_acc();
+                    cbar();
+                }
+                axpy_rows(M, a.ldr, md.nrows, v, nu, md.row0);
+                __syncwarp();
+                if (lane == 0) mbar_arrive(&empty[slot]);
+                if (f & F_LAST) {
+                    // ubar = -Rbar^-1 v (Ri is symmetric, stored negated)
+                    reduce_acc(a.ldr, xu, a.ldr);  // xu is free during the backward pass
+                    for (int e = tid; e < NR * nu; e += kCW * 32) {
+                        const int k = e / nu, cc = e - k * nu;
+                        a.ubar[k * a.u_stride + (long long)i * nu + cc] = xu[k * a.ldr + cc];
+                    }
+                    zero_acc();
+                }
+            } else if (md.kind == KIND_BK) {
+                const int i = md.node;
+                axpy_rows(M, a.ldk, md.nrows, v, nu, md.row0);
+                __syncwarp();
+                if (lane == 0) mbar_arrive(&empty[slot]);
+                if (f & F_LAST) {
+                    // s^i = y_x/2 + acc_A + K'v + gx
+                    reduce_acc(a.ldk, xj, a.ldk);
+                    const long long oi = (long long)i * a.nxu;
+                    const T sci = a.scaled ? a.sqp[i] : T(1);
+                    for (int e = tid; e < NR * nx; e += kCW * 32) {
+                        const int k = e / nx, cc = e - k * nx;
+                        const T val = T(0.5) * sci * a.y[k][oi + cc] + accs[k * a.ldg + cc] + xj[k * a.ldk + cc] +
+                                      (a.homog ? T(0) : a.gx[(size_t)i * nx + cc]);
+                        s_out[e] = val;
+                        if (f & F_END_ITEM) a.s[k * a.s_stride + (long long)i * nx + cc] = val;
+                    }
+                    zero_acc();
+                    cbar();
+                    if ((f & F_END_ITEM) && tid == 0) {
+                        __threadfence();
+                        st_release(a.flags + i, epoch);
+                    }
+                }
+            } else if (md.kind == KIND_FG) {
+                const int j = md.node;
+                if (f & F_FIRST) {
+                    cbar();  // every warp is done with the previous xu / xj
+                    if (f & F_INSEG) {
+                        // parent = previous node of the segment: [x; u] from xj, uj
+                        for (int e = tid; e < NR * a.ldg; e += kCW * 32) {
+                            const int k = e / a.ldg, cc = e - k * a.ldg;
+                            xu[e] = cc < nx ? xj[k * a.ldk + cc] : (cc < nx + nu ? uj[k * nu + cc - nx] : T(0));
+                        }
+                    } else {
+                        const int i = a.parent[j];
+                        if (tid == 0) wait_flag(a.flags + a.Nn + i, epoch, a.err);
+                        cbar();
+                        for (int e = tid; e < NR * a.ldg; e += kCW * 32) {
+                            const int k = e / a.ldg, cc = e - k * a.ldg;
+                            T val = T(0);
+                            if (cc < nx)
+                                val = __ldcg(a.xs + k * a.s_stride + (long long)i * nx + cc);
+                            else if (cc < nx + nu)
+                                val = __ldcg(a.us + k * a.u_stride + (long long)i * nu + cc - nx);
+                            xu[e] = val;
+                        }
+                    }
+                    cbar();
+                }
+                dot_rows(M, a.ldg, md.nrows, xu, a.ldg, xj, a.ldk, md.row0,
+                         a.homog ? nullptr : a.c + (size_t)j * nx, 0);
+                __syncwarp();
+                if (lane == 0) mbar_arrive(&empty[slot]);
+                if (f & F_END_NODE) {  // leaf: no K step
+                    cbar();
+                    const long long oj = dual_off(j, a.Np, a.nxu, nx);
+                    const T scj = a.scaled ? a.sqp[j] : T(1);
+                    for (int e = tid; e < NR * nx; e += kCW * 32) {
+                        const int k = e / nx, r = e - k * nx;
+                        const T val = xj[k * a.ldk + r];
+                        a.h[k][oj + r] = scj * val;
+                        a.xs[k * a.s_stride + (long long)j * nx + r] = val;
+                    }
+                }
+            } else if (md.kind == KIND_FK) {
+                const int j = md.node;
+                if (f & F_FIRST) {
+                    if (f & F_ROOT) {
+                        if (tid == 0) wait_flag(a.flags + 0, epoch, a.err);  // backward pass finished
+                        cbar();
+                        for (int e = tid; e < NR * a.ldk; e += kCW * 32) {
+                            const int r = e % a.ldk;
+                            xj[e] = (r < nx && !a.homog) ? a.x0[r] : T(0);
+                        }
+                    } else {
+                        // zero the padding of x^j so the dot form may read whole 16-byte groups
+                        for (int e = tid; e < NR * (a.ldk - nx); e += kCW * 32) {
+                            const int k = e / (a.ldk - nx), r = nx + e % (a.ldk - nx);
+                            xj[k * a.ldk + r] = T(0);
+                        }
+                    }
+                    cbar();
+                }
+                dot_rows(M, a.ldk, md.nrows, xj, a.ldk, uj, nu, md.row0, a.ubar + (long long)j * nu, a.u_stride);
+                __syncwarp();
+                if (lane == 0) mbar_arrive(&empty[slot]);
+                if (f & F_LAST) {
+                    cbar();
+                    const long long oj = dual_off(j, a.Np, a.nxu, nx);
+                    const T scj = a.scaled ? a.sqp[j] : T(1);
+                    for (int e = tid; e < NR * (nx + nu); e += kCW * 32) {
+                        const int k = e / (nx + nu), r = e - k * (nx + nu);
+                        const T val = r < nx ? xj[k * a.ldk + r] : uj[k * nu + r - nx];
+                        a.h[k][oj + r] = scj * val;
+                        if (r < nx)
+                            a.xs[k * a.s_stride + (long long)j * nx + r] = val;
+                        else
+                            a.us[k * a.u_stride + (long long)j * nu + r - nx] = val;
+                    }
+                    cbar();
+                    if ((f & F_END_ITEM) && tid == 0) {
+                        __threadfence();
+                        st_release(a.flags + a.Nn + j, epoch);
+                    }
+                }
+            }
+            ++n;
         }
     }
+};
+
+template <class T, int NR, int KV>
+__global__ void __launch_bounds__(kThreadsT, 2) k_tree(TreeArgs<T> a, unsigned epoch, unsigned long long tbase) {
+    extern __shared__ __align__(1024) unsigned char smem[];
+    __shared__ int abort_flag;
+    unsigned char *ring = smem;
+    Meta *meta = reinterpret_cast<Meta *>(smem + kSlots * kChunk);
+    uint64_t *full = reinterpret_cast<uint64_t *>(meta + kSlots);
+    uint64_t *empty = full + kSlots;
+    T *vec = reinterpret_cast<T *>(empty + kSlots);
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    if (threadIdx.x == 0) {
+        abort_flag = 0;
+        for (int s = 0; s < kSlots; ++s) {
+            mbar_init(&full[s], 1);
+            mbar_init(&empty[s], kCW);
+        }
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    __syncthreads();
+    if (warp == kCW) {
+        if (lane == 0) {
+            Producer<T> p(a, ring, meta, full, empty);
+            p.run(tbase);
+        }
+        return;
+    }
+    Consumer<T, NR, KV> c{a, ring, meta, full, empty, epoch, warp, lane, (int)threadIdx.x, &abort_flag};
+    const int nx = a.nx, nu = a.nu;
+    // shared vectors (offsets multiple of 16 bytes: every width is padded to a 16-byte multiple)
+    T *p = vec;
+    c.s_in = p;
+    p += NR * a.ldk;
+    c.s_out = p;
+    p += NR * a.ldk;
+    c.part = p;
+    p += kCW * NR * a.ldg;
+    c.accs = p;
+    p += NR * a.ldg;
+    c.v = p;
+    p += NR * a.ldr;
+    c.xu = p;
+    p += NR * a.ldg;
+    c.xj = p;
+    p += NR * a.ldk;
+    c.uj = p;
+    (void)nx;
+    (void)nu;
+    c.run();
 }
 
-// Forward pass over one stage: one CTA per node (the root when first == 0).
-template <class T, int NR>
-__global__ void __launch_bounds__(256) k_fwd(SolveArgs<T> a, int first) {
-    using VT = typename V16<T>::type;
-    constexpr int VN = V16<T>::n;
-    extern __shared__ __align__(16) unsigned char smem_raw[];
-    T *sm = reinterpret_cast<T *>(smem_raw);
-    const int nx = a.nx, nu = a.nu, ldg = a.ldg, ldk = a.ldk;
-    T *xu = sm;                 // [NR][ldg]
-    T *xj = xu + NR * ldg;      // [NR][ldk]
-    const int j = first + blockIdx.x;
-    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const T scj = a.scaled ? a.sqp[j] : T(1);
-    if (j == 0) {
-        for (int e = threadIdx.x; e < NR * ldk; e += blockDim.x) {
-            const int k = e / ldk, r = e - k * ldk;
-            xj[e] = (r < nx && !a.homog) ? a.x0[r] : T(0);
-        }
-        __syncthreads();
-    } else {
-        const int i = a.parent[j];
-        for (int e = threadIdx.x; e < NR * ldg; e += blockDim.x) {
-            const int k = e / ldg, c = e - k * ldg;
-            T v = T(0);
-            if (c < nx)
-                v = a.xs[k * a.s_stride + (long long)i * nx + c];
-            else if (c < nx + nu)
-                v = a.us[k * a.u_stride + (long long)i * nu + (c - nx)];
-            xu[e] = v;
-        }
-        for (int e = threadIdx.x; e < NR * ldk; e += blockDim.x) xj[e] = T(0);
-        __syncthreads();
-        const int nvec = ldg / VN;
-        const VT *Gj = reinterpret_cast<const VT *>(a.G + (size_t)j * nx * ldg);
-        for (int r = warp; r < nx; r += kWarps) {
-            const VT *row = Gj + (size_t)r * nvec;
-            T sum[NR];
-#pragma unroll
-            for (int k = 0; k < NR; ++k) sum[k] = T(0);
-            for (int cv = lane; cv < nvec; cv += 32) {
-                const VT g = __ldg(row + cv);
-#pragma unroll
-                for (int k = 0; k < NR; ++k) sum[k] += v_dot<T>(g, xu + k * ldg + cv * VN);
-            }
-#pragma unroll
-            for (int k = 0; k < NR; ++k) {
-                const T tot = warp_sum(sum[k]);
-                if (lane == 0) xj[k * ldk + r] = tot + (a.homog ? T(0) : a.c[(size_t)j * nx + r]);
-            }
-        }
-        __syncthreads();
-    }
-    const long long oj = dual_off(j, a.Np, a.nxu, nx);
-    for (int e = threadIdx.x; e < NR * nx; e += blockDim.x) {
-        const int k = e / nx, r = e - k * nx;
-        const T val = xj[k * ldk + r];
-        a.xs[k * a.s_stride + (long long)j * nx + r] = val;
-        a.h[k][oj + r] = scj * val;
-    }
-    if (j < a.Np) {
-        const int nvec = ldk / VN;
-        const VT *Kj = reinterpret_cast<const VT *>(a.K + (size_t)j * nu * ldk);
-        for (int r = warp; r < nu; r += kWarps) {
-            const VT *row = Kj + (size_t)r * nvec;
-            T sum[NR];
-#pragma unroll
-            for (int k = 0; k < NR; ++k) sum[k] = T(0);
-            for (int cv = lane; cv < nvec; cv += 32) {
-                const VT g = __ldg(row + cv);
-#pragma unroll
-                for (int k = 0; k < NR; ++k) sum[k] += v_dot<T>(g, xj + k * ldk + cv * VN);
-            }
-#pragma unroll
-            for (int k = 0; k < NR; ++k) {
-                const T tot = warp_sum(sum[k]);
-                if (lane == 0) {
-                    const T uval = tot + a.ubar[k * a.u_stride + (long long)j * nu + r];
-                    a.us[k * a.u_stride + (long long)j * nu + r] = uval;
-                    a.h[k][oj + nx + r] = scj * uval;
-                }
-            }
-        }
-    }
+size_t tree_smem(int NR, int ldg, int ldk, int ldr, size_t esz) {
+    const size_t vec = (size_t)NR * (3 * ldk + (kCW + 2) * ldg + ldr) + (size_t)NR * ldr;
+    return (size_t)kSlots * kChunk + kSlots * sizeof(Meta) + 2 * kSlots * sizeof(uint64_t) + vec * esz;
 }
 
 template <class T, int NR, int KV>
-void launch_bwd(const SolveArgs<T> &a, int first, int count, cudaStream_t st) {
-    const size_t smem = sizeof(T) * ((size_t)NR * a.nx + (size_t)kWarps * NR * a.ldg + (size_t)NR * a.ldg + (size_t)NR * a.nu);
-    if (smem > 48 * 1024) cudaFuncSetAttribute(k_bwd<T, NR, KV>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    k_bwd<T, NR, KV><<<count, 256, smem, st>>>(a, first);
+void launch_tree(stotree_t h, const TreeArgs<T> &a, unsigned epoch, unsigned long long tbase, int grid,
+                 cudaStream_t st) {
+    const size_t smem = tree_smem(NR, a.ldg, a.ldk, a.ldr, sizeof(T));
+    cudaFuncSetAttribute(k_tree<T, NR, KV>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    k_tree<T, NR, KV><<<grid, kThreadsT, smem, st>>>(a, epoch, tbase);
 }
 
 template <class T, int NR>
-void launch_bwd_kv(const SolveArgs<T> &a, int first, int count, cudaStream_t st) {
-    const int nvec = a.ldg / V16<T>::n;
-    const int kv = (nvec + 31) / 32;
+void launch_tree_kv(stotree_t h, const TreeArgs<T> &a, unsigned epoch, unsigned long long tbase, int grid,
+                    cudaStream_t st) {
+    const int kv = (a.ldg / V16<T>::n + 31) / 32;
     switch (kv) {
-        case 1: launch_bwd<T, NR, 1>(a, first, count, st); break;
-        case 2: launch_bwd<T, NR, 2>(a, first, count, st); break;
-        case 3: launch_bwd<T, NR, 3>(a, first, count, st); break;
-        default: launch_bwd<T, NR, 4>(a, first, count, st); break;
+        case 1: launch_tree<T, NR, 1>(h, a, epoch, tbase, grid, st); break;
+        case 2: launch_tree<T, NR, 2>(h, a, epoch, tbase, grid, st); break;
+        case 3: launch_tree<T, NR, 3>(h, a, epoch, tbase, grid, st); break;
+        default: launch_tree<T, NR, 4>(h, a, epoch, tbase, grid, st); break;
     }
 }
 
+// CTAs of the persistent kernel: every CTA must be resident at once (items wait on earlier ones).
 template <class T, int NR>
-void launch_fwd(const SolveArgs<T> &a, int first, int count, cudaStream_t st) {
-    const size_t smem = sizeof(T) * ((size_t)NR * a.ldg + (size_t)NR * a.ldk);
-    k_fwd<T, NR><<<count, 256, smem, st>>>(a, first);
-}
-
-template <class T, int NR>
-void run_round(stotree_t h, const SolveArgs<T> &a, cudaStream_t st) {
-    for (int t = h->N - 1; t >= 0; --t) {
-        const int first = h->soff[t], count = h->soff[t + 1] - first;
-        launch_bwd_kv<T, NR>(a, first, count, st);
+int tree_grid(const TreeArgs<T> &a) {
+    int dev = 0, sms = 0, per_sm = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    const size_t smem = tree_smem(NR, a.ldg, a.ldk, a.ldr, sizeof(T));
+    const int kv = (a.ldg / V16<T>::n + 31) / 32;
+    cudaError_t e;
+    switch (kv) {
+        case 1: cudaFuncSetAttribute(k_tree<T, NR, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+                e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_tree<T, NR, 1>, kThreadsT, smem); break;
+        case 2: cudaFuncSetAttribute(k_tree<T, NR, 2>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+                e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_tree<T, NR, 2>, kThreadsT, smem); break;
+        case 3: cudaFuncSetAttribute(k_tree<T, NR, 3>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+                e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_tree<T, NR, 3>, kThreadsT, smem); break;
+        default: cudaFuncSetAttribute(k_tree<T, NR, 4>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+                 e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_tree<T, NR, 4>, kThreadsT, smem); break;
     }
-    for (int t = 0; t <= h->N; ++t) {
-        const int first = h->soff[t], count = h->soff[t + 1] - first;
-        launch_fwd<T, NR>(a, first, count, st);
-    }
-    h->launches += 2 * h->N + 1;
+    if (e != cudaSuccess || per_sm < 1) return 0;
+    return sms * (per_sm < 2 ? per_sm : 2);
 }
 
 template <class T>
 sto_status solve_impl(stotree_t h, const void *const *y, const void *x0, void *const *hx, int nrhs, bool homog,
                       bool scaled, cudaStream_t st, const SolveScratch *scratch) {
     const Layout &L = h->L;
-    SolveArgs<T> a;
+    TreeArgs<T> a;
     a.nx = h->nx;
     a.nu = h->nu;
     a.ldg = h->ldg;
     a.ldk = h->ldk;
     a.ldr = h->ldr;
     a.Np = h->Np;
+    a.Nn = h->Nn;
     a.nxu = h->nx + h->nu;
+    a.Tb = (int)h->bstart.size() - 1;
+    a.Tf = (int)h->fstart.size() - 1;
+    a.bstart = h->at<int>(L.bstart);
+    a.bnodes = h->at<int>(L.bnodes);
+    a.fstart = h->at<int>(L.fstart);
+    a.fnodes = h->at<int>(L.fnodes);
+    a.cbeg = h->at<int>(L.cbeg);
+    a.ccnt = h->at<int>(L.ccnt);
+    a.parent = h->at<int>(L.parent);
     a.G = h->at<T>(L.G);
     a.K = h->at<T>(L.K);
     a.Ri = h->at<T>(L.Ri);
@@ -337,38 +705,71 @@ sto_status solve_impl(stotree_t h, const void *const *y, const void *x0, void *c
     a.sqp = h->at<T>(L.sqp);
     a.pN = h->at<T>(L.cost) + (2 * h->nx + h->nu) + h->nx + h->nu;  // ell = [q | r | pN]
     a.prob = h->at<double>(L.prob64);
-    a.cbeg = h->at<int>(L.cbeg);
-    a.ccnt = h->at<int>(L.ccnt);
-    a.parent = h->at<int>(L.parent);
     for (int k = 0; k < kMaxRhs; ++k) {
         a.y[k] = static_cast<const T *>(y[k < nrhs ? k : 0]);
         a.h[k] = static_cast<T *>(hx[k < nrhs ? k : 0]);
     }
     a.x0 = static_cast<const T *>(x0);
-    if (scratch) {  // caller-supplied scratch for one right-hand side
+    a.s_stride = (long long)h->Nn * h->nx;
+    a.u_stride = (long long)h->Np * h->nu;
+    a.homog = homog ? 1 : 0;
+    a.scaled = scaled ? 1 : 0;
+    a.rpcG = kChunk / (h->ldg * (int)sizeof(T));
+    a.rpcR = kChunk / (h->ldr * (int)sizeof(T));
+    a.rpcK = kChunk / (h->ldk * (int)sizeof(T));
+    a.err = h->at<int>(L.fstatus) + 8;
+    unsigned epoch;
+    unsigned long long tbase;
+    int &grid = h->grid_ctas[nrhs];
+    if (grid <= 0) {
+        switch (nrhs) {
+            case 1: grid = tree_grid<T, 1>(a); break;
+            case 2: grid = tree_grid<T, 2>(a); break;
+            case 3: grid = tree_grid<T, 3>(a); break;
+            default: grid = tree_grid<T, 4>(a); break;
+        }
+        if (grid <= 0) {
+            h->err = "solve kernel does not fit on this device";
+            return STO_ERR_CUDA;
+        }
+    }
+    if (scratch) {  // caller scratch for one right-hand side: its flags and counter are cleared first
         a.s = static_cast<T *>(scratch->s);
         a.ubar = static_cast<T *>(scratch->ubar);
         a.xs = static_cast<T *>(scratch->xs);
         a.us = static_cast<T *>(scratch->us);
+        a.flags = static_cast<unsigned *>(scratch->flags);
+        a.ticket = static_cast<unsigned long long *>(scratch->ticket);
+        STO_CUDA(h, cudaMemsetAsync(scratch->flags, 0, (size_t)2 * h->Nn * sizeof(unsigned), st));
+        STO_CUDA(h, cudaMemsetAsync(scratch->ticket, 0, sizeof(unsigned long long), st));
+        epoch = 1;
+        tbase = 0;
     } else {
         a.s = h->at<T>(L.s);
         a.ubar = h->at<T>(L.ubar);
         a.xs = h->at<T>(L.xs);
         a.us = h->at<T>(L.us);
+        a.flags = h->at<unsigned>(L.flags);
+        a.ticket = h->at<unsigned long long>(L.ticket);
+        if (h->epoch == 0xffffffffu) {  // epochs wrapped: start the flags over
+            STO_CUDA(h, cudaMemsetAsync(a.flags, 0, (size_t)2 * h->Nn * sizeof(unsigned), st));
+            h->epoch = 0;
+        }
+        epoch = ++h->epoch;
+        tbase = h->ticket_base;
+        // every CTA's producer draws one ticket past the last item
+        h->ticket_base += (unsigned long long)(a.Tb + a.Tf + grid);
     }
-    a.s_stride = (long long)h->Nn * h->nx;
-    a.u_stride = (long long)h->Np * h->nu;
-    a.homog = homog ? 1 : 0;
-    a.scaled = scaled ? 1 : 0;
     cudaEvent_t ev;
     timing_begin(h, st, &ev);
     switch (nrhs) {
-        case 1: run_round<T, 1>(h, a, st); break;
-        case 2: run_round<T, 2>(h, a, st); break;
-        case 3: run_round<T, 3>(h, a, st); break;
-        default: run_round<T, 4>(h, a, st); break;
+        case 1: launch_tree_kv<T, 1>(h, a, epoch, tbase, grid, st); break;
+        case 2: launch_tree_kv<T, 2>(h, a, epoch, tbase, grid, st); break;
+        case 3: launch_tree_kv<T, 3>(h, a, epoch, tbase, grid, st); break;
+        default: launch_tree_kv<T, 4>(h, a, epoch, tbase, grid, st); break;
     }
     timing_end(h, st, ev, nrhs);
+    h->launches += 1;
     h->solve_calls += nrhs;
     STO_CUDA(h, cudaGetLastError());
     return STO_OK;
@@ -381,6 +782,28 @@ sto_status solve_round(stotree_t h, const void *const *y, const void *x0, void *
     if (scratch && nrhs != 1) return STO_ERR_INVALID_ARG;
     return h->prec == STO_FP64 ? solve_impl<double>(h, y, x0, hx, nrhs, homog, scaled, st, scratch)
                                : solve_impl<float>(h, y, x0, hx, nrhs, homog, scaled, st, scratch);
+}
+
+}  // namespace sto
+
+namespace sto {
+
+// After a synchronising call: report a bounded device wait that expired (STO_ERR_TIMEOUT) and
+// reset the round state it may have left inconsistent (flags, ticket counter, error flag).
+sto_status check_round_error(stotree_t h, cudaStream_t st) {
+    int err = 0;
+    int *dev_err = h->at<int>(h->L.fstatus) + 8;
+    STO_CUDA(h, cudaMemcpyAsync(&err, dev_err, sizeof(int), cudaMemcpyDeviceToHost, st));
+    STO_CUDA(h, cudaStreamSynchronize(st));
+    if (err == 0) return STO_OK;
+    STO_CUDA(h, cudaMemsetAsync(h->ws + h->L.flags, 0, (size_t)2 * h->Nn * sizeof(unsigned), st));
+    STO_CUDA(h, cudaMemsetAsync(h->ws + h->L.ticket, 0, 64, st));
+    STO_CUDA(h, cudaMemsetAsync(dev_err, 0, sizeof(int), st));
+    STO_CUDA(h, cudaStreamSynchronize(st));
+    h->epoch = 0;
+    h->ticket_base = 0;
+    h->err = err == 1 ? "a solve round gave up waiting for a dependency" : "a solve round gave up waiting for a copy";
+    return STO_ERR_TIMEOUT;
 }
 
 }  // namespace sto

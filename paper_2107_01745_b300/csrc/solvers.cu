@@ -128,14 +128,16 @@ __device__ bool reduce_last(double *sums, double *maxs, double *partials, unsign
     __syncthreads();
     if (!last) return false;
     __threadfence();
-    if (threadIdx.x < NV) {
-        const int k = threadIdx.x;
+    // warp w sums slots w, w+8, ...; lane l takes blocks l, l+32, ... in order, then a fixed
+    // butterfly: the result does not depend on which block finished last
+    for (int k = warp; k < NV; k += kThreads / 32) {
         double acc = k < NS ? 0.0 : -INFINITY;
-        for (int b = 0; b < (int)gridDim.x; ++b) {
+        for (int b = lane; b < (int)gridDim.x; b += 32) {
             const double v = __ldcg(partials + b * kRedSlots + k);
             acc = k < NS ? acc + v : fmax(acc, v);
         }
-        out[k] = acc;
+        acc = k < NS ? warp_sum_d(acc) : warp_max_d(acc);
+        if (lane == 0) out[k] = acc;
     }
     if (threadIdx.x == 0) *counter = 0u;
     __syncthreads();
@@ -703,6 +705,10 @@ sto_status solver_impl(stotree_t h, int method, const sto_opts *o, const void *x
     STO_CUDA(h, cudaEventRecord(e1, st));
     STO_CUDA(h, cudaMemcpyAsync(hs, sc, sizeof(SolverScalars), cudaMemcpyDeviceToHost, st));
     STO_CUDA(h, cudaStreamSynchronize(st));
+    {
+        const sto_status es = check_round_error(h, st);
+        if (es != STO_OK) result = es;
+    }
     float ms = 0.f;
     cudaEventElapsedTime(&ms, e0, e1);
     cudaEventDestroy(e0);
@@ -746,6 +752,8 @@ sto_status lambda_impl(stotree_t h, void *r0, int iters, double safety, double *
     SolverScalars *hs = h->host_scal;
     STO_CUDA(h, cudaMemcpyAsync(hs, sc, sizeof(SolverScalars), cudaMemcpyDeviceToHost, st));
     STO_CUDA(h, cudaStreamSynchronize(st));
+    const sto_status es = check_round_error(h, st);
+    if (es != STO_OK) return es;
     if (!(hs->pw_L > 0.0)) {
         h->err = "power iteration gave a non-positive estimate";
         return STO_ERR_NUMERICAL;
