@@ -108,8 +108,9 @@ typedef struct {
 } sto_info;
 
 /* Validate the tree and create a handle.  No device work.
- * Errors: STO_ERR_INVALID_ARG (null pointer, nx < 1, nu < 1, nx + nu > 512 for FP32 or
- * > 256 for FP64, m >= 2^31), STO_ERR_TREE. */
+ * Errors: STO_ERR_INVALID_ARG (null pointer, nx < 1, nu < 1, m >= 2^31, or a padded row width
+ * above the solve kernel's register tiling: max(pad(nx + nu), pad(nx) + pad(nu)) > 512 for FP32
+ * or > 256 for FP64, pad = round up to 16 bytes), STO_ERR_TREE. */
 STO_API sto_status stotree_create(const sto_tree_desc *tree, int32_t precision, stotree_t *out);
 
 /* Release the handle (host memory only; the workspace belongs to the caller). */

@@ -104,7 +104,9 @@ static void compute_layout(stotree_t h) {
     L.fstatus = add(64);
     L.G = add(Nn * nx * h->ldg * es);
     L.K = add(Np * nu * h->ldk * es);
-    L.Ri = add(Np * nu * h->ldr * es);
+    L.RK = add(Np * nu * h->ldrk * es);
+    L.Gt = add(Nn * (nx + nu) * h->ldk * es);
+    L.Kt = add(Np * nx * h->ldr * es);
     L.gu = add(Np * nu * es);
     L.gx = add(Np * nx * es);
     L.c = add(Nn * nx * es);
@@ -243,7 +245,9 @@ sto_status stotree_create(const sto_tree_desc *t, int32_t precision, stotree_t *
     h->ldg = (int)round_up(h->nx + h->nu, vec);
     h->ldk = (int)round_up(h->nx, vec);
     h->ldr = (int)round_up(h->nu, vec);
-    if (h->nx + h->nu > (precision == STO_FP64 ? 256 : 512)) {  // register tiling of the solve kernels
+    h->ldrk = h->ldr + h->ldk;
+    // register tiling of the solve kernel: padded row widths of [A | B] and [-Rbar^-1 | K]
+    if (std::max(h->ldg, h->ldrk) > (precision == STO_FP64 ? 256 : 512)) {
         delete h;
         return STO_ERR_INVALID_ARG;
     }

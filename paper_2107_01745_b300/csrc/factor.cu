@@ -12,7 +12,7 @@
 //   K^i  = -Rinv M,  P^i = N + M' K^i  (symmetrised: the antisymmetric part of the
 //   rounding error would otherwise be carried along by the open-loop A from stage to stage)
 // with P^l = pi^l P_N at the leaves.  The solve arrays (Algorithm 3/4) are then written in
-// the handle's precision: G^j = [A^j | B^j], K^i, -Rinv^i, gu^i, gx^i, c^j.
+// the handle's precision: G^j = [A^j | B^j], K^i, [-Rinv^i | K^i], gu^i, gx^i, c^j.
 #include "internal.h"
 
 namespace sto {
@@ -140,9 +140,10 @@ __global__ void k_assemble(int first, int child_first, int nx, int nu, int ld64,
     }
 }
 
-// Per parent: Cholesky Rbar = L L' in place, Z = L^-1, Rbar <- Rinv = Z'Z; -Rinv to the solve array.
+// Per parent: Cholesky Rbar = L L' in place, Z = L^-1, Rbar <- Rinv = Z'Z; -Rinv into the first ldr
+// columns of the parent's RK block (rows of ldrk).
 template <class T>
-__global__ void k_chol_inv(int first, int nu, int ldr, double *Rb, double *Zb, T *Ri, int *fstatus) {
+__global__ void k_chol_inv(int first, int nu, int ldr, int ldrk, double *Rb, double *Zb, T *RK, int *fstatus) {
     const int b = blockIdx.x, i = first + b;
     double *A = Rb + (size_t)b * nu * nu;
     double *Z = Zb + (size_t)b * nu * nu;
@@ -195,13 +196,15 @@ __global__ void k_chol_inv(int first, int nu, int ldr, double *Rb, double *Zb, T
     __syncthreads();
     for (int e = threadIdx.x; e < nu * ldr; e += blockDim.x) {
         const int a = e / ldr, c = e % ldr;
-        Ri[(size_t)i * nu * ldr + e] = c < nu ? (T)(-A[a * nu + c]) : (T)0;
+        RK[(size_t)i * nu * ldrk + (size_t)a * ldrk + c] = c < nu ? (T)(-A[a * nu + c]) : (T)0;
     }
 }
 
-// Symmetrise P^i and write K^i in the solve precision.
+// Symmetrise P^i and write K^i in the solve precision: alone, after -Rinv in the RK block (backward
+// pass) and transposed (forward pass).
 template <class T>
-__global__ void k_finish(int first, int nx, int nu, int ldk, double *Pcur, const double *K64, T *K) {
+__global__ void k_finish(int first, int nx, int nu, int ldk, int ldr, int ldrk, double *Pcur, const double *K64, T *K,
+                         T *RK, T *Kt) {
     const int b = blockIdx.x, i = first + b;
     double *P = Pcur + (size_t)b * nx * nx;
     for (int e = threadIdx.x; e < nx * nx; e += blockDim.x) {
@@ -215,19 +218,35 @@ __global__ void k_finish(int first, int nx, int nu, int ldk, double *Pcur, const
     const double *Kb = K64 + (size_t)b * nu * nx;
     for (int e = threadIdx.x; e < nu * ldk; e += blockDim.x) {
         const int a = e / ldk, c = e % ldk;
-        K[(size_t)i * nu * ldk + e] = c < nx ? (T)Kb[a * nx + c] : (T)0;
+        const T val = c < nx ? (T)Kb[a * nx + c] : (T)0;
+        K[(size_t)i * nu * ldk + e] = val;
+        RK[(size_t)i * nu * ldrk + (size_t)a * ldrk + ldr + c] = val;
+    }
+    for (int e = threadIdx.x; e < nx * ldr; e += blockDim.x) {
+        const int r = e / ldr, a = e % ldr;
+        Kt[(size_t)i * nx * ldr + e] = a < nu ? (T)Kb[a * nx + r] : (T)0;
     }
 }
 
-// Solve arrays of the dynamics: G^j = [A^j | B^j] (padded rows) and c^j in the solve precision.
+// Solve arrays of the dynamics: G^j = [A^j | B^j] (padded rows), its transpose G^j' (nx+nu rows
+// of ldk) and c^j, in the solve precision.
 template <class T>
-__global__ void k_downcast_dyn(int Nn, int nx, int nu, int ld64, int ldg, const double *G64, T *G, T *c) {
+__global__ void k_downcast_dyn(int Nn, int nx, int nu, int ld64, int ldg, int ldk, const double *G64, T *G, T *Gt,
+                               T *c) {
     const long long rows = (long long)Nn * nx;
     for (long long rr = blockIdx.x; rr < rows; rr += gridDim.x) {
         const double *src = G64 + rr * ld64;
         T *dst = G + rr * ldg;
         for (int k = threadIdx.x; k < ldg; k += blockDim.x) dst[k] = k < nx + nu ? (T)src[k] : (T)0;
         if (threadIdx.x == 0) c[rr] = (T)src[nx + nu];
+    }
+    const long long trows = (long long)Nn * (nx + nu);
+    for (long long tr = blockIdx.x; tr < trows; tr += gridDim.x) {
+        const long long j = tr / (nx + nu);
+        const int col = (int)(tr - j * (nx + nu));
+        T *dst = Gt + tr * ldk;
+        for (int r = threadIdx.x; r < ldk; r += blockDim.x)
+            dst[r] = r < nx ? (T)G64[((size_t)j * nx + r) * ld64 + col] : (T)0;
     }
 }
 
@@ -260,19 +279,20 @@ sto_status factor_impl(stotree_t h, cudaStream_t st) {
                                           h->at<double>(L.prob64), h->at<double>(L.cost64), W,
                                           h->at<double>(L.Rb), h->at<double>(L.M), Pcur, h->at<T>(L.gu),
                                           h->at<T>(L.gx));
-        k_chol_inv<T><<<np, 256, 0, st>>>(pf, nu, h->ldr, h->at<double>(L.Rb), h->at<double>(L.Zb), h->at<T>(L.Ri),
-                                          h->at<int>(L.fstatus));
+        k_chol_inv<T><<<np, 256, 0, st>>>(pf, nu, h->ldr, h->ldrk, h->at<double>(L.Rb), h->at<double>(L.Zb),
+                                          h->at<T>(L.RK), h->at<int>(L.fstatus));
         // K = -Rinv M  (nu x nx)
         dgemm(st, false, nu, nx, nu, -1.0, h->at<double>(L.Rb), nu, (long long)nu * nu, h->at<double>(L.M), nx,
               (long long)nu * nx, 0.0, h->at<double>(L.K64), nx, (long long)nu * nx, np);
         // P = N + M'K  (nx x nx)
         dgemm(st, true, nx, nx, nu, 1.0, h->at<double>(L.M), nx, (long long)nu * nx, h->at<double>(L.K64), nx,
               (long long)nu * nx, 1.0, Pcur, nx, (long long)nx * nx, np);
-        k_finish<T><<<np, 256, 0, st>>>(pf, nx, nu, h->ldk, Pcur, h->at<double>(L.K64), h->at<T>(L.K));
+        k_finish<T><<<np, 256, 0, st>>>(pf, nx, nu, h->ldk, h->ldr, h->ldrk, Pcur, h->at<double>(L.K64),
+                                        h->at<T>(L.K), h->at<T>(L.RK), h->at<T>(L.Kt));
     }
     const long long rows = (long long)h->Nn * nx;
-    k_downcast_dyn<T><<<(int)std::min<long long>(rows, 65535), 128, 0, st>>>(h->Nn, nx, nu, ld64, h->ldg, G64,
-                                                                             h->at<T>(L.G), h->at<T>(L.c));
+    k_downcast_dyn<T><<<(int)std::min<long long>(rows, 65535), 128, 0, st>>>(
+        h->Nn, nx, nu, ld64, h->ldg, h->ldk, G64, h->at<T>(L.G), h->at<T>(L.Gt), h->at<T>(L.c));
     STO_CUDA(h, cudaGetLastError());
     return STO_OK;
 }

@@ -6,7 +6,7 @@
 #include <string>
 #include <vector>
 
-#include "../../include/stotree.h"
+#include "stotree.h"
 
 namespace sto {
 
@@ -59,7 +59,8 @@ struct Layout {
     size_t P[2], PG, W, Rb, Zb, M, K64;
     size_t fstatus;              // int
     // solve arrays (real)
-    size_t G, K, Ri, gu, gx, c;
+    size_t G, K, RK, gu, gx, c;  // RK = [-Rbar^-1 | K] per nonleaf node (nu rows of ldrk)
+    size_t Gt, Kt;               // forward pass: [A | B]' per node (nx+nu rows of ldk), K' (nx rows of ldr)
     size_t cost, box;            // real copies: W (Q|R|PN), ell (q|r|pN), lo/hi (x|u)
     // solve scratch (real)
     size_t s, ubar, xs, us;
@@ -91,7 +92,8 @@ struct stotree_s {
     int ld64 = 0;     // G64 row length (nx + nu + 1 rounded to 2)
     int ldg = 0;      // solve G row length (nx + nu rounded to 16 bytes)
     int ldk = 0;      // K row length (nx rounded)
-    int ldr = 0;      // Ri row length (nu rounded)
+    int ldr = 0;      // -Rbar^-1 columns in RK (nu rounded)
+    int ldrk = 0;     // RK row length (ldr + ldk)
     size_t esz = 4;   // sizeof(real)
     sto::Layout L;
     char *ws = nullptr;

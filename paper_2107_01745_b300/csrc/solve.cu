@@ -23,10 +23,10 @@
 //
 // Data movement.  The node matrices are independent of the solve, so one producer warp per
 // CTA streams the matrices of its items with cp.async.bulk (TMA bulk copies) into a ring of
-// shared-memory slots, running ahead of the eight consumer warps by up to the ring depth; the
-// consumers read the slots (backward: axpy form, warps over rows, lanes over 16-byte column
-// groups; forward: dot form, one warp per row, shuffle reduction) and release them through
-// mbarriers.  Every wait is bounded: on expiry the kernel raises an error flag, stops waiting
+// shared-memory slots, running ahead of the four consumer warps by up to the ring depth; the
+// consumers read the slots in axpy form (warps over rows, lanes over 16-byte column groups,
+// one cross-warp reduction per matrix; the forward pass reads transposed copies G^j', K^j' so
+// that it has the same form) and release them through mbarriers.  Every wait is bounded: on expiry the kernel raises an error flag, stops waiting
 // and runs to its end, and the host reports STO_ERR_TIMEOUT.
 #include <cstdint>
 
@@ -35,13 +35,14 @@
 namespace sto {
 namespace {
 
-constexpr int kCW = 8;               // consumer warps
+constexpr int kCW = 4;               // consumer warps
+constexpr int kCtasPerSm = 3;        // resident CTAs per SM (shared memory and registers allow 3)
 constexpr int kThreadsT = (kCW + 1) * 32;
 constexpr int kSlots = 4;            // ring depth
-constexpr int kChunk = 16384;        // bytes per ring slot
+constexpr int kChunk = 15360;        // bytes per ring slot (three CTAs fit in an SM's shared memory)
 constexpr unsigned long long kWaitNs = 1500000000ull;  // bounded waits: 1.5 s of wall time
 
-enum : int { KIND_END = 0, KIND_BG = 1, KIND_BR = 2, KIND_BK = 3, KIND_FG = 4, KIND_FK = 5 };
+enum : int { KIND_END = 0, KIND_BG = 1, KIND_BP = 2, KIND_FG = 4, KIND_FK = 5 };
 enum : int {
     F_FIRST = 1,        // first chunk of this (kind, node) run
     F_LAST = 2,         // last chunk of this run
@@ -170,15 +171,30 @@ __device__ __forceinline__ void wait_flag(const unsigned *f, unsigned epoch, int
     }
     atomicExch(err, 1);
 }
+// Asynchronous element copies global -> shared (the small per-node vectors); the issuing thread
+// waits for its own copies with cp_async_wait, a named barrier then publishes them.
+template <int B>
+__device__ __forceinline__ void cp_async_elem(void *dst, const void *src);
+template <>
+__device__ __forceinline__ void cp_async_elem<4>(void *dst, const void *src) {
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 4;" ::"r"(sm_addr(dst)), "l"(src) : "memory");
+}
+template <>
+__device__ __forceinline__ void cp_async_elem<8>(void *dst, const void *src) {
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 8;" ::"r"(sm_addr(dst)), "l"(src) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+__device__ __forceinline__ void cp_async_wait() { asm volatile("cp.async.wait_all;" ::: "memory"); }
+
 __device__ __forceinline__ void cbar() { asm volatile("bar.sync 1, %0;" ::"n"(kCW * 32) : "memory"); }
 
 template <class T>
 struct TreeArgs {
-    int nx, nu, ldg, ldk, ldr, Np, Nn, nxu;
+    int nx, nu, ldg, ldk, ldr, ldrk, lda, Np, Nn, nxu;  // lda = max(ldg, ldrk): accumulator row width
     int Tb, Tf;
     const int *bstart, *bnodes, *fstart, *fnodes;
     const int *cbeg, *ccnt, *parent;
-    const T *G, *K, *Ri, *gu, *gx, *c, *sqp, *pN;
+    const T *G, *RK, *Gt, *Kt, *gu, *gx, *c, *sqp, *pN;
     const double *prob;
     const T *y[kMaxRhs];
     T *h[kMaxRhs];
@@ -189,7 +205,7 @@ struct TreeArgs {
     unsigned long long *ticket;
     int *err;
     int homog, scaled;
-    int rpcG, rpcR, rpcK;   // rows per ring slot
+    int rpcG, rpcRK, rpcGt, rpcKt;  // rows per ring slot
 };
 
 __device__ __forceinline__ long long dual_off(int i, int Np, int nxu, int nx) {
@@ -256,7 +272,7 @@ struct Producer {
         }
     }
     __device__ void emit(int kind, int node, int aux, int row0, int nrows, int flags, const T *base) {
-        const int ld = kind == KIND_BR ? a.ldr : ((kind == KIND_BK || kind == KIND_FK) ? a.ldk : a.ldg);
+        const int ld = kind == KIND_BG ? a.ldg : (kind == KIND_BP ? a.ldrk : (kind == KIND_FG ? a.ldk : a.ldr));
         emit(kind, node, aux, row0, nrows, flags, base, ld);
     }
 
@@ -279,8 +295,7 @@ struct Producer {
                         int ff = (j == jb ? F_FIRST_CHILD : 0) | (k > b0 ? F_INSEG : 0);
                         matrix(KIND_BG, j, i, a.G + (size_t)j * nx * a.ldg, nx, a.ldg, a.rpcG, ff, 0);
                     }
-                    matrix(KIND_BR, i, -1, a.Ri + (size_t)i * nu * a.ldr, nu, a.ldr, a.rpcR, 0, 0);
-                    matrix(KIND_BK, i, -1, a.K + (size_t)i * nu * a.ldk, nu, a.ldk, a.rpcK, 0,
+                    matrix(KIND_BP, i, -1, a.RK + (size_t)i * nu * a.ldrk, nu, a.ldrk, a.rpcRK, 0,
                            F_END_NODE | (last_node ? F_END_ITEM : 0));
                 }
             } else {
@@ -292,10 +307,10 @@ struct Producer {
                     const int endf = F_END_NODE | (last_node ? F_END_ITEM : 0);
                     const bool nonleaf = j < a.Np;
                     if (j != 0)
-                        matrix(KIND_FG, j, -1, a.G + (size_t)j * nx * a.ldg, nx, a.ldg, a.rpcG, k > f0 ? F_INSEG : 0,
-                               nonleaf ? 0 : endf);
+                        matrix(KIND_FG, j, -1, a.Gt + (size_t)j * (nx + nu) * a.ldk, nx + nu, a.ldk, a.rpcGt,
+                               k > f0 ? F_INSEG : 0, nonleaf ? 0 : endf);
                     if (nonleaf)
-                        matrix(KIND_FK, j, -1, a.K + (size_t)j * nu * a.ldk, nu, a.ldk, a.rpcK, j == 0 ? F_ROOT : 0,
+                        matrix(KIND_FK, j, -1, a.Kt + (size_t)j * nx * a.ldr, nx, a.ldr, a.rpcKt, j == 0 ? F_ROOT : 0,
                                endf);
                 }
             }
@@ -318,6 +333,12 @@ struct Consumer {
     int *abort_flag;  // shared
     // shared vectors
     T *s_in, *s_out, *part, *accs, *v, *xu, *xj, *uj;
+    T *pre;  // per-node vectors copied ahead of use (backward: y block, gu, gx; forward: c, ubar)
+
+    // cp.async of n reals from src to pre + off, one element per thread and step
+    __device__ void prefetch(int off, const T *src, int n) {
+        for (int e = tid; e < n; e += kCW * 32) cp_async_elem<sizeof(T)>(pre + off + e, src + e);
+    }
     T acc[NR][KV][VN];
 
     __device__ void zero_acc() {
@@ -337,7 +358,7 @@ struct Consumer {
             for (int q = 0; q < KV; ++q) {
                 const int cv = lane + 32 * q;
                 if (cv < nvec)
-                    *reinterpret_cast<VT *>(part + ((size_t)warp * NR + k) * a.ldg + cv * VN) =
+                    *reinterpret_cast<VT *>(part + ((size_t)warp * NR + k) * a.lda + cv * VN) =
                         *reinterpret_cast<const VT *>(acc[k][q]);
             }
         cbar();
@@ -345,54 +366,43 @@ struct Consumer {
             const int k = e / width, c = e - k * width;
             T sum = T(0);
 #pragma unroll
-            for (int w = 0; w < kCW; ++w) sum += part[((size_t)w * NR + k) * a.ldg + c];
+            for (int w = 0; w < kCW; ++w) sum += part[((size_t)w * NR + k) * a.lda + c];
             dst[k * dst_stride + c] = sum;
         }
         cbar();
     }
-    // acc[k] += coef[k][row0 + r] * M[r][:] over the rows of the slot
+    // acc[k] += coef[k][row0 + r] * M[r][:] over the rows of the slot; two rows per step so that
+    // their shared-memory loads are in flight together
     __device__ void axpy_rows(const T *M, int ld, int nrows, const T *coef, int cstride, int row0) {
         const int nvec = ld / VN;
-        for (int r = warp; r < nrows; r += kCW) {
-            T cr[NR];
+        constexpr int RU = 2;
+        for (int rb = warp; rb < nrows; rb += kCW * RU) {
+            T cr[RU][NR];
+            VT g[RU][KV];
 #pragma unroll
-            for (int k = 0; k < NR; ++k) cr[k] = coef[k * cstride + row0 + r];
-            const VT *row = reinterpret_cast<const VT *>(M + (size_t)r * ld);
+            for (int u = 0; u < RU; ++u) {
+                const int r = rb + u * kCW;
+                const bool ok = r < nrows;
 #pragma unroll
-            for (int q = 0; q < KV; ++q) {
-                const int cv = lane + 32 * q;
-                if (cv < nvec) {
-                    const VT g = row[cv];
+                for (int k = 0; k < NR; ++k) cr[u][k] = ok ? coef[k * cstride + row0 + r] : T(0);
+                const VT *row = reinterpret_cast<const VT *>(M + (size_t)(ok ? r : 0) * ld);
 #pragma unroll
-                    for (int k = 0; k < NR; ++k) v_fma<T>(cr[k], g, acc[k][q]);
+                for (int q = 0; q < KV; ++q) {
+                    const int cv = lane + 32 * q;
+                    if (cv < nvec) g[u][q] = row[cv];
                 }
             }
+#pragma unroll
+            for (int u = 0; u < RU; ++u)
+#pragma unroll
+                for (int q = 0; q < KV; ++q) {
+                    const int cv = lane + 32 * q;
+                    if (cv < nvec)
+#pragma unroll
+                        for (int k = 0; k < NR; ++k) v_fma<T>(cr[u][k], g[u][q], acc[k][q]);
+                }
         }
     }
-    // out[k][row0 + r] = M[r] . x[k] + add[row0 + r]   (add may be null)
-    __device__ void dot_rows(const T *M, int ld, int nrows, const T *x, int xstride, T *out, int ostride, int row0,
-                             const T *add, long long add_kstride) {
-        const int nvec = ld / VN;
-        for (int r = warp; r < nrows; r += kCW) {
-            const VT *row = reinterpret_cast<const VT *>(M + (size_t)r * ld);
-            T sum[NR];
-#pragma unroll
-            for (int k = 0; k < NR; ++k) sum[k] = T(0);
-            for (int cv = lane; cv < nvec; cv += 32) {
-                const VT g = row[cv];
-#pragma unroll
-                for (int k = 0; k < NR; ++k)
-                    sum[k] += v_dot<T>(g, *reinterpret_cast<const VT *>(x + k * xstride + cv * VN));
-            }
-#pragma unroll
-            for (int k = 0; k < NR; ++k) {
-                const T tot = warp_sum(sum[k]);
-                if (lane == 0)
-                    out[k * ostride + row0 + r] = tot + (add ? __ldcg(add + k * add_kstride + row0 + r) : T(0));
-            }
-        }
-    }
-
     __device__ void run() {
         const int nx = a.nx, nu = a.nu;
         unsigned long long n = 0;
@@ -413,7 +423,17 @@ struct Consumer {
                 if (f & F_FIRST) {
                     const int j = md.node;
                     cbar();  // every warp is done with the previous s_in
-                    if (f & F_FIRST_CHILD) zero_acc();
+                    if (f & F_FIRST_CHILD) {
+                        zero_acc();
+                        // node md.aux's y block [NR][nx+nu], gu, gx: consumed after its G chunks
+                        const int i = md.aux;
+                        for (int k = 0; k < NR; ++k) prefetch(k * a.nxu, a.y[k] + (long long)i * a.nxu, a.nxu);
+                        if (!a.homog) {
+                            prefetch(NR * a.nxu, a.gu + (size_t)i * nu, nu);
+                            prefetch(NR * a.nxu + nu, a.gx + (size_t)i * nx, nx);
+                        }
+                        cp_async_commit();
+                    }
                     if (f & F_INSEG) {
                         for (int e = tid; e < NR * nx; e += kCW * 32) s_in[e] = s_out[e];
                     } else if (j >= a.Np) {
@@ -437,47 +457,37 @@ struct Consumer {
                 axpy_rows(M, a.ldg, md.nrows, s_in, nx, md.row0);
                 __syncwarp();
                 if (lane == 0) mbar_arrive(&empty[slot]);
-            } else if (md.kind == KIND_BR) {
+            } else if (md.kind == KIND_BP) {
+                // parent step over RK^i = [-Rbar^-1 | K^i]: [ubar ; K'v] = RK' v (Rbar symmetric)
                 const int i = md.node;
                 if (f & F_FIRST) {
                     // all children done: accs = sum over warps, v = y_u/2 + acc_B + gu
-                    reduce_acc(a.ldg, accs, a.ldg);
-                    const long long oi = (long long)i * a.nxu;
+                    cp_async_wait();
+                    reduce_acc(a.ldg, accs, a.lda);
                     const T sci = a.scaled ? a.sqp[i] : T(1);
                     for (int e = tid; e < NR * nu; e += kCW * 32) {
                         const int k = e / nu, cc = e - k * nu;
-                        v[e] = T(0.5) * sci * a.y[k][oi + nx + cc] + accs[k * a.ldg + nx + cc] +
-                               (a.homog ? T(0) : a.gu[(size_t)i * nu + cc]);
+                        v[e] = T(0.5) * sci * pre[k * a.nxu + nx + cc] + accs[k * a.lda + nx + cc] +
+                               (a.homog ? T(0) : pre[NR * a.nxu + cc]);
                     }
                     zero_acc();
                     cbar();
                 }
-                axpy_rows(M, a.ldr, md.nrows, v, nu, md.row0);
+                axpy_rows(M, a.ldrk, md.nrows, v, nu, md.row0);
                 __syncwarp();
                 if (lane == 0) mbar_arrive(&empty[slot]);
                 if (f & F_LAST) {
-                    // ubar = -Rbar^-1 v (Ri is symmetric, stored negated)
-                    reduce_acc(a.ldr, xu, a.ldr);  // xu is free during the backward pass
+                    // ubar = -Rbar^-1 v;  s^i = y_x/2 + acc_A + K'v + gx
+                    reduce_acc(a.ldrk, xu, a.lda);  // xu is free during the backward pass
+                    const T sci = a.scaled ? a.sqp[i] : T(1);
                     for (int e = tid; e < NR * nu; e += kCW * 32) {
                         const int k = e / nu, cc = e - k * nu;
-                        a.ubar[k * a.u_stride + (long long)i * nu + cc] = xu[k * a.ldr + cc];
+                        a.ubar[k * a.u_stride + (long long)i * nu + cc] = xu[k * a.lda + cc];
                     }
-                    zero_acc();
-                }
-            } else if (md.kind == KIND_BK) {
-                const int i = md.node;
-                axpy_rows(M, a.ldk, md.nrows, v, nu, md.row0);
-                __syncwarp();
-                if (lane == 0) mbar_arrive(&empty[slot]);
-                if (f & F_LAST) {
-                    // s^i = y_x/2 + acc_A + K'v + gx
-                    reduce_acc(a.ldk, xj, a.ldk);
-                    const long long oi = (long long)i * a.nxu;
-                    const T sci = a.scaled ? a.sqp[i] : T(1);
                     for (int e = tid; e < NR * nx; e += kCW * 32) {
                         const int k = e / nx, cc = e - k * nx;
-                        const T val = T(0.5) * sci * a.y[k][oi + cc] + accs[k * a.ldg + cc] + xj[k * a.ldk + cc] +
-                                      (a.homog ? T(0) : a.gx[(size_t)i * nx + cc]);
+                        const T val = T(0.5) * sci * pre[k * a.nxu + cc] + accs[k * a.lda + cc] +
+                                      xu[k * a.lda + a.ldr + cc] + (a.homog ? T(0) : pre[NR * a.nxu + nu + cc]);
                         s_out[e] = val;
                         if (f & F_END_ITEM) a.s[k * a.s_stride + (long long)i * nx + cc] = val;
                     }
@@ -489,14 +499,15 @@ struct Consumer {
                     }
                 }
             } else if (md.kind == KIND_FG) {
+                // x^j = G^j [x^i; u^i] + c^j, axpy form over the rows of G^j' (one row per input)
                 const int j = md.node;
                 if (f & F_FIRST) {
-                    cbar();  // every warp is done with the previous xu / xj
+                    cbar();  // every warp is done with the previous xu / xj and pre
                     if (f & F_INSEG) {
                         // parent = previous node of the segment: [x; u] from xj, uj
                         for (int e = tid; e < NR * a.ldg; e += kCW * 32) {
                             const int k = e / a.ldg, cc = e - k * a.ldg;
-                            xu[e] = cc < nx ? xj[k * a.ldk + cc] : (cc < nx + nu ? uj[k * nu + cc - nx] : T(0));
+                            xu[e] = cc < nx ? xj[k * a.ldk + cc] : (cc < nx + nu ? uj[k * a.ldr + cc - nx] : T(0));
                         }
                     } else {
                         const int i = a.parent[j];
@@ -512,14 +523,31 @@ struct Consumer {
                             xu[e] = val;
                         }
                     }
+                    // c^j and ubar^j, consumed at the end of the node's G and K runs.  ubar^j comes
+                    // from the backward pass: read only after this item's dependency wait, which
+                    // (through the forward chain from the root) follows the whole backward pass.
+                    if (!a.homog) prefetch(0, a.c + (size_t)j * nx, nx);
+                    if (j < a.Np)
+                        for (int k = 0; k < NR; ++k)
+                            prefetch(nx + k * nu, a.ubar + k * a.u_stride + (long long)j * nu, nu);
+                    cp_async_commit();
                     cbar();
                 }
-                dot_rows(M, a.ldg, md.nrows, xu, a.ldg, xj, a.ldk, md.row0,
-                         a.homog ? nullptr : a.c + (size_t)j * nx, 0);
+                axpy_rows(M, a.ldk, md.nrows, xu, a.ldg, md.row0);
                 __syncwarp();
                 if (lane == 0) mbar_arrive(&empty[slot]);
-                if (f & F_END_NODE) {  // leaf: no K step
+                if (f & F_LAST) {
+                    cp_async_wait();
+                    reduce_acc(a.ldk, xj, a.ldk);  // the padding columns of G' are zero
+                    if (!a.homog)
+                        for (int e = tid; e < NR * nx; e += kCW * 32) {
+                            const int k = e / nx, r = e - k * nx;
+                            xj[k * a.ldk + r] += pre[r];
+                        }
+                    zero_acc();
                     cbar();
+                }
+                if (f & F_END_NODE) {  // leaf: no K step
                     const long long oj = dual_off(j, a.Np, a.nxu, nx);
                     const T scj = a.scaled ? a.sqp[j] : T(1);
                     for (int e = tid; e < NR * nx; e += kCW * 32) {
@@ -530,34 +558,36 @@ struct Consumer {
                     }
                 }
             } else if (md.kind == KIND_FK) {
+                // u^j = K^j x^j + ubar^j, axpy form over the rows of K^j'
                 const int j = md.node;
-                if (f & F_FIRST) {
-                    if (f & F_ROOT) {
-                        if (tid == 0) wait_flag(a.flags + 0, epoch, a.err);  // backward pass finished
-                        cbar();
-                        for (int e = tid; e < NR * a.ldk; e += kCW * 32) {
-                            const int r = e % a.ldk;
-                            xj[e] = (r < nx && !a.homog) ? a.x0[r] : T(0);
-                        }
-                    } else {
-                        // zero the padding of x^j so the dot form may read whole 16-byte groups
-                        for (int e = tid; e < NR * (a.ldk - nx); e += kCW * 32) {
-                            const int k = e / (a.ldk - nx), r = nx + e % (a.ldk - nx);
-                            xj[k * a.ldk + r] = T(0);
-                        }
+                if ((f & F_FIRST) && (f & F_ROOT)) {
+                    if (tid == 0) wait_flag(a.flags + 0, epoch, a.err);  // backward pass finished
+                    cbar();
+                    for (int k = 0; k < NR; ++k) prefetch(nx + k * nu, a.ubar + k * a.u_stride, nu);
+                    cp_async_commit();
+                    for (int e = tid; e < NR * a.ldk; e += kCW * 32) {
+                        const int r = e % a.ldk;
+                        xj[e] = (r < nx && !a.homog) ? a.x0[r] : T(0);
                     }
                     cbar();
                 }
-                dot_rows(M, a.ldk, md.nrows, xj, a.ldk, uj, nu, md.row0, a.ubar + (long long)j * nu, a.u_stride);
+                axpy_rows(M, a.ldr, md.nrows, xj, a.ldk, md.row0);
                 __syncwarp();
                 if (lane == 0) mbar_arrive(&empty[slot]);
                 if (f & F_LAST) {
+                    cp_async_wait();
+                    reduce_acc(a.ldr, uj, a.ldr);
+                    for (int e = tid; e < NR * nu; e += kCW * 32) {
+                        const int k = e / nu, r = e - k * nu;
+                        uj[k * a.ldr + r] += pre[nx + e];
+                    }
+                    zero_acc();
                     cbar();
                     const long long oj = dual_off(j, a.Np, a.nxu, nx);
                     const T scj = a.scaled ? a.sqp[j] : T(1);
                     for (int e = tid; e < NR * (nx + nu); e += kCW * 32) {
                         const int k = e / (nx + nu), r = e - k * (nx + nu);
-                        const T val = r < nx ? xj[k * a.ldk + r] : uj[k * nu + r - nx];
+                        const T val = r < nx ? xj[k * a.ldk + r] : uj[k * a.ldr + r - nx];
                         a.h[k][oj + r] = scj * val;
                         if (r < nx)
                             a.xs[k * a.s_stride + (long long)j * nx + r] = val;
@@ -577,7 +607,7 @@ struct Consumer {
 };
 
 template <class T, int NR, int KV>
-__global__ void __launch_bounds__(kThreadsT, 2) k_tree(TreeArgs<T> a, unsigned epoch, unsigned long long tbase) {
+__global__ void __launch_bounds__(kThreadsT, kCtasPerSm) k_tree(TreeArgs<T> a, unsigned epoch, unsigned long long tbase) {
     extern __shared__ __align__(1024) unsigned char smem[];
     __shared__ int abort_flag;
     unsigned char *ring = smem;
@@ -611,30 +641,34 @@ __global__ void __launch_bounds__(kThreadsT, 2) k_tree(TreeArgs<T> a, unsigned e
     c.s_out = p;
     p += NR * a.ldk;
     c.part = p;
-    p += kCW * NR * a.ldg;
+    p += kCW * NR * a.lda;
     c.accs = p;
-    p += NR * a.ldg;
+    p += NR * a.lda;
     c.v = p;
     p += NR * a.ldr;
     c.xu = p;
-    p += NR * a.ldg;
+    p += NR * a.lda;
     c.xj = p;
     p += NR * a.ldk;
     c.uj = p;
+    p += NR * a.ldr;
+    c.pre = p;
     (void)nx;
     (void)nu;
     c.run();
 }
 
-size_t tree_smem(int NR, int ldg, int ldk, int ldr, size_t esz) {
-    const size_t vec = (size_t)NR * (3 * ldk + (kCW + 2) * ldg + ldr) + (size_t)NR * ldr;
+size_t tree_smem(int NR, int lda, int ldg, int ldk, int ldr, size_t esz) {
+    // s_in, s_out, xj: NR ldk; part: kCW NR lda; accs, xu: NR lda; v, uj: NR ldr;
+    // pre: NR (nx + nu) + nx + nu <= (NR + 1) ldg
+    const size_t vec = (size_t)NR * (3 * ldk + (kCW + 2) * lda + 2 * ldr) + (size_t)(NR + 1) * ldg;
     return (size_t)kSlots * kChunk + kSlots * sizeof(Meta) + 2 * kSlots * sizeof(uint64_t) + vec * esz;
 }
 
 template <class T, int NR, int KV>
 void launch_tree(stotree_t h, const TreeArgs<T> &a, unsigned epoch, unsigned long long tbase, int grid,
                  cudaStream_t st) {
-    const size_t smem = tree_smem(NR, a.ldg, a.ldk, a.ldr, sizeof(T));
+    const size_t smem = tree_smem(NR, a.lda, a.ldg, a.ldk, a.ldr, sizeof(T));
     cudaFuncSetAttribute(k_tree<T, NR, KV>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     k_tree<T, NR, KV><<<grid, kThreadsT, smem, st>>>(a, epoch, tbase);
 }
@@ -642,7 +676,7 @@ void launch_tree(stotree_t h, const TreeArgs<T> &a, unsigned epoch, unsigned lon
 template <class T, int NR>
 void launch_tree_kv(stotree_t h, const TreeArgs<T> &a, unsigned epoch, unsigned long long tbase, int grid,
                     cudaStream_t st) {
-    const int kv = (a.ldg / V16<T>::n + 31) / 32;
+    const int kv = (a.lda / V16<T>::n + 31) / 32;
     switch (kv) {
         case 1: launch_tree<T, NR, 1>(h, a, epoch, tbase, grid, st); break;
         case 2: launch_tree<T, NR, 2>(h, a, epoch, tbase, grid, st); break;
@@ -657,8 +691,8 @@ int tree_grid(const TreeArgs<T> &a) {
     int dev = 0, sms = 0, per_sm = 0;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-    const size_t smem = tree_smem(NR, a.ldg, a.ldk, a.ldr, sizeof(T));
-    const int kv = (a.ldg / V16<T>::n + 31) / 32;
+    const size_t smem = tree_smem(NR, a.lda, a.ldg, a.ldk, a.ldr, sizeof(T));
+    const int kv = (a.lda / V16<T>::n + 31) / 32;
     cudaError_t e;
     switch (kv) {
         case 1: cudaFuncSetAttribute(k_tree<T, NR, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
@@ -671,7 +705,7 @@ int tree_grid(const TreeArgs<T> &a) {
                  e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_tree<T, NR, 4>, kThreadsT, smem); break;
     }
     if (e != cudaSuccess || per_sm < 1) return 0;
-    return sms * (per_sm < 2 ? per_sm : 2);
+    return sms * (per_sm < kCtasPerSm ? per_sm : kCtasPerSm);
 }
 
 template <class T>
@@ -684,6 +718,8 @@ sto_status solve_impl(stotree_t h, const void *const *y, const void *x0, void *c
     a.ldg = h->ldg;
     a.ldk = h->ldk;
     a.ldr = h->ldr;
+    a.ldrk = h->ldrk;
+    a.lda = h->ldrk > h->ldg ? h->ldrk : h->ldg;
     a.Np = h->Np;
     a.Nn = h->Nn;
     a.nxu = h->nx + h->nu;
@@ -697,8 +733,9 @@ sto_status solve_impl(stotree_t h, const void *const *y, const void *x0, void *c
     a.ccnt = h->at<int>(L.ccnt);
     a.parent = h->at<int>(L.parent);
     a.G = h->at<T>(L.G);
-    a.K = h->at<T>(L.K);
-    a.Ri = h->at<T>(L.Ri);
+    a.Gt = h->at<T>(L.Gt);
+    a.Kt = h->at<T>(L.Kt);
+    a.RK = h->at<T>(L.RK);
     a.gu = h->at<T>(L.gu);
     a.gx = h->at<T>(L.gx);
     a.c = h->at<T>(L.c);
@@ -715,8 +752,9 @@ sto_status solve_impl(stotree_t h, const void *const *y, const void *x0, void *c
     a.homog = homog ? 1 : 0;
     a.scaled = scaled ? 1 : 0;
     a.rpcG = kChunk / (h->ldg * (int)sizeof(T));
-    a.rpcR = kChunk / (h->ldr * (int)sizeof(T));
-    a.rpcK = kChunk / (h->ldk * (int)sizeof(T));
+    a.rpcRK = kChunk / (h->ldrk * (int)sizeof(T));
+    a.rpcGt = kChunk / (h->ldk * (int)sizeof(T));
+    a.rpcKt = kChunk / (h->ldr * (int)sizeof(T));
     a.err = h->at<int>(L.fstatus) + 8;
     unsigned epoch;
     unsigned long long tbase;
