@@ -225,6 +225,61 @@ STO_API sto_status stotree_solve_bytes(stotree_t h, double *matrix_bytes, double
 STO_API const char *stotree_status_str(sto_status s);
 STO_API const char *stotree_last_error(stotree_t h);
 
+/* ---------------------------------------------------------------------------------------------
+ * Batched instances.  Many MPC problems solved together: shape groups that share the tree, the
+ * dynamics (A, B), the diagonal costs and the box, and instances that differ in the root state
+ * x0 and the disturbances c^j.  The group's tree has `branching` children per node for the first
+ * `branch_stages` stages and one child after that, so node probabilities are uniform within a
+ * stage and the factor of Section III-D reduces to one matrix set per stage (R~_t, K_t); a solve
+ * round (Algorithm 3/4) processes every (node, instance) column of a stage of every group
+ * together, and NAMA (Algorithm 2) runs per instance with the readings of stotree_nama_solve.
+ * Limits: nx <= 64, nu <= 32, horizon <= 64, zero linear cost terms, FP32 solve path.
+ * Batch vectors hold the instances one after another (groups in order, instances in order),
+ * each in the single-instance dual layout.
+ * ------------------------------------------------------------------------------------------- */
+typedef struct stobatch_s *stobatch_t;
+
+typedef struct {
+    int32_t horizon, branching, branch_stages, nx, nu, num_instances;
+    const double *A, *B;             /* [nx][nx], [nx][nu], shared by the group; host, copied */
+    const double *Q, *R, *PN;        /* diagonals */
+    const double *xlo, *xhi, *ulo, *uhi;
+} sto_group_desc;
+
+/* Create a batch from ngroups group descriptions.  Errors: STO_ERR_INVALID_ARG (limits above). */
+STO_API sto_status stobatch_create(const sto_group_desc *groups, int32_t ngroups, stobatch_t *out);
+STO_API void stobatch_destroy(stobatch_t b);
+
+/* Total batch vector length, number of instances, and per-instance offset / length (arrays of
+ * num_instances entries, may be NULL). */
+STO_API sto_status stobatch_sizes(stobatch_t b, int64_t *total_dual, int32_t *num_instances, int64_t *inst_offsets,
+                                  int64_t *inst_sizes);
+STO_API sto_status stobatch_workspace_size(stobatch_t b, size_t *bytes);
+STO_API sto_status stobatch_bind_workspace(stobatch_t b, void *dev_ptr, size_t bytes, sto_stream_t stream);
+
+/* Instance data: x0 [nx] and disturbances c [Nn][nx] of the group's tree (row 0 unused), host
+ * FP64.  Invalidates the factor. */
+STO_API sto_status stobatch_set_instance(stobatch_t b, int32_t group, int32_t instance, const double *x0,
+                                         const double *c, sto_stream_t stream);
+
+/* FP64 stage factor of every group and the affine terms of every instance.  Synchronises;
+ * STO_ERR_NUMERICAL if some R + B'PB is not positive definite. */
+STO_API sto_status stobatch_factor(stobatch_t b, sto_stream_t stream);
+
+/* One batched solve round (Algorithm 3 / 4, one right-hand side per instance): y, hx device
+ * float batch vectors; scaled as in stotree_solve_step.  Asynchronous. */
+STO_API sto_status stobatch_solve_step(stobatch_t b, const void *y, void *hx, int32_t homogeneous, int32_t scaled,
+                                       sto_stream_t stream);
+
+/* NAMA for every instance (opts.lbfgs_mem <= 8).  lambdas [ngroups] host.  y (device float batch
+ * vector, unscaled; zeros for a cold start) receives the final duals, z and hx (may be NULL) the
+ * z_lambda and Hx of each instance's final iterate; infos [num_instances] (may be NULL).  An
+ * instance stops at its own tolerance; the call returns STO_NOT_CONVERGED if some instance hit
+ * max_iter.  Synchronises the stream. */
+STO_API sto_status stobatch_nama_solve(stobatch_t b, const sto_opts *opts, const double *lambdas, void *y, void *z,
+                                       void *hx, sto_info *infos, sto_stream_t stream);
+STO_API const char *stobatch_last_error(stobatch_t b);
+
 #ifdef __cplusplus
 }
 #endif

@@ -88,6 +88,24 @@ def lib():
         L.stotree_last_error.restype = ctypes.c_char_p
         L.stotree_status_str.argtypes = [ctypes.c_int]
         L.stotree_status_str.restype = ctypes.c_char_p
+        bsigs = {
+            "stobatch_create": [vp, i32, vp],
+            "stobatch_sizes": [vp, vp, vp, vp, vp],
+            "stobatch_workspace_size": [vp, vp],
+            "stobatch_bind_workspace": [vp, vp, sz, vp],
+            "stobatch_set_instance": [vp, i32, i32, vp, vp, vp],
+            "stobatch_factor": [vp, vp],
+            "stobatch_solve_step": [vp, vp, vp, i32, i32, vp],
+            "stobatch_nama_solve": [vp, vp, vp, vp, vp, vp, vp, vp],
+        }
+        for name, args in bsigs.items():
+            fn = getattr(L, name)
+            fn.argtypes = args
+            fn.restype = ctypes.c_int
+        L.stobatch_destroy.argtypes = [vp]
+        L.stobatch_destroy.restype = None
+        L.stobatch_last_error.argtypes = [vp]
+        L.stobatch_last_error.restype = ctypes.c_char_p
         _lib = L
     return _lib
 
@@ -97,7 +115,10 @@ def exported_symbols():
                         "stotree_bind_workspace", "stotree_set_dynamics", "stotree_set_costs", "stotree_set_box",
                         "stotree_factor", "stotree_solve_step", "stotree_solve_step_noalloc", "stotree_last_primal", "stotree_estimate_lambda",
                         "stotree_nama_solve", "stotree_minfbe_solve", "stotree_kkt_check", "stotree_set_timing",
-                        "stotree_get_timing", "stotree_solve_bytes", "stotree_status_str", "stotree_last_error")]
+                        "stotree_get_timing", "stotree_solve_bytes", "stotree_status_str", "stotree_last_error",
+                        "stobatch_create", "stobatch_destroy", "stobatch_sizes", "stobatch_workspace_size",
+                        "stobatch_bind_workspace", "stobatch_set_instance", "stobatch_factor",
+                        "stobatch_solve_step", "stobatch_nama_solve", "stobatch_last_error")]
 
 
 def _np_ptr(a):
@@ -264,3 +285,113 @@ class StoTree:
         a, b = ctypes.c_double(), ctypes.c_double()
         lib().stotree_solve_bytes(self.h, ctypes.byref(a), ctypes.byref(b))
         return a.value, b.value
+
+
+class _GroupDesc(ctypes.Structure):
+    _fields_ = [("horizon", ctypes.c_int32), ("branching", ctypes.c_int32), ("branch_stages", ctypes.c_int32),
+                ("nx", ctypes.c_int32), ("nu", ctypes.c_int32), ("num_instances", ctypes.c_int32),
+                ("A", ctypes.c_void_p), ("B", ctypes.c_void_p), ("Q", ctypes.c_void_p), ("R", ctypes.c_void_p),
+                ("PN", ctypes.c_void_p), ("xlo", ctypes.c_void_p), ("xhi", ctypes.c_void_p), ("ulo", ctypes.c_void_p),
+                ("uhi", ctypes.c_void_p)]
+
+
+class StoBatch:
+    """Many instances in shape groups (workloads.Group) solved together on one GPU."""
+
+    def __init__(self, groups, device="cuda:0"):
+        self.device = torch.device(device)
+        self.groups = groups
+        L = lib()
+        self._keep = []
+        descs = (_GroupDesc * len(groups))()
+        for k, g in enumerate(groups):
+            arrs = [np.ascontiguousarray(v, dtype=np.float64) for v in (g.A, g.B, g.Q, g.R, g.PN, g.xlo, g.xhi,
+                                                                        g.ulo, g.uhi)]
+            self._keep.append(arrs)
+            descs[k] = _GroupDesc(g.horizon, g.branching, g.branch_stages, g.nx, g.nu, g.num_instances,
+                                  *[_np_ptr(a) for a in arrs])
+        h = ctypes.c_void_p()
+        code = L.stobatch_create(descs, len(groups), ctypes.byref(h))
+        if code != 0:
+            raise StoError(code, "stobatch_create")
+        self.h = h
+        M, n = ctypes.c_int64(), ctypes.c_int32()
+        L.stobatch_sizes(h, ctypes.byref(M), ctypes.byref(n), None, None)
+        self.M, self.ninst = M.value, n.value
+        offs = np.zeros(self.ninst, dtype=np.int64)
+        sizes = np.zeros(self.ninst, dtype=np.int64)
+        L.stobatch_sizes(h, None, None, _np_ptr(offs), _np_ptr(sizes))
+        self.offsets, self.sizes = offs, sizes
+        wb = ctypes.c_size_t()
+        L.stobatch_workspace_size(h, ctypes.byref(wb))
+        self.workspace_bytes = wb.value
+        with torch.cuda.device(self.device):
+            self.ws = torch.empty(self.workspace_bytes, dtype=torch.uint8, device=self.device)
+            self._check(L.stobatch_bind_workspace(h, _t_ptr(self.ws), self.workspace_bytes, _stream()), "bind")
+            for gi, g in enumerate(groups):
+                for k in range(g.num_instances):
+                    x0 = np.ascontiguousarray(g.x0[k], dtype=np.float64)
+                    c = np.ascontiguousarray(g.c[k], dtype=np.float64)
+                    self._check(L.stobatch_set_instance(h, gi, k, _np_ptr(x0), _np_ptr(c), _stream()),
+                                "set_instance")
+
+    def _check(self, code, where):
+        if code != 0:
+            raise StoError(code, where, lib().stobatch_last_error(self.h).decode())
+
+    def close(self):
+        if getattr(self, "h", None):
+            lib().stobatch_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def factor(self):
+        self._check(lib().stobatch_factor(self.h, _stream()), "factor")
+
+    def vec(self):
+        return torch.zeros(self.M, dtype=torch.float32, device=self.device)
+
+    def split(self, v):
+        """Per-instance views of a batch vector."""
+        return [v[o:o + n] for o, n in zip(self.offsets, self.sizes)]
+
+    def pack(self, per_instance):
+        return torch.cat([torch.as_tensor(np.asarray(a), dtype=torch.float32) for a in per_instance]).to(self.device)
+
+    def solve_step(self, y, homogeneous=False, scaled=False):
+        out = torch.empty_like(y)
+        self._check(lib().stobatch_solve_step(self.h, _t_ptr(y), _t_ptr(out), 1 if homogeneous else 0,
+                                              1 if scaled else 0, _stream()), "solve_step")
+        return out
+
+    def nama(self, lambdas, tol=1e-4, mem=5, max_iter=500, max_ls=30, eps_curv=1e-8, y0=None, outputs=True,
+             allow_not_converged=False):
+        y = self.vec() if y0 is None else y0.clone().contiguous()
+        z = self.vec() if outputs else None
+        hx = self.vec() if outputs else None
+        lam = np.ascontiguousarray(lambdas, dtype=np.float64)
+        o = Opts(0.0, tol, eps_curv, mem, max_iter, max_ls)
+        infos = (Info * self.ninst)()
+        code = lib().stobatch_nama_solve(self.h, ctypes.byref(o), _np_ptr(lam), _t_ptr(y), _t_ptr(z), _t_ptr(hx),
+                                         infos, _stream())
+        if code != 0 and not (allow_not_converged and code == STO_NOT_CONVERGED):
+            self._check(code, "nama")
+        return dict(y=y, z=z, hx=hx, infos=[i.as_dict() for i in infos])
+
+    def group_lambdas(self, iters=50, safety=0.9, seed=7):
+        """lambda per group from the single-instance power iteration on the group's first instance
+        (the dual Hessian does not depend on x0 or c)."""
+        out = []
+        for g in self.groups:
+            st = StoTree(g.instance(0), precision="fp32", device=self.device)
+            st.factor()
+            r0 = torch.as_tensor(np.random.default_rng(seed).standard_normal(st.m), dtype=torch.float32,
+                                 device=self.device)
+            out.append(st.estimate_lambda(r0, iters=iters, safety=safety)[0])
+            st.close()
+        return np.array(out)

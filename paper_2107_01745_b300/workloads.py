@@ -297,3 +297,93 @@ def random_dual(p: Problem, seed: int, scale: float = 1.0) -> np.ndarray:
     y = scale * rng.standard_normal(p.num_dual)
     y[:p.nx] = 0.0
     return y
+
+
+# --------------------------------------------------------------------------------------
+# Batched uneven instances: shape groups that share the tree, A, B, costs and box, and
+# instances that draw their own x0 and disturbances.
+# --------------------------------------------------------------------------------------
+
+@dataclass
+class Group:
+    """One shape group: a tree with `branching` children per node for the first
+    `branch_stages` stages and one child after that, shared A, B, Q, R, P_N and box."""
+    horizon: int
+    branching: int
+    branch_stages: int
+    nx: int
+    nu: int
+    A: np.ndarray          # [nx, nx]
+    B: np.ndarray          # [nx, nu]
+    Q: np.ndarray
+    R: np.ndarray
+    PN: np.ndarray
+    xlo: np.ndarray
+    xhi: np.ndarray
+    ulo: np.ndarray
+    uhi: np.ndarray
+    x0: np.ndarray         # [I, nx]
+    c: np.ndarray          # [I, Nn, nx]; c[:, 0] unused
+
+    @property
+    def num_instances(self) -> int:
+        return int(self.x0.shape[0])
+
+    def tree(self) -> Tree:
+        return tree_from_branching([self.branching] * self.branch_stages + [1] * (self.horizon - self.branch_stages))
+
+    def instance(self, k: int) -> Problem:
+        """Instance k as a stand-alone problem (per-node copies of the shared data)."""
+        t = self.tree()
+        nn = t.num_nodes
+        A = np.broadcast_to(self.A, (nn, self.nx, self.nx)).copy()
+        B = np.broadcast_to(self.B, (nn, self.nx, self.nu)).copy()
+        A[0] = 0.0
+        B[0] = 0.0
+        return Problem(tree=t, nx=self.nx, nu=self.nu, A=A, B=B, c=self.c[k].copy(), Q=self.Q, R=self.R,
+                       PN=self.PN, q=np.zeros(self.nx), r=np.zeros(self.nu), pN=np.zeros(self.nx),
+                       xlo=self.xlo, xhi=self.xhi, ulo=self.ulo, uhi=self.uhi, x0=self.x0[k].copy(),
+                       name=f"group_instance{k}")
+
+
+# (branching, branch stages) pairs with b^s in [64, 1024]: the reading of "branching 2 or 3 for
+# the first U{3..8} stages (64-1024 scenarios)" (other draws are redrawn).
+_BATCH_SHAPES = [(2, 6), (2, 7), (2, 8), (3, 4), (3, 5), (3, 6)]
+
+
+def make_group(rng: np.random.Generator, horizon: int, branching: int, branch_stages: int, nx: int, nu: int,
+               instances: int, w_std: float = 0.05) -> Group:
+    """A group with the tiny workload's costs and box: A Gaussian at spectral radius 0.95,
+    B ~ N(0,1), Q = I, R = 0.1 I, P_N = I, |u| <= 1, |x| <= 5; per instance x0 ~ U[-3, 3] and
+    c ~ N(0, w_std^2) per node.  Draw order: A, B, x0, c."""
+    A = spectral_rescale(rng.standard_normal((nx, nx)), 0.95)
+    B = rng.standard_normal((nx, nu))
+    nn = tree_from_branching([branching] * branch_stages + [1] * (horizon - branch_stages)).num_nodes
+    x0 = rng.uniform(-3.0, 3.0, size=(instances, nx))
+    c = w_std * rng.standard_normal((instances, nn, nx))
+    c[:, 0] = 0.0
+    return Group(horizon=horizon, branching=branching, branch_stages=branch_stages, nx=nx, nu=nu, A=A, B=B,
+                 Q=np.ones(nx), R=0.1 * np.ones(nu), PN=np.ones(nx),
+                 xlo=-5.0 * np.ones(nx), xhi=5.0 * np.ones(nx), ulo=-np.ones(nu), uhi=np.ones(nu),
+                 x0=x0, c=c)
+
+
+def batched_uneven(seed: int = 3, groups: int = 16, instances: int = 32):
+    """The batched workload: `groups` shape groups x `instances` instances (512 in total by
+    default).  Each group draws horizon U{10..30}, (branching, branching stages) from the pairs
+    with 64..1024 scenarios, nx from {16, 32, 64} and nu = nx / 2."""
+    rng = np.random.default_rng(seed)
+    out = []
+    for _ in range(groups):
+        horizon = int(rng.integers(10, 31))
+        b, s = _BATCH_SHAPES[int(rng.integers(0, len(_BATCH_SHAPES)))]
+        nx = int(rng.choice([16, 32, 64]))
+        out.append(make_group(rng, horizon, b, s, nx, nx // 2, instances))
+    return out
+
+
+def batched_small(seed: int = 30, instances: int = 3):
+    """Small batched case for parity tests: three groups of different shapes."""
+    rng = np.random.default_rng(seed)
+    return [make_group(rng, 4, 2, 2, 3, 2, instances), make_group(rng, 6, 3, 1, 4, 2, instances),
+            make_group(rng, 3, 2, 3, 5, 3, instances)]
