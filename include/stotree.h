@@ -280,6 +280,80 @@ STO_API sto_status stobatch_nama_solve(stobatch_t b, const sto_opts *opts, const
                                        void *hx, sto_info *infos, sto_stream_t stream);
 STO_API const char *stobatch_last_error(stobatch_t b);
 
+/* ---------------------------------------------------------------------------------------------
+ * Learned warm start: a per-node perceptron that predicts the scaled dual ybar^i = y^i/sqrt(pi^i)
+ * (Section III-E) of every node of a tree from the node's data, trained with Adam on the duals
+ * that the batched solver returns.  The paper's own warm start is a few accelerated dual
+ * gradient steps (Section III-E); this predictor replaces them for families of problems that
+ * share a tree and its dynamics.
+ *
+ * Network: d_in = 4 nx + 1 inputs [x0, t/N, c^i, c^anc(i), c^anc(anc(i))] (missing ancestors and
+ * the root's c are zeros) -> hidden -> hidden -> d_out = nx + nu, GELU (tanh form) on the hidden
+ * layers.  Products run on the tensor cores in BF16 with FP32 accumulation; weights are kept in
+ * FP32 for Adam and copied to BF16 after each step; hidden activations and output gradients are
+ * stored in BF16.  Loss: mean over the valid outputs (nx + nu at nonleaf nodes, nx at leaves) of
+ * the squared difference to ybar.
+ *
+ * Parameter vector order (FP32, host): W1 [hidden][d_in], b1 [hidden], W2 [hidden][hidden],
+ * b2 [hidden], W3 [d_out][hidden], b3 [d_out].
+ * ------------------------------------------------------------------------------------------- */
+typedef struct stowarm_s *stowarm_t;
+
+typedef struct {
+    int32_t num_nodes, horizon, nx, nu;  /* tree and sizes, rules as in sto_tree_desc (nx + nu <= 256) */
+    const int32_t *parent;               /* host [num_nodes] */
+    const double *prob;                  /* host [num_nodes] */
+    int32_t hidden;                      /* 128 or 256 */
+    int32_t batch;                       /* rows per training step: a multiple of 256, at most 65536 */
+    uint64_t seed;                       /* weight initialisation: U(-1/sqrt(fan_in), 1/sqrt(fan_in)) */
+} sto_warm_desc;
+
+/* STO_ERR_INVALID_ARG / STO_ERR_TREE on bad sizes or tree. */
+STO_API sto_status stowarm_create(const sto_warm_desc *desc, stowarm_t *out);
+STO_API void stowarm_destroy(stowarm_t h);
+STO_API sto_status stowarm_dims(stowarm_t h, int32_t *d_in, int32_t *d_out, int64_t *num_params);
+STO_API sto_status stowarm_workspace_size(stowarm_t h, size_t *bytes);
+/* Device workspace (>= workspace_size bytes, 1024-byte aligned, caller-owned); initialises the
+ * weights and the Adam state.  Synchronises. */
+STO_API sto_status stowarm_bind_workspace(stowarm_t h, void *dev_ptr, size_t bytes, sto_stream_t stream);
+/* Host FP32 parameter vector in the order above; set_params also resets the Adam state.
+ * Both synchronise. */
+STO_API sto_status stowarm_set_params(stowarm_t h, const float *params, sto_stream_t stream);
+STO_API sto_status stowarm_get_params(stowarm_t h, float *params, sto_stream_t stream);
+/* Inference on caller features: X device [rows][d_in] FP32 -> Y device [rows][d_out] FP32;
+ * rows <= batch.  Asynchronous. */
+STO_API sto_status stowarm_forward(stowarm_t h, const float *X, int32_t rows, float *Y, sto_stream_t stream);
+/* Loss and gradient (device [num_params] FP32; loss: device scalar, may be NULL) of one batch
+ * of caller rows: X [rows][d_in], targets T [rows][d_out], nvalid [rows] (outputs beyond
+ * nvalid[r] are ignored).  Asynchronous. */
+STO_API sto_status stowarm_gradients(stowarm_t h, const float *X, const float *T, const int32_t *nvalid,
+                                     int32_t rows, float *grad, float *loss, sto_stream_t stream);
+/* One Adam step (beta1 0.9, beta2 0.999, eps 1e-8) on one batch of caller rows.  Asynchronous. */
+STO_API sto_status stowarm_train_batch(stowarm_t h, const float *X, const float *T, const int32_t *nvalid,
+                                       int32_t rows, float lr, sto_stream_t stream);
+/* Training set: num_draws problems on the tree, device FP32 x0 [D][nx], c [D][num_nodes][nx]
+ * (row 0 unused) and, for training, their duals y [D][m] (unscaled, the dual layout of the
+ * single-instance API; may be NULL for prediction only).  The arrays stay caller-owned and
+ * must outlive their use. */
+STO_API sto_status stowarm_set_draws(stowarm_t h, int32_t num_draws, const float *x0, const float *c,
+                                     const float *y);
+/* `steps` Adam steps on batches of (draw, node) samples, each epoch visiting the samples in
+ * the order of a seeded affine permutation of the sample index (the remainder of an epoch
+ * that does not fill a batch is skipped).  loss_hist: device [steps] or NULL.  Replays one
+ * CUDA graph per step; asynchronous. */
+STO_API sto_status stowarm_train(stowarm_t h, int32_t steps, float lr, uint64_t shuffle_seed, float *loss_hist,
+                                 sto_stream_t stream);
+/* Predicted duals of draws [draw0, draw0 + num_draws): y_out device [num_draws][m], unscaled
+ * (sqrt(pi^i) times the predicted ybar^i).  Asynchronous. */
+STO_API sto_status stowarm_predict(stowarm_t h, int32_t draw0, int32_t num_draws, float *y_out,
+                                   sto_stream_t stream);
+/* The tensor-core product used above, on its own: C [M][N] (FP32, row stride ldc) = A B' with
+ * A [M][K] and B [N][K] BF16, row strides lda, ldb (elements, multiples of 8), device pointers
+ * aligned to 16 bytes.  Asynchronous. */
+STO_API sto_status stowarm_gemm_bf16(const void *A, int64_t lda, const void *B, int64_t ldb, float *C, int64_t ldc,
+                                     int32_t M, int32_t N, int32_t K, sto_stream_t stream);
+STO_API const char *stowarm_last_error(stowarm_t h);
+
 #ifdef __cplusplus
 }
 #endif

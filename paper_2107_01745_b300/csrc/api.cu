@@ -178,6 +178,45 @@ const char *stotree_status_str(sto_status s) {
 
 const char *stotree_last_error(stotree_t h) { return h ? h->err.c_str() : ""; }
 
+}  // extern "C"
+
+namespace sto {
+
+// Tree conventions (Section II-A with the numbering of the boundary): root 0 with probability 1,
+// parent[i] < i, stage-major order with the children of a node contiguous, positive
+// probabilities that sum over the children to the parent's, leaves exactly at the last stage.
+sto_status validate_tree(const int32_t *parent, const double *prob, int Nn, int horizon, std::vector<int32_t> &stage,
+                         std::vector<int32_t> &ccnt, std::vector<int32_t> &cbeg) {
+    stage.assign(Nn, 0);
+    ccnt.assign(Nn, 0);
+    cbeg.assign(Nn, 0);
+    if (parent[0] != -1 || std::fabs(prob[0] - 1.0) > 1e-9) return STO_ERR_TREE;
+    for (int i = 1; i < Nn; ++i) {
+        int p = parent[i];
+        if (p < 0 || p >= i) return STO_ERR_TREE;
+        if (i >= 2 && p < parent[i - 1]) return STO_ERR_TREE;  // children contiguous, BFS order
+        stage[i] = stage[p] + 1;
+        if (stage[i] < stage[i - 1]) return STO_ERR_TREE;
+        if (ccnt[p] == 0) cbeg[p] = i;
+        ccnt[p] += 1;
+        if (!(prob[i] > 0.0)) return STO_ERR_TREE;
+    }
+    for (int i = 0; i < Nn; ++i) {
+        const bool leaf = ccnt[i] == 0;
+        if (leaf != (stage[i] == horizon)) return STO_ERR_TREE;
+        if (!leaf) {
+            double s = 0.0;
+            for (int j = cbeg[i]; j < cbeg[i] + ccnt[i]; ++j) s += prob[j];
+            if (std::fabs(s - prob[i]) > 1e-9 * std::fmax(1.0, prob[i])) return STO_ERR_TREE;
+        }
+    }
+    return STO_OK;
+}
+
+}  // namespace sto
+
+extern "C" {
+
 sto_status stotree_create(const sto_tree_desc *t, int32_t precision, stotree_t *out) {
     if (!t || !out || !t->parent || !t->prob) return STO_ERR_INVALID_ARG;
     if (t->nx < 1 || t->nu < 1 || t->nx > kMaxDim || t->nu > kMaxDim || t->num_nodes < 2 ||
@@ -185,27 +224,8 @@ sto_status stotree_create(const sto_tree_desc *t, int32_t precision, stotree_t *
         return STO_ERR_INVALID_ARG;
     if (precision != STO_FP64 && precision != STO_FP32) return STO_ERR_INVALID_ARG;
     const int Nn = t->num_nodes;
-    std::vector<int32_t> stage(Nn, 0), ccnt(Nn, 0), cbeg(Nn, 0);
-    if (t->parent[0] != -1 || std::fabs(t->prob[0] - 1.0) > 1e-9) return STO_ERR_TREE;
-    for (int i = 1; i < Nn; ++i) {
-        int p = t->parent[i];
-        if (p < 0 || p >= i) return STO_ERR_TREE;
-        if (i >= 2 && p < t->parent[i - 1]) return STO_ERR_TREE;  // children contiguous, BFS order
-        stage[i] = stage[p] + 1;
-        if (stage[i] < stage[i - 1]) return STO_ERR_TREE;
-        if (ccnt[p] == 0) cbeg[p] = i;
-        ccnt[p] += 1;
-        if (!(t->prob[i] > 0.0)) return STO_ERR_TREE;
-    }
-    for (int i = 0; i < Nn; ++i) {
-        const bool leaf = ccnt[i] == 0;
-        if (leaf != (stage[i] == t->horizon)) return STO_ERR_TREE;
-        if (!leaf) {
-            double s = 0.0;
-            for (int j = cbeg[i]; j < cbeg[i] + ccnt[i]; ++j) s += t->prob[j];
-            if (std::fabs(s - t->prob[i]) > 1e-9 * std::fmax(1.0, t->prob[i])) return STO_ERR_TREE;
-        }
-    }
+    std::vector<int32_t> stage, ccnt, cbeg;
+    if (validate_tree(t->parent, t->prob, Nn, t->horizon, stage, ccnt, cbeg) != STO_OK) return STO_ERR_TREE;
     stotree_t h = new stotree_s();
     h->Nn = Nn;
     h->N = t->horizon;

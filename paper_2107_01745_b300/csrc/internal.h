@@ -125,6 +125,8 @@ struct stotree_s {
 namespace sto {
 
 sto_status cuda_fail(stotree_t h, cudaError_t e, const char *what);
+sto_status validate_tree(const int32_t *parent, const double *prob, int Nn, int horizon, std::vector<int32_t> &stage,
+                         std::vector<int32_t> &ccnt, std::vector<int32_t> &cbeg);
 #define STO_CUDA(h, call)                                       \
     do {                                                        \
         cudaError_t _e = (call);                                \

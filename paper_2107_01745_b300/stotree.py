@@ -106,6 +106,30 @@ def lib():
         L.stobatch_destroy.restype = None
         L.stobatch_last_error.argtypes = [vp]
         L.stobatch_last_error.restype = ctypes.c_char_p
+        i64, f32, u64 = ctypes.c_int64, ctypes.c_float, ctypes.c_uint64
+        wsigs = {
+            "stowarm_create": [vp, vp],
+            "stowarm_dims": [vp, vp, vp, vp],
+            "stowarm_workspace_size": [vp, vp],
+            "stowarm_bind_workspace": [vp, vp, sz, vp],
+            "stowarm_set_params": [vp, vp, vp],
+            "stowarm_get_params": [vp, vp, vp],
+            "stowarm_forward": [vp, vp, i32, vp, vp],
+            "stowarm_gradients": [vp, vp, vp, vp, i32, vp, vp, vp],
+            "stowarm_train_batch": [vp, vp, vp, vp, i32, f32, vp],
+            "stowarm_set_draws": [vp, i32, vp, vp, vp],
+            "stowarm_train": [vp, i32, f32, u64, vp, vp],
+            "stowarm_predict": [vp, i32, i32, vp, vp],
+            "stowarm_gemm_bf16": [vp, i64, vp, i64, vp, i64, i32, i32, i32, vp],
+        }
+        for name, args in wsigs.items():
+            fn = getattr(L, name)
+            fn.argtypes = args
+            fn.restype = ctypes.c_int
+        L.stowarm_destroy.argtypes = [vp]
+        L.stowarm_destroy.restype = None
+        L.stowarm_last_error.argtypes = [vp]
+        L.stowarm_last_error.restype = ctypes.c_char_p
         _lib = L
     return _lib
 
@@ -118,7 +142,11 @@ def exported_symbols():
                         "stotree_get_timing", "stotree_solve_bytes", "stotree_status_str", "stotree_last_error",
                         "stobatch_create", "stobatch_destroy", "stobatch_sizes", "stobatch_workspace_size",
                         "stobatch_bind_workspace", "stobatch_set_instance", "stobatch_factor",
-                        "stobatch_solve_step", "stobatch_nama_solve", "stobatch_last_error")]
+                        "stobatch_solve_step", "stobatch_nama_solve", "stobatch_last_error",
+                        "stowarm_create", "stowarm_destroy", "stowarm_dims", "stowarm_workspace_size",
+                        "stowarm_bind_workspace", "stowarm_set_params", "stowarm_get_params", "stowarm_forward",
+                        "stowarm_gradients", "stowarm_train_batch", "stowarm_set_draws", "stowarm_train",
+                        "stowarm_predict", "stowarm_gemm_bf16", "stowarm_last_error")]
 
 
 def _np_ptr(a):
@@ -395,3 +423,136 @@ class StoBatch:
             out.append(st.estimate_lambda(r0, iters=iters, safety=safety)[0])
             st.close()
         return np.array(out)
+
+
+class _WarmDesc(ctypes.Structure):
+    _fields_ = [("num_nodes", ctypes.c_int32), ("horizon", ctypes.c_int32), ("nx", ctypes.c_int32),
+                ("nu", ctypes.c_int32), ("parent", ctypes.c_void_p), ("prob", ctypes.c_void_p),
+                ("hidden", ctypes.c_int32), ("batch", ctypes.c_int32), ("seed", ctypes.c_uint64)]
+
+
+def gemm_bf16(A, B):
+    """C = A B' on the tensor cores: A [M, K], B [N, K] BF16 CUDA tensors -> FP32 [M, N]."""
+    M, K = A.shape
+    N = B.shape[0]
+    C = torch.empty(M, N, dtype=torch.float32, device=A.device)
+    code = lib().stowarm_gemm_bf16(_t_ptr(A), A.stride(0), _t_ptr(B), B.stride(0), _t_ptr(C), C.stride(0), M, N, K,
+                                   _stream())
+    if code != 0:
+        raise StoError(code, "stowarm_gemm_bf16")
+    return C
+
+
+class StoWarm:
+    """Learned warm start (per-node perceptron on the tensor cores) for problems on one tree."""
+
+    def __init__(self, tree, nx, nu, hidden=256, batch=8192, seed=0, device="cuda:0"):
+        self.device = torch.device(device)
+        self.tree = tree
+        parent = np.ascontiguousarray(tree.parent, dtype=np.int32)
+        prob = np.ascontiguousarray(tree.prob, dtype=np.float64)
+        st = np.zeros(len(parent), dtype=np.int64)
+        for i in range(1, len(parent)):
+            st[i] = st[parent[i]] + 1
+        horizon = int(st.max())
+        nonleaf = np.zeros(len(parent), dtype=bool)
+        nonleaf[parent[1:]] = True
+        self.m = int(nonleaf.sum()) * (nx + nu) + int((~nonleaf).sum()) * nx
+        d = _WarmDesc(len(parent), horizon, nx, nu, parent.ctypes.data, prob.ctypes.data, hidden, batch, seed)
+        h = ctypes.c_void_p()
+        L = lib()
+        code = L.stowarm_create(ctypes.byref(d), ctypes.byref(h))
+        if code != 0:
+            raise StoError(code, "stowarm_create")
+        self.h = h
+        di, do, npar = ctypes.c_int32(), ctypes.c_int32(), ctypes.c_int64()
+        L.stowarm_dims(h, ctypes.byref(di), ctypes.byref(do), ctypes.byref(npar))
+        self.d_in, self.d_out, self.num_params = di.value, do.value, npar.value
+        self.nx, self.nu, self.hidden, self.batch = nx, nu, hidden, batch
+        wb = ctypes.c_size_t()
+        L.stowarm_workspace_size(h, ctypes.byref(wb))
+        with torch.cuda.device(self.device):
+            self._raw = torch.empty(wb.value + 1024, dtype=torch.uint8, device=self.device)
+            off = (-self._raw.data_ptr()) % 1024
+            self.ws = self._raw[off:off + wb.value]
+            self._check(L.stowarm_bind_workspace(h, _t_ptr(self.ws), wb.value, _stream()), "bind")
+        self._draws = None
+
+    def _check(self, code, where):
+        if code != 0:
+            raise StoError(code, where, lib().stowarm_last_error(self.h).decode())
+
+    def close(self):
+        if getattr(self, "h", None):
+            lib().stowarm_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def params(self):
+        p = np.empty(self.num_params, dtype=np.float32)
+        self._check(lib().stowarm_get_params(self.h, _np_ptr(p), _stream()), "get_params")
+        return p
+
+    def set_params(self, p):
+        p = np.ascontiguousarray(p, dtype=np.float32)
+        assert p.size == self.num_params
+        self._check(lib().stowarm_set_params(self.h, _np_ptr(p), _stream()), "set_params")
+
+    def unflatten(self, p):
+        """Parameter vector -> dict in the oracle's shapes."""
+        H, di, do = self.hidden, self.d_in, self.d_out
+        out, k = {}, 0
+        for name, shape in (("W1", (H, di)), ("b1", (H,)), ("W2", (H, H)), ("b2", (H,)), ("W3", (do, H)),
+                            ("b3", (do,))):
+            n = int(np.prod(shape))
+            out[name] = np.asarray(p[k:k + n]).reshape(shape)
+            k += n
+        return out
+
+    @staticmethod
+    def flatten(d):
+        return np.concatenate([np.ravel(d[k]) for k in ("W1", "b1", "W2", "b2", "W3", "b3")])
+
+    def forward(self, X):
+        X = X.contiguous().float()
+        Y = torch.empty(X.shape[0], self.d_out, dtype=torch.float32, device=self.device)
+        self._check(lib().stowarm_forward(self.h, _t_ptr(X), X.shape[0], _t_ptr(Y), _stream()), "forward")
+        return Y
+
+    def gradients(self, X, T, nvalid):
+        X, T = X.contiguous().float(), T.contiguous().float()
+        nv = nvalid.contiguous().to(torch.int32)
+        g = torch.empty(self.num_params, dtype=torch.float32, device=self.device)
+        loss = torch.empty(1, dtype=torch.float32, device=self.device)
+        self._check(lib().stowarm_gradients(self.h, _t_ptr(X), _t_ptr(T), _t_ptr(nv), X.shape[0], _t_ptr(g),
+                                            _t_ptr(loss), _stream()), "gradients")
+        return g, float(loss.item())
+
+    def train_batch(self, X, T, nvalid, lr=1e-3):
+        X, T = X.contiguous().float(), T.contiguous().float()
+        nv = nvalid.contiguous().to(torch.int32)
+        self._check(lib().stowarm_train_batch(self.h, _t_ptr(X), _t_ptr(T), _t_ptr(nv), X.shape[0], lr, _stream()),
+                    "train_batch")
+
+    def set_draws(self, x0, c, y=None):
+        """x0 [D, nx], c [D, Nn, nx], y [D, m] (unscaled duals) FP32 device tensors (kept alive here)."""
+        self._draws = (x0.contiguous().float(), c.contiguous().float(), None if y is None else y.contiguous().float())
+        x0, c, y = self._draws
+        self._check(lib().stowarm_set_draws(self.h, x0.shape[0], _t_ptr(x0), _t_ptr(c), _t_ptr(y)), "set_draws")
+
+    def train(self, steps, lr=1e-3, seed=0):
+        hist = torch.empty(max(steps, 1), dtype=torch.float32, device=self.device)
+        self._check(lib().stowarm_train(self.h, steps, lr, seed, _t_ptr(hist), _stream()), "train")
+        return hist[:steps]
+
+    def predict(self, draw0, num_draws, out=None):
+        """Predicted unscaled duals of draws [draw0, draw0 + num_draws) as [num_draws, m]."""
+        if out is None:
+            out = torch.zeros(num_draws, self.m, dtype=torch.float32, device=self.device)
+        self._check(lib().stowarm_predict(self.h, draw0, num_draws, _t_ptr(out), _stream()), "predict")
+        return out

@@ -21,6 +21,7 @@ constraints on x and u are shared vectors.
 """
 from __future__ import annotations
 
+import dataclasses
 import json
 import os
 from dataclasses import dataclass, field
@@ -387,3 +388,50 @@ def batched_small(seed: int = 30, instances: int = 3):
     rng = np.random.default_rng(seed)
     return [make_group(rng, 4, 2, 2, 3, 2, instances), make_group(rng, 6, 3, 1, 4, 2, instances),
             make_group(rng, 3, 2, 3, 5, 3, instances)]
+
+
+# Warm-start workload: horizon 15, branching 4 for the first 4 stages (256 scenarios, 3157 nodes),
+# nx = 20, nu = 10, the tiny workload's recipe for A, B and the costs.  The input box is
+# |u| <= 0.3 (|x| <= 5 as in the tiny workload): with |u| <= 1 the box almost never binds at
+# this size (B ~ N(0,1) with 10 inputs), NAMA stops after 0-2 iterations and there is nothing
+# for a warm start to save.
+WARM_SHAPE = dict(horizon=15, branching=4, branch_stages=4, nx=20, nu=10)
+WARM_UMAX = 0.3
+WARM_TRAIN_SEED = 40000
+WARM_EVAL_SEED = 90000
+
+
+def warm_start_system(seed: int = 4) -> Group:
+    """Shared data of the warm-start workload (no instances yet).  Draw order: A, B."""
+    rng = np.random.default_rng(seed)
+    nx, nu = WARM_SHAPE["nx"], WARM_SHAPE["nu"]
+    A = spectral_rescale(rng.standard_normal((nx, nx)), 0.95)
+    B = rng.standard_normal((nx, nu))
+    nn = tree_from_branching([WARM_SHAPE["branching"]] * WARM_SHAPE["branch_stages"] +
+                             [1] * (WARM_SHAPE["horizon"] - WARM_SHAPE["branch_stages"])).num_nodes
+    return Group(horizon=WARM_SHAPE["horizon"], branching=WARM_SHAPE["branching"],
+                 branch_stages=WARM_SHAPE["branch_stages"], nx=nx, nu=nu, A=A, B=B,
+                 Q=np.ones(nx), R=0.1 * np.ones(nu), PN=np.ones(nx),
+                 xlo=-5.0 * np.ones(nx), xhi=5.0 * np.ones(nx), ulo=-WARM_UMAX * np.ones(nu),
+                 uhi=WARM_UMAX * np.ones(nu), x0=np.zeros((0, nx)), c=np.zeros((0, nn, nx)))
+
+
+def warm_start_draws(system: Group, first_seed: int, count: int, dtype=np.float64) -> Group:
+    """`count` draws of the warm-start workload; draw k uses its own generator seeded
+    first_seed + k (x0 ~ U[-3, 3], then c ~ N(0, 0.1^2) per node, c[0] = 0), so any single
+    draw can be regenerated on its own."""
+    from concurrent.futures import ThreadPoolExecutor
+    nx = system.nx
+    nn = system.c.shape[1]
+    x0 = np.empty((count, nx), dtype=dtype)
+    c = np.empty((count, nn, nx), dtype=dtype)
+
+    def one(k):
+        r = np.random.default_rng(first_seed + k)
+        x0[k] = r.uniform(-3.0, 3.0, size=nx)
+        c[k] = 0.1 * r.standard_normal((nn, nx))
+        c[k, 0] = 0.0
+
+    with ThreadPoolExecutor(min(16, os.cpu_count() or 1)) as ex:
+        list(ex.map(one, range(count)))
+    return dataclasses.replace(system, x0=x0, c=c)

@@ -12,7 +12,7 @@ from tests.conftest import ROOT
 
 def _declared():
     src = open(os.path.join(ROOT, "include", "stotree.h")).read()
-    return sorted(set(re.findall(r"STO_API\s+[^;]*?\b(sto(?:tree|batch)_\w+)\s*\(", src)))
+    return sorted(set(re.findall(r"STO_API\s+[^;]*?\b(sto(?:tree|batch|warm)_\w+)\s*\(", src)))
 
 
 @pytest.fixture(scope="module")
