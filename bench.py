@@ -225,6 +225,7 @@ def run_ours(args):
     d2h = 4 * (st.m + st.Nn * st.nx + st.Np * st.nu)
 
     batched = run_batched(dev, max(1, min(args.steps, 3)))
+    warm = run_warm(dev, args.warm_train_draws, 512) if args.warm_train_draws > 0 else None
     line = None
     if rank == 0:
         cpu = cpu_baseline(p, lam, nama_infos[0]["iters"])
@@ -251,6 +252,7 @@ def run_ours(args):
             "e2e": {"value": round(e2e_ms, 4), "unit": "ms", "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
             "gpu_launches": launches,
             "batched": batched,
+            "warm_start": warm,
             "clocks": clk.summary(),
             "cpu_baseline": cpu,
         }
@@ -258,6 +260,53 @@ def run_ours(args):
         pg.barrier()
         pg.destroy_process_group()
     return line
+
+
+def run_warm(dev, train_draws, eval_draws):
+    """Learned warm start on the warm-start workload: labels from the batched NAMA, Adam training
+    of the tensor-core perceptron, then batched NAMA on held-out draws from y0 = 0 and from the
+    learned start (inference and the phi fallback test counted in the warm time)."""
+    import torch
+    from paper_2107_01745_b300 import warmstart as WS
+    from paper_2107_01745_b300 import workloads as W
+    system = W.warm_start_system(4)
+    lam = WS.batch_lambda(system, device=dev)
+    t0 = time.time()
+    data = WS.make_dataset(system, W.WARM_TRAIN_SEED, train_draws, lam, device=dev)
+    label_s = time.time() - t0
+    label_solve_ms, label_iters = data["solve_ms"], float(data["iters"].mean())
+    starter = WS.WarmStarter(system, hidden=256, batch=8192, seed=0, device=dev)
+    fit = starter.fit(data, epochs=10, lr=1e-3)
+    del data
+    ev = WS.EvalSet(W.warm_start_draws(system, W.WARM_EVAL_SEED, eval_draws, dtype=np.float32), lam, device=dev)
+    WS.warm_vs_cold(starter, ev)  # warm-up (graph capture)
+    r = WS.warm_vs_cold(starter, ev)
+    ev.close()
+    net = starter.net
+    # algorithmic FLOPs of one training step (unpadded widths): forward 3 products, backward 2
+    # data products (no input gradient) and 3 weight products
+    flops = 2.0 * net.batch * (2 * net.d_in * net.hidden + 3 * net.hidden ** 2 + 3 * net.hidden * net.d_out)
+    step_ms = fit["ms"] / max(1, fit["steps"])
+    peaks = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json"))) if os.path.exists(
+        os.path.join(ROOT, "MEASURED_PEAKS.json")) else {}
+    peak = float(peaks.get("bf16_tflops_sustained", 1400.0))
+    achieved = flops / (step_ms * 1e-3) / 1e12
+    L = fit["loss"]
+    return {"workload": "warm start: horizon 15, branching 4 for stages 0-3 (256 scenarios, 3157 nodes), nx=20, "
+                        "nu=10, shared A (rho 0.95), B ~ N(0,1), Q=I, R=0.1I, P_N=I, |u|<=0.3, |x|<=5, per draw "
+                        "x0 ~ U[-3,3], c ~ N(0,0.1^2), seed 4; train draws seeds 40000+, eval draws 90000+",
+            "train_draws": train_draws, "eval_draws": eval_draws, "label_s": round(label_s, 2),
+            "label_solve_ms": round(label_solve_ms, 1), "label_iters_mean": label_iters,
+            "train_steps": fit["steps"], "train_ms": round(fit["ms"], 1), "train_step_us": round(1e3 * step_ms, 1),
+            "loss_first": float(L[:10].mean()), "loss_last": float(L[-100:].mean()),
+            "train_roofline": {"bound": "tensor", "achieved": round(achieved, 2), "peak": peak, "unit": "TFLOP/s",
+                               "frac": round(achieved / peak, 4), "peak_source": "measured bf16 sustained" if peaks
+                               else "fallback", "flops_per_step": flops},
+            "cold_ms": round(r["cold_ms"], 2), "warm_ms": round(r["warm_ms"], 2),
+            "warm_infer_ms": round(r["warm_infer_ms"], 2), "warm_fallback_test_ms": round(r["warm_fallback_test_ms"], 2),
+            "cold_iters_mean": r["cold_iters_mean"], "warm_iters_mean": r["warm_iters_mean"],
+            "cold_iters_max": r["cold_iters_max"], "warm_iters_max": r["warm_iters_max"],
+            "fallbacks": r["fallbacks"], "all_converged": r["converged"]}
 
 
 def run_batched(dev, steps):
@@ -381,6 +430,8 @@ def main():
     ap.add_argument("--steps", type=int, default=5)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--warm-train-draws", type=int, default=8192,
+                    help="training draws of the learned warm start (0 skips it)")
     ap.add_argument("--profile", choices=["nama", "minfbe"], default=None,
                     help="run one solve inside a profiler range (no JSON benchmark line)")
     args = ap.parse_args()

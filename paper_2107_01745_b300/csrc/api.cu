@@ -4,6 +4,9 @@
 #include <cstdio>
 #include <cstring>
 
+#include <map>
+#include <mutex>
+
 #include "internal.h"
 
 using namespace sto;
@@ -181,6 +184,20 @@ const char *stotree_last_error(stotree_t h) { return h ? h->err.c_str() : ""; }
 }  // extern "C"
 
 namespace sto {
+
+cudaError_t raise_smem_cap(const void *func, size_t bytes) {
+    static std::mutex mu;
+    static std::map<std::pair<int, const void *>, size_t> caps;
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return e;
+    std::lock_guard<std::mutex> lock(mu);
+    size_t &cap = caps[{dev, func}];
+    if (bytes <= cap) return cudaSuccess;
+    e = cudaFuncSetAttribute(func, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
+    if (e == cudaSuccess) cap = bytes;
+    return e;
+}
 
 // Tree conventions (Section II-A with the numbering of the boundary): root 0 with probability 1,
 // parent[i] < i, stage-major order with the children of a node contiguous, positive

@@ -83,11 +83,6 @@ __device__ __forceinline__ double wmax(double v) {
 __device__ __forceinline__ long long doff(const GroupDev &g, int i) {
     return i < g.Np ? (long long)i * g.nxu : (long long)g.Np * g.nxu + (long long)(i - g.Np) * g.nx;
 }
-__device__ __forceinline__ int stage_of(const GroupDev &g, int i) {
-    int t = 0;
-    while (t < g.N && g.soff[t + 1] <= i) ++t;
-    return t;
-}
 
 // ---------------------------------------------------------------------------------------------
 // Solve rounds.  A task is a tile of up to kTC columns of one (group, stage); column c of a stage
@@ -1207,8 +1202,8 @@ namespace {
 
 template <int NR>
 void launch_round(stobatch_t b, const RoundArgs<NR> &a, cudaStream_t st) {
-    cudaFuncSetAttribute(k_bbwd<NR>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bwd_smem<NR>());
-    cudaFuncSetAttribute(k_bfwd<NR>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)fwd_smem<NR>());
+    raise_smem_cap((const void *)k_bbwd<NR>, bwd_smem<NR>());
+    raise_smem_cap((const void *)k_bfwd<NR>, fwd_smem<NR>());
     for (size_t p = 0; p + 1 < b->bwd_phase.size(); ++p) {
         const int t0 = b->bwd_phase[p], nt = b->bwd_phase[p + 1] - t0;
         if (nt > 0) k_bbwd<NR><<<nt, kBT, bwd_smem<NR>(), st>>>(a, t0);

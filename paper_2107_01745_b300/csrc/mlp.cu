@@ -31,6 +31,8 @@ namespace {
 constexpr int kBM = 128;     // rows of an output tile (one TMEM lane per row)
 constexpr int kBK = 64;      // K per stage: one 128-byte swizzle atom of BF16
 constexpr int kStages = 4;   // shared-memory ring depth
+constexpr int kThreads = 256; // 8 warps: 2 per TMEM lane quarter in the epilogue
+constexpr int kMaxBN = 64;   // column tile of the network's products (more CTAs for the epilogues)
 constexpr int kSplitK = 256; // batch rows per CTA in the weight-gradient products
 constexpr unsigned long long kMmaWaitNs = 1000000000ull;  // bounded waits: 1 s
 constexpr float kGeluC = 0.7978845608028654f;            // sqrt(2/pi)
@@ -169,12 +171,13 @@ struct EpiArgs {
 };
 
 template <int EPI>
-__global__ void __launch_bounds__(128, 1)
+__global__ void __launch_bounds__(kThreads, 1)
     k_umma(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB, int BN, int nk,
            unsigned tmem_cols, EpiArgs ep) {
     __shared__ __align__(8) uint64_t full[kStages], empty[kStages], done;
     __shared__ uint32_t tmem_slot;
     __shared__ volatile int abort_flag;
+    __shared__ float sbias[256];
     extern __shared__ uint8_t dsm_raw[];
     uint8_t *dsm = reinterpret_cast<uint8_t *>((reinterpret_cast<uintptr_t>(dsm_raw) + 1023) & ~uintptr_t(1023));
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
@@ -193,6 +196,8 @@ __global__ void __launch_bounds__(128, 1)
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     }
     if (warp == 1) tmem_alloc(&tmem_slot, tmem_cols);
+    if (EPI == EPI_GELU || EPI == EPI_OUT || EPI == EPI_PRED)
+        for (int i = threadIdx.x; i < BN; i += kThreads) sbias[i] = ep.bias[n0 + i];
     tc_fence_before();
     __syncthreads();
     tc_fence_after();
@@ -223,11 +228,15 @@ __global__ void __launch_bounds__(128, 1)
     __syncwarp();
     const bool ok = mb_wait(&done, 0, &abort_flag, ep.err);
     tc_fence_after();
-    const int row = m0 + warp * 32 + lane;
-    const uint32_t trow = tbase + ((uint32_t)(warp * 32) << 16);
+    // warp w reads TMEM lanes 32 (w % 4) .. + 31 (its rows) and the (w / 4)-th half of the columns
+    const int quarter = warp & 3, half = warp >> 2;
+    const int row = m0 + quarter * 32 + lane;
+    const uint32_t trow = tbase + ((uint32_t)(quarter * 32) << 16);
+    const int hc = (BN + 31) / 32 * 16;
+    const int c_begin = half * hc, c_end = min(BN, (half + 1) * hc);
     float sq_err = 0.f;
     if (ok) {
-        for (int c0 = 0; c0 < BN; c0 += 16) {
+        for (int c0 = c_begin; c0 < c_end; c0 += 16) {
             float v[16];
             tmem_ld16(trow + (uint32_t)c0, v);
             const int nb = n0 + c0;
@@ -244,7 +253,7 @@ __global__ void __launch_bounds__(128, 1)
                 __align__(16) __nv_bfloat16 a[16];
 #pragma unroll
                 for (int j = 0; j < 16; ++j) {
-                    const float zz = v[j] + ep.bias[nb + j];
+                    const float zz = v[j] + sbias[c0 + j];
                     v[j] = zz;
                     a[j] = __float2bfloat16_rn(gelu_f(zz));
                 }
@@ -280,7 +289,7 @@ __global__ void __launch_bounds__(128, 1)
                 __align__(16) __nv_bfloat16 d[16];
 #pragma unroll
                 for (int j = 0; j < 16; ++j) {
-                    const float yy = v[j] + ep.bias[nb + j];
+                    const float yy = v[j] + sbias[c0 + j];
                     y[j] = yy;
                     const float diff = nb + j < nv ? yy - ep.T[(long long)row * ep.ldt + nb + j] : 0.f;
                     sq_err += diff * diff;
@@ -297,7 +306,7 @@ __global__ void __launch_bounds__(128, 1)
                 if (off >= 0) {
                     const float sq = ep.row_sq[row];
                     for (int j = 0; j < 16; ++j)
-                        if (nb + j < nv) ep.yout[off + nb + j] = sq * (v[j] + ep.bias[nb + j]);
+                        if (nb + j < nv) ep.yout[off + nb + j] = sq * (v[j] + sbias[c0 + j]);
                 }
             }
         }
@@ -305,7 +314,7 @@ __global__ void __launch_bounds__(128, 1)
     if (EPI == EPI_OUT) {
 #pragma unroll
         for (int o = 16; o > 0; o >>= 1) sq_err += __shfl_xor_sync(0xffffffffu, sq_err, o);
-        if (lane == 0) ep.loss_part[(blockIdx.x * gridDim.y + blockIdx.y) * 4 + warp] = sq_err;
+        if (lane == 0) ep.loss_part[(blockIdx.x * gridDim.y + blockIdx.y) * 8 + warp] = sq_err;
     }
     tc_fence_before();
     __syncthreads();
@@ -365,10 +374,10 @@ struct Gemm {
 
 template <int EPI>
 cudaError_t run_gemm(const Gemm &g, const EpiArgs &ep, cudaStream_t st) {
-    const size_t sm = umma_smem(g.BN, g.nk);
-    cudaError_t e = cudaFuncSetAttribute(k_umma<EPI>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+    cudaError_t e = raise_smem_cap((const void *)k_umma<EPI>, umma_smem(g.BN, g.nk));
     if (e != cudaSuccess) return e;
-    k_umma<EPI><<<g.grid, 128, sm, st>>>(g.a, g.b, g.BN, g.nk, tmem_cols_for(g.BN), ep);
+    const size_t sm = umma_smem(g.BN, g.nk);
+    k_umma<EPI><<<g.grid, kThreads, sm, st>>>(g.a, g.b, g.BN, g.nk, tmem_cols_for(g.BN), ep);
     return cudaGetLastError();
 }
 
@@ -392,13 +401,14 @@ struct NetDev {
     __nv_bfloat16 *X, *XT;
     float *T;
     int *nvalid, *count, *tstep;
+    double *adam_pow;  // beta1^t, beta2^t after t steps
     long long *row_off;
     float *row_sq;
     float *Z1, *Z2, *Y;
     __nv_bfloat16 *A1, *A1T, *A2, *A2T, *dY, *dYT, *dZ2, *dZ2T, *dZ1T;
     float *P1, *P2, *P3;   // weight-gradient partials [S][H][D0], [S][H][H], [S][H][DO]
     float *gbias;          // [DO | H | H]: bias gradients of layers 3, 2, 1
-    float *loss_part;      // [B/128 * 4]
+    float *loss_part;      // [B/128 * 8]: per (row tile, warp) of the output product
     const NodeInfo *nodes;
     long long *perm;       // per epoch: multiplier, offset
     int *err;
@@ -412,26 +422,32 @@ __host__ __device__ inline long long w3_off(const NetDev &n) { return b2_off(n) 
 __host__ __device__ inline long long b3_off(const NetDev &n) { return w3_off(n) + (long long)n.DO * n.H; }
 __host__ __device__ inline long long nparam_padded(const NetDev &n) { return b3_off(n) + n.DO; }
 
-// One batch row per thread: the (draw, node) sample's features, target and valid count.
-// mode 0: training sample from the permutation of epoch e; mode 1: sample index base + b
-// (prediction); past the end of the samples a row is all zeros with nvalid = 0.
-__global__ void k_gather(NetDev n, const float *x0, const float *c, const float *y, long long num_samples,
-                         long long base, long long steps_per_epoch, int t0, int mode, int draw0) {
-    const int b = blockIdx.x * blockDim.x + threadIdx.x;
+// Batch rows of (draw, node) samples: features, target and valid count; one warp per row, 32
+// rows per block, the transposed copy staged in shared memory so both copies are written in
+// contiguous runs.  mode 0: training sample from the permutation of the current epoch; mode 1:
+// sample index base + b (prediction).  Past the end of the samples a row is zeros, nvalid 0.
+constexpr int kGatherRows = 16;
+__global__ void __launch_bounds__(256) k_gather(NetDev n, const float *x0, const float *c, const float *y,
+                                                long long num_samples, long long base, long long steps_per_epoch,
+                                                int t0, int mode, int draw0) {
+    __shared__ __nv_bfloat16 tile[256][kGatherRows + 2];
     __shared__ int cnt;
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int b0 = blockIdx.x * kGatherRows;
     if (threadIdx.x == 0) cnt = 0;
     __syncthreads();
-    if (b < n.B) {
+    const long long st = mode == 0 ? (long long)(*n.tstep - t0) : 0;
+    for (int rr = warp; rr < kGatherRows; rr += blockDim.x / 32) {
+        const int b = b0 + rr;
         long long j = -1;
         if (mode == 0) {
-            const long long st = *n.tstep - t0;
             const long long e = st / steps_per_epoch, k = (st % steps_per_epoch) * n.B + b;
-            j = (long long)(((unsigned long long)n.perm[2 * e] * (unsigned long long)k + (unsigned long long)n.perm[2 * e + 1]) %
+            j = (long long)(((unsigned long long)n.perm[2 * e] * (unsigned long long)k +
+                             (unsigned long long)n.perm[2 * e + 1]) %
                             (unsigned long long)num_samples);
         } else if (base + b < num_samples) {
             j = base + b;
         }
-        __align__(16) __nv_bfloat16 row[8];
         int nv = 0;
         long long off = -1;
         float sq = 1.f;
@@ -442,45 +458,46 @@ __global__ void k_gather(NetDev n, const float *x0, const float *c, const float 
             nv = ni.nvalid;
             sq = ni.sq;
             off = (d - (mode == 1 ? draw0 : 0)) * n.m + ni.doff;
-            // features: x0 | t/N | c^i | c^anc | c^anc^2
-            int anc[3] = {i, -1, -1};
-            anc[1] = i > 0 ? ni.parent : -1;
-            anc[2] = anc[1] > 0 ? n.nodes[anc[1]].parent : -1;
-            for (int f0 = 0; f0 < n.D0; f0 += 8) {
-#pragma unroll
-                for (int q = 0; q < 8; ++q) {
-                    const int f = f0 + q;
-                    float v = 0.f;
-                    if (f < n.nx) {
-                        v = x0[d * n.nx + f];
-                    } else if (f == n.nx) {
-                        v = (float)ni.stage / (float)n.horizon;
-                    } else if (f < n.d_in) {
-                        const int a = (f - n.nx - 1) / n.nx, r = (f - n.nx - 1) % n.nx;
-                        const int node = anc[a];
-                        if (node > 0) v = c[(d * n.Nn + node) * n.nx + r];
-                    }
-                    row[q] = __float2bfloat16_rn(v);
-                    n.XT[(long long)f * n.B + b] = row[q];
+            const int anc1 = i > 0 ? ni.parent : -1;
+            const int anc2 = anc1 > 0 ? n.nodes[anc1].parent : -1;
+            // features: x0 | t/N | c^i | c^anc | c^anc^2 (zeros for the root and missing ancestors)
+            for (int f = lane; f < n.D0; f += 32) {
+                float v = 0.f;
+                if (f < n.nx) {
+                    v = x0[d * n.nx + f];
+                } else if (f == n.nx) {
+                    v = (float)ni.stage / (float)n.horizon;
+                } else if (f < n.d_in) {
+                    const int a = (f - n.nx - 1) / n.nx, r = (f - n.nx - 1) % n.nx;
+                    const int node = a == 0 ? i : (a == 1 ? anc1 : anc2);
+                    if (node > 0) v = c[(d * n.Nn + node) * n.nx + r];
                 }
-                *reinterpret_cast<uint4 *>(n.X + (long long)b * n.D0 + f0) = *reinterpret_cast<uint4 *>(row);
+                const __nv_bfloat16 bv = __float2bfloat16_rn(v);
+                n.X[(long long)b * n.D0 + f] = bv;
+                tile[f][rr] = bv;
             }
             if (y)
-                for (int k = 0; k < n.DO; ++k)
+                for (int k = lane; k < n.DO; k += 32)
                     n.T[(long long)b * n.DO + k] = k < nv ? y[d * n.m + ni.doff + k] / ni.sq : 0.f;
         } else {
-            for (int f = 0; f < n.D0; ++f) {
+            for (int f = lane; f < n.D0; f += 32) {
                 n.X[(long long)b * n.D0 + f] = __float2bfloat16_rn(0.f);
-                n.XT[(long long)f * n.B + b] = __float2bfloat16_rn(0.f);
+                tile[f][rr] = __float2bfloat16_rn(0.f);
             }
-            for (int k = 0; k < n.DO; ++k) n.T[(long long)b * n.DO + k] = 0.f;
+            for (int k = lane; k < n.DO; k += 32) n.T[(long long)b * n.DO + k] = 0.f;
         }
-        n.nvalid[b] = nv;
-        n.row_off[b] = off;
-        n.row_sq[b] = sq;
-        atomicAdd(&cnt, nv);
+        if (lane == 0) {
+            n.nvalid[b] = nv;
+            n.row_off[b] = off;
+            n.row_sq[b] = sq;
+            atomicAdd(&cnt, nv);
+        }
     }
     __syncthreads();
+    for (int e = threadIdx.x; e < n.D0 * kGatherRows; e += blockDim.x) {
+        const int f = e / kGatherRows, rr = e % kGatherRows;
+        n.XT[(long long)f * n.B + b0 + rr] = tile[f][rr];
+    }
     if (threadIdx.x == 0) atomicAdd(n.count, cnt);   // integer sums: order-independent
 }
 
@@ -518,8 +535,15 @@ __global__ void k_bias_grad(NetDev n) {
     const __nv_bfloat16 *src = r < n.DO ? n.dYT + (long long)r * n.B
                                         : (r < n.DO + n.H ? n.dZ2T + (long long)(r - n.DO) * n.B
                                                           : n.dZ1T + (long long)(r - n.DO - n.H) * n.B);
+    const uint4 *src4 = reinterpret_cast<const uint4 *>(src);   // B is a multiple of 256
     float s = 0.f;
-    for (int b = lane; b < n.B; b += 32) s += __bfloat162float(src[b]);
+#pragma unroll 8
+    for (int q = lane; q < n.B / 8; q += 32) {
+        const uint4 u = src4[q];
+        const __nv_bfloat16 *hv = reinterpret_cast<const __nv_bfloat16 *>(&u);
+#pragma unroll
+        for (int k = 0; k < 8; ++k) s += __bfloat162float(hv[k]);
+    }
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
     if (lane == 0) n.gbias[r] = s;
@@ -531,11 +555,13 @@ __device__ __forceinline__ float param_grad(const NetDev &n, long long p) {
     if (p < b1_off(n)) {
         const long long o = p / n.D0, i = p % n.D0;
         if (i < n.d_in)
+            #pragma unroll 8
             for (int s = 0; s < n.S; ++s) g += n.P1[((long long)s * n.H + o) * n.D0 + i];
     } else if (p < w2_off(n)) {
         g = n.gbias[n.DO + n.H + (p - b1_off(n))];
     } else if (p < b2_off(n)) {
         const long long q = p - w2_off(n), o = q / n.H, i = q % n.H;
+#pragma unroll 8
         for (int s = 0; s < n.S; ++s) g += n.P2[((long long)s * n.H + o) * n.H + i];
     } else if (p < w3_off(n)) {
         g = n.gbias[n.DO + (p - b2_off(n))];
@@ -571,7 +597,7 @@ __global__ void k_adam(NetDev n, int mode, float lr, float *grad, float *loss, f
     const int t = *n.tstep;
     if (p == 0 && (loss || loss_hist)) {
         float s = 0.f;
-        for (int k = 0; k < (n.B / kBM) * 4; ++k) s += n.loss_part[k];
+        for (int k = 0; k < (n.B / kBM) * 8; ++k) s += n.loss_part[k];
         const float l = s / (float)max(1, *n.count);
         if (loss) *loss = l;
         if (loss_hist) loss_hist[t - t0] = l;
@@ -602,7 +628,8 @@ __global__ void k_adam(NetDev n, int mode, float lr, float *grad, float *loss, f
     const float v = b2 * n.vel[p] + (1.f - b2) * g * g;
     n.mom[p] = m;
     n.vel[p] = v;
-    const float c1 = 1.f - powf(b1, (float)(t + 1)), c2 = 1.f - powf(b2, (float)(t + 1));
+    // bias corrections 1 - beta^(t+1) from the running powers (no per-thread pow)
+    const float c1 = (float)(1.0 - n.adam_pow[0] * 0.9), c2 = (float)(1.0 - n.adam_pow[1] * 0.999);
     const float w = n.W[p] - lr * (m / c1) / (sqrtf(v / c2) + eps);
     n.W[p] = w;
     write_bf16_copies(n, p, w);
@@ -616,6 +643,13 @@ __global__ void k_refresh_bf16(NetDev n) {
 __global__ void k_tick(NetDev n) {
     *n.tstep += 1;
     *n.count = 0;
+    n.adam_pow[0] *= 0.9;
+    n.adam_pow[1] *= 0.999;
+}
+__global__ void k_reset_step(NetDev n) {
+    *n.tstep = 0;
+    n.adam_pow[0] = 1.0;
+    n.adam_pow[1] = 1.0;
 }
 __global__ void k_zero_count(NetDev n) { *n.count = 0; }
 
@@ -634,7 +668,7 @@ struct stowarm_s {
     size_t total = 0;
     std::vector<std::pair<size_t *, size_t>> layout;
     size_t o_W, o_mom, o_vel, o_W1b, o_W2b, o_W3b, o_W2bT, o_W3bT, o_X, o_XT, o_T, o_nv, o_cnt, o_t, o_roff, o_rsq,
-        o_Z1, o_Z2, o_Y, o_A1, o_A1T, o_A2, o_A2T, o_dY, o_dYT, o_dZ2, o_dZ2T, o_dZ1T, o_P1, o_P2, o_P3, o_gb, o_lp,
+        o_pow, o_Z1, o_Z2, o_Y, o_A1, o_A1T, o_A2, o_A2T, o_dY, o_dYT, o_dZ2, o_dZ2T, o_dZ1T, o_P1, o_P2, o_P3, o_gb, o_lp,
         o_nodes, o_perm, o_err;
     int max_epochs = 4096;
     Gemm g_l1, g_l2, g_l3, g_da2, g_da1, g_dw3, g_dw2, g_dw1;
@@ -681,6 +715,7 @@ void compute_layout(stowarm_t h) {
     take(h->o_nv, B * 4);
     take(h->o_cnt, 4);
     take(h->o_t, 4);
+    take(h->o_pow, 16);
     take(h->o_roff, B * 8);
     take(h->o_rsq, B * 4);
     take(h->o_Z1, B * H * 4);
@@ -699,7 +734,7 @@ void compute_layout(stowarm_t h) {
     take(h->o_P2, S * H * H * 4);
     take(h->o_P3, S * H * DO * 4);
     take(h->o_gb, (DO + 2 * H) * 4);
-    take(h->o_lp, (B / kBM) * 4 * 4);
+    take(h->o_lp, (B / kBM) * 8 * 4);
     take(h->o_nodes, h->nodes.size() * sizeof(NodeInfo));
     take(h->o_perm, (size_t)h->max_epochs * 2 * 8);
     take(h->o_err, 4);
@@ -716,10 +751,10 @@ bool setup_gemms(stowarm_t h) {
     const int B = n.B, H = n.H, D0 = n.D0, DO = n.DO;
     bool ok = true;
     auto fwd = [&](Gemm &g, const void *A, int K, const void *W, int N) {
-        ok = ok && make_map(&g.a, A, K, B, K, kBM) && make_map(&g.b, W, K, N, K, N);
-        g.BN = N;
+        g.BN = N < kMaxBN ? N : kMaxBN;
+        ok = ok && make_map(&g.a, A, K, B, K, kBM) && make_map(&g.b, W, K, N, K, g.BN);
         g.nk = (K + kBK - 1) / kBK;
-        g.grid = dim3(B / kBM, 1, 1);
+        g.grid = dim3(B / kBM, (N + g.BN - 1) / g.BN, 1);
     };
     fwd(h->g_l1, n.X, D0, n.W1b, H);
     fwd(h->g_l2, n.A1, H, n.W2b, H);
@@ -727,10 +762,10 @@ bool setup_gemms(stowarm_t h) {
     fwd(h->g_da2, n.dY, DO, n.W3bT, H);
     fwd(h->g_da1, n.dZ2, H, n.W2bT, H);
     auto wgrad = [&](Gemm &g, const void *AT, const void *BT, int N) {
-        ok = ok && make_map(&g.a, AT, B, H, B, kBM) && make_map(&g.b, BT, B, N, B, N);
-        g.BN = N;
+        g.BN = N < kMaxBN ? N : kMaxBN;
+        ok = ok && make_map(&g.a, AT, B, H, B, kBM) && make_map(&g.b, BT, B, N, B, g.BN);
         g.nk = kSplitK / kBK;
-        g.grid = dim3(H / kBM, 1, n.S);
+        g.grid = dim3(H / kBM, (N + g.BN - 1) / g.BN, n.S);
     };
     wgrad(h->g_dw3, n.A2T, n.dYT, DO);
     wgrad(h->g_dw2, n.dZ2T, n.A1T, H);
@@ -921,6 +956,7 @@ STO_API sto_status stowarm_bind_workspace(stowarm_t h, void *dev_ptr, size_t byt
     n.nvalid = at<int>(h, h->o_nv);
     n.count = at<int>(h, h->o_cnt);
     n.tstep = at<int>(h, h->o_t);
+    n.adam_pow = at<double>(h, h->o_pow);
     n.row_off = at<long long>(h, h->o_roff);
     n.row_sq = at<float>(h, h->o_rsq);
     n.Z1 = at<float>(h, h->o_Z1);
@@ -990,7 +1026,7 @@ STO_API sto_status stowarm_set_params(stowarm_t h, const float *params, sto_stre
     WCUDA(h, cudaMemcpyAsync(n.W, pad.data(), bytes, cudaMemcpyHostToDevice, st));
     WCUDA(h, cudaMemsetAsync(n.mom, 0, bytes, st));
     WCUDA(h, cudaMemsetAsync(n.vel, 0, bytes, st));
-    WCUDA(h, cudaMemsetAsync(n.tstep, 0, 4, st));
+    k_reset_step<<<1, 1, 0, st>>>(n);
     h->tstep_host = 0;
     k_refresh_bf16<<<adam_blocks(n), 256, 0, st>>>(n);
     WCUDA(h, cudaGetLastError());
@@ -1102,7 +1138,7 @@ STO_API sto_status stowarm_train(stowarm_t h, int32_t steps, float lr, uint64_t 
     cudaStream_t cap;
     WCUDA(h, cudaStreamCreateWithFlags(&cap, cudaStreamNonBlocking));
     WCUDA(h, cudaStreamBeginCapture(cap, cudaStreamCaptureModeThreadLocal));
-    k_gather<<<(n.B + 255) / 256, 256, 0, cap>>>(n, h->x0, h->c, h->y, S, 0, spe, t0, 0, 0);
+    k_gather<<<n.B / kGatherRows, 256, 0, cap>>>(n, h->x0, h->c, h->y, S, 0, spe, t0, 0, 0);
     sto_status s = run_net(h, true, false, nullptr, cap);
     k_adam<<<adam_blocks(n), 256, 0, cap>>>(n, 1, lr, nullptr, nullptr, loss_hist, t0);
     k_tick<<<1, 1, 0, cap>>>(n);
@@ -1134,7 +1170,7 @@ STO_API sto_status stowarm_predict(stowarm_t h, int32_t draw0, int32_t num_draws
     const long long first = (long long)draw0 * h->Nn, last = (long long)(draw0 + num_draws) * h->Nn;
     for (long long base = first; base < last; base += n.B) {
         k_zero_count<<<1, 1, 0, st>>>(n);
-        k_gather<<<(n.B + 255) / 256, 256, 0, st>>>(n, h->x0, h->c, nullptr, last, base, 1, 0, 1, draw0);
+        k_gather<<<n.B / kGatherRows, 256, 0, st>>>(n, h->x0, h->c, nullptr, last, base, 1, 0, 1, draw0);
         WCUDA(h, cudaGetLastError());
         sto_status s = run_net(h, false, true, y_out, st);
         if (s != STO_OK) return s;

@@ -669,7 +669,7 @@ template <class T, int NR, int KV>
 void launch_tree(stotree_t h, const TreeArgs<T> &a, unsigned epoch, unsigned long long tbase, int grid,
                  cudaStream_t st) {
     const size_t smem = tree_smem(NR, a.lda, a.ldg, a.ldk, a.ldr, sizeof(T));
-    cudaFuncSetAttribute(k_tree<T, NR, KV>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    raise_smem_cap((const void *)k_tree<T, NR, KV>, smem);
     k_tree<T, NR, KV><<<grid, kThreadsT, smem, st>>>(a, epoch, tbase);
 }
 
@@ -695,13 +695,13 @@ int tree_grid(const TreeArgs<T> &a) {
     const int kv = (a.lda / V16<T>::n + 31) / 32;
     cudaError_t e;
     switch (kv) {
-        case 1: cudaFuncSetAttribute(k_tree<T, NR, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        case 1: raise_smem_cap((const void *)k_tree<T, NR, 1>, smem);
                 e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_tree<T, NR, 1>, kThreadsT, smem); break;
-        case 2: cudaFuncSetAttribute(k_tree<T, NR, 2>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        case 2: raise_smem_cap((const void *)k_tree<T, NR, 2>, smem);
                 e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_tree<T, NR, 2>, kThreadsT, smem); break;
-        case 3: cudaFuncSetAttribute(k_tree<T, NR, 3>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        case 3: raise_smem_cap((const void *)k_tree<T, NR, 3>, smem);
                 e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_tree<T, NR, 3>, kThreadsT, smem); break;
-        default: cudaFuncSetAttribute(k_tree<T, NR, 4>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        default: raise_smem_cap((const void *)k_tree<T, NR, 4>, smem);
                  e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_tree<T, NR, 4>, kThreadsT, smem); break;
     }
     if (e != cudaSuccess || per_sm < 1) return 0;

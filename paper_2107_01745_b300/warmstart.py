@@ -101,43 +101,67 @@ class WarmStarter:
         return self.net.predict(0, x0.shape[0])
 
 
-def choose_start(group: W.Group, lam: float, y0: torch.Tensor, device="cuda:0"):
+class EvalSet:
+    """Evaluation draws in one factored batch, reused by the cold and the warm solve."""
+
+    def __init__(self, group: W.Group, lam: float, device="cuda:0"):
+        self.group, self.lam, self.device = group, lam, device
+        self.sb = StoBatch([group], device=device)
+        self.sb.factor()
+        self.D = group.num_instances
+        self.m = int(self.sb.sizes[0])
+        self.x0 = torch.as_tensor(group.x0, dtype=torch.float32, device=device)
+        self.c = torch.as_tensor(group.c, dtype=torch.float32, device=device)
+
+    def nama(self, y0=None, tol=1e-4, max_iter=500):
+        yin = None if y0 is None else y0.reshape(-1).contiguous()
+        res = self.sb.nama(np.array([self.lam]), tol=tol, max_iter=max_iter, y0=yin, outputs=False)
+        return res["y"].reshape(self.D, self.m), res["infos"]
+
+    def phi(self, y0=None):
+        """phi_lambda at the start point of every draw (a zero-iteration NAMA)."""
+        yin = None if y0 is None else y0.reshape(-1).contiguous()
+        infos = self.sb.nama(np.array([self.lam]), max_iter=0, y0=yin, outputs=False,
+                             allow_not_converged=True)["infos"]
+        return np.array([i["fbe"] for i in infos])
+
+    def close(self):
+        self.sb.close()
+
+
+def choose_start(ev: EvalSet, y0: torch.Tensor):
     """Per draw: y0 if phi_lambda(y0) <= phi_lambda(0), else zeros.  Returns the start and the
     number of draws that fell back."""
-    sb = StoBatch([group], device=device)
-    sb.factor()
-    D = group.num_instances
-    f_warm = sb.nama(np.array([lam]), max_iter=0, y0=y0.reshape(-1).contiguous(), outputs=False,
-                     allow_not_converged=True)["infos"]
-    f_cold = sb.nama(np.array([lam]), max_iter=0, outputs=False, allow_not_converged=True)["infos"]
-    sb.close()
-    keep = torch.tensor([fw["fbe"] <= fc["fbe"] for fw, fc in zip(f_warm, f_cold)], device=y0.device)
-    start = torch.where(keep[:, None], y0.reshape(D, -1), torch.zeros_like(y0.reshape(D, -1)))
-    return start, int(D - keep.sum().item())
+    keep = torch.as_tensor(ev.phi(y0) <= ev.phi(None), device=y0.device)
+    start = torch.where(keep[:, None], y0, torch.zeros_like(y0))
+    return start, int(ev.D - int(keep.sum().item()))
 
 
-def warm_vs_cold(system: W.Group, starter: WarmStarter, eval_group: W.Group, lam: float, tol=1e-4,
-                 device="cuda:0"):
-    """Batched NAMA on the evaluation draws from y0 = 0 and from the learned start (inference
-    and the fallback test included in the warm time)."""
-    cold = solve_draws(eval_group, lam, tol=tol, device=device)
-    cold["sb"].close()
-    x0 = torch.as_tensor(eval_group.x0, dtype=torch.float32, device=device)
-    c = torch.as_tensor(eval_group.c, dtype=torch.float32, device=device)
+def warm_vs_cold(starter: WarmStarter, ev: EvalSet, tol=1e-4):
+    """Batched NAMA on the evaluation draws from y0 = 0 and from the learned start; the warm time
+    includes inference and the fallback test."""
     torch.cuda.synchronize()
     e0, e1 = _events()
     e0.record()
-    y0 = starter.predict(x0, c)
-    start, fallbacks = choose_start(eval_group, lam, y0, device=device)
+    y_cold, cold = ev.nama(None, tol=tol)
     e1.record()
     torch.cuda.synchronize()
-    prep_ms = e0.elapsed_time(e1)
-    warm = solve_draws(eval_group, lam, tol=tol, y0=start, device=device)
-    warm["sb"].close()
-    ci = np.array([i["iters"] for i in cold["infos"]])
-    wi = np.array([i["iters"] for i in warm["infos"]])
-    ok = all(i["status"] == 0 for i in cold["infos"] + warm["infos"])
-    return dict(draws=eval_group.num_instances, cold_ms=cold["ms"], warm_ms=warm["ms"] + prep_ms,
-                warm_solve_ms=warm["ms"], warm_prep_ms=prep_ms, cold_iters_mean=float(ci.mean()),
-                warm_iters_mean=float(wi.mean()), cold_iters_max=int(ci.max()), warm_iters_max=int(wi.max()),
-                fallbacks=fallbacks, converged=ok, y_warm=warm["y"], y_cold=cold["y"])
+    cold_ms = e0.elapsed_time(e1)
+    e0, e1 = _events()
+    e2, e3 = _events()
+    e0.record()
+    y0 = starter.predict(ev.x0, ev.c)
+    e1.record()
+    start, fallbacks = choose_start(ev, y0)
+    e2.record()
+    y_warm, warm = ev.nama(start, tol=tol)
+    e3.record()
+    torch.cuda.synchronize()
+    ci = np.array([i["iters"] for i in cold])
+    wi = np.array([i["iters"] for i in warm])
+    ok = all(i["status"] == 0 for i in cold + warm)
+    return dict(draws=ev.D, cold_ms=cold_ms, warm_ms=e0.elapsed_time(e3), warm_infer_ms=e0.elapsed_time(e1),
+                warm_fallback_test_ms=e1.elapsed_time(e2), warm_solve_ms=e2.elapsed_time(e3),
+                cold_iters_mean=float(ci.mean()), warm_iters_mean=float(wi.mean()), cold_iters_max=int(ci.max()),
+                warm_iters_max=int(wi.max()), fallbacks=fallbacks, converged=ok, y_warm=y_warm, y_cold=y_cold,
+                y0=y0)
