@@ -106,7 +106,6 @@ static void compute_layout(stotree_t h) {
     L.K64 = add(Wd * nu * nx * 8);
     L.fstatus = add(64);
     L.G = add(Nn * nx * h->ldg * es);
-    L.K = add(Np * nu * h->ldk * es);
     L.RK = add(Np * nu * h->ldrk * es);
     L.Gt = add(Nn * (nx + nu) * h->ldk * es);
     L.Kt = add(Np * nx * h->ldr * es);

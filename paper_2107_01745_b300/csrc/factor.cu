@@ -200,10 +200,10 @@ __global__ void k_chol_inv(int first, int nu, int ldr, int ldrk, double *Rb, dou
     }
 }
 
-// Symmetrise P^i and write K^i in the solve precision: alone, after -Rinv in the RK block (backward
+// Symmetrise P^i and write K^i in the solve precision: after -Rinv in the RK block (backward
 // pass) and transposed (forward pass).
 template <class T>
-__global__ void k_finish(int first, int nx, int nu, int ldk, int ldr, int ldrk, double *Pcur, const double *K64, T *K,
+__global__ void k_finish(int first, int nx, int nu, int ldk, int ldr, int ldrk, double *Pcur, const double *K64,
                          T *RK, T *Kt) {
     const int b = blockIdx.x, i = first + b;
     double *P = Pcur + (size_t)b * nx * nx;
@@ -219,7 +219,6 @@ __global__ void k_finish(int first, int nx, int nu, int ldk, int ldr, int ldrk, 
     for (int e = threadIdx.x; e < nu * ldk; e += blockDim.x) {
         const int a = e / ldk, c = e % ldk;
         const T val = c < nx ? (T)Kb[a * nx + c] : (T)0;
-        K[(size_t)i * nu * ldk + e] = val;
         RK[(size_t)i * nu * ldrk + (size_t)a * ldrk + ldr + c] = val;
     }
     for (int e = threadIdx.x; e < nx * ldr; e += blockDim.x) {
@@ -288,7 +287,7 @@ sto_status factor_impl(stotree_t h, cudaStream_t st) {
         dgemm(st, true, nx, nx, nu, 1.0, h->at<double>(L.M), nx, (long long)nu * nx, h->at<double>(L.K64), nx,
               (long long)nu * nx, 1.0, Pcur, nx, (long long)nx * nx, np);
         k_finish<T><<<np, 256, 0, st>>>(pf, nx, nu, h->ldk, h->ldr, h->ldrk, Pcur, h->at<double>(L.K64),
-                                        h->at<T>(L.K), h->at<T>(L.RK), h->at<T>(L.Kt));
+                                        h->at<T>(L.RK), h->at<T>(L.Kt));
     }
     const long long rows = (long long)h->Nn * nx;
     k_downcast_dyn<T><<<(int)std::min<long long>(rows, 65535), 128, 0, st>>>(

@@ -59,7 +59,7 @@ struct Layout {
     size_t P[2], PG, W, Rb, Zb, M, K64;
     size_t fstatus;              // int
     // solve arrays (real)
-    size_t G, K, RK, gu, gx, c;  // RK = [-Rbar^-1 | K] per nonleaf node (nu rows of ldrk)
+    size_t G, RK, gu, gx, c;     // RK = [-Rbar^-1 | K] per nonleaf node (nu rows of ldrk)
     size_t Gt, Kt;               // forward pass: [A | B]' per node (nx+nu rows of ldk), K' (nx rows of ldr)
     size_t cost, box;            // real copies: W (Q|R|PN), ell (q|r|pN), lo/hi (x|u)
     // solve scratch (real)
