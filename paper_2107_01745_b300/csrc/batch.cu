@@ -541,17 +541,30 @@ __device__ __forceinline__ float term(float h, float w, float lam, float ilam, c
     return h * (M.w * h) + dz * (w + 0.5f * lam * dz);
 }
 
-// Per-instance reduction of NS sums and NM maxima; true in the instance's last block.
+__device__ __forceinline__ float wsumf(float v) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    return v;
+}
+__device__ __forceinline__ float wmaxf(float v) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v = fmaxf(v, __shfl_xor_sync(0xffffffffu, v, o));
+    return v;
+}
+
+// Per-instance reduction of NS sums and NM maxima; true in the instance's last block.  Warp
+// and block levels in FP32 (the FP64 pipe is slow on this part), block partials and the sum
+// over the instance's blocks in FP64.
 template <int NS, int NM>
-__device__ bool inst_reduce(const ElemArgs &a, int inst, double *sums, double *maxs, double *out) {
+__device__ bool inst_reduce(const ElemArgs &a, int inst, float *sums, float *maxs, double *out) {
     constexpr int NV = NS + NM;
-    __shared__ double red[kBT / 32][NV > 0 ? NV : 1];
+    __shared__ float red[kBT / 32][NV > 0 ? NV : 1];
     __shared__ bool last;
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
 #pragma unroll
-    for (int k = 0; k < NS; ++k) sums[k] = wsum(sums[k]);
+    for (int k = 0; k < NS; ++k) sums[k] = wsumf(sums[k]);
 #pragma unroll
-    for (int k = 0; k < NM; ++k) maxs[k] = wmax(maxs[k]);
+    for (int k = 0; k < NM; ++k) maxs[k] = wmaxf(maxs[k]);
     if (lane == 0) {
 #pragma unroll
         for (int k = 0; k < NS; ++k) red[warp][k] = sums[k];
@@ -561,11 +574,11 @@ __device__ bool inst_reduce(const ElemArgs &a, int inst, double *sums, double *m
     __syncthreads();
     if (threadIdx.x < NV) {
         const int k = threadIdx.x;
-        double acc = k < NS ? 0.0 : -INFINITY;
-        for (int w = 0; w < kBT / 32; ++w) acc = k < NS ? acc + red[w][k] : fmax(acc, red[w][k]);
-        a.partials[(size_t)blockIdx.x * kRedSlots + k] = acc;
+        float acc = k < NS ? 0.f : -INFINITY;
+        for (int w = 0; w < kBT / 32; ++w) acc = k < NS ? acc + red[w][k] : fmaxf(acc, red[w][k]);
+        a.partials[(size_t)k * gridDim.x + blockIdx.x] = (double)acc;  // slot-major: coalesced in the tail
+        __threadfence();  // only the writers of partials publish anything
     }
-    __threadfence();
     __syncthreads();
     const InstDev &in = a.insts[inst];
     if (threadIdx.x == 0) last = atomicAdd(&a.sc[inst].counter, 1u) == (unsigned)in.nblocks - 1;
@@ -573,10 +586,15 @@ __device__ bool inst_reduce(const ElemArgs &a, int inst, double *sums, double *m
     if (!last) return false;
     __threadfence();
     for (int k = warp; k < NV; k += kBT / 32) {
-        double acc = k < NS ? 0.0 : -INFINITY;
-        for (int b = lane; b < in.nblocks; b += 32) {
-            const double v = __ldcg(a.partials + (size_t)(in.block0 + b) * kRedSlots + k);
-            acc = k < NS ? acc + v : fmax(acc, v);
+        const double ident = k < NS ? 0.0 : -INFINITY;
+        const double *src = a.partials + (size_t)k * gridDim.x + in.block0;
+        double acc = ident;
+        for (int b0 = lane; b0 < in.nblocks; b0 += 32 * 4) {  // four loads in flight, summed in order
+            double v[4];
+#pragma unroll
+            for (int q = 0; q < 4; ++q) v[q] = b0 + 32 * q < in.nblocks ? __ldcg(src + b0 + 32 * q) : ident;
+#pragma unroll
+            for (int q = 0; q < 4; ++q) acc = k < NS ? acc + v[q] : fmax(acc, v[q]);
         }
         acc = k < NS ? wsum(acc) : wmax(acc);
         if (lane == 0) out[k] = acc;
@@ -604,8 +622,7 @@ __global__ void __launch_bounds__(kBT) k_bpoint(ElemArgs a, const float *yb, con
     __shared__ double tot[8];
     const float lam = (float)S.lambda, ilam = 1.f / lam;
     const int p = (S.lb_head + S.lb_count) % (a.mem + 1);
-    float fs = 0.f, sq = 0.f, s2 = 0.f, g2 = 0.f;
-    double mx = 0.0;
+    float fs = 0.f, sq = 0.f, s2 = 0.f, g2 = 0.f, mx = 0.f;
     int nan = 0;
     for (int e = e0 + threadIdx.x; e < e1; e += kBT) {
         const EMeta M = emeta(g, e);
@@ -616,7 +633,7 @@ __global__ void __launch_bounds__(kBT) k_bpoint(ElemArgs a, const float *yb, con
         fs += term(he, ye, lam, ilam, M);
         const float ra = fabsf(re) / M.sq;
         if (!(ra <= 3.0e38f)) nan = 1;
-        mx = fmax(mx, (double)ra);
+        mx = fmaxf(mx, ra);
         if (pair) {
             const float ro = r[ge], q = re - ro, s = ringS[p * a.vstride + ge];
             ringY[p * a.vstride + ge] = q;
@@ -626,8 +643,8 @@ __global__ void __launch_bounds__(kBT) k_bpoint(ElemArgs a, const float *yb, con
         }
         r[ge] = re;
     }
-    double sums[5] = {fs, sq, s2, g2, (double)nan};
-    double maxs[1] = {mx};
+    float sums[5] = {fs, sq, s2, g2, (float)nan};
+    float maxs[1] = {mx};
     if (inst_reduce<5, 1>(a, inst, sums, maxs, tot) && threadIdx.x == 0) {
         S.phi = -tot[0];
         S.res_inf = tot[5];
@@ -676,7 +693,7 @@ __global__ void __launch_bounds__(kBT) k_blb_dots(ElemArgs a, const float *gv, c
                 dv[k] += qe * yn;
             }
     }
-    double sums[4 * MEM];
+    float sums[4 * MEM];
 #pragma unroll
     for (int k = 0; k < MEM; ++k) {
         sums[k] = av[k];
@@ -684,7 +701,7 @@ __global__ void __launch_bounds__(kBT) k_blb_dots(ElemArgs a, const float *gv, c
         sums[2 * MEM + k] = cv[k];
         sums[3 * MEM + k] = dv[k];
     }
-    double maxs[1];
+    float maxs[1];
     if (inst_reduce<4 * MEM, 0>(a, inst, sums, maxs, tot) && threadIdx.x == 0) {
         int sl[MEM];
         for (int k = 0; k < cnt; ++k) sl[k] = (head + k) % M1;
@@ -769,10 +786,10 @@ __global__ void __launch_bounds__(kBT) k_bls(ElemArgs a, const float *yb, const 
 #pragma unroll
         for (int j = 0; j < J; ++j) acc[j] += term(ha + tau[j] * hb, wa + tau[j] * wb, lam, ilam, M) - c0;
     }
-    double sums[J];
+    float sums[J];
 #pragma unroll
     for (int j = 0; j < J; ++j) sums[j] = acc[j];
-    double maxs[1];
+    float maxs[1];
     if (inst_reduce<J, 0>(a, inst, sums, maxs, tot) && threadIdx.x == 0) {
         for (int j = 0; j < nc; ++j) {
             if (-tot[j] <= 0.0) {

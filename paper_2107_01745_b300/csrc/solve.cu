@@ -371,11 +371,11 @@ struct Consumer {
         }
         cbar();
     }
-    // acc[k] += coef[k][row0 + r] * M[r][:] over the rows of the slot; two rows per step so that
+    // acc[k] += coef[k][row0 + r] * M[r][:] over the rows of the slot; RU rows per step so that
     // their shared-memory loads are in flight together
     __device__ void axpy_rows(const T *M, int ld, int nrows, const T *coef, int cstride, int row0) {
         const int nvec = ld / VN;
-        constexpr int RU = 2;
+        constexpr int RU = KV <= 1 ? 4 : 2;  // rows in flight per warp (register budget of 3 CTAs/SM)
         for (int rb = warp; rb < nrows; rb += kCW * RU) {
             T cr[RU][NR];
             VT g[RU][KV];
@@ -493,10 +493,9 @@ struct Consumer {
                     }
                     zero_acc();
                     cbar();
-                    if ((f & F_END_ITEM) && tid == 0) {
-                        __threadfence();
-                        st_release(a.flags + i, epoch);
-                    }
+                    // the named barrier above orders every consumer's stores before thread 0's
+                    // release store (release is cumulative), so no separate fence is needed
+                    if ((f & F_END_ITEM) && tid == 0) st_release(a.flags + i, epoch);
                 }
             } else if (md.kind == KIND_FG) {
                 // x^j = G^j [x^i; u^i] + c^j, axpy form over the rows of G^j' (one row per input)
@@ -595,10 +594,7 @@ struct Consumer {
                             a.us[k * a.u_stride + (long long)j * nu + r - nx] = val;
                     }
                     cbar();
-                    if ((f & F_END_ITEM) && tid == 0) {
-                        __threadfence();
-                        st_release(a.flags + a.Nn + j, epoch);
-                    }
+                    if ((f & F_END_ITEM) && tid == 0) st_release(a.flags + a.Nn + j, epoch);
                 }
             }
             ++n;

@@ -37,12 +37,14 @@ constexpr int kThreads = 256;
 template <class T>
 struct DualView {
     int m, Np, nx, nu, nxu, leaf_base;
+    float inv_nxu, inv_nx;
     const T *sqp, *box, *Wc;  // box = [lo x|u][hi x|u], Wc = [Q|R|PN][q|r|pN]
 
     struct Meta {
         T sq, lo, hi, w, l;
     };
 
+    // Scalar path (caller-facing conversions): per-entry constants read from global memory.
     __device__ __forceinline__ Meta meta(int e) const {
         int node, comp, kind;
         if (e < leaf_base) {
@@ -73,6 +75,152 @@ struct DualView {
     }
 };
 
+// Position of a dual entry in the node blocks ([x; u] per nonleaf node, [x] per leaf): found
+// once per vector of entries by a float reciprocal with an exact integer fix-up, then advanced
+// entry by entry, so the passes need no integer division per entry.
+struct Pos {
+    int node, comp;
+    bool leaf;
+};
+__device__ __forceinline__ int div_fix(int e, int d, float inv, int &r) {
+    int q = (int)((float)e * inv);
+    r = e - q * d;
+    while (r < 0) {
+        --q;
+        r += d;
+    }
+    while (r >= d) {
+        ++q;
+        r -= d;
+    }
+    return q;
+}
+template <class T>
+__device__ __forceinline__ Pos pos_of(const DualView<T> &dv, int e) {
+    Pos p;
+    if (e < dv.leaf_base) {
+        p.node = div_fix(e, dv.nxu, dv.inv_nxu, p.comp);
+        p.leaf = false;
+    } else {
+        p.node = dv.Np + div_fix(e - dv.leaf_base, dv.nx, dv.inv_nx, p.comp);
+        p.leaf = true;
+    }
+    return p;
+}
+template <class T>
+__device__ __forceinline__ void pos_next(const DualView<T> &dv, Pos &p) {
+    ++p.comp;
+    if (!p.leaf) {
+        if (p.comp == dv.nxu) {
+            p.comp = 0;
+            ++p.node;
+            p.leaf = p.node >= dv.Np;
+        }
+    } else if (p.comp == dv.nx) {
+        p.comp = 0;
+        ++p.node;
+    }
+}
+
+// Per-component constants of the dual layout in shared memory (dynamic, 6 (nx + nu) reals):
+// nonleaf [x; u] lo, hi, quadratic and linear cost weights; leaf quadratic and linear weights
+// (the leaf box is the x part of the nonleaf box).
+template <class T>
+struct CompTab {
+    T *lo, *hi, *w, *l, *wl, *ll;
+    __device__ void load(const DualView<T> &dv, T *sm) {
+        const int n = dv.nxu;
+        lo = sm;
+        hi = sm + n;
+        w = sm + 2 * n;
+        l = sm + 3 * n;
+        wl = sm + 4 * n;
+        ll = sm + 5 * n;
+        nx_ = dv.nx;
+        for (int c = threadIdx.x; c < n; c += blockDim.x) {
+            lo[c] = dv.box[c];
+            hi[c] = dv.box[n + c];
+            w[c] = dv.Wc[c];
+            l[c] = dv.Wc[2 * dv.nx + dv.nu + c];
+            if (c < dv.nx) {
+                wl[c] = dv.Wc[n + c];
+                ll[c] = dv.Wc[2 * dv.nx + dv.nu + n + c];
+            }
+        }
+        __syncthreads();
+    }
+    // the constants of the entry at p, scaled by sq = sqrt(pi) of its node
+    __device__ __forceinline__ typename DualView<T>::Meta meta(const Pos &p, T sq) const {
+        typename DualView<T>::Meta M;
+        M.sq = sq;
+        const int c = p.comp;
+        if (!p.leaf && p.node == 0 && c < nx_) {  // the root state is the parameter: unboxed
+            M.lo = -INFINITY;
+            M.hi = INFINITY;
+        } else {
+            M.lo = sq * lo[c];
+            M.hi = sq * hi[c];
+        }
+        M.w = p.leaf ? wl[c] : w[c];
+        M.l = sq * (p.leaf ? ll[c] : l[c]);
+        return M;
+    }
+    int nx_;
+};
+template <class T>
+size_t comp_tab_bytes(const DualView<T> &dv) {
+    return (size_t)6 * dv.nxu * sizeof(T);
+}
+
+template <class T>
+struct Vec16;
+template <>
+struct Vec16<float> {
+    using type = float4;
+    static constexpr int n = 4;
+};
+template <>
+struct Vec16<double> {
+    using type = double2;
+    static constexpr int n = 2;
+};
+// n entries (n = VN: one 16-byte load) of v starting at e0 into x[]
+template <class T>
+__device__ __forceinline__ void ldv(const T *v, int e0, int n, T *x) {
+    constexpr int VN = Vec16<T>::n;
+    if (n == VN) {
+        const typename Vec16<T>::type t = *reinterpret_cast<const typename Vec16<T>::type *>(v + e0);
+        const T *tt = reinterpret_cast<const T *>(&t);
+#pragma unroll
+        for (int q = 0; q < VN; ++q) x[q] = tt[q];
+    } else {
+#pragma unroll
+        for (int q = 0; q < VN; ++q) x[q] = q < n ? v[e0 + q] : T(0);
+    }
+}
+template <class T>
+__device__ __forceinline__ void stv(T *v, int e0, int n, const T *x) {
+    constexpr int VN = Vec16<T>::n;
+    if (n == VN) {
+        typename Vec16<T>::type t;
+        T *tt = reinterpret_cast<T *>(&t);
+#pragma unroll
+        for (int q = 0; q < VN; ++q) tt[q] = x[q];
+        *reinterpret_cast<typename Vec16<T>::type *>(v + e0) = t;
+    } else {
+        for (int q = 0; q < n; ++q) v[e0 + q] = x[q];
+    }
+}
+// Grid-stride loop over 16-byte vectors of entries [0, m): f(e0, n) with n = VN, and the last
+// m % VN entries by one thread.  Every solver vector starts on a 256-byte boundary.
+template <class T, class F>
+__device__ __forceinline__ void for_vectors(int m, F f) {
+    constexpr int VN = Vec16<T>::n;
+    const int nvec = m / VN;
+    for (int v = blockIdx.x * blockDim.x + threadIdx.x; v < nvec; v += gridDim.x * blockDim.x) f(v * VN, VN);
+    if (nvec * VN < m && blockIdx.x == gridDim.x - 1 && threadIdx.x == blockDim.x - 1) f(nvec * VN, m - nvec * VN);
+}
+
 template <class T>
 __device__ __forceinline__ T clampv(T v, T lo, T hi) {
     return v < lo ? lo : (v > hi ? hi : v);
@@ -98,17 +246,32 @@ __device__ __forceinline__ double warp_max_d(double v) {
 }
 
 // Two-level deterministic reduction of NS sums and NM maxima.  Returns true in the last
-// block to finish, where out[0..NS+NM) holds the totals (summed in block order).
-template <int NS, int NM>
-__device__ bool reduce_last(double *sums, double *maxs, double *partials, unsigned *counter, double *out) {
+// block to finish, where out[0..NS+NM) holds the totals (summed in block order).  The warp and
+// block levels run in the kernel's type T (the FP64 pipe is slow on this part: an FP64 shuffle
+// tree per value would dominate an elementwise pass); each block's partial and the sum over
+// blocks are FP64.
+template <class T>
+__device__ __forceinline__ T warp_sum_t(T v) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    return v;
+}
+template <class T>
+__device__ __forceinline__ T warp_max_t(T v) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v = fmax(v, __shfl_xor_sync(0xffffffffu, v, o));
+    return v;
+}
+template <class T, int NS, int NM>
+__device__ bool reduce_last(T *sums, T *maxs, double *partials, unsigned *counter, double *out) {
     constexpr int NV = NS + NM;
-    __shared__ double red[kThreads / 32][NV > 0 ? NV : 1];
+    __shared__ T red[kThreads / 32][NV > 0 ? NV : 1];
     __shared__ bool last;
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
 #pragma unroll
-    for (int k = 0; k < NS; ++k) sums[k] = warp_sum_d(sums[k]);
+    for (int k = 0; k < NS; ++k) sums[k] = warp_sum_t(sums[k]);
 #pragma unroll
-    for (int k = 0; k < NM; ++k) maxs[k] = warp_max_d(maxs[k]);
+    for (int k = 0; k < NM; ++k) maxs[k] = warp_max_t(maxs[k]);
     if (lane == 0) {
 #pragma unroll
         for (int k = 0; k < NS; ++k) red[warp][k] = sums[k];
@@ -116,26 +279,34 @@ __device__ bool reduce_last(double *sums, double *maxs, double *partials, unsign
         for (int k = 0; k < NM; ++k) red[warp][NS + k] = maxs[k];
     }
     __syncthreads();
+    // partials are slot-major ([slot][block]) so that the last block reads them coalesced
     if (threadIdx.x < NV) {
         const int k = threadIdx.x;
-        double acc = k < NS ? 0.0 : -INFINITY;
+        T acc = k < NS ? T(0) : T(-INFINITY);
         for (int w = 0; w < kThreads / 32; ++w) acc = k < NS ? acc + red[w][k] : fmax(acc, red[w][k]);
-        partials[blockIdx.x * kRedSlots + k] = acc;
+        partials[k * kRedBlocks + blockIdx.x] = (double)acc;
+        __threadfence();  // only the writers of partials publish anything
     }
-    __threadfence();
     __syncthreads();
     if (threadIdx.x == 0) last = atomicAdd(counter, 1u) == gridDim.x - 1;
     __syncthreads();
     if (!last) return false;
     __threadfence();
-    // warp w sums slots w, w+8, ...; lane l takes blocks l, l+32, ... in order, then a fixed
-    // butterfly: the result does not depend on which block finished last
+    // warp w sums slots w, w+8, ...; lane l takes blocks l, l+32, ... (all loads issued before
+    // the first add), sums them in that order, then a fixed butterfly: the result does not
+    // depend on which block finished last
+    constexpr int kPerLane = (kRedBlocks + 31) / 32;
     for (int k = warp; k < NV; k += kThreads / 32) {
-        double acc = k < NS ? 0.0 : -INFINITY;
-        for (int b = lane; b < (int)gridDim.x; b += 32) {
-            const double v = __ldcg(partials + b * kRedSlots + k);
-            acc = k < NS ? acc + v : fmax(acc, v);
+        const double ident = k < NS ? 0.0 : -INFINITY;
+        double v[kPerLane];
+#pragma unroll
+        for (int q = 0; q < kPerLane; ++q) {
+            const int b = lane + 32 * q;
+            v[q] = b < (int)gridDim.x ? __ldcg(partials + k * kRedBlocks + b) : ident;
         }
+        double acc = ident;
+#pragma unroll
+        for (int q = 0; q < kPerLane; ++q) acc = k < NS ? acc + v[q] : fmax(acc, v[q]);
         acc = k < NS ? warp_sum_d(acc) : warp_max_d(acc);
         if (lane == 0) out[k] = acc;
     }
@@ -153,40 +324,57 @@ __global__ void __launch_bounds__(kThreads) k_point(DualView<T> dv, const T *__r
                                                     T *r, T *ringS, T *ringY, long long vstride, int pair,
                                                     SolverScalars *sc, double *partials) {
     __shared__ double tot[8];
+    extern __shared__ __align__(16) unsigned char tab_raw[];
+    CompTab<T> tab;
+    tab.load(dv, reinterpret_cast<T *>(tab_raw));
+    constexpr int VN = Vec16<T>::n;
     const T lam = (T)sc->lambda, ilam = T(1) / lam;
     const int p = (sc->lb_head + sc->lb_count) % (sc->mem + 1);
     const T *sv = ringS + p * vstride;
     T *qv = ringY + p * vstride;
-    T fsum = 0, sq_dot = 0, s2 = 0, g2 = 0;
-    double sums[5] = {0, 0, 0, 0, 0};
-    double maxs[1] = {0.0};
+    T fsum = 0, sq_dot = 0, s2 = 0, g2 = 0, rmax = 0;
     int nan = 0;
-    for (int e = blockIdx.x * kThreads + threadIdx.x; e < dv.m; e += gridDim.x * kThreads) {
-        const auto M = dv.meta(e);
-        const T he = h[e], ye = yb[e];
-        const T z = clampv(he + ye * ilam, M.lo, M.hi);
-        const T re = z - he;
-        fsum += fbe_term<T>(he, ye, lam, ilam, M);
-        const T ra = fabs(re) / M.sq;
-        if (!(ra <= T(3.0e38))) nan = 1;
-        maxs[0] = fmax(maxs[0], (double)ra);
+    for_vectors<T>(dv.m, [&](int e0, int n) {
+        T he[VN], ye[VN], re[VN], ro[VN], se[VN], q[VN];
+        ldv(h, e0, n, he);
+        ldv(yb, e0, n, ye);
         if (pair) {
-            const T ro = r[e];
-            const T q = re - ro;
-            const T s = sv[e];
-            qv[e] = q;
-            sq_dot += s * q;
-            s2 += s * s;
-            g2 += ro * ro;
+            ldv<T>(r, e0, n, ro);
+            ldv(sv, e0, n, se);
         }
-        r[e] = re;
-    }
-    sums[0] = fsum;
-    sums[1] = sq_dot;
-    sums[2] = s2;
-    sums[3] = g2;
-    sums[4] = nan;
-    if (reduce_last<5, 1>(sums, maxs, partials, &sc->red_counter, tot) && threadIdx.x == 0) {
+        Pos ps = pos_of(dv, e0);
+        int cur = -1;
+        T sq = 1, isq = 1;
+#pragma unroll
+        for (int k = 0; k < VN; ++k) {
+            if (k < n) {
+                if (ps.node != cur) {
+                    cur = ps.node;
+                    sq = dv.sqp[cur];
+                    isq = T(1) / sq;
+                }
+                const auto M = tab.meta(ps, sq);
+                const T z = clampv(he[k] + ye[k] * ilam, M.lo, M.hi);
+                re[k] = z - he[k];
+                fsum += fbe_term<T>(he[k], ye[k], lam, ilam, M);
+                const T ra = fabs(re[k]) * isq;
+                if (!(ra <= T(3.0e38))) nan = 1;
+                rmax = fmax(rmax, ra);
+                if (pair) {
+                    q[k] = re[k] - ro[k];
+                    sq_dot += se[k] * q[k];
+                    s2 += se[k] * se[k];
+                    g2 += ro[k] * ro[k];
+                }
+                pos_next(dv, ps);
+            }
+        }
+        if (pair) stv(qv, e0, n, q);
+        stv(r, e0, n, re);
+    });
+    T sums[5] = {fsum, sq_dot, s2, g2, (T)nan};
+    T maxs[1] = {rmax};
+    if (reduce_last<T, 5, 1>(sums, maxs, partials, &sc->red_counter, tot) && threadIdx.x == 0) {
         sc->phi = -tot[0];
         sc->res_inf = tot[5];
         if (tot[4] > 0.0 || !(tot[0] == tot[0])) sc->nan_flag = 1;
@@ -209,28 +397,37 @@ __global__ void __launch_bounds__(kThreads) k_grad(int m, const T *__restrict__ 
                                                    T *ringS, T *ringY, long long vstride, SolverScalars *sc,
                                                    double *partials) {
     __shared__ double tot[8];
+    constexpr int VN = Vec16<T>::n;
     const T lam = (T)sc->lambda;
     const int pair = sc->lb_pending_valid;
     const int p = (sc->lb_head + sc->lb_count) % (sc->mem + 1);
     const T *sv = ringS + p * vstride;
     T *qv = ringY + p * vstride;
     T sq_dot = 0, s2 = 0, g2 = 0;
-    for (int e = blockIdx.x * kThreads + threadIdx.x; e < m; e += gridDim.x * kThreads) {
-        const T gn = r[e] + lam * hr[e];
+    for_vectors<T>(m, [&](int e0, int n) {
+        T re[VN], he[VN], gn[VN], go[VN], se[VN], q[VN];
+        ldv(r, e0, n, re);
+        ldv(hr, e0, n, he);
         if (pair) {
-            const T go = g[e];
-            const T q = gn - go;
-            const T s = sv[e];
-            qv[e] = q;
-            sq_dot += s * q;
-            s2 += s * s;
-            g2 += go * go;
+            ldv<T>(g, e0, n, go);
+            ldv(sv, e0, n, se);
         }
-        g[e] = gn;
-    }
-    double sums[3] = {sq_dot, s2, g2};
-    double maxs[1];
-    if (reduce_last<3, 0>(sums, maxs, partials, &sc->red_counter, tot) && threadIdx.x == 0) {
+#pragma unroll
+        for (int k = 0; k < VN; ++k) {
+            gn[k] = re[k] + lam * he[k];
+            if (pair && k < n) {
+                q[k] = gn[k] - go[k];
+                sq_dot += se[k] * q[k];
+                s2 += se[k] * se[k];
+                g2 += go[k] * go[k];
+            }
+        }
+        if (pair) stv(qv, e0, n, q);
+        stv(g, e0, n, gn);
+    });
+    T sums[3] = {sq_dot, s2, g2};
+    T maxs[1];
+    if (reduce_last<T, 3, 0>(sums, maxs, partials, &sc->red_counter, tot) && threadIdx.x == 0) {
         if (pair) {
             if (tot[0] > sc->eps_curv * tot[1] * tot[2]) {
                 if (sc->lb_count < sc->mem)
@@ -269,24 +466,35 @@ __global__ void __launch_bounds__(kThreads) k_lb_dots(int m, const T *__restrict
         sp[k] = ringS + sl * vstride;
         yp[k] = ringY + sl * vstride;
     }
+    constexpr int VN = Vec16<T>::n;
     T a[MEM], b[MEM], c[MEM], d[MEM];
 #pragma unroll
     for (int k = 0; k < MEM; ++k) a[k] = b[k] = c[k] = d[k] = T(0);
-    for (int e = blockIdx.x * kThreads + threadIdx.x; e < m; e += gridDim.x * kThreads) {
-        const T ge = g[e];
-        const T ye = newp ? yn[e] : T(0);
+    for_vectors<T>(m, [&](int e0, int n) {
+        T ge[VN], ye[VN];
+        ldv(g, e0, n, ge);
+        if (newp)
+            ldv(yn, e0, n, ye);
+        else
+#pragma unroll
+            for (int q = 0; q < VN; ++q) ye[q] = T(0);
 #pragma unroll
         for (int k = 0; k < MEM; ++k) {
             if (k < cnt) {
-                const T se = sp[k][e], qe = yp[k][e];
-                a[k] += se * ge;
-                b[k] += qe * ge;
-                c[k] += se * ye;
-                d[k] += qe * ye;
+                T se[VN], qe[VN];
+                ldv(sp[k], e0, n, se);
+                ldv(yp[k], e0, n, qe);
+#pragma unroll
+                for (int q = 0; q < VN; ++q) {
+                    a[k] += se[q] * ge[q];
+                    b[k] += qe[q] * ge[q];
+                    c[k] += se[q] * ye[q];
+                    d[k] += qe[q] * ye[q];
+                }
             }
         }
-    }
-    double sums[4 * MEM];
+    });
+    T sums[4 * MEM];
 #pragma unroll
     for (int k = 0; k < MEM; ++k) {
         sums[k] = a[k];
@@ -294,8 +502,8 @@ __global__ void __launch_bounds__(kThreads) k_lb_dots(int m, const T *__restrict
         sums[2 * MEM + k] = c[k];
         sums[3 * MEM + k] = d[k];
     }
-    double maxs[1];
-    if (reduce_last<4 * MEM, 0>(sums, maxs, partials, &sc->red_counter, tot) && threadIdx.x == 0) {
+    T maxs[1];
+    if (reduce_last<T, 4 * MEM, 0>(sums, maxs, partials, &sc->red_counter, tot) && threadIdx.x == 0) {
         int sl[MEM];
         for (int k = 0; k < cnt; ++k) sl[k] = (head + k) % M1;
         if (newp) {
@@ -350,13 +558,25 @@ __global__ void __launch_bounds__(kThreads) k_lb_dir(int m, const T *__restrict_
         sp[k] = ringS + sl * vstride;
         yp[k] = ringY + sl * vstride;
     }
-    for (int e = blockIdx.x * kThreads + threadIdx.x; e < m; e += gridDim.x * kThreads) {
-        T acc = gamma * g[e];
+    constexpr int VN = Vec16<T>::n;
+    for_vectors<T>(m, [&](int e0, int n) {
+        T acc[VN];
+        ldv(g, e0, n, acc);
+#pragma unroll
+        for (int q = 0; q < VN; ++q) acc[q] *= gamma;
 #pragma unroll
         for (int k = 0; k < MEM; ++k)
-            if (k < cnt) acc += cs[k] * sp[k][e] + cy[k] * yp[k][e];
-        dvec[e] = -acc;
-    }
+            if (k < cnt) {
+                T se[VN], qe[VN];
+                ldv(sp[k], e0, n, se);
+                ldv(yp[k], e0, n, qe);
+#pragma unroll
+                for (int q = 0; q < VN; ++q) acc[q] += cs[k] * se[q] + cy[k] * qe[q];
+            }
+#pragma unroll
+        for (int q = 0; q < VN; ++q) acc[q] = -acc[q];
+        stv(dvec, e0, n, acc);
+    });
 }
 
 template <class T, int MEM>
@@ -394,37 +614,61 @@ __global__ void __launch_bounds__(kThreads) k_ls(DualView<T> dv, const T *__rest
     T tau[J];
 #pragma unroll
     for (int j = 0; j < J; ++j) tau[j] = (T)ldexp(1.0, -(e0 + j));
+    extern __shared__ __align__(16) unsigned char tab_raw[];
+    CompTab<T> tab;
+    tab.load(dv, reinterpret_cast<T *>(tab_raw));
+    constexpr int VN = Vec16<T>::n;
     T acc[J];
 #pragma unroll
     for (int j = 0; j < J; ++j) acc[j] = T(0);
-    for (int e = blockIdx.x * kThreads + threadIdx.x; e < dv.m; e += gridDim.x * kThreads) {
-        const auto M = dv.meta(e);
-        const T y0 = yb[e], h0 = h[e];
-        T wa, wb, ha, hb;
+    for_vectors<T>(dv.m, [&](int e0, int n) {
+        T y0[VN], h0[VN], re[VN], dd[VN], hre[VN], hdd[VN];
+        ldv(yb, e0, n, y0);
+        ldv(h, e0, n, h0);
+        ldv(dvec, e0, n, dd);
+        ldv(hd, e0, n, hdd);
         if (nama) {
-            const T re = r[e], hre = hr[e];
-            wa = y0 - lam * re;
-            wb = dvec[e] + lam * re;
-            ha = h0 - lam * hre;
-            hb = hd[e] + lam * hre;
-        } else {
-            wa = y0;
-            wb = dvec[e];
-            ha = h0;
-            hb = hd[e];
+            ldv(r, e0, n, re);
+            ldv(hr, e0, n, hre);
         }
-        const T c0 = fbe_term<T>(h0, y0, lam, ilam, M);
+        Pos ps = pos_of(dv, e0);
+        int cur = -1;
+        T sq = 1;
 #pragma unroll
-        for (int j = 0; j < J; ++j) {
-            const T cj = fbe_term<T>(ha + tau[j] * hb, wa + tau[j] * wb, lam, ilam, M);
-            acc[j] += cj - c0;
+        for (int k = 0; k < VN; ++k) {
+            if (k < n) {
+                if (ps.node != cur) {
+                    cur = ps.node;
+                    sq = dv.sqp[cur];
+                }
+                const auto M = tab.meta(ps, sq);
+                T wa, wb, ha, hb;
+                if (nama) {
+                    wa = y0[k] - lam * re[k];
+                    wb = dd[k] + lam * re[k];
+                    ha = h0[k] - lam * hre[k];
+                    hb = hdd[k] + lam * hre[k];
+                } else {
+                    wa = y0[k];
+                    wb = dd[k];
+                    ha = h0[k];
+                    hb = hdd[k];
+                }
+                const T c0 = fbe_term<T>(h0[k], y0[k], lam, ilam, M);
+#pragma unroll
+                for (int j = 0; j < J; ++j) {
+                    const T cj = fbe_term<T>(ha + tau[j] * hb, wa + tau[j] * wb, lam, ilam, M);
+                    acc[j] += cj - c0;
+                }
+                pos_next(dv, ps);
+            }
         }
-    }
-    double sums[J];
+    });
+    T sums[J];
 #pragma unroll
     for (int j = 0; j < J; ++j) sums[j] = acc[j];
-    double maxs[1];
-    if (reduce_last<J, 0>(sums, maxs, partials, &sc->red_counter, tot) && threadIdx.x == 0) {
+    T maxs[1];
+    if (reduce_last<T, J, 0>(sums, maxs, partials, &sc->red_counter, tot) && threadIdx.x == 0) {
         // FBE(w) - FBE(ybar) = -sum_e (term(w) - term(ybar))
         for (int j = 0; j < nc; ++j) {
             sc->cand[e0 + j] = -tot[j];
@@ -452,23 +696,48 @@ __global__ void __launch_bounds__(kThreads) k_fbstep(DualView<T> dv, T *yb, cons
     const T tau = (T)sc->tau;
     const int p = (sc->lb_head + sc->lb_count) % (sc->mem + 1);
     T *sv = ringS + p * vstride;
-    for (int e = blockIdx.x * kThreads + threadIdx.x; e < dv.m; e += gridDim.x * kThreads) {
-        const auto M = dv.meta(e);
-        const T y0 = yb[e], h0 = h[e];
-        T w, hw;
+    extern __shared__ __align__(16) unsigned char tab_raw[];
+    CompTab<T> tab;
+    tab.load(dv, reinterpret_cast<T *>(tab_raw));
+    constexpr int VN = Vec16<T>::n;
+    for_vectors<T>(dv.m, [&](int e0, int n) {
+        T y0[VN], h0[VN], re[VN], dd[VN], hre[VN], hdd[VN], yn[VN], sn[VN];
+        ldv(yb, e0, n, y0);
+        ldv(h, e0, n, h0);
+        ldv(dvec, e0, n, dd);
+        ldv(hd, e0, n, hdd);
         if (nama) {
-            const T re = r[e], hre = hr[e];
-            w = y0 - lam * re + tau * (dvec[e] + lam * re);
-            hw = h0 - lam * hre + tau * (hd[e] + lam * hre);
-        } else {
-            w = y0 + tau * dvec[e];
-            hw = h0 + tau * hd[e];
+            ldv(r, e0, n, re);
+            ldv(hr, e0, n, hre);
         }
-        const T z = clampv(hw + w * ilam, M.lo, M.hi);
-        const T yn = w + lam * (hw - z);
-        sv[e] = yn - y0;
-        yb[e] = yn;
-    }
+        Pos ps = pos_of(dv, e0);
+        int cur = -1;
+        T sq = 1;
+#pragma unroll
+        for (int k = 0; k < VN; ++k) {
+            if (k < n) {
+                if (ps.node != cur) {
+                    cur = ps.node;
+                    sq = dv.sqp[cur];
+                }
+                const auto M = tab.meta(ps, sq);
+                T w, hw;
+                if (nama) {
+                    w = y0[k] - lam * re[k] + tau * (dd[k] + lam * re[k]);
+                    hw = h0[k] - lam * hre[k] + tau * (hdd[k] + lam * hre[k]);
+                } else {
+                    w = y0[k] + tau * dd[k];
+                    hw = h0[k] + tau * hdd[k];
+                }
+                const T z = clampv(hw + w * ilam, M.lo, M.hi);
+                yn[k] = w + lam * (hw - z);
+                sn[k] = yn[k] - y0[k];
+                pos_next(dv, ps);
+            }
+        }
+        stv(sv, e0, n, sn);
+        stv(yb, e0, n, yn);
+    });
     if (blockIdx.x == 0 && threadIdx.x == 0) {
         sc->lb_pending_valid = 1;
         sc->ls_done = 0;
@@ -523,9 +792,9 @@ __global__ void __launch_bounds__(kThreads) k_power_dots(int m, const T *r, cons
         b += he * he;
         c += re * re;
     }
-    double sums[3] = {a, b, c};
-    double maxs[1];
-    if (reduce_last<3, 0>(sums, maxs, partials, &sc->red_counter, tot) && threadIdx.x == 0) {
+    T sums[3] = {a, b, c};
+    T maxs[1];
+    if (reduce_last<T, 3, 0>(sums, maxs, partials, &sc->red_counter, tot) && threadIdx.x == 0) {
         sc->pw_L = tot[0] / tot[2];
         sc->pw_inv_norm = tot[1] > 0.0 ? 1.0 / sqrt(tot[1]) : 0.0;
     }
@@ -542,9 +811,9 @@ __global__ void k_normalize(int m, T *r, SolverScalars *sc, double *partials) {
     __shared__ double tot[1];
     T a = 0;
     for (int e = blockIdx.x * kThreads + threadIdx.x; e < m; e += gridDim.x * kThreads) a += r[e] * r[e];
-    double sums[1] = {a};
-    double maxs[1];
-    if (reduce_last<1, 0>(sums, maxs, partials, &sc->red_counter, tot) && threadIdx.x == 0)
+    T sums[1] = {a};
+    T maxs[1];
+    if (reduce_last<T, 1, 0>(sums, maxs, partials, &sc->red_counter, tot) && threadIdx.x == 0)
         sc->pw_inv_norm = tot[0] > 0.0 ? 1.0 / sqrt(tot[0]) : 0.0;
 }
 
@@ -568,6 +837,8 @@ DualView<T> make_view(stotree_t h) {
     dv.nu = h->nu;
     dv.nxu = h->nx + h->nu;
     dv.leaf_base = h->Np * (h->nx + h->nu);
+    dv.inv_nxu = 1.0f / (float)dv.nxu;
+    dv.inv_nx = 1.0f / (float)dv.nx;
     dv.sqp = h->at<T>(h->L.sqp);
     dv.box = h->at<T>(h->L.box);
     dv.Wc = h->at<T>(h->L.cost);
@@ -590,6 +861,7 @@ sto_status solver_impl(stotree_t h, int method, const sto_opts *o, const void *x
     const DualView<T> dv = make_view<T>(h);
     const int grid = red_grid(m);
     const bool nama = method == 0;
+    const size_t tabb = comp_tab_bytes(dv);
 
     cudaEvent_t e0, e1;
     STO_CUDA(h, cudaEventCreate(&e0));
@@ -640,7 +912,7 @@ sto_status solver_impl(stotree_t h, int method, const sto_opts *o, const void *x
     h->launches += 1;
     sto_status s = full_solve();
     if (s != STO_OK) return s;
-    k_point<T><<<grid, kThreads, 0, st>>>(dv, yb, hv, r, ringS, ringY, vs, 0, sc, part);
+    k_point<T><<<grid, kThreads, tabb, st>>>(dv, yb, hv, r, ringS, ringY, vs, 0, sc, part);
     h->launches += 1;
     if (!nama) {
         if ((s = lin_solve(r, hr)) != STO_OK) return s;
@@ -675,18 +947,18 @@ sto_status solver_impl(stotree_t h, int method, const sto_opts *o, const void *x
         for (int k = 0; k < ng; ++k) {
             const int last = k == ng - 1;
             if (k == 0)
-                k_ls<T, 4><<<grid, kThreads, 0, st>>>(dv, yb, hv, r, d, hr, hd, nama, gfirst[k], gcount[k], last, sc,
+                k_ls<T, 4><<<grid, kThreads, tabb, st>>>(dv, yb, hv, r, d, hr, hd, nama, gfirst[k], gcount[k], last, sc,
                                                      part);
             else if (k == 1)
-                k_ls<T, 8><<<grid, kThreads, 0, st>>>(dv, yb, hv, r, d, hr, hd, nama, gfirst[k], gcount[k], last, sc,
+                k_ls<T, 8><<<grid, kThreads, tabb, st>>>(dv, yb, hv, r, d, hr, hd, nama, gfirst[k], gcount[k], last, sc,
                                                      part);
             else
-                k_ls<T, 19><<<grid, kThreads, 0, st>>>(dv, yb, hv, r, d, hr, hd, nama, gfirst[k], gcount[k], last, sc,
+                k_ls<T, 19><<<grid, kThreads, tabb, st>>>(dv, yb, hv, r, d, hr, hd, nama, gfirst[k], gcount[k], last, sc,
                                                       part);
         }
-        k_fbstep<T><<<grid, kThreads, 0, st>>>(dv, yb, hv, r, d, hr, hd, nama, ringS, vs, sc);
+        k_fbstep<T><<<grid, kThreads, tabb, st>>>(dv, yb, hv, r, d, hr, hd, nama, ringS, vs, sc);
         if ((s = full_solve()) != STO_OK) return s;
-        k_point<T><<<grid, kThreads, 0, st>>>(dv, yb, hv, r, ringS, ringY, vs, nama ? 1 : 0, sc, part);
+        k_point<T><<<grid, kThreads, tabb, st>>>(dv, yb, hv, r, ringS, ringY, vs, nama ? 1 : 0, sc, part);
         if (!nama) {
             if ((s = lin_solve(r, hr)) != STO_OK) return s;
             k_grad<T><<<grid, kThreads, 0, st>>>(m, r, hr, g, ringS, ringY, vs, sc, part);
