@@ -96,6 +96,37 @@ __device__ __forceinline__ double v_dot<double>(const double2 &g, const double2 
     return fma(g.x, x.x, g.y * x.y);
 }
 
+// Explicit shared-space loads (the ring and the small vectors live in shared memory; the
+// pointers reach the consumer as generic pointers).
+template <class T>
+__device__ __forceinline__ typename V16<T>::type lds_vec(unsigned addr);
+template <>
+__device__ __forceinline__ float4 lds_vec<float>(unsigned addr) {
+    float4 v;
+    asm volatile("ld.shared.v4.f32 {%0, %1, %2, %3}, [%4];" : "=f"(v.x), "=f"(v.y), "=f"(v.z), "=f"(v.w) : "r"(addr));
+    return v;
+}
+template <>
+__device__ __forceinline__ double2 lds_vec<double>(unsigned addr) {
+    double2 v;
+    asm volatile("ld.shared.v2.f64 {%0, %1}, [%2];" : "=d"(v.x), "=d"(v.y) : "r"(addr));
+    return v;
+}
+template <class T>
+__device__ __forceinline__ T lds_one(unsigned addr);
+template <>
+__device__ __forceinline__ float lds_one<float>(unsigned addr) {
+    float v;
+    asm volatile("ld.shared.f32 %0, [%1];" : "=f"(v) : "r"(addr));
+    return v;
+}
+template <>
+__device__ __forceinline__ double lds_one<double>(unsigned addr) {
+    double v;
+    asm volatile("ld.shared.f64 %0, [%1];" : "=d"(v) : "r"(addr));
+    return v;
+}
+
 template <class T>
 __device__ __forceinline__ T warp_sum(T v) {
 #pragma unroll
@@ -376,6 +407,7 @@ struct Consumer {
     __device__ void axpy_rows(const T *M, int ld, int nrows, const T *coef, int cstride, int row0) {
         const int nvec = ld / VN;
         constexpr int RU = KV <= 1 ? 4 : 2;  // rows in flight per warp (register budget of 3 CTAs/SM)
+        const unsigned m_addr = sm_addr(M), c_addr = sm_addr(coef);
         for (int rb = warp; rb < nrows; rb += kCW * RU) {
             T cr[RU][NR];
             VT g[RU][KV];
@@ -384,12 +416,13 @@ struct Consumer {
                 const int r = rb + u * kCW;
                 const bool ok = r < nrows;
 #pragma unroll
-                for (int k = 0; k < NR; ++k) cr[u][k] = ok ? coef[k * cstride + row0 + r] : T(0);
-                const VT *row = reinterpret_cast<const VT *>(M + (size_t)(ok ? r : 0) * ld);
+                for (int k = 0; k < NR; ++k)
+                    cr[u][k] = ok ? lds_one<T>(c_addr + (unsigned)((k * cstride + row0 + r) * sizeof(T))) : T(0);
+                const unsigned row = m_addr + (unsigned)((ok ? r : 0) * ld * sizeof(T));
 #pragma unroll
                 for (int q = 0; q < KV; ++q) {
                     const int cv = lane + 32 * q;
-                    if (cv < nvec) g[u][q] = row[cv];
+                    if (cv < nvec) g[u][q] = lds_vec<T>(row + (unsigned)(cv * 16));
                 }
             }
 #pragma unroll
