@@ -30,7 +30,7 @@
 namespace sto {
 namespace {
 
-constexpr int kTC = 32;        // columns per solve tile (one per lane)
+constexpr int kTC = 64;        // columns per solve tile
 constexpr int kBT = 256;       // threads per block
 constexpr int kChunkE = 2048;  // elements per block of the elementwise passes
 constexpr int kMaxStages = 64;
@@ -109,227 +109,340 @@ struct RoundArgs {
 };
 
 constexpr int kMaxXU = 96;   // nx + nu <= 96 in the batched engine (nx <= 64)
+constexpr int kTP = kTC + 4; // row stride of the column tiles in shared memory (16-byte aligned)
+constexpr int kCG = kTC / 4; // column groups of 4 (one per thread of a row group)
+constexpr int kRG = kBT / kCG;  // row groups
+constexpr int kMR = (kMaxXU + kRG - 1) / kRG;  // output rows per thread, at most
+
+// Stage products as register-blocked FP32 GEMMs: thread (rg, cg) owns up to kMR consecutive
+// output rows and four columns of a tile, so each step of the inner dimension loads one float4 of
+// the tile and kMR matrix entries for 4 kMR fused multiply-adds per right-hand side.
+template <int NR>
+constexpr size_t bwd_smem() {  // G [nx][nxu], K [nu][nx], R~^-1 [nu][nu], S [NR][64][kTP], V [NR][32][kTP]
+    return sizeof(float) * (64 * kMaxXU + 32 * 64 + 32 * 32 + NR * 64 * kTP + NR * 32 * kTP);
+}
+template <int NR>
+constexpr size_t fwd_smem() {  // G [nx][nxu], K [nu][nx], X [NR][kMaxXU][kTP]
+    return sizeof(float) * (64 * kMaxXU + 32 * 64 + NR * kMaxXU * kTP);
+}
+
+// Columns of a task: instance data and node of each column, and whether its instance is active.
+struct ColInfo {
+    long long elem[kTC], sb[kTC], ub[kTC];
+    int node[kTC], ok[kTC];
+};
+template <int NR>
+__device__ __forceinline__ void load_cols(const RoundArgs<NR> &a, const GroupDev &g, const Task &tk, int n_t,
+                                          ColInfo &ci) {
+    if (threadIdx.x < kTC) {
+        const int col = threadIdx.x;
+        int ok = 0;
+        if (col < tk.ncols) {
+            const int cc = tk.col0 + col, inst = cc / n_t;
+            const InstDev &in = a.insts[g.inst0 + inst];
+            ci.elem[col] = in.elem0;
+            ci.sb[col] = in.sbase;
+            ci.ub[col] = in.ubase;
+            ci.node[col] = g.soff[tk.stage] + cc % n_t;
+            ok = !a.active || a.active[g.inst0 + inst];
+        }
+        ci.ok[col] = ok;
+    }
+}
 
 // Backward: parents of stage t.  S = sum_children s, o = [A | B]' S, v = y_u/2 + o_B + gu,
 // ubar = -(1/pi_t) R~^-1 v, s = y_x/2 + o_A + K_t' v + gx.
-template <int NR>
-constexpr size_t bwd_smem() {
-    return sizeof(float) * (64 * kMaxXU + 32 * 64 + 32 * 32 + NR * 64 * (kTC + 1) + NR * kMaxXU * (kTC + 1) +
-                            NR * 32 * (kTC + 1));
-}
-template <int NR>
-constexpr size_t fwd_smem() {
-    return sizeof(float) * (64 * kMaxXU + 32 * 64 + NR * kMaxXU * (kTC + 1));
-}
-
 template <int NR>
 __global__ void __launch_bounds__(kBT) k_bbwd(RoundArgs<NR> a, int task0) {
     const Task tk = a.tasks[task0 + blockIdx.x];
     const GroupDev &g = a.groups[tk.group];
     const int nx = g.nx, nu = g.nu, nxu = g.nxu, t = tk.stage;
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    extern __shared__ float bsm[];
-    float *Gs = bsm;                                   // [r][c], r < nx, c < nx+nu
-    float *Ks = Gs + 64 * kMaxXU;                      // K_t [a][c]
-    float *Rs = Ks + 32 * 64;                          // R~_t^-1 [a][b]
-    auto S = reinterpret_cast<float(*)[64][kTC + 1]>(Rs + 32 * 32);
-    auto O = reinterpret_cast<float(*)[kMaxXU][kTC + 1]>(Rs + 32 * 32 + NR * 64 * (kTC + 1));
-    auto V = reinterpret_cast<float(*)[32][kTC + 1]>(Rs + 32 * 32 + NR * 64 * (kTC + 1) + NR * kMaxXU * (kTC + 1));
+    extern __shared__ __align__(16) float bsm[];
+    __shared__ ColInfo ci;
+    float *Gs = bsm;                 // [r][c], r < nx, c < nx + nu
+    float *Ks = Gs + 64 * kMaxXU;    // K_t [a][c]
+    float *Rs = Ks + 32 * 64;        // R~_t^-1 [a][b]
+    float *S = Rs + 32 * 32;         // [k][r][col]; afterwards s (without y_x/2 + gx)
+    float *V = S + NR * 64 * kTP;    // [k][a][col]: v; afterwards ubar
     for (int e = threadIdx.x; e < nx * nxu; e += kBT) Gs[e] = g.G[e];
     for (int e = threadIdx.x; e < nu * nx; e += kBT) Ks[e] = g.Kt[(size_t)t * nu * nx + e];
     for (int e = threadIdx.x; e < nu * nu; e += kBT) Rs[e] = g.Ri[(size_t)t * nu * nu + e];
     const int n_t = g.soff[t + 1] - g.soff[t];
     const int bt = t < g.s ? g.b : 1;
     const bool leaf_children = t + 1 == g.N;
-    // S[k][r][col] = sum over the children of the column's parent
+    load_cols(a, g, tk, n_t, ci);
+    __syncthreads();
+    // S[k][r][col] = sum over the children of the column's node
     for (int e = threadIdx.x; e < NR * nx * kTC; e += kBT) {
         const int k = e / (nx * kTC), rem = e - k * nx * kTC, col = rem / nx, r = rem - col * nx;
         float acc = 0.f;
-        if (col < tk.ncols) {
-            const int cc = tk.col0 + col, inst = cc / n_t, i = g.soff[t] + cc % n_t;
-            const InstDev &in = a.insts[g.inst0 + inst];
-            if (!a.active || a.active[g.inst0 + inst]) {
-                const int j0 = g.soff[t + 1] + (i - g.soff[t]) * bt;
-                for (int j = j0; j < j0 + bt; ++j) {
-                    if (leaf_children) {
-                        const float sc = a.scaled ? g.sq[t + 1] : 1.f;
-                        acc += 0.5f * sc * a.y[k][in.elem0 + doff(g, j) + r];
-                    } else {
-                        acc += a.s[k * a.s_stride + in.sbase + (long long)j * nx + r];
-                    }
+        if (ci.ok[col]) {
+            const int i = ci.node[col];
+            const int j0 = g.soff[t + 1] + (i - g.soff[t]) * bt;
+            for (int j = j0; j < j0 + bt; ++j) {
+                if (leaf_children) {
+                    const float sc = a.scaled ? g.sq[t + 1] : 1.f;
+                    acc += 0.5f * sc * a.y[k][ci.elem[col] + doff(g, j) + r];
+                } else {
+                    acc += a.s[k * a.s_stride + ci.sb[col] + (long long)j * nx + r];
                 }
             }
         }
-        S[k][r][col] = acc;
+        S[(k * 64 + r) * kTP + col] = acc;
     }
     __syncthreads();
-    // O = [A | B]' S: warp over output rows, lane over columns
-    for (int c = warp; c < nxu; c += kBT / 32) {
-        float acc[NR];
+    const int cg = threadIdx.x % kCG, rg = threadIdx.x / kCG;
+    const int mr = (nxu + kRG - 1) / kRG, r0 = rg * mr;
+    float acc[NR][kMR][4];
 #pragma unroll
-        for (int k = 0; k < NR; ++k) acc[k] = 0.f;
-        for (int r = 0; r < nx; ++r) {
-            const float gv = Gs[r * nxu + c];
+    for (int k = 0; k < NR; ++k)
 #pragma unroll
-            for (int k = 0; k < NR; ++k) acc[k] = fmaf(gv, S[k][r][lane], acc[k]);
-        }
+        for (int m = 0; m < kMR; ++m)
 #pragma unroll
-        for (int k = 0; k < NR; ++k) O[k][c][lane] = acc[k];
+            for (int q = 0; q < 4; ++q) acc[k][m][q] = 0.f;
+    // o = [A | B]' S
+    for (int r = 0; r < nx; ++r) {
+        float4 s4[NR];
+#pragma unroll
+        for (int k = 0; k < NR; ++k) s4[k] = *reinterpret_cast<const float4 *>(S + (k * 64 + r) * kTP + cg * 4);
+#pragma unroll
+        for (int m = 0; m < kMR; ++m)
+            if (m < mr && r0 + m < nxu) {
+                const float gv = Gs[r * nxu + r0 + m];
+#pragma unroll
+                for (int k = 0; k < NR; ++k) {
+                    acc[k][m][0] = fmaf(gv, s4[k].x, acc[k][m][0]);
+                    acc[k][m][1] = fmaf(gv, s4[k].y, acc[k][m][1]);
+                    acc[k][m][2] = fmaf(gv, s4[k].z, acc[k][m][2]);
+                    acc[k][m][3] = fmaf(gv, s4[k].w, acc[k][m][3]);
+                }
+            }
     }
-    __syncthreads();
-    // v = y_u/2 + o_B + gu
-    for (int e = threadIdx.x; e < NR * nu * kTC; e += kBT) {
-        const int k = e / (nu * kTC), rem = e - k * nu * kTC, col = rem / nu, aa = rem - col * nu;
-        float val = 0.f;
-        if (col < tk.ncols) {
-            const int cc = tk.col0 + col, inst = cc / n_t, i = g.soff[t] + cc % n_t;
-            const InstDev &in = a.insts[g.inst0 + inst];
-            const long long o = in.elem0 + doff(g, i) + nx + aa;
-            const float sc = a.scaled ? g.sq[t] : 1.f;
-            val = 0.5f * sc * a.y[k][o] + O[k][nx + aa][col] + (a.homog ? 0.f : a.gam[o]);
-        }
-        V[k][aa][col] = val;
-    }
-    __syncthreads();
-    // ubar = -(1/pi_t) R~^-1 v  (rows a of the output: warps)
-    const float ipi = 1.f / g.pi[t];
-    for (int aa = warp; aa < nu; aa += kBT / 32) {
-        float acc[NR];
+    // o_B rows -> V; then v = o_B + y_u/2 + gu
 #pragma unroll
-        for (int k = 0; k < NR; ++k) acc[k] = 0.f;
-        for (int bb = 0; bb < nu; ++bb) {
-            const float rv = Rs[aa * nu + bb];
-#pragma unroll
-            for (int k = 0; k < NR; ++k) acc[k] = fmaf(rv, V[k][bb][lane], acc[k]);
-        }
-        if (lane < tk.ncols) {
-            const int cc = tk.col0 + lane, inst = cc / n_t, i = g.soff[t] + cc % n_t;
-            const InstDev &in = a.insts[g.inst0 + inst];
-#pragma unroll
-            for (int k = 0; k < NR; ++k) a.ubar[k * a.u_stride + in.ubase + (long long)i * nu + aa] = -ipi * acc[k];
-        }
-    }
-    // s = y_x/2 + o_A + K' v + gx
-    for (int r = warp; r < nx; r += kBT / 32) {
-        float acc[NR];
-#pragma unroll
-        for (int k = 0; k < NR; ++k) acc[k] = O[k][r][lane];
-        for (int aa = 0; aa < nu; ++aa) {
-            const float kv = Ks[aa * nx + r];
-#pragma unroll
-            for (int k = 0; k < NR; ++k) acc[k] = fmaf(kv, V[k][aa][lane], acc[k]);
-        }
-        if (lane < tk.ncols) {
-            const int cc = tk.col0 + lane, inst = cc / n_t, i = g.soff[t] + cc % n_t;
-            const InstDev &in = a.insts[g.inst0 + inst];
-            const long long o = in.elem0 + doff(g, i) + r;
-            const float sc = a.scaled ? g.sq[t] : 1.f;
+    for (int m = 0; m < kMR; ++m) {
+        const int c = r0 + m;
+        if (m < mr && c >= nx && c < nxu)
 #pragma unroll
             for (int k = 0; k < NR; ++k)
-                a.s[k * a.s_stride + in.sbase + (long long)i * nx + r] =
-                    acc[k] + 0.5f * sc * a.y[k][o] + (a.homog ? 0.f : a.gam[o]);
+                *reinterpret_cast<float4 *>(V + (k * 32 + c - nx) * kTP + cg * 4) =
+                    make_float4(acc[k][m][0], acc[k][m][1], acc[k][m][2], acc[k][m][3]);
+    }
+    __syncthreads();
+    {
+        const float sc = a.scaled ? g.sq[t] : 1.f;
+        for (int e = threadIdx.x; e < NR * nu * kTC; e += kBT) {
+            const int k = e / (nu * kTC), rem = e - k * nu * kTC, col = rem / nu, aa = rem - col * nu;
+            if (ci.ok[col]) {
+                const long long o = ci.elem[col] + doff(g, ci.node[col]) + nx + aa;
+                V[(k * 32 + aa) * kTP + col] += 0.5f * sc * a.y[k][o] + (a.homog ? 0.f : a.gam[o]);
+            }
+        }
+    }
+    __syncthreads();
+    // rows c < nx: s = o_A + K' v; rows c = nx + a: ubar = -(1/pi_t) R~^-1 v
+#pragma unroll
+    for (int m = 0; m < kMR; ++m)
+        if (r0 + m >= nx)
+#pragma unroll
+            for (int k = 0; k < NR; ++k)
+#pragma unroll
+                for (int q = 0; q < 4; ++q) acc[k][m][q] = 0.f;
+    for (int aa = 0; aa < nu; ++aa) {
+        float4 v4[NR];
+#pragma unroll
+        for (int k = 0; k < NR; ++k) v4[k] = *reinterpret_cast<const float4 *>(V + (k * 32 + aa) * kTP + cg * 4);
+#pragma unroll
+        for (int m = 0; m < kMR; ++m) {
+            const int c = r0 + m;
+            if (m < mr && c < nxu) {
+                const float cf = c < nx ? Ks[aa * nx + c] : Rs[(c - nx) * nu + aa];
+#pragma unroll
+                for (int k = 0; k < NR; ++k) {
+                    acc[k][m][0] = fmaf(cf, v4[k].x, acc[k][m][0]);
+                    acc[k][m][1] = fmaf(cf, v4[k].y, acc[k][m][1]);
+                    acc[k][m][2] = fmaf(cf, v4[k].z, acc[k][m][2]);
+                    acc[k][m][3] = fmaf(cf, v4[k].w, acc[k][m][3]);
+                }
+            }
+        }
+    }
+    __syncthreads();  // every thread is done with S and V
+    const float ipi = 1.f / g.pi[t];
+#pragma unroll
+    for (int m = 0; m < kMR; ++m) {
+        const int c = r0 + m;
+        if (m < mr && c < nxu)
+#pragma unroll
+            for (int k = 0; k < NR; ++k) {
+                float *dst = c < nx ? S + (k * 64 + c) * kTP + cg * 4 : V + (k * 32 + c - nx) * kTP + cg * 4;
+                const float f = c < nx ? 1.f : -ipi;
+                *reinterpret_cast<float4 *>(dst) =
+                    make_float4(f * acc[k][m][0], f * acc[k][m][1], f * acc[k][m][2], f * acc[k][m][3]);
+            }
+    }
+    __syncthreads();
+    // coalesced write-out: ubar, and s = y_x/2 + (o_A + K'v) + gx
+    for (int e = threadIdx.x; e < NR * nu * kTC; e += kBT) {
+        const int k = e / (nu * kTC), rem = e - k * nu * kTC, col = rem / nu, aa = rem - col * nu;
+        if (ci.ok[col])
+            a.ubar[k * a.u_stride + ci.ub[col] + (long long)ci.node[col] * nu + aa] = V[(k * 32 + aa) * kTP + col];
+    }
+    {
+        const float sc = a.scaled ? g.sq[t] : 1.f;
+        for (int e = threadIdx.x; e < NR * nx * kTC; e += kBT) {
+            const int k = e / (nx * kTC), rem = e - k * nx * kTC, col = rem / nx, r = rem - col * nx;
+            if (ci.ok[col]) {
+                const int i = ci.node[col];
+                const long long o = ci.elem[col] + doff(g, i) + r;
+                a.s[k * a.s_stride + ci.sb[col] + (long long)i * nx + r] =
+                    S[(k * 64 + r) * kTP + col] + 0.5f * sc * a.y[k][o] + (a.homog ? 0.f : a.gam[o]);
+            }
         }
     }
 }
 
-// Forward: nodes of stage t.  x from the parent's pass (or x0 at the root); u = K_t x + ubar;
+// Forward: nodes of stage t.  x from the parent's pass (or x0 at the root); u = K x + ubar;
 // h = S [x; u]; every child j gets x^j = A x + B u + c^j.  Leaves (t = N) only write h.
 template <int NR>
 __global__ void __launch_bounds__(kBT) k_bfwd(RoundArgs<NR> a, int task0) {
     const Task tk = a.tasks[task0 + blockIdx.x];
     const GroupDev &g = a.groups[tk.group];
     const int nx = g.nx, nu = g.nu, nxu = g.nxu, t = tk.stage;
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    extern __shared__ float bsm[];
+    extern __shared__ __align__(16) float bsm[];
+    __shared__ ColInfo ci;
     float *Gs = bsm;
     float *Ks = Gs + 64 * kMaxXU;
-    auto X = reinterpret_cast<float(*)[kMaxXU][kTC + 1]>(Ks + 32 * 64);  // [x; u] per column
+    float *X = Ks + 32 * 64;  // [k][row][col]: x then u per column
     const bool leaf = t == g.N;
     for (int e = threadIdx.x; e < nx * nxu; e += kBT) Gs[e] = g.G[e];
     if (!leaf)
         for (int e = threadIdx.x; e < nu * nx; e += kBT) Ks[e] = g.Kt[(size_t)t * nu * nx + e];
     const int n_t = g.soff[t + 1] - g.soff[t];
+    load_cols(a, g, tk, n_t, ci);
+    __syncthreads();
     for (int e = threadIdx.x; e < NR * nx * kTC; e += kBT) {
         const int k = e / (nx * kTC), rem = e - k * nx * kTC, col = rem / nx, r = rem - col * nx;
         float val = 0.f;
-        if (col < tk.ncols) {
-            const int cc = tk.col0 + col, inst = cc / n_t, i = g.soff[t] + cc % n_t;
-            const InstDev &in = a.insts[g.inst0 + inst];
-            if (t == 0)
+        if (ci.ok[col]) {
+            if (t == 0) {
+                const int inst = (tk.col0 + col) / n_t;
                 val = a.homog ? 0.f : a.x0[(long long)(g.inst0 + inst) * 64 + r];
-            else
-                val = a.xs[k * a.s_stride + in.sbase + (long long)i * nx + r];
+            } else {
+                val = a.xs[k * a.s_stride + ci.sb[col] + (long long)ci.node[col] * nx + r];
+            }
         }
-        X[k][r][col] = val;
+        X[(k * kMaxXU + r) * kTP + col] = val;
     }
     __syncthreads();
+    const int cg = threadIdx.x % kCG, rg = threadIdx.x / kCG;
     const float sc = a.scaled ? g.sq[t] : 1.f;
-    if (leaf) {
-        for (int e = threadIdx.x; e < NR * nx * kTC; e += kBT) {
-            const int k = e / (nx * kTC), rem = e - k * nx * kTC, col = rem / nx, r = rem - col * nx;
-            if (col < tk.ncols) {
-                const int cc = tk.col0 + col, inst = cc / n_t, i = g.soff[t] + cc % n_t;
-                const InstDev &in = a.insts[g.inst0 + inst];
-                if (!a.active || a.active[g.inst0 + inst]) a.h[k][in.elem0 + doff(g, i) + r] = sc * X[k][r][col];
-            }
+    if (!leaf) {
+        // u = K x (rows a of u over the row groups), then + ubar
+        const int mu = (nu + kRG - 1) / kRG, a0 = rg * mu;
+        constexpr int kMU = (32 + kRG - 1) / kRG;
+        float u[NR][kMU][4];
+#pragma unroll
+        for (int k = 0; k < NR; ++k)
+#pragma unroll
+            for (int m = 0; m < kMU; ++m)
+#pragma unroll
+                for (int q = 0; q < 4; ++q) u[k][m][q] = 0.f;
+        for (int r = 0; r < nx; ++r) {
+            float4 x4[NR];
+#pragma unroll
+            for (int k = 0; k < NR; ++k)
+                x4[k] = *reinterpret_cast<const float4 *>(X + (k * kMaxXU + r) * kTP + cg * 4);
+#pragma unroll
+            for (int m = 0; m < kMU; ++m)
+                if (m < mu && a0 + m < nu) {
+                    const float kv = Ks[(a0 + m) * nx + r];
+#pragma unroll
+                    for (int k = 0; k < NR; ++k) {
+                        u[k][m][0] = fmaf(kv, x4[k].x, u[k][m][0]);
+                        u[k][m][1] = fmaf(kv, x4[k].y, u[k][m][1]);
+                        u[k][m][2] = fmaf(kv, x4[k].z, u[k][m][2]);
+                        u[k][m][3] = fmaf(kv, x4[k].w, u[k][m][3]);
+                    }
+                }
         }
-        return;
+#pragma unroll
+        for (int m = 0; m < kMU; ++m)
+            if (m < mu && a0 + m < nu)
+#pragma unroll
+                for (int k = 0; k < NR; ++k)
+                    *reinterpret_cast<float4 *>(X + (k * kMaxXU + nx + a0 + m) * kTP + cg * 4) =
+                        make_float4(u[k][m][0], u[k][m][1], u[k][m][2], u[k][m][3]);
+        __syncthreads();
+        for (int e = threadIdx.x; e < NR * nu * kTC; e += kBT) {
+            const int k = e / (nu * kTC), rem = e - k * nu * kTC, col = rem / nu, aa = rem - col * nu;
+            if (ci.ok[col])
+                X[(k * kMaxXU + nx + aa) * kTP + col] +=
+                    a.ubar[k * a.u_stride + ci.ub[col] + (long long)ci.node[col] * nu + aa];
+        }
+        __syncthreads();
     }
-    // u = K x + ubar
-    for (int aa = warp; aa < nu; aa += kBT / 32) {
-        float acc[NR];
-#pragma unroll
-        for (int k = 0; k < NR; ++k) acc[k] = 0.f;
-        for (int c = 0; c < nx; ++c) {
-            const float kv = Ks[aa * nx + c];
-#pragma unroll
-            for (int k = 0; k < NR; ++k) acc[k] = fmaf(kv, X[k][c][lane], acc[k]);
-        }
-        if (lane < tk.ncols) {
-            const int cc = tk.col0 + lane, inst = cc / n_t, i = g.soff[t] + cc % n_t;
-            const InstDev &in = a.insts[g.inst0 + inst];
-#pragma unroll
-            for (int k = 0; k < NR; ++k) acc[k] += a.ubar[k * a.u_stride + in.ubase + (long long)i * nu + aa];
-        }
-#pragma unroll
-        for (int k = 0; k < NR; ++k) X[k][nx + aa][lane] = acc[k];
-    }
-    __syncthreads();
     // h for the stage's nodes, primal scratch
-    for (int e = threadIdx.x; e < NR * nxu * kTC; e += kBT) {
-        const int k = e / (nxu * kTC), rem = e - k * nxu * kTC, col = rem / nxu, r = rem - col * nxu;
-        if (col < tk.ncols) {
-            const int cc = tk.col0 + col, inst = cc / n_t, i = g.soff[t] + cc % n_t;
-            const InstDev &in = a.insts[g.inst0 + inst];
-            if (!a.active || a.active[g.inst0 + inst]) {
-                const float val = X[k][r][col];
-                a.h[k][in.elem0 + doff(g, i) + r] = sc * val;
-                if (r < nx)
-                    a.xs[k * a.s_stride + in.sbase + (long long)i * nx + r] = val;
-                else
-                    a.us[k * a.u_stride + in.ubase + (long long)i * nu + r - nx] = val;
-            }
+    const int rows = leaf ? nx : nxu;
+    for (int e = threadIdx.x; e < NR * rows * kTC; e += kBT) {
+        const int k = e / (rows * kTC), rem = e - k * rows * kTC, col = rem / rows, r = rem - col * rows;
+        if (ci.ok[col]) {
+            const int i = ci.node[col];
+            const float val = X[(k * kMaxXU + r) * kTP + col];
+            a.h[k][ci.elem[col] + doff(g, i) + r] = sc * val;
+            if (r < nx)
+                a.xs[k * a.s_stride + ci.sb[col] + (long long)i * nx + r] = val;
+            else
+                a.us[k * a.u_stride + ci.ub[col] + (long long)i * nu + r - nx] = val;
         }
     }
-    // children: x^j = [A | B][x; u] + c^j
+    if (leaf) return;
+    // children: x^j = [A | B][x; u] + c^j (rows r of x over the row groups)
+    const int mx = (nx + kRG - 1) / kRG, x0r = rg * mx;
+    constexpr int kMX = (64 + kRG - 1) / kRG;
+    float acc[NR][kMX][4];
+#pragma unroll
+    for (int k = 0; k < NR; ++k)
+#pragma unroll
+        for (int m = 0; m < kMX; ++m)
+#pragma unroll
+            for (int q = 0; q < 4; ++q) acc[k][m][q] = 0.f;
+    for (int qq = 0; qq < nxu; ++qq) {
+        float4 x4[NR];
+#pragma unroll
+        for (int k = 0; k < NR; ++k) x4[k] = *reinterpret_cast<const float4 *>(X + (k * kMaxXU + qq) * kTP + cg * 4);
+#pragma unroll
+        for (int m = 0; m < kMX; ++m)
+            if (m < mx && x0r + m < nx) {
+                const float gv = Gs[(x0r + m) * nxu + qq];
+#pragma unroll
+                for (int k = 0; k < NR; ++k) {
+                    acc[k][m][0] = fmaf(gv, x4[k].x, acc[k][m][0]);
+                    acc[k][m][1] = fmaf(gv, x4[k].y, acc[k][m][1]);
+                    acc[k][m][2] = fmaf(gv, x4[k].z, acc[k][m][2]);
+                    acc[k][m][3] = fmaf(gv, x4[k].w, acc[k][m][3]);
+                }
+            }
+    }
+    __syncthreads();  // every thread is done with X
+#pragma unroll
+    for (int m = 0; m < kMX; ++m)
+        if (m < mx && x0r + m < nx)
+#pragma unroll
+            for (int k = 0; k < NR; ++k)
+                *reinterpret_cast<float4 *>(X + (k * kMaxXU + x0r + m) * kTP + cg * 4) =
+                    make_float4(acc[k][m][0], acc[k][m][1], acc[k][m][2], acc[k][m][3]);
+    __syncthreads();
     const int bt = t < g.s ? g.b : 1;
-    for (int r = warp; r < nx; r += kBT / 32) {
-        float acc[NR];
-#pragma unroll
-        for (int k = 0; k < NR; ++k) acc[k] = 0.f;
-        for (int c = 0; c < nxu; ++c) {
-            const float gv = Gs[r * nxu + c];
-#pragma unroll
-            for (int k = 0; k < NR; ++k) acc[k] = fmaf(gv, X[k][c][lane], acc[k]);
-        }
-        if (lane < tk.ncols) {
-            const int cc = tk.col0 + lane, inst = cc / n_t, i = g.soff[t] + cc % n_t;
-            const InstDev &in = a.insts[g.inst0 + inst];
+    for (int e = threadIdx.x; e < NR * nx * kTC; e += kBT) {
+        const int k = e / (nx * kTC), rem = e - k * nx * kTC, col = rem / nx, r = rem - col * nx;
+        if (ci.ok[col]) {
+            const int i = ci.node[col];
             const int j0 = g.soff[t + 1] + (i - g.soff[t]) * bt;
+            const float xv = X[(k * kMaxXU + r) * kTP + col];
             for (int j = j0; j < j0 + bt; ++j) {
-                const float cj = a.homog ? 0.f : a.c[in.sbase + (long long)j * nx + r];
-#pragma unroll
-                for (int k = 0; k < NR; ++k) a.xs[k * a.s_stride + in.sbase + (long long)j * nx + r] = acc[k] + cj;
+                const float cj = a.homog ? 0.f : a.c[ci.sb[col] + (long long)j * nx + r];
+                a.xs[k * a.s_stride + ci.sb[col] + (long long)j * nx + r] = xv + cj;
             }
         }
     }
@@ -345,36 +458,41 @@ __global__ void k_bgamma(const GroupDev *groups, const InstDev *insts, const Tas
     const int n_t = g.soff[t + 1] - g.soff[t];
     const int bt = t < g.s ? g.b : 1;
     const double *P = Pt + ptoff[tk.group] + (size_t)(t + 1) * nx * nx;
-    __shared__ double cs[64][kTC];
-    __shared__ double w[64][kTC];
-    for (int e = threadIdx.x; e < nx * kTC; e += blockDim.x) {
-        const int col = e / nx, r = e % nx;
-        double acc = 0.0;
-        if (col < tk.ncols) {
-            const int cc = tk.col0 + col, inst = cc / n_t, i = g.soff[t] + cc % n_t;
-            const InstDev &in = insts[g.inst0 + inst];
-            const int j0 = g.soff[t + 1] + (i - g.soff[t]) * bt;
-            for (int j = j0; j < j0 + bt; ++j) acc += (double)c[in.sbase + (long long)j * nx + r];
-        }
-        cs[r][col] = acc;
-    }
-    __syncthreads();
-    for (int e = threadIdx.x; e < nx * kTC; e += blockDim.x) {
-        const int col = e / nx, r = e % nx;
-        double acc = 0.0;
-        for (int k = 0; k < nx; ++k) acc += P[r * nx + k] * cs[k][col];
-        w[r][col] = acc;
-    }
-    __syncthreads();
+    constexpr int kGH = 32;  // columns per pass (FP64 tiles within the static shared-memory limit)
+    __shared__ double cs[64][kGH];
+    __shared__ double w[64][kGH];
     const double pnext = g.pi[t + 1];
-    for (int e = threadIdx.x; e < nxu * kTC; e += blockDim.x) {
-        const int col = e / nxu, cidx = e % nxu;
-        if (col >= tk.ncols) continue;
-        const int cc = tk.col0 + col, inst = cc / n_t, i = g.soff[t] + cc % n_t;
-        const InstDev &in = insts[g.inst0 + inst];
-        double acc = 0.0;
-        for (int r = 0; r < nx; ++r) acc += (double)g.G[r * nxu + cidx] * w[r][col];
-        gam[in.elem0 + doff(g, i) + cidx] = (float)(pnext * acc);
+    for (int h0 = 0; h0 < tk.ncols; h0 += kGH) {
+        const int nc = min(kGH, tk.ncols - h0);
+        for (int e = threadIdx.x; e < nx * kGH; e += blockDim.x) {
+            const int col = e / nx, r = e % nx;
+            double acc = 0.0;
+            if (col < nc) {
+                const int cc = tk.col0 + h0 + col, inst = cc / n_t, i = g.soff[t] + cc % n_t;
+                const InstDev &in = insts[g.inst0 + inst];
+                const int j0 = g.soff[t + 1] + (i - g.soff[t]) * bt;
+                for (int j = j0; j < j0 + bt; ++j) acc += (double)c[in.sbase + (long long)j * nx + r];
+            }
+            cs[r][col] = acc;
+        }
+        __syncthreads();
+        for (int e = threadIdx.x; e < nx * kGH; e += blockDim.x) {
+            const int col = e / nx, r = e % nx;
+            double acc = 0.0;
+            for (int k = 0; k < nx; ++k) acc += P[r * nx + k] * cs[k][col];
+            w[r][col] = acc;
+        }
+        __syncthreads();
+        for (int e = threadIdx.x; e < nxu * kGH; e += blockDim.x) {
+            const int col = e / nxu, cidx = e % nxu;
+            if (col >= nc) continue;
+            const int cc = tk.col0 + h0 + col, inst = cc / n_t, i = g.soff[t] + cc % n_t;
+            const InstDev &in = insts[g.inst0 + inst];
+            double acc = 0.0;
+            for (int r = 0; r < nx; ++r) acc += (double)g.G[r * nxu + cidx] * w[r][col];
+            gam[in.elem0 + doff(g, i) + cidx] = (float)(pnext * acc);
+        }
+        __syncthreads();
     }
 }
 
