@@ -29,6 +29,20 @@ RECIPES = {
 }
 
 
+def largest_box(frac=0.8):
+    """The largest instance's box (its statement says only "box constraints"): inputs only, at
+    80 % of the largest |u_k| of the unconstrained solution on a calibration tree built by the
+    same recipe (horizon 24, binary for the first 4 stages: 351 nodes, small enough for the
+    oracle); states unbounded, so every draw stays feasible."""
+    p = W.largest_unboxed(5, tree=W.largest_tree(branch_stages=4))
+    nn = p.tree.num_nodes
+    dense = W.Problem(tree=p.tree, nx=p.nx, nu=p.nu, A=p.A[0:nn], B=p.B[0:nn], c=p.c[0:nn], Q=p.Q, R=p.R, PN=p.PN,
+                      q=p.q, r=p.r, pN=p.pN, xlo=p.xlo, xhi=p.xhi, ulo=p.ulo, uhi=p.uhi, x0=p.x0)
+    o = LQOracle(dense)
+    _, u = o.solve(np.zeros(o.m))
+    return np.full(p.nx, np.inf), frac * np.max(np.abs(u), axis=0)
+
+
 def box_of(p, frac=0.8, protect=2, margin=1.02):
     o = LQOracle(p)
     x, u = o.solve(np.zeros(o.m))
@@ -47,13 +61,20 @@ def main(names):
         with open(path) as f:
             boxes = json.load(f)
     for name in names:
-        xmax, umax = box_of(RECIPES[name]())
-        boxes[name] = {"xmax": [float(v) for v in xmax], "umax": [float(v) for v in umax],
-                       "recipe": "max(0.8 * max over nodes, 1.02 * max over stages 1-2 (inputs 0-1)) of |x_k|, |u_k| of the oracle's x(0)"}
+        if name == "largest":
+            xmax, umax = largest_box()
+            boxes[name] = {"xmax": None, "umax": [float(v) for v in umax],
+                           "recipe": "inputs only: 0.8 * max over nodes of |u_k| of the oracle's x(0) on the "
+                                     "calibration tree (horizon 24, binary for 4 stages); states unbounded"}
+        else:
+            xmax, umax = box_of(RECIPES[name]())
+            boxes[name] = {"xmax": [float(v) for v in xmax], "umax": [float(v) for v in umax],
+                           "recipe": "max(0.8 * max over nodes, 1.02 * max over stages 1-2 (inputs 0-1)) of |x_k|, "
+                                     "|u_k| of the oracle's x(0)"}
         print(name, "xmax range", xmax.min(), xmax.max(), "umax range", umax.min(), umax.max())
     with open(path, "w") as f:
         json.dump(boxes, f, indent=1)
 
 
 if __name__ == "__main__":
-    main(sys.argv[1:] or list(RECIPES))
+    main(sys.argv[1:] or list(RECIPES) + ["largest"])

@@ -242,7 +242,10 @@ def load_box(name: str):
     if name not in boxes:
         raise KeyError(f"no stored box for workload {name!r}; run oracle/make_boxes.py")
     b = boxes[name]
-    return np.asarray(b["xmax"], dtype=np.float64), np.asarray(b["umax"], dtype=np.float64)
+    umax = np.asarray(b["umax"], dtype=np.float64)
+    xmax = np.full(LARGEST_SHAPE["nx"] if b["xmax"] is None else len(b["xmax"]), np.inf) if b["xmax"] is None \
+        else np.asarray(b["xmax"], dtype=np.float64)
+    return xmax, umax
 
 
 def with_box(p: Problem, xmax: np.ndarray, umax: np.ndarray) -> Problem:
@@ -435,3 +438,106 @@ def warm_start_draws(system: Group, first_seed: int, count: int, dtype=np.float6
     with ThreadPoolExecutor(min(16, os.cpu_count() or 1)) as ex:
         list(ex.map(one, range(count)))
     return dataclasses.replace(system, x0=x0, c=c)
+
+
+# Largest single instance: horizon 24, binary for 12 stages then one child (4096 scenarios,
+# 57,343 nodes), nx = 200, nu = 100 (16.8 M primal and dual variables).  Its per-node data would
+# take 27.5 GB of FP64 host memory, so it is generated block by block on demand: node block b
+# (512 nodes) comes from its own generator seeded (seed, b) and is identical however it is
+# requested.
+LARGEST_SHAPE = dict(horizon=24, branching=2, branch_stages=12, nx=200, nu=100)
+LARGE_BLOCK = 512
+
+
+class NodeBlocks:
+    """Per-node A_j = A + pert N(0,1), B_j = N(0,1) / sqrt(nx), c_j = w_std N(0,1) (node 0: zeros),
+    generated in blocks of LARGE_BLOCK nodes.  Draw order inside a block: A perturbations, B, c."""
+
+    def __init__(self, seed: int, num_nodes: int, nx: int, nu: int, A0: np.ndarray, pert: float, w_std: float):
+        self.seed, self.nn, self.nx, self.nu = seed, num_nodes, nx, nu
+        self.A0, self.pert, self.w_std = A0, pert, w_std
+        self._cache = {}
+
+    def block(self, b: int):
+        if b not in self._cache:
+            f = b * LARGE_BLOCK
+            n = min(LARGE_BLOCK, self.nn - f)
+            r = np.random.default_rng([self.seed, b])
+            A = self.A0[None] + self.pert * r.standard_normal((n, self.nx, self.nx))
+            B = r.standard_normal((n, self.nx, self.nu)) * (1.0 / np.sqrt(self.nx))
+            c = self.w_std * r.standard_normal((n, self.nx))
+            if f == 0:
+                A[0], B[0], c[0] = 0.0, 0.0, 0.0
+            if len(self._cache) >= 8:
+                self._cache.pop(next(iter(self._cache)))
+            self._cache[b] = (A, B, c)
+        return self._cache[b]
+
+    def prefetch(self, first: int, stop: int):
+        """Generate the blocks covering nodes [first, stop) in parallel (the generator releases the GIL)."""
+        from concurrent.futures import ThreadPoolExecutor
+        bs = [b for b in range(first // LARGE_BLOCK, (stop - 1) // LARGE_BLOCK + 1) if b not in self._cache]
+        if len(bs) > 1:
+            with ThreadPoolExecutor(min(8, len(bs))) as ex:
+                out = list(ex.map(lambda b: (b, NodeBlocks.block(self, b)), bs))
+            for b, v in out:
+                self._cache[b] = v
+
+    def rows(self, field: int, first: int, stop: int) -> np.ndarray:
+        self.prefetch(first, stop)
+        parts = []
+        n = first
+        while n < stop:
+            b = n // LARGE_BLOCK
+            lo = n - b * LARGE_BLOCK
+            hi = min(stop - b * LARGE_BLOCK, LARGE_BLOCK)
+            parts.append(self.block(b)[field][lo:hi])
+            n = b * LARGE_BLOCK + hi
+        return np.concatenate(parts, axis=0)
+
+
+class NodeArray:
+    """Sliceable view of one field (0: A, 1: B, 2: c) of NodeBlocks: x[f:s] generates on demand."""
+
+    def __init__(self, blocks: NodeBlocks, field: int, shape):
+        self.blocks, self.field, self.shape = blocks, field, shape
+
+    def __len__(self):
+        return self.shape[0]
+
+    def __getitem__(self, key):
+        if isinstance(key, slice):
+            first, stop, step = key.indices(self.shape[0])
+            assert step == 1
+            return self.blocks.rows(self.field, first, stop)
+        return self.blocks.rows(self.field, int(key), int(key) + 1)[0]
+
+
+def largest_tree(horizon: int = LARGEST_SHAPE["horizon"], branch_stages: int = LARGEST_SHAPE["branch_stages"]) -> Tree:
+    return tree_from_branching([LARGEST_SHAPE["branching"]] * branch_stages + [1] * (horizon - branch_stages))
+
+
+def largest_unboxed(seed: int = 5, tree: Tree | None = None) -> Problem:
+    """The largest instance before its box: A at spectral radius 0.98 with per-node perturbation
+    0.02 N(0,1), B ~ N(0, 1/nx), w ~ N(0, 0.05^2), Q = I, R = 0.1 I, P_N = I, x0 ~ U[-3, 3].
+    Draw order of the shared data: A, x0."""
+    nx, nu = LARGEST_SHAPE["nx"], LARGEST_SHAPE["nu"]
+    rng = np.random.default_rng(seed)
+    A0 = spectral_rescale(rng.standard_normal((nx, nx)), 0.98)
+    x0 = rng.uniform(-3.0, 3.0, size=nx)
+    tree = largest_tree() if tree is None else tree
+    nn = tree.num_nodes
+    blocks = NodeBlocks(seed, nn, nx, nu, A0, 0.02, 0.05)
+    inf = np.inf
+    return Problem(tree=tree, nx=nx, nu=nu, A=NodeArray(blocks, 0, (nn, nx, nx)), B=NodeArray(blocks, 1, (nn, nx, nu)),
+                   c=NodeArray(blocks, 2, (nn, nx)), Q=np.ones(nx), R=0.1 * np.ones(nu), PN=np.ones(nx),
+                   q=np.zeros(nx), r=np.zeros(nu), pN=np.zeros(nx),
+                   xlo=-inf * np.ones(nx), xhi=inf * np.ones(nx), ulo=-inf * np.ones(nu), uhi=inf * np.ones(nu),
+                   x0=x0, name="largest")
+
+
+def largest(seed: int = 5) -> Problem:
+    """The largest instance with its stored input box (states unbounded, see oracle/make_boxes.py)."""
+    p = largest_unboxed(seed)
+    xmax, umax = load_box("largest")
+    return with_box(p, xmax, umax)
