@@ -307,14 +307,15 @@ struct Producer {
         emit(kind, node, aux, row0, nrows, flags, base, ld);
     }
 
-    __device__ void run(unsigned long long tbase) {
+    // phase 0: the backward items [0, Tb); phase 1: the forward items [Tb, Tb + Tf)
+    __device__ void run(unsigned long long tbase, int phase) {
         const int nx = a.nx, nu = a.nu;
-        const int total = a.Tb + a.Tf;
+        const int total = phase == 0 ? a.Tb : a.Tf;
         for (;;) {
             if (dead) return;
             const unsigned long long tk = atomicAdd(a.ticket, 1ull) - tbase;
             if (tk >= (unsigned long long)total) break;
-            const int item = (int)tk;
+            const int item = (int)tk + (phase == 0 ? 0 : a.Tb);
             if (item < a.Tb) {
                 const int b0 = a.bstart[item], b1 = a.bstart[item + 1];
                 for (int k = b0; k < b1; ++k) {
@@ -351,7 +352,7 @@ struct Producer {
 };
 
 // ---- consumers ---------------------------------------------------------------------------
-template <class T, int NR, int KV>
+template <class T, int NR, int KV, int PH>
 struct Consumer {
     using VT = typename V16<T>::type;
     static constexpr int VN = V16<T>::n;
@@ -451,6 +452,7 @@ struct Consumer {
             if (md.kind == KIND_END) break;
             const T *M = reinterpret_cast<const T *>(ring + (size_t)slot * kChunk);
             const int f = md.flags;
+            if constexpr (PH == 0) {
             if (md.kind == KIND_BG) {
                 // child md.node of parent md.aux: s of the child into s_in
                 if (f & F_FIRST) {
@@ -530,7 +532,9 @@ struct Consumer {
                     // release store (release is cumulative), so no separate fence is needed
                     if ((f & F_END_ITEM) && tid == 0) st_release(a.flags + i, epoch);
                 }
-            } else if (md.kind == KIND_FG) {
+            }
+            } else {
+            if (md.kind == KIND_FG) {
                 // x^j = G^j [x^i; u^i] + c^j, axpy form over the rows of G^j' (one row per input)
                 const int j = md.node;
                 if (f & F_FIRST) {
@@ -630,12 +634,13 @@ struct Consumer {
                     if ((f & F_END_ITEM) && tid == 0) st_release(a.flags + a.Nn + j, epoch);
                 }
             }
+            }
             ++n;
         }
     }
 };
 
-template <class T, int NR, int KV>
+template <class T, int NR, int KV, int PH>
 __global__ void __launch_bounds__(kThreadsT, kCtasPerSm) k_tree(TreeArgs<T> a, unsigned epoch, unsigned long long tbase) {
     extern __shared__ __align__(1024) unsigned char smem[];
     __shared__ int abort_flag;
@@ -657,11 +662,11 @@ __global__ void __launch_bounds__(kThreadsT, kCtasPerSm) k_tree(TreeArgs<T> a, u
     if (warp == kCW) {
         if (lane == 0) {
             Producer<T> p(a, ring, meta, full, empty);
-            p.run(tbase);
+            p.run(tbase, PH);
         }
         return;
     }
-    Consumer<T, NR, KV> c{a, ring, meta, full, empty, epoch, warp, lane, (int)threadIdx.x, &abort_flag};
+    Consumer<T, NR, KV, PH> c{a, ring, meta, full, empty, epoch, warp, lane, (int)threadIdx.x, &abort_flag};
     const int nx = a.nx, nu = a.nu;
     // shared vectors (offsets multiple of 16 bytes: every width is padded to a 16-byte multiple)
     T *p = vec;
@@ -694,23 +699,26 @@ size_t tree_smem(int NR, int lda, int ldg, int ldk, int ldr, size_t esz) {
     return (size_t)kSlots * kChunk + kSlots * sizeof(Meta) + 2 * kSlots * sizeof(uint64_t) + vec * esz;
 }
 
-template <class T, int NR, int KV>
+template <class T, int NR, int KV, int PH>
 void launch_tree(stotree_t h, const TreeArgs<T> &a, unsigned epoch, unsigned long long tbase, int grid,
                  cudaStream_t st) {
     const size_t smem = tree_smem(NR, a.lda, a.ldg, a.ldk, a.ldr, sizeof(T));
-    raise_smem_cap((const void *)k_tree<T, NR, KV>, smem);
-    k_tree<T, NR, KV><<<grid, kThreadsT, smem, st>>>(a, epoch, tbase);
+    raise_smem_cap((const void *)k_tree<T, NR, KV, PH>, smem);
+    k_tree<T, NR, KV, PH><<<grid, kThreadsT, smem, st>>>(a, epoch, tbase);
 }
 
+// One round: the backward launch, then the forward launch (each with a consumer loop for its own
+// item kinds); the forward items of the same epoch start after the whole backward pass.
 template <class T, int NR>
 void launch_tree_kv(stotree_t h, const TreeArgs<T> &a, unsigned epoch, unsigned long long tbase, int grid,
                     cudaStream_t st) {
     const int kv = (a.lda / V16<T>::n + 31) / 32;
+    const unsigned long long tb1 = tbase + (unsigned long long)(a.Tb + grid);  // phase 1's first ticket
     switch (kv) {
-        case 1: launch_tree<T, NR, 1>(h, a, epoch, tbase, grid, st); break;
-        case 2: launch_tree<T, NR, 2>(h, a, epoch, tbase, grid, st); break;
-        case 3: launch_tree<T, NR, 3>(h, a, epoch, tbase, grid, st); break;
-        default: launch_tree<T, NR, 4>(h, a, epoch, tbase, grid, st); break;
+        case 1: launch_tree<T, NR, 1, 0>(h, a, epoch, tbase, grid, st); launch_tree<T, NR, 1, 1>(h, a, epoch, tb1, grid, st); break;
+        case 2: launch_tree<T, NR, 2, 0>(h, a, epoch, tbase, grid, st); launch_tree<T, NR, 2, 1>(h, a, epoch, tb1, grid, st); break;
+        case 3: launch_tree<T, NR, 3, 0>(h, a, epoch, tbase, grid, st); launch_tree<T, NR, 3, 1>(h, a, epoch, tb1, grid, st); break;
+        default: launch_tree<T, NR, 4, 0>(h, a, epoch, tbase, grid, st); launch_tree<T, NR, 4, 1>(h, a, epoch, tb1, grid, st); break;
     }
 }
 
@@ -724,14 +732,14 @@ int tree_grid(const TreeArgs<T> &a) {
     const int kv = (a.lda / V16<T>::n + 31) / 32;
     cudaError_t e;
     switch (kv) {
-        case 1: raise_smem_cap((const void *)k_tree<T, NR, 1>, smem);
-                e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_tree<T, NR, 1>, kThreadsT, smem); break;
-        case 2: raise_smem_cap((const void *)k_tree<T, NR, 2>, smem);
-                e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_tree<T, NR, 2>, kThreadsT, smem); break;
-        case 3: raise_smem_cap((const void *)k_tree<T, NR, 3>, smem);
-                e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_tree<T, NR, 3>, kThreadsT, smem); break;
-        default: raise_smem_cap((const void *)k_tree<T, NR, 4>, smem);
-                 e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_tree<T, NR, 4>, kThreadsT, smem); break;
+        case 1: raise_smem_cap((const void *)k_tree<T, NR, 1, 0>, smem);
+                e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_tree<T, NR, 1, 0>, kThreadsT, smem); break;
+        case 2: raise_smem_cap((const void *)k_tree<T, NR, 2, 0>, smem);
+                e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_tree<T, NR, 2, 0>, kThreadsT, smem); break;
+        case 3: raise_smem_cap((const void *)k_tree<T, NR, 3, 0>, smem);
+                e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_tree<T, NR, 3, 0>, kThreadsT, smem); break;
+        default: raise_smem_cap((const void *)k_tree<T, NR, 4, 0>, smem);
+                 e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_tree<T, NR, 4, 0>, kThreadsT, smem); break;
     }
     if (e != cudaSuccess || per_sm < 1) return 0;
     return sms * (per_sm < kCtasPerSm ? per_sm : kCtasPerSm);
@@ -825,7 +833,7 @@ sto_status solve_impl(stotree_t h, const void *const *y, const void *x0, void *c
         epoch = ++h->epoch;
         tbase = h->ticket_base;
         // every CTA's producer draws one ticket past the last item
-        h->ticket_base += (unsigned long long)(a.Tb + a.Tf + grid);
+        h->ticket_base += (unsigned long long)(a.Tb + a.Tf + 2 * grid);
     }
     cudaEvent_t ev;
     timing_begin(h, st, &ev);
@@ -836,7 +844,7 @@ sto_status solve_impl(stotree_t h, const void *const *y, const void *x0, void *c
         default: launch_tree_kv<T, 4>(h, a, epoch, tbase, grid, st); break;
     }
     timing_end(h, st, ev, nrhs);
-    h->launches += 1;
+    h->launches += 2;
     h->solve_calls += nrhs;
     STO_CUDA(h, cudaGetLastError());
     return STO_OK;
