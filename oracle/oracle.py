@@ -21,6 +21,9 @@ the paper's definitions directly:
 * Section III-E: diagonal preconditioning ybar^i = y^i / sqrt(pi^i); the solvers
   iterate on ybar (equivalently on S H and the box S Y with S = diag(sqrt(pi))).
   The termination test uses the unscaled residual ||z - Hx||_inf.
+* Section III-E (warm start) and Section IV (comparison method): GPAD, the accelerated
+  dual projected gradient, here in the theta form of Patrinos and Bemporad (2014):
+  w = ybar + theta_k (1/theta_{k-1} - 1)(ybar - ybar_prev), ybar+ = T(w).
 
 Line searches evaluate phi_lambda(w) with a full solve at every trial point
 (no affine shortcut), so the oracle is slow but obviously follows the text.
@@ -319,7 +322,7 @@ def power_lambda(o: LQOracle, r0: np.ndarray, iters: int = 50, safety: float = 0
 
 
 # --------------------------------------------------------------------------------------
-# Algorithms 1 and 2.
+# Algorithms 1 and 2, and GPAD.
 # --------------------------------------------------------------------------------------
 
 def _result(o, pt, k, hist, status, t0):
@@ -403,3 +406,43 @@ def minfbe(o: LQOracle, lam: float, y0: np.ndarray | None = None, tol: float = 1
         hist["tau"].append(tau)
         hist["res"].append(pt["res_inf"])
     return _result(o, pt, k, hist, "converged", t0)
+
+
+def gpad_theta(k: int) -> float:
+    """theta_k of the accelerated dual gradient projection: theta_{-1} = theta_0 = 1,
+    theta_{k+1} = (sqrt(theta_k^4 + 4 theta_k^2) - theta_k^2) / 2."""
+    th = 1.0
+    for _ in range(max(0, k)):
+        th = 0.5 * (np.sqrt(th ** 4 + 4.0 * th * th) - th * th)
+    return th
+
+
+def gpad(o: LQOracle, lam: float, y0: np.ndarray | None = None, tol: float = 1e-8,
+         max_iter: int = 1000) -> dict:
+    """GPAD on the preconditioned dual (the warm start of Section III-E and the comparison
+    method of Section IV).  y0 is unscaled.
+
+    Iteration k at the extrapolated point w_k = ybar_k + theta_k (1/theta_{k-1} - 1)
+    (ybar_k - ybar_{k-1}) (w_0 = ybar_0): one full solve x(w_k), the stopping test
+    ||z(w_k) - Hx(w_k)||_inf <= tol (unscaled), then ybar_{k+1} = T_lambda(w_k).  The result
+    is the point of the last stopping test, w_k, with x(w_k) and z(w_k); `iters` counts the
+    forward-backward steps taken before it."""
+    t0 = time.perf_counter()
+    o.solve_calls = 0
+    yb = np.zeros(o.m) if y0 is None else np.asarray(y0, dtype=np.float64) / o.sq
+    y_prev = yb.copy()
+    th_prev, th = 1.0, 1.0
+    hist = dict(phi=[], tau=[], res=[])
+    k = 0
+    while True:
+        w = yb + th * (1.0 / th_prev - 1.0) * (yb - y_prev)
+        pt = fb_point(o, w, lam)
+        hist["phi"].append(pt["phi"])
+        hist["res"].append(pt["res_inf"])
+        if pt["res_inf"] <= tol:
+            return _result(o, pt, k, hist, "converged", t0)
+        if k >= max_iter:
+            return _result(o, pt, k, hist, "not_converged", t0)
+        y_prev, yb = yb, pt["T"]
+        th_prev, th = th, 0.5 * (np.sqrt(th ** 4 + 4.0 * th * th) - th * th)
+        k += 1
