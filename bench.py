@@ -31,6 +31,7 @@ if ROOT not in sys.path:
     sys.path.insert(0, ROOT)
 
 METRIC = "ms to KKT tol 1e-4 (MINFBE/NAMA), batched/warm vs plain; solve-step GB/s"
+GPAD_MAX_ITER = 5000
 TOL = 1e-4
 WORKLOAD = ("paper_scale: horizon 20, branching 2 for stages 0-9 then 1 (1024 scenarios, 12287 nodes), "
             "nx=100, nu=50, per-node A_j = A + 0.05 N(0,1) (rho(A)=0.98), B_j ~ N(0,1/nx), w ~ N(0,0.05^2), "
@@ -188,6 +189,7 @@ def run_ours(args):
     solve_ms, rounds, rhs = st.get_timing()
     st.set_timing(False)
     minfbe_ms, minfbe_infos = timed("minfbe", args.steps)
+    gpad = run_gpad(st, lam, x0, stream, pg, dev, args.steps)
 
     mat_bytes, vec_bytes = st.solve_bytes()
     alg_bytes = rounds * mat_bytes + rhs * vec_bytes
@@ -251,6 +253,7 @@ def run_ours(args):
             "solve_step_gbs": round(achieved, 1),
             "e2e": {"value": round(e2e_ms, 4), "unit": "ms", "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
             "gpu_launches": launches,
+            "gpad": gpad,
             "batched": batched,
             "warm_start": warm,
             "clocks": clk.summary(),
@@ -260,6 +263,37 @@ def run_ours(args):
         pg.barrier()
         pg.destroy_process_group()
     return line
+
+
+def run_gpad(st, lam, x0, stream, pg, dev, steps):
+    """GPAD (accelerated dual projected gradient) on the same instance: its five-step warm start
+    of Section III-E followed by NAMA, timed as one step, and one cold GPAD run to the same
+    tolerance (the comparison method of Section IV)."""
+    import torch
+
+    def warm_nama():
+        g = st.solve("gpad", lam, x0=x0, tol=TOL, max_iter=5, allow_not_converged=True, outputs=False)
+        res = st.solve("nama", lam, x0=x0, y0=g["y"], tol=TOL, mem=5, max_iter=500, outputs=False)
+        if res["info"]["res_inf"] > TOL:
+            raise RuntimeError(f"NAMA after GPAD stopped at residual {res['info']['res_inf']}")
+        return g["info"], res["info"]
+
+    warm_nama()
+    if pg is not None:
+        pg.barrier()
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(steps):
+        gi, ni = warm_nama()
+    e1.record(stream)
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1) / steps
+    cold = st.solve("gpad", lam, x0=x0, tol=TOL, max_iter=GPAD_MAX_ITER, allow_not_converged=True, outputs=False)
+    ci = cold["info"]
+    return {"warm5_then_nama_ms": round(ms, 4), "gpad5_ms": round(gi["ms"], 4), "nama_iters_after_gpad5": ni["iters"],
+            "gpad_to_tol": {"ms": round(ci["ms"], 3), "iters": ci["iters"], "res_inf": ci["res_inf"],
+                            "converged": ci["status"] == 0, "max_iter": GPAD_MAX_ITER}}
 
 
 def run_warm(dev, train_draws, eval_draws):

@@ -201,6 +201,21 @@ STO_API sto_status stotree_nama_solve(stotree_t h, const sto_opts *opts, const v
 STO_API sto_status stotree_minfbe_solve(stotree_t h, const sto_opts *opts, const void *x0, void *y, void *x,
                                 void *u, void *z, sto_info *info, sto_stream_t stream);
 
+/* GPAD, the accelerated dual projected gradient (Section III-E, where a few of its steps warm
+ * start Algorithms 1 and 2, and Section IV, where it is the comparison method), on the
+ * preconditioned dual with the theta sequence of Patrinos and Bemporad (2014):
+ * w_k = ybar_k + theta_k (1/theta_{k-1} - 1)(ybar_k - ybar_{k-1}), w_0 = ybar_0,
+ * ybar_{k+1} = T_lambda(w_k), theta_{-1} = theta_0 = 1,
+ * theta_{k+1} = (sqrt(theta_k^4 + 4 theta_k^2) - theta_k^2) / 2.
+ * Each iteration is one solve round at w_k and one elementwise pass.  The stopping test
+ * ||z - Hx||_inf <= tol (unscaled) is applied at w_k; on return y = w_k (unscaled) and
+ * x, u, z are x(w_k), z_lambda(w_k), with info->iters = the number of steps taken before it
+ * (max_iter = 5 gives the five-step warm start: six solve rounds).  opts->lbfgs_mem, max_ls
+ * and eps_curv are not used but must be valid.  Arguments, synchronisation and errors as
+ * stotree_nama_solve. */
+STO_API sto_status stotree_gpad_solve(stotree_t h, const sto_opts *opts, const void *x0, void *y, void *x,
+                              void *u, void *z, sto_info *info, sto_stream_t stream);
+
 /* FP64 optimality check of a primal-dual pair (x, u, y), all device real, against the FP64
  * problem data (conditions listed under Algorithm 1):
  *   out[0] = max |x^j - A^j x^i - B^j u^i - c^j|              (dynamics, x^0 = x0)

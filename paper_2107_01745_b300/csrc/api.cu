@@ -515,6 +515,15 @@ sto_status stotree_minfbe_solve(stotree_t h, const sto_opts *o, const void *x0, 
     return solver_run(h, 1, o, x0, y, x, u, z, info, reinterpret_cast<cudaStream_t>(stream));
 }
 
+sto_status stotree_gpad_solve(stotree_t h, const sto_opts *o, const void *x0, void *y, void *x, void *u,
+                              void *z, sto_info *info, sto_stream_t stream) {
+    if (!h || !x0 || !y) return STO_ERR_INVALID_ARG;
+    sto_status s = check_opts(o);
+    if (s != STO_OK) return s;
+    if (!h->factored || !h->have_box) return STO_ERR_NOT_READY;
+    return solver_run(h, 2, o, x0, y, x, u, z, info, reinterpret_cast<cudaStream_t>(stream));
+}
+
 sto_status stotree_kkt_check(stotree_t h, const void *x0, const void *x, const void *u, const void *y,
                              double tol_active, double *out, sto_stream_t stream) {
     if (!h || !x0 || !x || !u || !y || !out) return STO_ERR_INVALID_ARG;

@@ -9,6 +9,7 @@
 //   k_lb_dots / k_lb_dir   L-BFGS direction d = -B g, compact form               (Alg. 1 line 3, Alg. 2 line 5)
 //   k_ls      FBE at up to 19 step sizes tau = 2^-k in one pass                    (Alg. 1 line 4, Alg. 2 line 6)
 //   k_fbstep  ybar+ = T_lam(w), s = ybar+ - ybar                                   (Alg. 1 line 5, Alg. 2 lines 7-8)
+//   k_gpad    GPAD step ybar+ = T_lam(w), next extrapolated point                 (Section III-E, Section IV)
 //
 // Readings of the text used here:
 //   * T_lam(y) = y + lam (Hx(y) - z_lam(y)), the sign used by Algorithm 2's update.
@@ -26,6 +27,7 @@
 //     pairs are kept when <s,q> > eps' ||s||^2 ||g||^2 (Alg. 1 line 7, Alg. 2 line 10).
 #include <cmath>
 #include <cstring>
+#include <utility>
 
 #include "internal.h"
 
@@ -745,6 +747,63 @@ __global__ void __launch_bounds__(kThreads) k_fbstep(DualView<T> dv, T *yb, cons
     }
 }
 
+// GPAD, the accelerated dual projected gradient of the warm start (Section III-E) and of the
+// comparison in Section IV, in the theta form of Patrinos and Bemporad (2014).  At the
+// extrapolated point w with h = S H x(w): z = proj(h + w/lam), r = z - h, the step
+// ybar+ = T_lam(w) = w - lam r, and the next extrapolated point
+// w+ = ybar+ + beta (ybar+ - ybar), beta = theta_{k+1} (1/theta_k - 1).  The FBE at w and
+// ||S^-1 r||_inf are reduced for the stopping test, which the host applies to w.
+template <class T>
+__global__ void __launch_bounds__(kThreads) k_gpad(DualView<T> dv, const T *__restrict__ w, const T *__restrict__ h,
+                                                   T *yb, T *wn, T beta, SolverScalars *sc, double *partials) {
+    __shared__ double tot[3];
+    extern __shared__ __align__(16) unsigned char tab_raw[];
+    CompTab<T> tab;
+    tab.load(dv, reinterpret_cast<T *>(tab_raw));
+    constexpr int VN = Vec16<T>::n;
+    const T lam = (T)sc->lambda, ilam = T(1) / lam;
+    T fsum = 0, rmax = 0;
+    int nan = 0;
+    for_vectors<T>(dv.m, [&](int e0, int n) {
+        T we[VN], he[VN], ye[VN], yn[VN], wv[VN];
+        ldv(w, e0, n, we);
+        ldv(h, e0, n, he);
+        ldv<T>(yb, e0, n, ye);
+        Pos ps = pos_of(dv, e0);
+        int cur = -1;
+        T sq = 1, isq = 1;
+#pragma unroll
+        for (int k = 0; k < VN; ++k) {
+            if (k < n) {
+                if (ps.node != cur) {
+                    cur = ps.node;
+                    sq = dv.sqp[cur];
+                    isq = T(1) / sq;
+                }
+                const auto M = tab.meta(ps, sq);
+                const T z = clampv(he[k] + we[k] * ilam, M.lo, M.hi);
+                const T r = z - he[k];
+                fsum += fbe_term<T>(he[k], we[k], lam, ilam, M);
+                const T ra = fabs(r) * isq;
+                if (!(ra <= T(3.0e38))) nan = 1;
+                rmax = fmax(rmax, ra);
+                yn[k] = we[k] - lam * r;
+                wv[k] = yn[k] + beta * (yn[k] - ye[k]);
+                pos_next(dv, ps);
+            }
+        }
+        stv(yb, e0, n, yn);
+        stv(wn, e0, n, wv);
+    });
+    T sums[2] = {fsum, (T)nan};
+    T maxs[1] = {rmax};
+    if (reduce_last<T, 2, 1>(sums, maxs, partials, &sc->red_counter, tot) && threadIdx.x == 0) {
+        sc->phi = -tot[0];
+        sc->res_inf = tot[2];
+        if (tot[1] > 0.0 || !(tot[0] == tot[0])) sc->nan_flag = 1;
+    }
+}
+
 // ybar = y / sqrt(pi) (in) and y = sqrt(pi) ybar, z = z_bar / sqrt(pi), x, u = S^-1 h (out).
 template <class T>
 __global__ void k_scale_in(DualView<T> dv, const T *y, T *yb) {
@@ -1000,6 +1059,100 @@ sto_status solver_impl(stotree_t h, int method, const sto_opts *o, const void *x
     return result;
 }
 
+// GPAD on the preconditioned dual.  Iteration k solves at the extrapolated point w_k
+// (w_0 = ybar_0), tests ||z(w_k) - Hx(w_k)||_inf <= tol and otherwise takes the step; the
+// result is the point of the last test, w_k, with x(w_k) and z(w_k).  theta_{-1} = theta_0 = 1,
+// theta_{k+1} = (sqrt(theta_k^4 + 4 theta_k^2) - theta_k^2) / 2.
+template <class T>
+sto_status gpad_impl(stotree_t h, const sto_opts *o, const void *x0v, void *yv, void *xv, void *uv, void *zv,
+                     sto_info *info, cudaStream_t st) {
+    const Layout &L = h->L;
+    const long long vs = (long long)vstride_of(h);
+    T *V = h->at<T>(L.vec);
+    T *yb = V, *hv = V + vs, *w = V + 3 * vs, *wn = V + 5 * vs;
+    SolverScalars *sc = h->at<SolverScalars>(L.scal);
+    double *part = h->at<double>(L.partials);
+    const DualView<T> dv = make_view<T>(h);
+    const int grid = red_grid(dv.m);
+    const size_t tabb = comp_tab_bytes(dv);
+
+    cudaEvent_t e0, e1;
+    STO_CUDA(h, cudaEventCreate(&e0));
+    STO_CUDA(h, cudaEventCreate(&e1));
+    STO_CUDA(h, cudaEventRecord(e0, st));
+    const int64_t calls0 = h->solve_calls;
+    const int64_t launches0 = h->launches;
+
+    SolverScalars *hs = h->host_scal;
+    std::memset(hs, 0, sizeof(SolverScalars));
+    hs->lambda = o->lambda;
+    hs->tol = o->tol;
+    hs->method = 2;
+    STO_CUDA(h, cudaMemcpyAsync(sc, hs, sizeof(SolverScalars), cudaMemcpyHostToDevice, st));
+    STO_CUDA(h, cudaStreamSynchronize(st));
+
+    k_scale_in<T><<<grid, kThreads, 0, st>>>(dv, static_cast<const T *>(yv), yb);
+    STO_CUDA(h, cudaMemcpyAsync(w, yb, (size_t)dv.m * sizeof(T), cudaMemcpyDeviceToDevice, st));
+    h->launches += 1;
+    double theta = 1.0;
+    sto_status result = STO_OK;
+    int iters = 0;
+    while (true) {
+        const void *ys[1] = {w};
+        void *hs_[1] = {hv};
+        const sto_status s = solve_round(h, ys, x0v, hs_, 1, false, true, st);
+        if (s != STO_OK) return s;
+        const double theta_next = 0.5 * (std::sqrt(theta * theta * theta * theta + 4.0 * theta * theta) - theta * theta);
+        const T beta = (T)(theta_next * (1.0 / theta - 1.0));
+        k_gpad<T><<<grid, kThreads, tabb, st>>>(dv, w, hv, yb, wn, beta, sc, part);
+        h->launches += 1;
+        STO_CUDA(h, cudaGetLastError());
+        STO_CUDA(h, cudaMemcpyAsync(hs, sc, kScalHead, cudaMemcpyDeviceToHost, st));
+        STO_CUDA(h, cudaStreamSynchronize(st));
+        if (hs->nan_flag) {
+            result = STO_ERR_NUMERICAL;
+            h->err = "NaN or Inf in the residual";
+            break;
+        }
+        if (hs->res_inf <= o->tol) break;
+        if (iters >= o->max_iter) {
+            result = STO_NOT_CONVERGED;
+            break;
+        }
+        std::swap(w, wn);
+        theta = theta_next;
+        ++iters;
+    }
+    h->launches += 1;
+    k_finish_out<T><<<grid, kThreads, 0, st>>>(dv, w, hv, sc, static_cast<T *>(yv), static_cast<T *>(zv),
+                                               static_cast<T *>(xv), static_cast<T *>(uv));
+    if (xv) STO_CUDA(h, cudaMemcpyAsync(xv, x0v, h->nx * sizeof(T), cudaMemcpyDeviceToDevice, st));
+    STO_CUDA(h, cudaEventRecord(e1, st));
+    STO_CUDA(h, cudaMemcpyAsync(hs, sc, sizeof(SolverScalars), cudaMemcpyDeviceToHost, st));
+    STO_CUDA(h, cudaStreamSynchronize(st));
+    {
+        const sto_status es = check_round_error(h, st);
+        if (es != STO_OK) result = es;
+    }
+    float ms = 0.f;
+    cudaEventElapsedTime(&ms, e0, e1);
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    if (info) {
+        info->iters = iters;
+        info->solve_calls = (int32_t)(h->solve_calls - calls0);
+        info->status = result;
+        info->ls_zero = 0;
+        info->res_inf = hs->res_inf;
+        info->fbe = hs->phi;
+        info->ms = ms;
+        info->launches = (int32_t)(h->launches - launches0);
+        info->reserved = 0;
+    }
+    STO_CUDA(h, cudaGetLastError());
+    return result;
+}
+
 template <class T>
 sto_status lambda_impl(stotree_t h, void *r0, int iters, double safety, double *lambda, double *Lout,
                        cudaStream_t st) {
@@ -1159,6 +1312,9 @@ sto_status kkt_impl(stotree_t h, const void *x0, const void *x, const void *u, c
 
 sto_status solver_run(stotree_t h, int method, const sto_opts *o, const void *x0, void *y, void *x, void *u,
                       void *z, sto_info *info, cudaStream_t st) {
+    if (method == 2)
+        return h->prec == STO_FP64 ? gpad_impl<double>(h, o, x0, y, x, u, z, info, st)
+                                   : gpad_impl<float>(h, o, x0, y, x, u, z, info, st);
     return h->prec == STO_FP64 ? solver_impl<double>(h, method, o, x0, y, x, u, z, info, st)
                                : solver_impl<float>(h, method, o, x0, y, x, u, z, info, st);
 }

@@ -73,6 +73,7 @@ def lib():
             "stotree_estimate_lambda": [vp, vp, i32, dbl, vp, vp, vp],
             "stotree_nama_solve": [vp, vp, vp, vp, vp, vp, vp, vp, vp],
             "stotree_minfbe_solve": [vp, vp, vp, vp, vp, vp, vp, vp, vp],
+            "stotree_gpad_solve": [vp, vp, vp, vp, vp, vp, vp, vp, vp],
             "stotree_kkt_check": [vp, vp, vp, vp, vp, dbl, vp, vp],
             "stotree_set_timing": [vp, i32],
             "stotree_get_timing": [vp, vp, vp, vp],
@@ -138,7 +139,7 @@ def exported_symbols():
     return [n for n in ("stotree_create", "stotree_destroy", "stotree_sizes", "stotree_workspace_size",
                         "stotree_bind_workspace", "stotree_set_dynamics", "stotree_set_costs", "stotree_set_box",
                         "stotree_factor", "stotree_solve_step", "stotree_solve_step_noalloc", "stotree_last_primal", "stotree_estimate_lambda",
-                        "stotree_nama_solve", "stotree_minfbe_solve", "stotree_kkt_check", "stotree_set_timing",
+                        "stotree_nama_solve", "stotree_minfbe_solve", "stotree_gpad_solve", "stotree_kkt_check", "stotree_set_timing",
                         "stotree_get_timing", "stotree_solve_bytes", "stotree_status_str", "stotree_last_error",
                         "stobatch_create", "stobatch_destroy", "stobatch_sizes", "stobatch_workspace_size",
                         "stobatch_bind_workspace", "stobatch_set_instance", "stobatch_factor",
@@ -275,7 +276,8 @@ class StoTree:
 
     def solve(self, method, lam, x0=None, y0=None, tol=1e-4, mem=5, max_iter=1000, max_ls=30, eps_curv=None,
               outputs=True, allow_not_converged=False):
-        """Algorithm 1 (method='minfbe') or 2 (method='nama').  Returns tensors and info."""
+        """Algorithm 1 (method='minfbe'), 2 (method='nama') or GPAD (method='gpad', the
+        accelerated dual projected gradient of Sections III-E and IV).  Returns tensors and info."""
         if eps_curv is None:
             eps_curv = 1e-12 if self.prec == STO_FP64 else 1e-8
         x0 = self.to_dev(self.p.x0) if x0 is None else x0
@@ -285,7 +287,8 @@ class StoTree:
         z = torch.empty(self.m, dtype=self.dtype, device=self.device) if outputs else None
         o = Opts(lam, tol, eps_curv, mem, max_iter, max_ls)
         info = Info()
-        fn = lib().stotree_nama_solve if method == "nama" else lib().stotree_minfbe_solve
+        fn = {"nama": lib().stotree_nama_solve, "minfbe": lib().stotree_minfbe_solve,
+              "gpad": lib().stotree_gpad_solve}[method]
         code = fn(self.h, ctypes.byref(o), _t_ptr(x0), _t_ptr(y), _t_ptr(x), _t_ptr(u), _t_ptr(z),
                   ctypes.byref(info), _stream())
         if code != 0 and not (allow_not_converged and code == STO_NOT_CONVERGED):

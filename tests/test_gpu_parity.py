@@ -129,6 +129,59 @@ def test_solver_fp32_matches_oracle(cuda_device, p, method):
     assert _relinf(res["y"].cpu().numpy(), ref["y"]) < 1e-3
 
 
+@pytest.mark.parametrize("p", BOXED, ids=lambda p: p.name)
+def test_gpad_fp64_follows_oracle_iterates(cuda_device, p):
+    """FP64 GPAD on the GPU returns the oracle's extrapolated point after every number of
+    steps (the five-step warm start of Section III-E among them)."""
+    o = O.LQOracle(p)
+    lam, _ = O.power_lambda(o, np.random.default_rng(0).standard_normal(o.m))
+    st = _st()(p, precision="fp64")
+    st.factor()
+    for K in (0, 1, 2, 5, 25):
+        ref = O.gpad(o, lam, tol=0.0, max_iter=K)
+        res = st.solve("gpad", lam, tol=1e-300, max_iter=K, allow_not_converged=True)
+        info = res["info"]
+        # where the box never binds (boxed42) both residuals sit at rounding level and may
+        # reach exactly zero at different steps; elsewhere the step counts agree exactly
+        if ref["res_inf"] > 1e-12:
+            assert info["status"] == 7 and info["iters"] == K and info["solve_calls"] == K + 1
+        assert _relinf(res["y"].cpu().numpy(), ref["y"]) < 1e-10, K
+        assert _relinf(res["x"].cpu().numpy(), ref["x"]) < 1e-10, K
+        assert _relinf(res["z"].cpu().numpy(), ref["z"]) < 1e-10, K
+        assert abs(info["res_inf"] - ref["res_inf"]) <= 1e-10 * max(1.0, ref["res_inf"])
+    assert info["iters"] > 0 or ref["res_inf"] <= 1e-12
+
+
+@pytest.mark.parametrize("p", BOXED, ids=lambda p: p.name)
+def test_gpad_fp64_to_tolerance(cuda_device, p):
+    o = O.LQOracle(p)
+    lam, _ = O.power_lambda(o, np.random.default_rng(0).standard_normal(o.m))
+    ref = O.gpad(o, lam, tol=1e-9, max_iter=50000)
+    st = _st()(p, precision="fp64")
+    st.factor()
+    res = st.solve("gpad", lam, tol=1e-9, max_iter=50000)
+    info = res["info"]
+    assert info["status"] == 0 and info["res_inf"] <= 1e-9
+    assert abs(info["iters"] - ref["iters"]) <= 1
+    assert _relinf(res["x"].cpu().numpy(), ref["x"]) < 1e-8
+    assert _relinf(res["u"].cpu().numpy(), ref["u"]) < 1e-8
+    kkt = st.kkt_check(st.to_dev(p.x0), res["x"], res["u"], res["y"], tol_active=1e-6)
+    assert kkt["dynamics"] < 1e-12 and kkt["feasibility"] < 1e-8
+
+
+@pytest.mark.parametrize("p", BOXED[1:], ids=lambda p: p.name)
+def test_gpad_fp32_matches_oracle(cuda_device, p):
+    o = O.LQOracle(p)
+    lam, _ = O.power_lambda(o, np.random.default_rng(0).standard_normal(o.m))
+    ref = O.gpad(o, lam, tol=1e-5, max_iter=50000)
+    st = _st()(p, precision="fp32")
+    st.factor()
+    res = st.solve("gpad", lam, tol=1e-5, max_iter=50000)
+    assert res["info"]["status"] == 0 and res["info"]["res_inf"] <= 1e-5
+    assert _relinf(res["x"].cpu().numpy(), ref["x"]) < 1e-4
+    assert _relinf(res["u"].cpu().numpy(), ref["u"]) < 1e-4
+
+
 def test_loose_box_returns_unconstrained_solution(cuda_device):
     p = W.random_problem(14, box_scale=1e6)
     st = _st()(p, precision="fp64")
@@ -191,3 +244,20 @@ def test_paper_scale_solver(cuda_device, paper_scale, method):
     assert _relinf(res["u"].cpu().numpy(), ref["u"]) < 1e-3
     kkt = st.kkt_check(st.to_dev(p.x0), res["x"], res["u"], res["y"], tol_active=1e-3)
     assert kkt["dynamics"] < 1e-4 and kkt["feasibility"] < 2e-4
+
+
+def test_paper_scale_gpad_warm_start(cuda_device, paper_scale):
+    """Five GPAD steps (the warm start of Section III-E) at full size against the oracle's five
+    steps, then NAMA from that point to ||z - Hx||_inf <= 1e-4."""
+    p, o = paper_scale
+    lam, _ = O.power_lambda(o, np.random.default_rng(7).standard_normal(o.m), iters=20)
+    ref = O.gpad(o, lam, tol=0.0, max_iter=5)
+    st = _st()(p, precision="fp32")
+    st.factor()
+    g = st.solve("gpad", lam, tol=1e-300, max_iter=5, allow_not_converged=True)
+    assert g["info"]["iters"] == 5 and g["info"]["solve_calls"] == 6
+    assert _rel2(g["y"].cpu().numpy().astype(np.float64), ref["y"]) < 1e-4
+    assert _rel2(g["x"].cpu().numpy().astype(np.float64), ref["x"]) < 1e-5
+    assert abs(g["info"]["res_inf"] - ref["res_inf"]) <= 1e-3 * ref["res_inf"]
+    res = st.solve("nama", lam, y0=g["y"], tol=1e-4, max_iter=300)
+    assert res["info"]["status"] == 0 and res["info"]["res_inf"] <= 1e-4
