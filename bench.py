@@ -190,6 +190,7 @@ def run_ours(args):
     st.set_timing(False)
     minfbe_ms, minfbe_infos = timed("minfbe", args.steps)
     gpad = run_gpad(st, lam, x0, stream, pg, dev, args.steps)
+    backtrack = run_backtrack(st, Lhat, x0)
 
     mat_bytes, vec_bytes = st.solve_bytes()
     alg_bytes = rounds * mat_bytes + rhs * vec_bytes
@@ -254,6 +255,7 @@ def run_ours(args):
             "e2e": {"value": round(e2e_ms, 4), "unit": "ms", "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
             "gpu_launches": launches,
             "gpad": gpad,
+            "backtracking": backtrack,
             "batched": batched,
             "warm_start": warm,
             "clocks": clk.summary(),
@@ -294,6 +296,19 @@ def run_gpad(st, lam, x0, stream, pg, dev, steps):
     return {"warm5_then_nama_ms": round(ms, 4), "gpad5_ms": round(gi["ms"], 4), "nama_iters_after_gpad5": ni["iters"],
             "gpad_to_tol": {"ms": round(ci["ms"], 3), "iters": ci["iters"], "res_inf": ci["res_inf"],
                             "converged": ci["status"] == 0, "max_iter": GPAD_MAX_ITER}}
+
+
+def run_backtrack(st, Lhat, x0):
+    """NAMA with the step-size backtracking of Section III-B when L is not known: started from
+    ten times the power-iteration estimate of 1/L, one solve per rule."""
+    out = {"lambda0": 10.0 / Lhat}
+    for rule, param in (("simple", 0.25), ("original", 0.1)):
+        st.solve("nama", 10.0 / Lhat, x0=x0, tol=TOL, max_iter=500, backtrack=rule, bt_param=param, outputs=False)
+        i = st.solve("nama", 10.0 / Lhat, x0=x0, tol=TOL, max_iter=500, backtrack=rule, bt_param=param,
+                     outputs=False)["info"]
+        out[rule] = {"param": param, "ms": round(i["ms"], 3), "iters": i["iters"], "halvings": i["halvings"],
+                     "lambda_final": i["lambda_"], "solve_calls": i["solve_calls"], "res_inf": i["res_inf"]}
+    return out
 
 
 def run_warm(dev, train_draws, eval_draws):

@@ -93,6 +93,19 @@ typedef struct {
     int32_t lbfgs_mem;  /* L-BFGS memory, 1..16 */
     int32_t max_iter;   /* iteration cap; STO_NOT_CONVERGED when hit */
     int32_t max_ls;     /* line-search halvings tau = 2^0 .. 2^-max_ls (<= 30), then tau = 0 */
+    int32_t backtrack;  /* step-size backtracking when L is unknown (Section III-B), Algorithms 1
+                           and 2 only: 0 = fixed lambda; 1 = eq. (original-backtracking): after
+                           the forward-backward step from the accepted line-search point w,
+                           lambda is halved if fhat(T(w)) > fhat(w) - lambda <grad fhat(w), R(w)>
+                           + (1 - beta) lambda/2 ||R(w)||^2 (for this quadratic fhat: if
+                           <R(w), Hx(T(w)) - Hx(w)> > (1 - beta) ||R(w)||^2), and the iteration is
+                           repeated from the current iterate; 2 = eq. (simple-backtracking): at
+                           the current iterate y, lambda is halved while lambda ||grad fhat(T(y))
+                           - grad fhat(y)|| > eps'' ||T(y) - y|| (= lambda ||H x_lin(R)|| >
+                           eps'' ||R||).  Every halving empties the L-BFGS memory. */
+    double bt_param;    /* beta in [0, 1) for backtrack = 1, eps'' in (0, 1/2) for backtrack = 2 */
+    int32_t max_halvings; /* cap on halvings (>= 0); STO_NOT_CONVERGED beyond it */
+    int32_t pad_;
 } sto_opts;
 
 typedef struct {
@@ -101,10 +114,11 @@ typedef struct {
     int32_t status;       /* sto_status of the solve */
     int32_t ls_zero;      /* iterations whose line search fell back to tau = 0 */
     int32_t launches;     /* CUDA kernels launched by the call */
-    int32_t reserved;
+    int32_t halvings;     /* step-size halvings of the backtracking (sto_opts.backtrack) */
     double res_inf;       /* ||z - Hx||_inf at the returned iterate */
     double fbe;           /* phi_lambda at the returned iterate (scaled dual) */
     double ms;            /* wall time of the call on the stream, milliseconds */
+    double lambda;        /* the step at return (opts->lambda unless backtracking halved it) */
 } sto_info;
 
 /* Validate the tree and create a handle.  No device work.

@@ -21,6 +21,13 @@ the paper's definitions directly:
 * Section III-E: diagonal preconditioning ybar^i = y^i / sqrt(pi^i); the solvers
   iterate on ybar (equivalently on S H and the box S Y with S = diag(sqrt(pi))).
   The termination test uses the unscaled residual ||z - Hx||_inf.
+* Section III-B, step-size backtracking when L is unknown: eq. (original-backtracking)
+  [TheStePat16], read as the descent-lemma test of the forward-backward step taken from the
+  accepted line-search point w (its three terms at w are the ones the line search evaluated
+  in phi(w)), evaluated through the exact second-order expansion of the quadratic fhat; on
+  failure lambda is halved, the L-BFGS memory emptied and the iteration repeated from ybar.  Eq. (simple-backtracking) [BelloCruz 2016, Linesearch 1] at ybar:
+  lambda ||grad fhat(T(ybar)) - grad fhat(ybar)|| > eps'' ||T(ybar) - ybar|| halves lambda,
+  empties the memory and is tested again.
 * Section III-E (warm start) and Section IV (comparison method): GPAD, the accelerated
   dual projected gradient, here in the theta form of Patrinos and Bemporad (2014):
   w = ybar + theta_k (1/theta_{k-1} - 1)(ybar - ybar_prev), ybar+ = T(w).
@@ -245,6 +252,41 @@ def fb_point(o: LQOracle, yb: np.ndarray, lam: float) -> dict:
                 res_inf=float(np.max(np.abs(r / o.sq))) if r.size else 0.0)
 
 
+def fhat_at(pt: dict) -> float:
+    """fhat at a point returned by fb_point: -(f(x) + <ybar, Hbar x>)."""
+    return -(pt["f"] + float(np.dot(pt["y"], pt["h"])))
+
+
+def original_backtrack_excess(o: LQOracle, wp: dict, new: dict, lam: float, beta: float) -> float:
+    """Eq. (original-backtracking) at the accepted point w (wp) and T(w) (new), literally:
+    fhat(T(w)) - [fhat(w) - lam <grad fhat(w), R(w)> + (1 - beta) lam / 2 ||R(w)||^2], with
+    grad fhat(w) = -Hbar x(w).  Positive means the test fails.  Evaluated from fhat values it
+    is exact only far from the solution: its margin is of the order of lam ||R||^2 while the
+    terms are of the order of ||R||, so near the solution rounding decides its sign."""
+    grad = -wp["h"]
+    rhs = fhat_at(wp) - lam * float(np.dot(grad, wp["r"])) + 0.5 * (1.0 - beta) * lam * float(np.dot(wp["r"], wp["r"]))
+    return fhat_at(new) - rhs
+
+
+def original_backtrack_fails(o: LQOracle, wp: dict, new: dict, lam: float, beta: float) -> bool:
+    """Eq. (original-backtracking) at w, evaluated without cancellation.  fhat is quadratic, so
+    fhat(T(w)) = fhat(w) + <grad fhat(w), T(w) - w> + 1/2 (T(w) - w)' grad^2 fhat (T(w) - w)
+    exactly, with T(w) - w = -lam R(w); the test is therefore
+    lam <R, grad^2 fhat R> > (1 - beta) ||R||^2, R = R(w), with the Hessian-vector product
+    grad^2 fhat R = -Hbar x_lin(R) of Algorithm 4 (one extra homogeneous solve)."""
+    R = wp["r"]
+    HR = -hbar_lin(o, R)
+    return lam * float(np.dot(R, HR)) > (1.0 - beta) * float(np.dot(R, R))
+
+
+def simple_backtrack_fails(o: LQOracle, pt: dict, lam: float, eps: float) -> bool:
+    """Eq. (simple-backtracking) at ybar (pt): lam ||grad fhat(T(ybar)) - grad fhat(ybar)||
+    > eps'' ||T(ybar) - ybar||, with grad fhat(T(ybar)) from a full solve at T(ybar)."""
+    hT, _, _ = hbar(o, pt["T"])
+    lhs = lam * float(np.linalg.norm(-hT + pt["h"]))
+    return lhs > eps * float(np.linalg.norm(pt["T"] - pt["y"]))
+
+
 def fhat(o: LQOracle, yb: np.ndarray) -> float:
     """fhat(ybar) = f*(-Hbar' ybar) = -(f(x(ybar)) + <ybar, Hbar x(ybar)>)."""
     h, x, u = hbar(o, yb)
@@ -329,22 +371,45 @@ def _result(o, pt, k, hist, status, t0):
     return dict(y=o.sq * pt["y"], ybar=pt["y"], x=pt["x"], u=pt["u"], z=pt["z"] / o.sq,
                 h=pt["h"] / o.sq, res_inf=pt["res_inf"], iters=k, status=status,
                 solve_calls=o.solve_calls, phi=hist["phi"], tau=hist["tau"], res=hist["res"],
-                seconds=time.perf_counter() - t0)
+                lam=hist.get("lam"), halvings=hist.get("halvings", 0), seconds=time.perf_counter() - t0)
+
+
+def _check_backtrack(backtrack, bt_beta, bt_eps):
+    if backtrack not in (None, "original", "simple"):
+        raise ValueError(f"unknown backtracking rule {backtrack!r}")
+    if not 0.0 <= bt_beta < 1.0 or not 0.0 < bt_eps < 0.5:
+        raise ValueError("need beta in [0, 1) and eps'' in (0, 1/2)")
 
 
 def nama(o: LQOracle, lam: float, y0: np.ndarray | None = None, tol: float = 1e-8, mem: int = 5,
-         max_iter: int = 1000, max_ls: int = 30, eps_curv: float = 1e-12) -> dict:
-    """Algorithm 2 on the preconditioned dual.  y0 is unscaled."""
+         max_iter: int = 1000, max_ls: int = 30, eps_curv: float = 1e-12, backtrack: str | None = None,
+         bt_beta: float = 0.0, bt_eps: float = 0.25, max_halvings: int = 60) -> dict:
+    """Algorithm 2 on the preconditioned dual.  y0 is unscaled.  backtrack: None (fixed lambda),
+    "original" (eq. original-backtracking with beta = bt_beta) or "simple" (eq.
+    simple-backtracking with eps'' = bt_eps)."""
+    _check_backtrack(backtrack, bt_beta, bt_eps)
     t0 = time.perf_counter()
     o.solve_calls = 0
     yb = np.zeros(o.m) if y0 is None else np.asarray(y0, dtype=np.float64) / o.sq
     lb = LBFGS(mem, lam)
     pt = fb_point(o, yb, lam)
-    hist = dict(phi=[pt["phi"]], tau=[], res=[pt["res_inf"]])
+    hist = dict(phi=[pt["phi"]], tau=[], res=[pt["res_inf"]], lam=lam, halvings=0)
+
+    def halve():
+        nonlocal lam, pt
+        lam *= 0.5
+        lb.clear()
+        lb.lam = lam
+        hist["lam"], hist["halvings"] = lam, hist["halvings"] + 1
+        pt = fb_point(o, pt["y"], lam)
+
     k = 0
     while pt["res_inf"] > tol:
-        if k >= max_iter:
+        if k >= max_iter or hist["halvings"] > max_halvings:
             return _result(o, pt, k, hist, "not_converged", t0)
+        if backtrack == "simple" and simple_backtrack_fails(o, pt, lam, bt_eps):
+            halve()
+            continue
         r = pt["r"]
         d = -lb.apply(r)
         fb_dir = pt["T"] - pt["y"]
@@ -358,6 +423,9 @@ def nama(o: LQOracle, lam: float, y0: np.ndarray | None = None, tol: float = 1e-
         if wp is None:
             tau, wp = 0.0, fb_point(o, pt["T"].copy(), lam)
         new = fb_point(o, wp["T"], lam)
+        if backtrack == "original" and original_backtrack_fails(o, wp, new, lam, bt_beta):
+            halve()
+            continue
         s = new["y"] - pt["y"]
         qv = new["r"] - r
         if float(np.dot(s, qv)) > eps_curv * float(np.dot(s, s)) * float(np.dot(r, r)):
@@ -371,19 +439,34 @@ def nama(o: LQOracle, lam: float, y0: np.ndarray | None = None, tol: float = 1e-
 
 
 def minfbe(o: LQOracle, lam: float, y0: np.ndarray | None = None, tol: float = 1e-8, mem: int = 5,
-           max_iter: int = 1000, max_ls: int = 30, eps_curv: float = 1e-12) -> dict:
-    """Algorithm 1 on the preconditioned dual.  y0 is unscaled."""
+           max_iter: int = 1000, max_ls: int = 30, eps_curv: float = 1e-12, backtrack: str | None = None,
+           bt_beta: float = 0.0, bt_eps: float = 0.25, max_halvings: int = 60) -> dict:
+    """Algorithm 1 on the preconditioned dual.  y0 is unscaled.  backtrack as for nama."""
+    _check_backtrack(backtrack, bt_beta, bt_eps)
     t0 = time.perf_counter()
     o.solve_calls = 0
     yb = np.zeros(o.m) if y0 is None else np.asarray(y0, dtype=np.float64) / o.sq
     lb = LBFGS(mem, lam)
     pt = fb_point(o, yb, lam)
     g = fbe_grad(o, yb, lam, pt)
-    hist = dict(phi=[pt["phi"]], tau=[], res=[pt["res_inf"]])
+    hist = dict(phi=[pt["phi"]], tau=[], res=[pt["res_inf"]], lam=lam, halvings=0)
+
+    def halve():
+        nonlocal lam, pt, g
+        lam *= 0.5
+        lb.clear()
+        lb.lam = lam
+        hist["lam"], hist["halvings"] = lam, hist["halvings"] + 1
+        pt = fb_point(o, pt["y"], lam)
+        g = fbe_grad(o, pt["y"], lam, pt)
+
     k = 0
     while pt["res_inf"] > tol:
-        if k >= max_iter:
+        if k >= max_iter or hist["halvings"] > max_halvings:
             return _result(o, pt, k, hist, "not_converged", t0)
+        if backtrack == "simple" and simple_backtrack_fails(o, pt, lam, bt_eps):
+            halve()
+            continue
         d = -lb.apply(g)
         tau, wp = 1.0, None
         for _ in range(max_ls + 1):
@@ -395,6 +478,9 @@ def minfbe(o: LQOracle, lam: float, y0: np.ndarray | None = None, tol: float = 1
         if wp is None:
             tau, wp = 0.0, pt
         new = fb_point(o, wp["T"], lam)
+        if backtrack == "original" and original_backtrack_fails(o, wp, new, lam, bt_beta):
+            halve()
+            continue
         g_new = fbe_grad(o, new["y"], lam, new)
         s = new["y"] - pt["y"]
         qv = g_new - g

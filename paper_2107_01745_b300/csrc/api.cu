@@ -494,6 +494,9 @@ static sto_status check_opts(const sto_opts *o) {
     if (!(o->lambda > 0.0) || !(o->tol > 0.0) || o->lbfgs_mem < 1 || o->lbfgs_mem > kMaxMem ||
         o->max_iter < 0 || o->max_ls < 0 || o->max_ls > 30 || !(o->eps_curv >= 0.0))
         return STO_ERR_INVALID_ARG;
+    if (o->backtrack < 0 || o->backtrack > 2 || o->max_halvings < 0) return STO_ERR_INVALID_ARG;
+    if (o->backtrack == 1 && !(o->bt_param >= 0.0 && o->bt_param < 1.0)) return STO_ERR_INVALID_ARG;
+    if (o->backtrack == 2 && !(o->bt_param > 0.0 && o->bt_param < 0.5)) return STO_ERR_INVALID_ARG;
     return STO_OK;
 }
 

@@ -1541,7 +1541,8 @@ STO_API sto_status stobatch_nama_solve(stobatch_t b, const sto_opts *o, const do
             infos[i].status = b->hs[i].nan_flag ? STO_ERR_NUMERICAL : (b->hs[i].active ? STO_NOT_CONVERGED : STO_OK);
             infos[i].ls_zero = b->hs[i].ls_zero;
             infos[i].launches = 0;
-            infos[i].reserved = 0;
+            infos[i].halvings = 0;
+            infos[i].lambda = lambdas[i];
             infos[i].res_inf = b->hs[i].res_inf;
             infos[i].fbe = b->hs[i].phi;
             infos[i].ms = ms;

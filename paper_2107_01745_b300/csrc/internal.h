@@ -27,6 +27,9 @@ struct SolverScalars {
     double res_inf;   // ||z - Hx||_inf (unscaled) at the current iterate
     double tau;       // accepted line-search step
     int ls_done, ls_zero, iters, status;
+    // step-size backtracking tests (Section III-B): <r_w, Hx(T(w)) - Hx(w)> and ||r_w||^2 of the
+    // last forward-backward step, ||r||^2 at the current iterate, ||S H x_lin(r)||^2 there
+    double bt_a, bt_b, r2, hr2;
     double cand[kMaxCand];
     // L-BFGS ring of mem+1 slots (slot order = oldest .. newest starting at head)
     int lb_count, lb_head, lb_pending_valid, lb_new_pair;
@@ -43,7 +46,7 @@ struct SolverScalars {
     unsigned int red_counter;
     unsigned int pad2;
 };
-constexpr size_t kScalHead = 80;
+constexpr size_t kScalHead = 112;
 
 struct Layout {
     size_t total = 0;
@@ -78,7 +81,7 @@ struct Layout {
 
 constexpr int kSegMax = 4;       // nodes per path segment (work item) of a solve round
 
-constexpr int kNumVec = 10;      // ybar, h, r, d, hr, hd, g, tmp0, tmp1, tmp2
+constexpr int kNumVec = 12;      // ybar, h, r, d, hr, hd, g, tmp0, tmp1, tmp2, tmp3, tmp4
 
 }  // namespace sto
 

@@ -318,14 +318,17 @@ __device__ bool reduce_last(T *sums, T *maxs, double *partials, unsigned *counte
 }
 
 // ---------------------------------------------------------------------------------------
-// k_point: residual, FBE and stopping test at the current ybar (h = S H x(ybar)).
+// k_point: residual, FBE and stopping test at the current ybar (h = S H x(ybar)), and ||r||^2.
 // pair = 1 (NAMA after a step): q = r_new - r_old -> Y[p], curvature test, commit pair.
+// rw, hw (non-null with the original backtracking test): r and h at the point w the step was
+// taken from; reduces <rw, h - hw> and ||rw||^2.
 // ---------------------------------------------------------------------------------------
 template <class T>
 __global__ void __launch_bounds__(kThreads) k_point(DualView<T> dv, const T *__restrict__ yb, const T *__restrict__ h,
                                                     T *r, T *ringS, T *ringY, long long vstride, int pair,
-                                                    SolverScalars *sc, double *partials) {
-    __shared__ double tot[8];
+                                                    SolverScalars *sc, double *partials, const T *__restrict__ rw,
+                                                    const T *__restrict__ hw) {
+    __shared__ double tot[9];
     extern __shared__ __align__(16) unsigned char tab_raw[];
     CompTab<T> tab;
     tab.load(dv, reinterpret_cast<T *>(tab_raw));
@@ -334,15 +337,19 @@ __global__ void __launch_bounds__(kThreads) k_point(DualView<T> dv, const T *__r
     const int p = (sc->lb_head + sc->lb_count) % (sc->mem + 1);
     const T *sv = ringS + p * vstride;
     T *qv = ringY + p * vstride;
-    T fsum = 0, sq_dot = 0, s2 = 0, g2 = 0, rmax = 0;
+    T fsum = 0, sq_dot = 0, s2 = 0, g2 = 0, rmax = 0, r2 = 0, bta = 0, btb = 0;
     int nan = 0;
     for_vectors<T>(dv.m, [&](int e0, int n) {
-        T he[VN], ye[VN], re[VN], ro[VN], se[VN], q[VN];
+        T he[VN], ye[VN], re[VN], ro[VN], se[VN], q[VN], rwe[VN], hwe[VN];
         ldv(h, e0, n, he);
         ldv(yb, e0, n, ye);
         if (pair) {
             ldv<T>(r, e0, n, ro);
             ldv(sv, e0, n, se);
+        }
+        if (rw) {
+            ldv(rw, e0, n, rwe);
+            ldv(hw, e0, n, hwe);
         }
         Pos ps = pos_of(dv, e0);
         int cur = -1;
@@ -362,6 +369,11 @@ __global__ void __launch_bounds__(kThreads) k_point(DualView<T> dv, const T *__r
                 const T ra = fabs(re[k]) * isq;
                 if (!(ra <= T(3.0e38))) nan = 1;
                 rmax = fmax(rmax, ra);
+                r2 += re[k] * re[k];
+                if (rw) {
+                    bta += rwe[k] * (he[k] - hwe[k]);
+                    btb += rwe[k] * rwe[k];
+                }
                 if (pair) {
                     q[k] = re[k] - ro[k];
                     sq_dot += se[k] * q[k];
@@ -374,11 +386,14 @@ __global__ void __launch_bounds__(kThreads) k_point(DualView<T> dv, const T *__r
         if (pair) stv(qv, e0, n, q);
         stv(r, e0, n, re);
     });
-    T sums[5] = {fsum, sq_dot, s2, g2, (T)nan};
+    T sums[8] = {fsum, sq_dot, s2, g2, (T)nan, r2, bta, btb};
     T maxs[1] = {rmax};
-    if (reduce_last<T, 5, 1>(sums, maxs, partials, &sc->red_counter, tot) && threadIdx.x == 0) {
+    if (reduce_last<T, 8, 1>(sums, maxs, partials, &sc->red_counter, tot) && threadIdx.x == 0) {
         sc->phi = -tot[0];
-        sc->res_inf = tot[5];
+        sc->res_inf = tot[8];
+        sc->r2 = tot[5];
+        sc->bt_a = tot[6];
+        sc->bt_b = tot[7];
         if (tot[4] > 0.0 || !(tot[0] == tot[0])) sc->nan_flag = 1;
         if (pair && sc->lb_pending_valid) {
             if (tot[1] > sc->eps_curv * tot[2] * tot[3]) {
@@ -393,7 +408,8 @@ __global__ void __launch_bounds__(kThreads) k_point(DualView<T> dv, const T *__r
     }
 }
 
-// MINFBE: g_new = r + lam hr = grad FBE; with a pending pair q = g_new - g_old -> Y[p].
+// MINFBE: g_new = r + lam hr = grad FBE; with a pending pair q = g_new - g_old -> Y[p];
+// ||hr||^2 for the simple backtracking test.
 template <class T>
 __global__ void __launch_bounds__(kThreads) k_grad(int m, const T *__restrict__ r, const T *__restrict__ hr, T *g,
                                                    T *ringS, T *ringY, long long vstride, SolverScalars *sc,
@@ -405,7 +421,7 @@ __global__ void __launch_bounds__(kThreads) k_grad(int m, const T *__restrict__ 
     const int p = (sc->lb_head + sc->lb_count) % (sc->mem + 1);
     const T *sv = ringS + p * vstride;
     T *qv = ringY + p * vstride;
-    T sq_dot = 0, s2 = 0, g2 = 0;
+    T sq_dot = 0, s2 = 0, g2 = 0, hr2 = 0;
     for_vectors<T>(m, [&](int e0, int n) {
         T re[VN], he[VN], gn[VN], go[VN], se[VN], q[VN];
         ldv(r, e0, n, re);
@@ -417,6 +433,7 @@ __global__ void __launch_bounds__(kThreads) k_grad(int m, const T *__restrict__ 
 #pragma unroll
         for (int k = 0; k < VN; ++k) {
             gn[k] = re[k] + lam * he[k];
+            hr2 += he[k] * he[k];  // zero past n (ldv pads)
             if (pair && k < n) {
                 q[k] = gn[k] - go[k];
                 sq_dot += se[k] * q[k];
@@ -427,9 +444,10 @@ __global__ void __launch_bounds__(kThreads) k_grad(int m, const T *__restrict__ 
         if (pair) stv(qv, e0, n, q);
         stv(g, e0, n, gn);
     });
-    T sums[3] = {sq_dot, s2, g2};
+    T sums[4] = {sq_dot, s2, g2, hr2};
     T maxs[1];
-    if (reduce_last<T, 3, 0>(sums, maxs, partials, &sc->red_counter, tot) && threadIdx.x == 0) {
+    if (reduce_last<T, 4, 0>(sums, maxs, partials, &sc->red_counter, tot) && threadIdx.x == 0) {
+        sc->hr2 = tot[3];
         if (pair) {
             if (tot[0] > sc->eps_curv * tot[1] * tot[2]) {
                 if (sc->lb_count < sc->mem)
@@ -689,11 +707,13 @@ __global__ void __launch_bounds__(kThreads) k_ls(DualView<T> dv, const T *__rest
 }
 
 // ybar+ = T_lam(w(tau)) = w + lam (h(w) - z(w)); s = ybar+ - ybar -> S[p]; ybar <- ybar+.
+// rw_out, hw_out (non-null with the original backtracking test): r(w) = z(w) - h(w) and h(w).
 template <class T>
 __global__ void __launch_bounds__(kThreads) k_fbstep(DualView<T> dv, T *yb, const T *__restrict__ h,
                                                      const T *__restrict__ r, const T *__restrict__ dvec,
                                                      const T *__restrict__ hr, const T *__restrict__ hd, int nama,
-                                                     T *ringS, long long vstride, SolverScalars *sc) {
+                                                     T *ringS, long long vstride, SolverScalars *sc, T *rw_out,
+                                                     T *hw_out) {
     const T lam = (T)sc->lambda, ilam = T(1) / lam;
     const T tau = (T)sc->tau;
     const int p = (sc->lb_head + sc->lb_count) % (sc->mem + 1);
@@ -703,7 +723,7 @@ __global__ void __launch_bounds__(kThreads) k_fbstep(DualView<T> dv, T *yb, cons
     tab.load(dv, reinterpret_cast<T *>(tab_raw));
     constexpr int VN = Vec16<T>::n;
     for_vectors<T>(dv.m, [&](int e0, int n) {
-        T y0[VN], h0[VN], re[VN], dd[VN], hre[VN], hdd[VN], yn[VN], sn[VN];
+        T y0[VN], h0[VN], re[VN], dd[VN], hre[VN], hdd[VN], yn[VN], sn[VN], rwv[VN], hwv[VN];
         ldv(yb, e0, n, y0);
         ldv(h, e0, n, h0);
         ldv(dvec, e0, n, dd);
@@ -734,11 +754,17 @@ __global__ void __launch_bounds__(kThreads) k_fbstep(DualView<T> dv, T *yb, cons
                 const T z = clampv(hw + w * ilam, M.lo, M.hi);
                 yn[k] = w + lam * (hw - z);
                 sn[k] = yn[k] - y0[k];
+                rwv[k] = z - hw;
+                hwv[k] = hw;
                 pos_next(dv, ps);
             }
         }
         stv(sv, e0, n, sn);
         stv(yb, e0, n, yn);
+        if (rw_out) {
+            stv(rw_out, e0, n, rwv);
+            stv(hw_out, e0, n, hwv);
+        }
     });
     if (blockIdx.x == 0 && threadIdx.x == 0) {
         sc->lb_pending_valid = 1;
@@ -802,6 +828,35 @@ __global__ void __launch_bounds__(kThreads) k_gpad(DualView<T> dv, const T *__re
         sc->res_inf = tot[2];
         if (tot[1] > 0.0 || !(tot[0] == tot[0])) sc->nan_flag = 1;
     }
+}
+
+// ||v||^2 -> sc->hr2 (the simple backtracking test of NAMA, v = S H x_lin(r)).
+template <class T>
+__global__ void __launch_bounds__(kThreads) k_norm2(int m, const T *__restrict__ v, SolverScalars *sc,
+                                                    double *partials) {
+    __shared__ double tot[1];
+    constexpr int VN = Vec16<T>::n;
+    T acc = 0;
+    for_vectors<T>(m, [&](int e0, int n) {
+        T x[VN];
+        ldv(v, e0, n, x);
+#pragma unroll
+        for (int k = 0; k < VN; ++k) acc += x[k] * x[k];
+    });
+    T sums[1] = {acc};
+    T maxs[1];
+    if (reduce_last<T, 1, 0>(sums, maxs, partials, &sc->red_counter, tot) && threadIdx.x == 0) sc->hr2 = tot[0];
+}
+
+// A halving of the step (Section III-B backtracking): the new lambda, and the L-BFGS memory
+// emptied.
+__global__ void k_set_lambda(SolverScalars *sc, double lam) {
+    sc->lambda = lam;
+    sc->lb_count = 0;
+    sc->lb_head = 0;
+    sc->lb_pending_valid = 0;
+    sc->lb_new_pair = 0;
+    sc->ls_done = 0;
 }
 
 // ybar = y / sqrt(pi) (in) and y = sqrt(pi) ybar, z = z_bar / sqrt(pi), x, u = S^-1 h (out).
@@ -914,6 +969,10 @@ sto_status solver_impl(stotree_t h, int method, const sto_opts *o, const void *x
     const long long vs = (long long)vstride_of(h);
     T *V = h->at<T>(L.vec);
     T *yb = V, *hv = V + vs, *r = V + 2 * vs, *d = V + 3 * vs, *hr = V + 4 * vs, *hd = V + 5 * vs, *g = V + 6 * vs;
+    // the original backtracking test keeps ybar, h of the iterate and r, h at the step's origin w
+    T *ysave = V + 7 * vs, *hsave = V + 8 * vs, *rw = V + 9 * vs, *hw = V + 10 * vs;
+    const int bt = o->backtrack;
+    T *rw_arg = bt == 1 ? rw : nullptr, *hw_arg = bt == 1 ? hw : nullptr;
     T *ringS = h->at<T>(L.ringS), *ringY = h->at<T>(L.ringY);
     SolverScalars *sc = h->at<SolverScalars>(L.scal);
     double *part = h->at<double>(L.partials);
@@ -971,27 +1030,57 @@ sto_status solver_impl(stotree_t h, int method, const sto_opts *o, const void *x
     h->launches += 1;
     sto_status s = full_solve();
     if (s != STO_OK) return s;
-    k_point<T><<<grid, kThreads, tabb, st>>>(dv, yb, hv, r, ringS, ringY, vs, 0, sc, part);
+    k_point<T><<<grid, kThreads, tabb, st>>>(dv, yb, hv, r, ringS, ringY, vs, 0, sc, part, nullptr, nullptr);
     h->launches += 1;
     if (!nama) {
         if ((s = lin_solve(r, hr)) != STO_OK) return s;
         k_grad<T><<<grid, kThreads, 0, st>>>(m, r, hr, g, ringS, ringY, vs, sc, part);
         h->launches += 1;
     }
+    // Backtracking (Section III-B): halve lambda, empty the L-BFGS memory and re-evaluate the
+    // residual (and for MINFBE the FBE gradient) at the current iterate, whose x(ybar) does not
+    // depend on lambda.
+    double lam = o->lambda;
+    int halvings = 0;
+    auto halve = [&]() -> sto_status {
+        lam *= 0.5;
+        ++halvings;
+        k_set_lambda<<<1, 1, 0, st>>>(sc, lam);
+        k_point<T><<<grid, kThreads, tabb, st>>>(dv, yb, hv, r, ringS, ringY, vs, 0, sc, part, nullptr, nullptr);
+        h->launches += 2;
+        if (!nama) {
+            const sto_status e = lin_solve(r, hr);
+            if (e != STO_OK) return e;
+            k_grad<T><<<grid, kThreads, 0, st>>>(m, r, hr, g, ringS, ringY, vs, sc, part);
+            h->launches += 1;
+        }
+        return STO_OK;
+    };
+    auto read_head = [&]() -> sto_status {
+        STO_CUDA(h, cudaMemcpyAsync(hs, sc, kScalHead, cudaMemcpyDeviceToHost, st));
+        STO_CUDA(h, cudaStreamSynchronize(st));
+        return STO_OK;
+    };
+    // lambda ||S H x_lin(r)|| > eps'' ||r||, i.e. eq. (simple-backtracking) with
+    // T(y) - y = -lambda r and grad fhat(T(y)) - grad fhat(y) = lambda S H x_lin(r)
+    auto simple_fails = [&]() { return lam * lam * hs->hr2 > o->bt_param * o->bt_param * hs->r2; };
     sto_status result = STO_OK;
     int iters = 0;
     while (true) {
-        STO_CUDA(h, cudaMemcpyAsync(hs, sc, kScalHead, cudaMemcpyDeviceToHost, st));
-        STO_CUDA(h, cudaStreamSynchronize(st));
+        if ((s = read_head()) != STO_OK) return s;
         if (hs->nan_flag) {
             result = STO_ERR_NUMERICAL;
             h->err = "NaN or Inf in the residual";
             break;
         }
         if (hs->res_inf <= o->tol) break;
-        if (iters >= o->max_iter) {
+        if (iters >= o->max_iter || halvings > o->max_halvings) {
             result = STO_NOT_CONVERGED;
             break;
+        }
+        if (bt == 2 && !nama && simple_fails()) {  // MINFBE: ||hr||^2 came with the FBE gradient
+            if ((s = halve()) != STO_OK) return s;
+            continue;
         }
         T *gdir = nama ? r : g;
         lb_direction<T>(o->lbfgs_mem, grid, st, m, gdir, ringS, ringY, vs, sc, part, d);
@@ -1000,6 +1089,15 @@ sto_status solver_impl(stotree_t h, int method, const sto_opts *o, const void *x
             const void *ys[2] = {r, d};
             void *outs[2] = {hr, hd};
             if ((s = solve_round(h, ys, nullptr, outs, 2, true, true, st)) != STO_OK) return s;
+            if (bt == 2) {  // NAMA: the test needs x_lin(r) of this round
+                k_norm2<T><<<grid, kThreads, 0, st>>>(m, hr, sc, part);
+                h->launches += 1;
+                if ((s = read_head()) != STO_OK) return s;
+                if (simple_fails()) {
+                    if ((s = halve()) != STO_OK) return s;
+                    continue;
+                }
+            }
         } else {
             if ((s = lin_solve(d, hd)) != STO_OK) return s;
         }
@@ -1015,9 +1113,25 @@ sto_status solver_impl(stotree_t h, int method, const sto_opts *o, const void *x
                 k_ls<T, 19><<<grid, kThreads, tabb, st>>>(dv, yb, hv, r, d, hr, hd, nama, gfirst[k], gcount[k], last, sc,
                                                       part);
         }
-        k_fbstep<T><<<grid, kThreads, tabb, st>>>(dv, yb, hv, r, d, hr, hd, nama, ringS, vs, sc);
+        if (bt == 1) {
+            STO_CUDA(h, cudaMemcpyAsync(ysave, yb, (size_t)m * sizeof(T), cudaMemcpyDeviceToDevice, st));
+            STO_CUDA(h, cudaMemcpyAsync(hsave, hv, (size_t)m * sizeof(T), cudaMemcpyDeviceToDevice, st));
+        }
+        k_fbstep<T><<<grid, kThreads, tabb, st>>>(dv, yb, hv, r, d, hr, hd, nama, ringS, vs, sc, rw_arg, hw_arg);
         if ((s = full_solve()) != STO_OK) return s;
-        k_point<T><<<grid, kThreads, tabb, st>>>(dv, yb, hv, r, ringS, ringY, vs, nama ? 1 : 0, sc, part);
+        k_point<T><<<grid, kThreads, tabb, st>>>(dv, yb, hv, r, ringS, ringY, vs, nama ? 1 : 0, sc, part, rw_arg,
+                                                 hw_arg);
+        if (bt == 1) {
+            // eq. (original-backtracking) at w: for the quadratic fhat it reads
+            // <r_w, h(T(w)) - h(w)> > (1 - beta) ||r_w||^2; on failure the step is rejected
+            if ((s = read_head()) != STO_OK) return s;
+            if (hs->nan_flag == 0 && hs->bt_a > (1.0 - o->bt_param) * hs->bt_b) {
+                STO_CUDA(h, cudaMemcpyAsync(yb, ysave, (size_t)m * sizeof(T), cudaMemcpyDeviceToDevice, st));
+                STO_CUDA(h, cudaMemcpyAsync(hv, hsave, (size_t)m * sizeof(T), cudaMemcpyDeviceToDevice, st));
+                if ((s = halve()) != STO_OK) return s;
+                continue;
+            }
+        }
         if (!nama) {
             if ((s = lin_solve(r, hr)) != STO_OK) return s;
             k_grad<T><<<grid, kThreads, 0, st>>>(m, r, hr, g, ringS, ringY, vs, sc, part);
@@ -1053,7 +1167,8 @@ sto_status solver_impl(stotree_t h, int method, const sto_opts *o, const void *x
         info->fbe = hs->phi;
         info->ms = ms;
         info->launches = (int32_t)(h->launches - launches0);
-        info->reserved = 0;
+        info->halvings = halvings;
+        info->lambda = lam;
     }
     STO_CUDA(h, cudaGetLastError());
     return result;
@@ -1147,7 +1262,8 @@ sto_status gpad_impl(stotree_t h, const sto_opts *o, const void *x0v, void *yv, 
         info->fbe = hs->phi;
         info->ms = ms;
         info->launches = (int32_t)(h->launches - launches0);
-        info->reserved = 0;
+        info->halvings = 0;
+        info->lambda = o->lambda;
     }
     STO_CUDA(h, cudaGetLastError());
     return result;

@@ -35,14 +35,16 @@ class _TreeDesc(ctypes.Structure):
 
 class Opts(ctypes.Structure):
     _fields_ = [("lambda_", ctypes.c_double), ("tol", ctypes.c_double), ("eps_curv", ctypes.c_double),
-                ("lbfgs_mem", ctypes.c_int32), ("max_iter", ctypes.c_int32), ("max_ls", ctypes.c_int32)]
+                ("lbfgs_mem", ctypes.c_int32), ("max_iter", ctypes.c_int32), ("max_ls", ctypes.c_int32),
+                ("backtrack", ctypes.c_int32), ("bt_param", ctypes.c_double), ("max_halvings", ctypes.c_int32),
+                ("pad_", ctypes.c_int32)]
 
 
 class Info(ctypes.Structure):
     _fields_ = [("iters", ctypes.c_int32), ("solve_calls", ctypes.c_int32), ("status", ctypes.c_int32),
-                ("ls_zero", ctypes.c_int32), ("launches", ctypes.c_int32), ("reserved", ctypes.c_int32),
+                ("ls_zero", ctypes.c_int32), ("launches", ctypes.c_int32), ("halvings", ctypes.c_int32),
                 ("res_inf", ctypes.c_double), ("fbe", ctypes.c_double),
-                ("ms", ctypes.c_double)]
+                ("ms", ctypes.c_double), ("lambda_", ctypes.c_double)]
 
     def as_dict(self):
         return {k: getattr(self, k) for k, _ in self._fields_}
@@ -275,9 +277,13 @@ class StoTree:
         return lam.value, L.value
 
     def solve(self, method, lam, x0=None, y0=None, tol=1e-4, mem=5, max_iter=1000, max_ls=30, eps_curv=None,
-              outputs=True, allow_not_converged=False):
+              outputs=True, allow_not_converged=False, backtrack=None, bt_param=None, max_halvings=60):
         """Algorithm 1 (method='minfbe'), 2 (method='nama') or GPAD (method='gpad', the
-        accelerated dual projected gradient of Sections III-E and IV).  Returns tensors and info."""
+        accelerated dual projected gradient of Sections III-E and IV).  Returns tensors and info.
+
+        backtrack (Algorithms 1 and 2): None (fixed lambda), 'original' (eq. original-backtracking,
+        bt_param = beta, default 0) or 'simple' (eq. simple-backtracking, bt_param = eps'',
+        default 0.25); the info dict then reports the final 'lambda_' and the 'halvings'."""
         if eps_curv is None:
             eps_curv = 1e-12 if self.prec == STO_FP64 else 1e-8
         x0 = self.to_dev(self.p.x0) if x0 is None else x0
@@ -285,7 +291,10 @@ class StoTree:
         x = torch.empty((self.Nn, self.nx), dtype=self.dtype, device=self.device) if outputs else None
         u = torch.empty((self.Np, self.nu), dtype=self.dtype, device=self.device) if outputs else None
         z = torch.empty(self.m, dtype=self.dtype, device=self.device) if outputs else None
-        o = Opts(lam, tol, eps_curv, mem, max_iter, max_ls)
+        bt_code = {None: 0, "original": 1, "simple": 2}[backtrack]
+        if bt_param is None:
+            bt_param = 0.25 if backtrack == "simple" else 0.0
+        o = Opts(lam, tol, eps_curv, mem, max_iter, max_ls, bt_code, bt_param, max_halvings, 0)
         info = Info()
         fn = {"nama": lib().stotree_nama_solve, "minfbe": lib().stotree_minfbe_solve,
               "gpad": lib().stotree_gpad_solve}[method]

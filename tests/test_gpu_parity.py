@@ -182,6 +182,65 @@ def test_gpad_fp32_matches_oracle(cuda_device, p):
     assert _relinf(res["u"].cpu().numpy(), ref["u"]) < 1e-4
 
 
+BT_BOXED = [D.boxed_problem(12, horizon=3, nx=3, nu=2), D.boxed_problem(17, horizon=4, nx=4, nu=2, frac=0.9),
+            D.boxed_problem(16, horizon=3, nx=5, nu=3, frac=0.9)]
+
+
+@pytest.mark.parametrize("rule,param", [("original", 0.1), ("simple", 0.25)])
+@pytest.mark.parametrize("method", ["nama", "minfbe"])
+@pytest.mark.parametrize("p", BT_BOXED, ids=lambda p: f"{p.name}-nx{p.nx}")
+def test_backtracking_fp64_matches_oracle(cuda_device, p, method, rule, param):
+    """Step-size backtracking (Section III-B) from lambda = 64 / L: the FP64 GPU run halves
+    lambda as often as the oracle, to the same step, and returns the same solution.  The
+    iterates agree to rounding until the residual nears 1e-8, where line-search comparisons of
+    FBE values at rounding level can go either way, so the iteration counts may differ by a
+    few."""
+    o = O.LQOracle(p)
+    _, L = O.power_lambda(o, np.random.default_rng(0).standard_normal(o.m), iters=200)
+    lam0 = 64.0 / L
+    kw = dict(bt_beta=param) if rule == "original" else dict(bt_eps=param)
+    ref = (O.nama if method == "nama" else O.minfbe)(o, lam0, tol=1e-10, max_iter=2000, backtrack=rule, **kw)
+    assert ref["status"] == "converged" and ref["halvings"] >= 1
+    st = _st()(p, precision="fp64")
+    st.factor()
+    res = st.solve(method, lam0, tol=1e-10, max_iter=2000, backtrack=rule, bt_param=param)
+    info = res["info"]
+    assert info["status"] == 0 and info["res_inf"] <= 1e-10
+    assert info["halvings"] == ref["halvings"]
+    assert info["lambda_"] == ref["lam"]
+    assert abs(info["iters"] - ref["iters"]) <= 6
+    assert _relinf(res["x"].cpu().numpy(), ref["x"]) < 1e-8
+    assert _relinf(res["y"].cpu().numpy(), ref["y"]) < 1e-7
+
+
+@pytest.mark.parametrize("rule,param", [("original", 0.1), ("simple", 0.25)])
+@pytest.mark.parametrize("method", ["nama", "minfbe"])
+def test_backtracking_fp32(cuda_device, method, rule, param):
+    p = BT_BOXED[2]
+    o = O.LQOracle(p)
+    _, L = O.power_lambda(o, np.random.default_rng(0).standard_normal(o.m), iters=200)
+    lam0 = 64.0 / L
+    st = _st()(p, precision="fp32")
+    st.factor()
+    res = st.solve(method, lam0, tol=1e-5, max_iter=2000, backtrack=rule, bt_param=param)
+    info = res["info"]
+    assert info["status"] == 0 and info["res_inf"] <= 1e-5 and info["halvings"] >= 1
+    bound = (1.0 - param) if rule == "original" else param
+    assert bound / (2.0 * L) * 0.99 <= info["lambda_"] <= lam0 / 2
+    ref = O.nama(o, 0.9 / L, tol=1e-10)
+    assert _relinf(res["x"].cpu().numpy(), ref["x"]) < 1e-4
+
+
+def test_backtracking_rejects_bad_options(cuda_device):
+    from paper_2107_01745_b300.stotree import StoError
+    st = _st()(BT_BOXED[0], precision="fp32")
+    st.factor()
+    for rule, param in (("original", 1.0), ("original", -0.1), ("simple", 0.5), ("simple", 0.0)):
+        with pytest.raises(StoError) as ei:
+            st.solve("nama", 0.1, backtrack=rule, bt_param=param)
+        assert ei.value.code == 1
+
+
 def test_loose_box_returns_unconstrained_solution(cuda_device):
     p = W.random_problem(14, box_scale=1e6)
     st = _st()(p, precision="fp64")
@@ -244,6 +303,29 @@ def test_paper_scale_solver(cuda_device, paper_scale, method):
     assert _relinf(res["u"].cpu().numpy(), ref["u"]) < 1e-3
     kkt = st.kkt_check(st.to_dev(p.x0), res["x"], res["u"], res["y"], tol_active=1e-3)
     assert kkt["dynamics"] < 1e-4 and kkt["feasibility"] < 2e-4
+
+
+@pytest.mark.slow
+def test_paper_scale_backtracking(cuda_device, paper_scale):
+    """Full size, NAMA with either backtracking rule from ten times the estimated 1/L: it
+    reaches the tolerance with a step no smaller than the rule's bound / (2 L), and the
+    solution passes the FP64 KKT check.  (The original rule tests the curvature only along
+    R(w), so it may keep a step above 1/L.)"""
+    p, o = paper_scale
+    st = _st()(p, precision="fp32")
+    st.factor()
+    r0 = torch.as_tensor(np.random.default_rng(7).standard_normal(st.m), dtype=torch.float32, device="cuda")
+    _, L = st.estimate_lambda(r0, iters=50, safety=0.9)
+    for rule, param in (("simple", 0.25), ("original", 0.1)):
+        res = st.solve("nama", 10.0 / L, tol=1e-4, max_iter=500, backtrack=rule, bt_param=param)
+        info = res["info"]
+        print("paper-scale backtracking", rule, info)
+        assert info["status"] == 0 and info["res_inf"] <= 1e-4
+        assert info["halvings"] >= 1 or rule == "original"
+        bound = param if rule == "simple" else 1.0 - param
+        assert info["lambda_"] >= bound / (2.0 * L) * 0.99
+        kkt = st.kkt_check(st.to_dev(p.x0), res["x"], res["u"], res["y"], tol_active=1e-3)
+        assert kkt["dynamics"] < 1e-4 and kkt["feasibility"] < 2e-4
 
 
 def test_paper_scale_gpad_warm_start(cuda_device, paper_scale):
