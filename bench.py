@@ -50,8 +50,8 @@ def _traffic_per_launch(rounds, rhs):
         return None
     text = open(path).read()
     m = re.search(r"sha256 `([0-9a-f]{64})`", text)
-    t1 = re.search(r"traffic_bytes_per_launch_1rhs: (\d+)", text)
-    t2 = re.search(r"traffic_bytes_per_launch_2rhs: (\d+)", text)
+    t1 = re.search(r"traffic_bytes_per_round_1rhs: (\d+)", text)
+    t2 = re.search(r"traffic_bytes_per_round_2rhs: (\d+)", text)
     if not (m and t1 and t2):
         return None
     if hashlib.sha256(open(src, "rb").read()).hexdigest() != m.group(1):
@@ -245,7 +245,7 @@ def run_ours(args):
                      "solve_calls": nama_infos[0]["solve_calls"], "ls_zero": nama_infos[0]["ls_zero"]},
             "minfbe": {"ms": round(minfbe_ms, 4), "iters": minfbe_infos[0]["iters"],
                        "solve_calls": minfbe_infos[0]["solve_calls"]},
-            "roofline": {"kernel": "k_tree (one Algorithm 3/4 solve round per launch)", "bound": "hbm",
+            "roofline": {"kernel": "k_tree (one Algorithm 3/4 solve round = a backward-pass launch + a forward-pass launch)", "bound": "hbm",
                          "achieved": round(achieved, 1), "peak": peak, "unit": "GB/s",
                          "frac": round(achieved / peak, 4), "peak_source": peak_kind,
                          "traffic": _traffic_per_launch(rounds, rhs), "rounds": rounds, "rhs": rhs,

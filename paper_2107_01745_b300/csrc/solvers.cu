@@ -318,12 +318,12 @@ __device__ bool reduce_last(T *sums, T *maxs, double *partials, unsigned *counte
 }
 
 // ---------------------------------------------------------------------------------------
-// k_point: residual, FBE and stopping test at the current ybar (h = S H x(ybar)), and ||r||^2.
+// k_point: residual, FBE and stopping test at the current ybar (h = S H x(ybar)).
 // pair = 1 (NAMA after a step): q = r_new - r_old -> Y[p], curvature test, commit pair.
-// rw, hw (non-null with the original backtracking test): r and h at the point w the step was
-// taken from; reduces <rw, h - hw> and ||rw||^2.
+// BT = 1 (original backtracking test): rw, hw are r and h at the point w the step was taken
+// from; reduces <rw, h - hw> and ||rw||^2.  BT = 2 (simple backtracking test): ||r||^2.
 // ---------------------------------------------------------------------------------------
-template <class T>
+template <class T, int BT>
 __global__ void __launch_bounds__(kThreads) k_point(DualView<T> dv, const T *__restrict__ yb, const T *__restrict__ h,
                                                     T *r, T *ringS, T *ringY, long long vstride, int pair,
                                                     SolverScalars *sc, double *partials, const T *__restrict__ rw,
@@ -347,7 +347,7 @@ __global__ void __launch_bounds__(kThreads) k_point(DualView<T> dv, const T *__r
             ldv<T>(r, e0, n, ro);
             ldv(sv, e0, n, se);
         }
-        if (rw) {
+        if constexpr (BT == 1) {
             ldv(rw, e0, n, rwe);
             ldv(hw, e0, n, hwe);
         }
@@ -369,8 +369,8 @@ __global__ void __launch_bounds__(kThreads) k_point(DualView<T> dv, const T *__r
                 const T ra = fabs(re[k]) * isq;
                 if (!(ra <= T(3.0e38))) nan = 1;
                 rmax = fmax(rmax, ra);
-                r2 += re[k] * re[k];
-                if (rw) {
+                if constexpr (BT == 2) r2 += re[k] * re[k];
+                if constexpr (BT == 1) {
                     bta += rwe[k] * (he[k] - hwe[k]);
                     btb += rwe[k] * rwe[k];
                 }
@@ -386,14 +386,27 @@ __global__ void __launch_bounds__(kThreads) k_point(DualView<T> dv, const T *__r
         if (pair) stv(qv, e0, n, q);
         stv(r, e0, n, re);
     });
-    T sums[8] = {fsum, sq_dot, s2, g2, (T)nan, r2, bta, btb};
+    constexpr int NS = BT == 0 ? 5 : (BT == 1 ? 7 : 6);
+    T sums[NS];
+    sums[0] = fsum;
+    sums[1] = sq_dot;
+    sums[2] = s2;
+    sums[3] = g2;
+    sums[4] = (T)nan;
+    if constexpr (BT == 1) {
+        sums[5] = bta;
+        sums[6] = btb;
+    }
+    if constexpr (BT == 2) sums[5] = r2;
     T maxs[1] = {rmax};
-    if (reduce_last<T, 8, 1>(sums, maxs, partials, &sc->red_counter, tot) && threadIdx.x == 0) {
+    if (reduce_last<T, NS, 1>(sums, maxs, partials, &sc->red_counter, tot) && threadIdx.x == 0) {
         sc->phi = -tot[0];
-        sc->res_inf = tot[8];
-        sc->r2 = tot[5];
-        sc->bt_a = tot[6];
-        sc->bt_b = tot[7];
+        sc->res_inf = tot[NS];
+        if constexpr (BT == 1) {
+            sc->bt_a = tot[5];
+            sc->bt_b = tot[6];
+        }
+        if constexpr (BT == 2) sc->r2 = tot[5];
         if (tot[4] > 0.0 || !(tot[0] == tot[0])) sc->nan_flag = 1;
         if (pair && sc->lb_pending_valid) {
             if (tot[1] > sc->eps_curv * tot[2] * tot[3]) {
@@ -972,7 +985,7 @@ sto_status solver_impl(stotree_t h, int method, const sto_opts *o, const void *x
     // the original backtracking test keeps ybar, h of the iterate and r, h at the step's origin w
     T *ysave = V + 7 * vs, *hsave = V + 8 * vs, *rw = V + 9 * vs, *hw = V + 10 * vs;
     const int bt = o->backtrack;
-    T *rw_arg = bt == 1 ? rw : nullptr, *hw_arg = bt == 1 ? hw : nullptr;
+    T *rw_arg = bt == 1 ? rw : nullptr, *hw_arg = bt == 1 ? hw : nullptr;  // k_fbstep outputs
     T *ringS = h->at<T>(L.ringS), *ringY = h->at<T>(L.ringY);
     SolverScalars *sc = h->at<SolverScalars>(L.scal);
     double *part = h->at<double>(L.partials);
@@ -1030,7 +1043,16 @@ sto_status solver_impl(stotree_t h, int method, const sto_opts *o, const void *x
     h->launches += 1;
     sto_status s = full_solve();
     if (s != STO_OK) return s;
-    k_point<T><<<grid, kThreads, tabb, st>>>(dv, yb, hv, r, ringS, ringY, vs, 0, sc, part, nullptr, nullptr);
+    // k_point with the backtracking reductions the rule needs
+    auto point = [&](int pair, const T *rwp, const T *hwp) {
+        if (bt == 1)
+            k_point<T, 1><<<grid, kThreads, tabb, st>>>(dv, yb, hv, r, ringS, ringY, vs, pair, sc, part, rwp, hwp);
+        else if (bt == 2)
+            k_point<T, 2><<<grid, kThreads, tabb, st>>>(dv, yb, hv, r, ringS, ringY, vs, pair, sc, part, rwp, hwp);
+        else
+            k_point<T, 0><<<grid, kThreads, tabb, st>>>(dv, yb, hv, r, ringS, ringY, vs, pair, sc, part, rwp, hwp);
+    };
+    point(0, hv, hv);  // (with BT = 1 the w terms of this call are not used)
     h->launches += 1;
     if (!nama) {
         if ((s = lin_solve(r, hr)) != STO_OK) return s;
@@ -1046,7 +1068,7 @@ sto_status solver_impl(stotree_t h, int method, const sto_opts *o, const void *x
         lam *= 0.5;
         ++halvings;
         k_set_lambda<<<1, 1, 0, st>>>(sc, lam);
-        k_point<T><<<grid, kThreads, tabb, st>>>(dv, yb, hv, r, ringS, ringY, vs, 0, sc, part, nullptr, nullptr);
+        point(0, hv, hv);
         h->launches += 2;
         if (!nama) {
             const sto_status e = lin_solve(r, hr);
@@ -1119,8 +1141,7 @@ sto_status solver_impl(stotree_t h, int method, const sto_opts *o, const void *x
         }
         k_fbstep<T><<<grid, kThreads, tabb, st>>>(dv, yb, hv, r, d, hr, hd, nama, ringS, vs, sc, rw_arg, hw_arg);
         if ((s = full_solve()) != STO_OK) return s;
-        k_point<T><<<grid, kThreads, tabb, st>>>(dv, yb, hv, r, ringS, ringY, vs, nama ? 1 : 0, sc, part, rw_arg,
-                                                 hw_arg);
+        point(nama ? 1 : 0, rw, hw);
         if (bt == 1) {
             // eq. (original-backtracking) at w: for the quadratic fhat it reads
             // <r_w, h(T(w)) - h(w)> > (1 - beta) ||r_w||^2; on failure the step is rejected
