@@ -269,7 +269,7 @@ def run_ours(args):
 
 def run_gpad(st, lam, x0, stream, pg, dev, steps):
     """GPAD (accelerated dual projected gradient) on the same instance: its five-step warm start
-    of Section III-E followed by NAMA, timed as one step, and one cold GPAD run to the same
+    of Section III-F followed by NAMA, timed as one step, and one cold GPAD run to the same
     tolerance (the comparison method of Section IV)."""
     import torch
 

@@ -215,7 +215,7 @@ STO_API sto_status stotree_nama_solve(stotree_t h, const sto_opts *opts, const v
 STO_API sto_status stotree_minfbe_solve(stotree_t h, const sto_opts *opts, const void *x0, void *y, void *x,
                                 void *u, void *z, sto_info *info, sto_stream_t stream);
 
-/* GPAD, the accelerated dual projected gradient (Section III-E, where a few of its steps warm
+/* GPAD, the accelerated dual projected gradient (Section III-F, where a few of its steps warm
  * start Algorithms 1 and 2, and Section IV, where it is the comparison method), on the
  * preconditioned dual with the theta sequence of Patrinos and Bemporad (2014):
  * w_k = ybar_k + theta_k (1/theta_{k-1} - 1)(ybar_k - ybar_{k-1}), w_0 = ybar_0,
@@ -313,7 +313,7 @@ STO_API const char *stobatch_last_error(stobatch_t b);
  * Learned warm start: a per-node perceptron that predicts the scaled dual ybar^i = y^i/sqrt(pi^i)
  * (Section III-E) of every node of a tree from the node's data, trained with Adam on the duals
  * that the batched solver returns.  The paper's own warm start is a few accelerated dual
- * gradient steps (Section III-E); this predictor replaces them for families of problems that
+ * gradient steps (Section III-F); this predictor replaces them for families of problems that
  * share a tree and its dynamics.
  *
  * Network: d_in = 4 nx + 1 inputs [x0, t/N, c^i, c^anc(i), c^anc(anc(i))] (missing ancestors and

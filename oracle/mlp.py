@@ -5,7 +5,7 @@ TEST INFRASTRUCTURE ONLY: imported by the tests, by the smoke check and by the b
 CPU-baseline leg, never by the library.  It shares no code with the CUDA path.
 
 The paper warm-starts its solvers from a few iterations of an accelerated dual gradient method
-(Section III-E); the learned predictor is the batched workload's alternative to that.  What it
+(Section III-F); the learned predictor is the batched workload's alternative to that.  What it
 computes:
 
 * features of node i of one draw (x0, c): [x0 (nx), t/N (1), c^i, c^anc(i), c^anc(anc(i))],

@@ -28,7 +28,7 @@ the paper's definitions directly:
   failure lambda is halved, the L-BFGS memory emptied and the iteration repeated from ybar.  Eq. (simple-backtracking) [BelloCruz 2016, Linesearch 1] at ybar:
   lambda ||grad fhat(T(ybar)) - grad fhat(ybar)|| > eps'' ||T(ybar) - ybar|| halves lambda,
   empties the memory and is tested again.
-* Section III-E (warm start) and Section IV (comparison method): GPAD, the accelerated
+* Section III-F (warm start) and Section IV (comparison method): GPAD, the accelerated
   dual projected gradient, here in the theta form of Patrinos and Bemporad (2014):
   w = ybar + theta_k (1/theta_{k-1} - 1)(ybar - ybar_prev), ybar+ = T(w).
 

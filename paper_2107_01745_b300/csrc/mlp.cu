@@ -1,7 +1,7 @@
 // Learned warm start: a per-node perceptron that predicts the scaled dual ybar^i of every node
 // of a scenario tree (the variable the solvers iterate on, Section III-E), trained with Adam on
 // solved draws.  The paper warm-starts from a few accelerated dual gradient steps (Section
-// III-E); this predictor stands in for them when many problems share a tree and its dynamics.
+// III-F); this predictor stands in for them when many problems share a tree and its dynamics.
 //
 // Every product runs on the 5th-generation tensor cores: C[128 x BN] tiles of A B' with A and B
 // K-major BF16, staged by TMA (cp.async.bulk.tensor, 128-byte swizzle) into a shared-memory ring

@@ -9,7 +9,7 @@
 //   k_lb_dots / k_lb_dir   L-BFGS direction d = -B g, compact form               (Alg. 1 line 3, Alg. 2 line 5)
 //   k_ls      FBE at up to 19 step sizes tau = 2^-k in one pass                    (Alg. 1 line 4, Alg. 2 line 6)
 //   k_fbstep  ybar+ = T_lam(w), s = ybar+ - ybar                                   (Alg. 1 line 5, Alg. 2 lines 7-8)
-//   k_gpad    GPAD step ybar+ = T_lam(w), next extrapolated point                 (Section III-E, Section IV)
+//   k_gpad    GPAD step ybar+ = T_lam(w), next extrapolated point                 (Section III-F, Section IV)
 //
 // Readings of the text used here:
 //   * T_lam(y) = y + lam (Hx(y) - z_lam(y)), the sign used by Algorithm 2's update.
@@ -786,7 +786,7 @@ __global__ void __launch_bounds__(kThreads) k_fbstep(DualView<T> dv, T *yb, cons
     }
 }
 
-// GPAD, the accelerated dual projected gradient of the warm start (Section III-E) and of the
+// GPAD, the accelerated dual projected gradient of the warm start (Section III-F) and of the
 // comparison in Section IV, in the theta form of Patrinos and Bemporad (2014).  At the
 // extrapolated point w with h = S H x(w): z = proj(h + w/lam), r = z - h, the step
 // ybar+ = T_lam(w) = w - lam r, and the next extrapolated point

@@ -279,7 +279,7 @@ class StoTree:
     def solve(self, method, lam, x0=None, y0=None, tol=1e-4, mem=5, max_iter=1000, max_ls=30, eps_curv=None,
               outputs=True, allow_not_converged=False, backtrack=None, bt_param=None, max_halvings=60):
         """Algorithm 1 (method='minfbe'), 2 (method='nama') or GPAD (method='gpad', the
-        accelerated dual projected gradient of Sections III-E and IV).  Returns tensors and info.
+        accelerated dual projected gradient of Sections III-F and IV).  Returns tensors and info.
 
         backtrack (Algorithms 1 and 2): None (fixed lambda), 'original' (eq. original-backtracking,
         bt_param = beta, default 0) or 'simple' (eq. simple-backtracking, bt_param = eps'',

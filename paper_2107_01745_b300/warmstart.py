@@ -7,7 +7,7 @@ dynamics (host orchestration; every computation runs in the library's kernels).
 3. Use: predicted y0 for new draws; per draw the start is kept only if its forward-backward
    envelope is not above that of y0 = 0 (phi_lambda is what both algorithms decrease), else the
    draw starts cold.  The paper's own warm start is a few accelerated dual gradient steps
-   (Section III-E); this replaces them.
+   (Section III-F); this replaces them.
 """
 from __future__ import annotations
 

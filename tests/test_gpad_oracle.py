@@ -1,4 +1,4 @@
-"""Pins of the oracle's GPAD (accelerated dual projected gradient; Section III-E warm start,
+"""Pins of the oracle's GPAD (accelerated dual projected gradient; Section III-F warm start,
 Section IV comparison method) against things other than itself:
 
 * the theta sequence against hand-computed values and the identity that defines Nesterov's

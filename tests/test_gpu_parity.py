@@ -132,7 +132,7 @@ def test_solver_fp32_matches_oracle(cuda_device, p, method):
 @pytest.mark.parametrize("p", BOXED, ids=lambda p: p.name)
 def test_gpad_fp64_follows_oracle_iterates(cuda_device, p):
     """FP64 GPAD on the GPU returns the oracle's extrapolated point after every number of
-    steps (the five-step warm start of Section III-E among them)."""
+    steps (the five-step warm start of Section III-F among them)."""
     o = O.LQOracle(p)
     lam, _ = O.power_lambda(o, np.random.default_rng(0).standard_normal(o.m))
     st = _st()(p, precision="fp64")
@@ -329,7 +329,7 @@ def test_paper_scale_backtracking(cuda_device, paper_scale):
 
 
 def test_paper_scale_gpad_warm_start(cuda_device, paper_scale):
-    """Five GPAD steps (the warm start of Section III-E) at full size against the oracle's five
+    """Five GPAD steps (the warm start of Section III-F) at full size against the oracle's five
     steps, then NAMA from that point to ||z - Hx||_inf <= 1e-4."""
     p, o = paper_scale
     lam, _ = O.power_lambda(o, np.random.default_rng(7).standard_normal(o.m), iters=20)
