@@ -9,7 +9,9 @@ The heavy lifting (offline factor, Algorithms 3 and 4) is in
 the paper's definitions directly:
 
 * Section II-D: prox, forward-backward map T_lambda, residual R_lambda = z - Hx,
-  x(y) = grad f*(-H'y), z_lambda(y) = prox_{g/lambda}(y/lambda + Hx(y)).
+  x(y) = grad f*(-H'y), z_lambda(y) = prox_{g/lambda}(y/lambda + Hx(y)).  g is separable
+  (Section II-B): per component the indicator of a box, rho times the distance to it (a soft
+  constraint; l1 when the box is a point) or rho times the Huber function of that distance.
   The sign of T_lambda follows the algorithms' own update, T(y) = y + lambda(Hx - z).
 * Section III-A: the forward-backward envelope (FBE) phi_lambda, evaluated both
   by its definition and by the equivalent augmented-Lagrangian expression
@@ -149,6 +151,18 @@ class LQOracle:
                 lo[o + nx:o + nx + nu], hi[o + nx:o + nx + nu] = p.ulo, p.uhi
         lo[:nx], hi[:nx] = -np.inf, np.inf
         self.lo, self.hi = lo, hi
+        # the nonsmooth term per element (Section II-B): kind, rho, delta of its component
+        kind, rho, dl = np.zeros(self.m, dtype=np.int32), np.zeros(self.m), np.ones(self.m)
+        if p.pen_kind is not None:
+            comp = np.empty(self.m, dtype=np.int64)
+            for i in range(self.Nn):
+                o = self.off[i]
+                comp[o:o + nx] = np.arange(nx)
+                if i < self.Np:
+                    comp[o + nx:o + nx + nu] = nx + np.arange(nu)
+            kind, rho, dl = p.pen_kind[comp].astype(np.int32), p.pen_rho[comp].astype(float), p.pen_delta[comp].astype(float)
+            kind[:nx] = 0  # the root state is the parameter: no term
+        self.kind, self.rho, self.delta = kind, rho, dl
 
     @property
     def Rbar(self) -> np.ndarray:
@@ -215,39 +229,103 @@ def proj_box(o: LQOracle, v: np.ndarray) -> np.ndarray:
     return np.minimum(np.maximum(v, o.sq * o.lo), o.sq * o.hi)
 
 
-def g_conj(o: LQOracle, v: np.ndarray) -> float:
-    """Support function of S Y: sum_k max(lo_k v_k, hi_k v_k); +inf off its domain."""
-    lo, hi = o.sq * o.lo, o.sq * o.hi
-    out = 0.0
-    pos, neg = v > 0, v < 0
-    if np.any(np.isinf(hi[pos])) or np.any(np.isinf(lo[neg])):
+def _huber(d: np.ndarray, delta: np.ndarray) -> np.ndarray:
+    return np.where(d <= delta, 0.5 * d * d, delta * (d - 0.5 * delta))
+
+
+def g_val(o: LQOracle, zb: np.ndarray) -> float:
+    """The scaled nonsmooth term g~(zbar) = sum_k g_k(zbar_k / sqrt(pi_k)) (Section II-B):
+    indicator of the box (kind 0), rho dist (kind 1), rho Huber_delta(dist) (kind 2), where
+    dist is the distance of the element to [lo, hi]."""
+    s = o.sq
+    # distance measured on the scaled box (s lo, s hi are the exact bounds prox_g returns)
+    d = (np.maximum(s * o.lo - zb, 0.0) + np.maximum(zb - s * o.hi, 0.0)) / s
+    k0, k1, k2 = o.kind == 0, o.kind == 1, o.kind == 2
+    if np.any(d[k0] > 0.0):
         return np.inf
-    out += float(np.sum(hi[pos] * v[pos])) + float(np.sum(lo[neg] * v[neg]))
+    return float(np.sum(o.rho[k1] * d[k1])) + float(np.sum(o.rho[k2] * _huber(d[k2], o.delta[k2])))
+
+
+def prox_g(o: LQOracle, v: np.ndarray, lam: float) -> np.ndarray:
+    """z_lambda: argmin_zbar g~(zbar) + lam/2 ||zbar - v||^2, element by element.  With
+    zbar = s z (s = sqrt(pi)) this is z = prox_{a g_k}(v / s), a = 1 / (lam s^2):
+    kind 0: clamp to [lo, hi]; kind 1: move toward the box by at most a rho, not past it;
+    kind 2: outside the box by e, e / (1 + a rho) if e <= delta (1 + a rho), else e - a rho delta
+    (the proximal map of the Huber function applied to the excess)."""
+    s = o.sq
+    t = v / s
+    a = 1.0 / (lam * s * s)
+    z = np.minimum(np.maximum(t, o.lo), o.hi)
+    e_up = np.where(t > o.hi, t - o.hi, 0.0)
+    e_dn = np.where(t < o.lo, o.lo - t, 0.0)
+    k1, k2 = o.kind == 1, o.kind == 2
+    ar = a * o.rho
+    z1 = np.where(t > o.hi, o.hi + np.maximum(e_up - ar, 0.0), np.where(t < o.lo, o.lo - np.maximum(e_dn - ar, 0.0), t))
+    shrink = lambda e: np.where(e <= o.delta * (1.0 + ar), e / (1.0 + ar), e - ar * o.delta)
+    z2 = np.where(t > o.hi, o.hi + shrink(e_up), np.where(t < o.lo, o.lo - shrink(e_dn), t))
+    z = np.where(k1, z1, np.where(k2, z2, z))
+    return s * z
+
+
+def _sigma(lo: np.ndarray, hi: np.ndarray, y: np.ndarray) -> np.ndarray:
+    """Support function of [lo, hi] per element (inf where unbounded in y's direction)."""
+    out = np.zeros_like(y)
+    pos, neg = y > 0, y < 0
+    out[pos] = hi[pos] * y[pos]
+    out[neg] = lo[neg] * y[neg]
     return out
+
+
+def g_conj(o: LQOracle, v: np.ndarray) -> float:
+    """Conjugate of the scaled term, g~*(v) = sum_k g_k*(s_k v_k), with
+    kind 0: sigma_[lo,hi]; kind 1: sigma on |y| <= rho; kind 2: sigma + y^2 / (2 rho) on
+    |y| <= rho delta (+inf off the domains)."""
+    y = o.sq * v
+    sig = _sigma(o.lo, o.hi, y)
+    k1, k2 = o.kind == 1, o.kind == 2
+    # (domains closed up to rounding: the prox puts multipliers exactly on their boundary)
+    if np.any(np.abs(y[k1]) > o.rho[k1] * (1 + 1e-12)) or np.any(np.abs(y[k2]) > o.rho[k2] * o.delta[k2] * (1 + 1e-12)):
+        return np.inf
+    tot = sig.copy()
+    tot[k2] += y[k2] ** 2 / (2.0 * o.rho[k2])
+    if np.any(np.isinf(tot)):
+        return np.inf
+    return float(np.sum(tot))
 
 
 def prox_g_conj(o: LQOracle, v: np.ndarray, lam: float) -> np.ndarray:
-    """prox_{lam g*}(v) = v - lam proj(v / lam) (Moreau decomposition)."""
-    return v - lam * proj_box(o, v / lam)
+    """prox_{lam g*}(v) = v - lam z(v / lam) (Moreau decomposition)."""
+    return v - lam * prox_g(o, v / lam, lam)
 
 
 def prox_g_conj_closed(o: LQOracle, v: np.ndarray, lam: float) -> np.ndarray:
-    """Two-sided shrink: v - lam hi if v > lam hi, v - lam lo if v < lam lo, else 0."""
-    lo, hi = o.sq * o.lo, o.sq * o.hi
-    out = np.zeros_like(v)
-    up, dn = v > lam * hi, v < lam * lo
-    out[up] = v[up] - lam * hi[up]
-    out[dn] = v[dn] - lam * lo[dn]
-    return out
+    """prox_{lam g~*}(v) from the conjugates' own closed forms: with y = s v and c = lam s^2,
+    eta = argmin g_k*(eta) + (eta - y)^2 / (2 c), returned as eta / s.  Box: two-sided shrink
+    (y - c hi if y > c hi, y - c lo if y < c lo, else 0); kind 1: that shrink clamped to
+    [-rho, rho]; kind 2: (y - c hi) / (1 + c / rho) or (y - c lo) / (1 + c / rho) on the same
+    sides, clamped to [-rho delta, rho delta]."""
+    s = o.sq
+    y = s * v
+    c = lam * s * s
+    eta = np.zeros_like(v)
+    up, dn = y > c * o.hi, y < c * o.lo
+    eta[up] = y[up] - c[up] * o.hi[up]
+    eta[dn] = y[dn] - c[dn] * o.lo[dn]
+    k1, k2 = o.kind == 1, o.kind == 2
+    eta[k1] = np.clip(eta[k1], -o.rho[k1], o.rho[k1])
+    e2 = eta[k2] / (1.0 + c[k2] / o.rho[k2])
+    eta[k2] = np.clip(e2, -o.rho[k2] * o.delta[k2], o.rho[k2] * o.delta[k2])
+    return eta / s
 
 
 def fb_point(o: LQOracle, yb: np.ndarray, lam: float) -> dict:
-    """Everything the algorithms need at one dual point (full solve)."""
+    """Everything the algorithms need at one dual point (full solve).  The FBE is minus the
+    augmented Lagrangian f(x) + g(z) + <y, Hx - z> + lam/2 ||Hx - z||^2 at z = z_lambda(y)."""
     h, x, u = hbar(o, yb)
-    z = proj_box(o, h + yb / lam)
+    z = prox_g(o, h + yb / lam, lam)
     r = z - h
     f = o.cost(x, u)
-    phi = -(f + float(np.dot(yb, h - z)) + 0.5 * lam * float(np.dot(h - z, h - z)))
+    phi = -(f + g_val(o, z) + float(np.dot(yb, h - z)) + 0.5 * lam * float(np.dot(h - z, h - z)))
     return dict(y=yb, h=h, x=x, u=u, z=z, r=r, f=f, phi=phi, T=yb - lam * r,
                 res_inf=float(np.max(np.abs(r / o.sq))) if r.size else 0.0)
 

@@ -150,6 +150,12 @@ class Problem:
     x0: np.ndarray      # [nx]
     name: str = "problem"
     meta: dict = field(default_factory=dict)
+    # Nonsmooth term g per component of [x; u] (Section II-B): kind 0 = indicator of the box
+    # [lo, hi] (hard constraint); 1 = rho * distance to the box (soft constraint; lo = hi = c
+    # gives rho |z - c|); 2 = rho * Huber_delta(distance to the box).  None = all kind 0.
+    pen_kind: np.ndarray | None = None   # [nx + nu] int
+    pen_rho: np.ndarray | None = None    # [nx + nu]
+    pen_delta: np.ndarray | None = None  # [nx + nu]
 
     @property
     def num_dual(self) -> int:
@@ -246,6 +252,15 @@ def load_box(name: str):
     xmax = np.full(LARGEST_SHAPE["nx"] if b["xmax"] is None else len(b["xmax"]), np.inf) if b["xmax"] is None \
         else np.asarray(b["xmax"], dtype=np.float64)
     return xmax, umax
+
+
+def with_penalty(p: Problem, kind, rho, delta=None) -> Problem:
+    """Set the per-component kinds of g (see Problem); rho, delta broadcast to nx + nu."""
+    n = p.nx + p.nu
+    p.pen_kind = np.broadcast_to(np.asarray(kind, dtype=np.int32), (n,)).copy()
+    p.pen_rho = np.broadcast_to(np.asarray(rho, dtype=np.float64), (n,)).copy()
+    p.pen_delta = np.broadcast_to(np.asarray(1.0 if delta is None else delta, dtype=np.float64), (n,)).copy()
+    return p
 
 
 def with_box(p: Problem, xmax: np.ndarray, umax: np.ndarray) -> Problem:
