@@ -158,6 +158,20 @@ STO_API sto_status stotree_set_costs(stotree_t h, const double *Q, const double 
 STO_API sto_status stotree_set_box(stotree_t h, const double *xlo, const double *xhi, const double *ulo,
                            const double *uhi, sto_stream_t stream);
 
+/* The nonsmooth term g of Section II-B beyond the indicator of the box, per component of
+ * [x; u] (host arrays of nx + nu; the leaf terms use the x part; the root state has none):
+ *   kind[k] = 0: indicator of [lo_k, hi_k] (hard constraint, the default);
+ *   kind[k] = 1: rho[k] * dist(z_k, [lo_k, hi_k]) (soft constraint, "distance-to-set";
+ *                lo_k = hi_k = c gives rho |z_k - c|, the l1 norm);
+ *   kind[k] = 2: rho[k] * Huber_delta[k](dist(z_k, [lo_k, hi_k])), Huber(d) = d^2/2 for
+ *                d <= delta, delta (d - delta/2) beyond (lo_k = hi_k = c: the Huber loss).
+ * Their proximal maps are element-wise (Section III-D), so Algorithms 1 and 2 and GPAD use
+ * them unchanged; the bounds come from stotree_set_box (+-INFINITY allowed).  kind = NULL
+ * restores all-hard.  Needs rho > 0 for kinds 1 and 2, delta > 0 for kind 2 (finite), else
+ * STO_ERR_INVALID_ARG.  Does not invalidate the factor.  Synchronises when the box is set. */
+STO_API sto_status stotree_set_penalty(stotree_t h, const int32_t *kind, const double *rho, const double *delta,
+                               sto_stream_t stream);
+
 /* Offline factor (Section III-D, Riccati-type recursion), FP64 on the device, then the
  * solve arrays in the handle's precision.  Enqueued on the stream; the positive
  * definiteness check of Rbar is reported by the next synchronising call, or here when
@@ -234,9 +248,12 @@ STO_API sto_status stotree_gpad_solve(stotree_t h, const sto_opts *opts, const v
  * problem data (conditions listed under Algorithm 1):
  *   out[0] = max |x^j - A^j x^i - B^j u^i - c^j|              (dynamics, x^0 = x0)
  *   out[1] = max |stationarity of f(x) + <y, Hx> in (x, u)|   (-H'y in the subdifferential of f)
- *   out[2] = max over box violation of Hx                      (primal feasibility)
- *   out[3] = max |y_k| over components strictly inside the box by more than tol_active
- *   out[4] = max of -y_k at upper bounds / +y_k at lower bounds (sign of the multipliers)
+ *   out[2] = max over box violation of Hx                      (primal feasibility, hard terms)
+ *   out[3] = max |y_k| over components strictly inside the box by more than tol_active;
+ *            for soft terms (stotree_set_penalty) the distance of y_k to the gradient of
+ *            g_k at Hx where g_k is differentiable there
+ *   out[4] = max of -y_k at upper bounds / +y_k at lower bounds (sign of the multipliers);
+ *            for soft terms the distance of y_k to the subdifferential at a kink
  * Synchronises.  out is host double[5]. */
 STO_API sto_status stotree_kkt_check(stotree_t h, const void *x0, const void *x, const void *u, const void *y,
                              double tol_active, double *out, sto_stream_t stream);

@@ -95,7 +95,7 @@ static void compute_layout(stotree_t h) {
     L.sqp = add(Nn * es);
     L.G64 = add(Nn * nx * h->ld64 * 8);
     L.cost64 = add((4 * nx + 2 * nu) * 8);
-    L.box64 = add(2 * (nx + nu) * 8);
+    L.box64 = add(5 * (nx + nu) * 8);
     L.P[0] = add(Wd * nx * nx * 8);
     L.P[1] = add(Wd * nx * nx * 8);
     L.PG = add(Wd * nx * h->ld64 * 8);
@@ -113,7 +113,7 @@ static void compute_layout(stotree_t h) {
     L.gx = add(Np * nx * es);
     L.c = add(Nn * nx * es);
     L.cost = add(2 * (2 * nx + nu) * es);
-    L.box = add(2 * (nx + nu) * es);
+    L.box = add(5 * (nx + nu) * es);
     L.s = add(kMaxRhs * Nn * nx * es);
     L.ubar = add(kMaxRhs * Np * nu * es);
     L.xs = add(kMaxRhs * Nn * nx * es);
@@ -406,12 +406,34 @@ sto_status stotree_set_costs(stotree_t h, const double *Q, const double *R, cons
     return STO_OK;
 }
 
+// Upload [lo | hi | rho | delta | kind] (each nx + nu, x part then u part) in FP64 and in the
+// handle's precision.
+static sto_status upload_g(stotree_t h, cudaStream_t st) {
+    const int n = h->nx + h->nu;
+    if (h->pen.size() != (size_t)3 * n) {  // default: every component a hard box
+        h->pen.assign((size_t)3 * n, 0.0);
+        for (int k = 0; k < n; ++k) h->pen[n + k] = 1.0;
+    }
+    std::vector<double> b(5 * (size_t)n);
+    std::copy(h->boxv.begin(), h->boxv.end(), b.begin());
+    std::copy(h->pen.begin(), h->pen.end(), b.begin() + 2 * n);
+    STO_CUDA(h, cudaMemcpyAsync(h->ws + h->L.box64, b.data(), b.size() * 8, cudaMemcpyHostToDevice, st));
+    if (h->prec == STO_FP64) {
+        STO_CUDA(h, cudaMemcpyAsync(h->ws + h->L.box, b.data(), b.size() * 8, cudaMemcpyHostToDevice, st));
+    } else {
+        std::vector<float> bf(b.begin(), b.end());
+        STO_CUDA(h, cudaMemcpyAsync(h->ws + h->L.box, bf.data(), bf.size() * 4, cudaMemcpyHostToDevice, st));
+    }
+    STO_CUDA(h, cudaStreamSynchronize(st));
+    return STO_OK;
+}
+
 sto_status stotree_set_box(stotree_t h, const double *xlo, const double *xhi, const double *ulo,
                            const double *uhi, sto_stream_t stream) {
     if (!h || !xlo || !xhi || !ulo || !uhi) return STO_ERR_INVALID_ARG;
     if (!h->ws) return STO_ERR_NOT_READY;
     const int nx = h->nx, nu = h->nu;
-    // box64 = [lo: x | u][hi: x | u]
+    // [lo: x | u][hi: x | u]
     std::vector<double> b(2 * (nx + nu));
     for (int k = 0; k < nx; ++k) {
         if (!(xlo[k] <= xhi[k])) return STO_ERR_INVALID_ARG;
@@ -423,17 +445,34 @@ sto_status stotree_set_box(stotree_t h, const double *xlo, const double *xhi, co
         b[nx + k] = ulo[k];
         b[2 * nx + nu + k] = uhi[k];
     }
-    cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
-    STO_CUDA(h, cudaMemcpyAsync(h->ws + h->L.box64, b.data(), b.size() * 8, cudaMemcpyHostToDevice, st));
-    if (h->prec == STO_FP64) {
-        STO_CUDA(h, cudaMemcpyAsync(h->ws + h->L.box, b.data(), b.size() * 8, cudaMemcpyHostToDevice, st));
-    } else {
-        std::vector<float> bf(b.begin(), b.end());
-        STO_CUDA(h, cudaMemcpyAsync(h->ws + h->L.box, bf.data(), bf.size() * 4, cudaMemcpyHostToDevice, st));
-    }
-    STO_CUDA(h, cudaStreamSynchronize(st));
+    h->boxv = b;
+    const sto_status s = upload_g(h, reinterpret_cast<cudaStream_t>(stream));
+    if (s != STO_OK) return s;
     h->have_box = true;
     return STO_OK;
+}
+
+sto_status stotree_set_penalty(stotree_t h, const int32_t *kind, const double *rho, const double *delta,
+                               sto_stream_t stream) {
+    if (!h) return STO_ERR_INVALID_ARG;
+    const int n = h->nx + h->nu;
+    std::vector<double> pen(3 * (size_t)n, 0.0);
+    for (int k = 0; k < n; ++k) {
+        const int kd = kind ? kind[k] : 0;
+        const double r = rho ? rho[k] : 0.0, d = delta ? delta[k] : 1.0;
+        if (kd < 0 || kd > 2) return STO_ERR_INVALID_ARG;
+        if (kd >= 1 && !(r > 0.0 && r < INFINITY)) return STO_ERR_INVALID_ARG;
+        if (kd == 2 && !(d > 0.0 && d < INFINITY)) return STO_ERR_INVALID_ARG;
+        pen[k] = kd >= 1 ? r : 0.0;
+        pen[n + k] = kd == 2 ? d : 1.0;
+        pen[2 * n + k] = kd;
+    }
+    h->pen = pen;
+    h->general = false;
+    for (int k = 0; k < n; ++k) h->general = h->general || pen[2 * n + k] != 0.0;
+    if (!h->have_box) return STO_OK;  // uploaded with the box
+    if (!h->ws) return STO_ERR_NOT_READY;
+    return upload_g(h, reinterpret_cast<cudaStream_t>(stream));
 }
 
 sto_status stotree_factor(stotree_t h, int32_t sync, sto_stream_t stream) {

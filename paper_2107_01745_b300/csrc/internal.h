@@ -57,14 +57,14 @@ struct Layout {
     // FP64 problem data
     size_t G64;                  // double [Nn][nx][ld64] = [A | B | c]
     size_t cost64;               // double [3nx + 3nu... ] Q R PN q r pN
-    size_t box64;                // double [2(nx+nu)]
+    size_t box64;                // double [5(nx+nu)]: lo, hi, rho, delta, kind
     // factor scratch (FP64)
     size_t P[2], PG, W, Rb, Zb, M, K64;
     size_t fstatus;              // int
     // solve arrays (real)
     size_t G, RK, gu, gx, c;     // RK = [-Rbar^-1 | K] per nonleaf node (nu rows of ldrk)
     size_t Gt, Kt;               // forward pass: [A | B]' per node (nx+nu rows of ldk), K' (nx rows of ldr)
-    size_t cost, box;            // real copies: W (Q|R|PN), ell (q|r|pN), lo/hi (x|u)
+    size_t cost, box;            // real copies: W (Q|R|PN), ell (q|r|pN), lo/hi/rho/delta/kind (x|u)
     // solve scratch (real)
     size_t s, ubar, xs, us;
     // solver
@@ -103,6 +103,10 @@ struct stotree_s {
     size_t ws_bytes = 0;
     std::vector<uint8_t> have_dyn;   // per node
     bool have_cost = false, have_box = false, factored = false;
+    // host copies of the nonsmooth term g (Section II-B): box [lo | hi] and per component
+    // [rho | delta | kind] (kind 0 = indicator of the box, 1 = rho dist, 2 = rho Huber(dist))
+    std::vector<double> boxv, pen;
+    bool general = false;   // some component's kind is not 0
     std::string err;
     // timing
     bool timing = false;

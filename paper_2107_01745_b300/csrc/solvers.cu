@@ -40,10 +40,13 @@ template <class T>
 struct DualView {
     int m, Np, nx, nu, nxu, leaf_base;
     float inv_nxu, inv_nx;
-    const T *sqp, *box, *Wc;  // box = [lo x|u][hi x|u], Wc = [Q|R|PN][q|r|pN]
+    const T *sqp, *box, *Wc;  // box = [lo x|u][hi x|u][rho][delta][kind], Wc = [Q|R|PN][q|r|pN]
 
+    // per element: sqrt(pi) of its node, scaled bounds sqrt(pi) lo, sqrt(pi) hi, cost weights,
+    // and the kind of its nonsmooth term g with rho, delta (Section II-B)
     struct Meta {
-        T sq, lo, hi, w, l;
+        T sq, lo, hi, w, l, rho, delta;
+        int kind;
     };
 
     // Scalar path (caller-facing conversions): per-entry constants read from global memory.
@@ -67,10 +70,14 @@ struct DualView {
         if (node == 0 && kind == 0) {
             M.lo = -INFINITY;
             M.hi = INFINITY;
+            M.kind = 0;
         } else {
             M.lo = M.sq * box[bi];
             M.hi = M.sq * box[nxu + bi];
+            M.kind = (int)box[4 * nxu + bi];
         }
+        M.rho = box[2 * nxu + bi];
+        M.delta = box[3 * nxu + bi];
         M.w = Wc[wi];
         M.l = M.sq * Wc[2 * nx + nu + wi];
         return M;
@@ -124,12 +131,12 @@ __device__ __forceinline__ void pos_next(const DualView<T> &dv, Pos &p) {
     }
 }
 
-// Per-component constants of the dual layout in shared memory (dynamic, 6 (nx + nu) reals):
+// Per-component constants of the dual layout in shared memory (dynamic, 9 (nx + nu) reals):
 // nonleaf [x; u] lo, hi, quadratic and linear cost weights; leaf quadratic and linear weights
-// (the leaf box is the x part of the nonleaf box).
+// (the leaf box is the x part of the nonleaf box); rho, delta and kind of the term g.
 template <class T>
 struct CompTab {
-    T *lo, *hi, *w, *l, *wl, *ll;
+    T *lo, *hi, *w, *l, *wl, *ll, *rh, *dl, *kd;
     __device__ void load(const DualView<T> &dv, T *sm) {
         const int n = dv.nxu;
         lo = sm;
@@ -138,10 +145,16 @@ struct CompTab {
         l = sm + 3 * n;
         wl = sm + 4 * n;
         ll = sm + 5 * n;
+        rh = sm + 6 * n;
+        dl = sm + 7 * n;
+        kd = sm + 8 * n;
         nx_ = dv.nx;
         for (int c = threadIdx.x; c < n; c += blockDim.x) {
             lo[c] = dv.box[c];
             hi[c] = dv.box[n + c];
+            rh[c] = dv.box[2 * n + c];
+            dl[c] = dv.box[3 * n + c];
+            kd[c] = dv.box[4 * n + c];
             w[c] = dv.Wc[c];
             l[c] = dv.Wc[2 * dv.nx + dv.nu + c];
             if (c < dv.nx) {
@@ -151,7 +164,9 @@ struct CompTab {
         }
         __syncthreads();
     }
-    // the constants of the entry at p, scaled by sq = sqrt(pi) of its node
+    // the constants of the entry at p, scaled by sq = sqrt(pi) of its node (G = false: the
+    // term's kind is the box for every element and rho, delta are not read)
+    template <bool G = true>
     __device__ __forceinline__ typename DualView<T>::Meta meta(const Pos &p, T sq) const {
         typename DualView<T>::Meta M;
         M.sq = sq;
@@ -159,10 +174,14 @@ struct CompTab {
         if (!p.leaf && p.node == 0 && c < nx_) {  // the root state is the parameter: unboxed
             M.lo = -INFINITY;
             M.hi = INFINITY;
+            M.kind = 0;
         } else {
             M.lo = sq * lo[c];
             M.hi = sq * hi[c];
+            M.kind = G ? (int)kd[c] : 0;
         }
+        M.rho = G ? rh[c] : T(0);
+        M.delta = G ? dl[c] : T(1);
         M.w = p.leaf ? wl[c] : w[c];
         M.l = sq * (p.leaf ? ll[c] : l[c]);
         return M;
@@ -171,7 +190,7 @@ struct CompTab {
 };
 template <class T>
 size_t comp_tab_bytes(const DualView<T> &dv) {
-    return (size_t)6 * dv.nxu * sizeof(T);
+    return (size_t)9 * dv.nxu * sizeof(T);
 }
 
 template <class T>
@@ -228,12 +247,54 @@ __device__ __forceinline__ T clampv(T v, T lo, T hi) {
     return v < lo ? lo : (v > hi ? hi : v);
 }
 
-// Per-entry term of -FBE: W h^2 + l h + w (h - z) + lam/2 (h - z)^2, z = proj(h + w/lam).
-template <class T>
+// z_lambda of one element (Section II-D): argmin_z g~(z) + lam/2 (z - v)^2 for the element's
+// term (Section II-B) in the scaled dual, g~(z) = g(z / s), s = sqrt(pi): kind 0 clamps to the
+// scaled box; outside it by e, kind 1 moves back by at most rho / (lam s) without crossing the
+// bound, kind 2 maps e to e / (1 + q) when e <= s delta (1 + q), q = rho / (lam s^2), and to
+// e - rho delta / (lam s) beyond (the proximal map of the Huber function).
+// G = false: every element's term is the indicator of its box (the projection only).
+template <class T, bool G>
+__device__ __forceinline__ T prox_el(T v, T lam, const typename DualView<T>::Meta &M) {
+    if (!G || M.kind == 0) return clampv(v, M.lo, M.hi);
+    T base, e, sg;
+    if (v > M.hi) {
+        base = M.hi;
+        e = v - M.hi;
+        sg = T(1);
+    } else if (v < M.lo) {
+        base = M.lo;
+        e = M.lo - v;
+        sg = T(-1);
+    } else {
+        return v;
+    }
+    const T sh = M.rho / (lam * M.sq);
+    T ez;
+    if (M.kind == 1) {
+        ez = fmax(e - sh, T(0));
+    } else {
+        const T q = sh / M.sq;
+        ez = e <= M.sq * M.delta * (T(1) + q) ? e / (T(1) + q) : e - sh * M.delta;
+    }
+    return base + sg * ez;
+}
+
+// g~(z) of one element: 0 (kind 0, z in the box), rho d (kind 1) or rho Huber_delta(d)
+// (kind 2), d = unscaled distance of z / s to the box.
+template <class T, bool G>
+__device__ __forceinline__ T g_el(T z, const typename DualView<T>::Meta &M) {
+    if (!G || M.kind == 0) return T(0);
+    const T d = (fmax(M.lo - z, T(0)) + fmax(z - M.hi, T(0))) / M.sq;
+    if (M.kind == 1) return M.rho * d;
+    return M.rho * (d <= M.delta ? T(0.5) * d * d : M.delta * (d - T(0.5) * M.delta));
+}
+
+// Per-entry term of -FBE: W h^2 + l h + g~(z) + w (h - z) + lam/2 (h - z)^2, z = z_lambda.
+template <class T, bool G>
 __device__ __forceinline__ T fbe_term(T h, T w, T lam, T ilam, const typename DualView<T>::Meta &M) {
-    const T z = clampv(h + w * ilam, M.lo, M.hi);
+    const T z = prox_el<T, G>(h + w * ilam, lam, M);
     const T dz = h - z;
-    return h * (M.w * h + M.l) + dz * (w + T(0.5) * lam * dz);
+    return h * (M.w * h + M.l) + g_el<T, G>(z, M) + dz * (w + T(0.5) * lam * dz);
 }
 
 __device__ __forceinline__ double warp_sum_d(double v) {
@@ -323,7 +384,7 @@ __device__ bool reduce_last(T *sums, T *maxs, double *partials, unsigned *counte
 // BT = 1 (original backtracking test): rw, hw are r and h at the point w the step was taken
 // from; reduces <rw, h - hw> and ||rw||^2.  BT = 2 (simple backtracking test): ||r||^2.
 // ---------------------------------------------------------------------------------------
-template <class T, int BT>
+template <class T, int BT, bool G>
 __global__ void __launch_bounds__(kThreads) k_point(DualView<T> dv, const T *__restrict__ yb, const T *__restrict__ h,
                                                     T *r, T *ringS, T *ringY, long long vstride, int pair,
                                                     SolverScalars *sc, double *partials, const T *__restrict__ rw,
@@ -362,10 +423,10 @@ __global__ void __launch_bounds__(kThreads) k_point(DualView<T> dv, const T *__r
                     sq = dv.sqp[cur];
                     isq = T(1) / sq;
                 }
-                const auto M = tab.meta(ps, sq);
-                const T z = clampv(he[k] + ye[k] * ilam, M.lo, M.hi);
+                const auto M = tab.template meta<G>(ps, sq);
+                const T z = prox_el<T, G>(he[k] + ye[k] * ilam, lam, M);
                 re[k] = z - he[k];
-                fsum += fbe_term<T>(he[k], ye[k], lam, ilam, M);
+                fsum += fbe_term<T, G>(he[k], ye[k], lam, ilam, M);
                 const T ra = fabs(re[k]) * isq;
                 if (!(ra <= T(3.0e38))) nan = 1;
                 rmax = fmax(rmax, ra);
@@ -636,7 +697,7 @@ void lb_direction(int mem, int grid, cudaStream_t st, int m, const T *g, const T
 // NAMA (nama = 1): w = ybar - lam r + tau (d + lam r),  h(w) = h - lam hr + tau (hd + lam hr).
 // MINFBE:          w = ybar + tau d,                     h(w) = h + tau hd.
 // Accept the largest tau with FBE(w) <= FBE(ybar); after the last group tau = 0.
-template <class T, int J>
+template <class T, int J, bool G>
 __global__ void __launch_bounds__(kThreads) k_ls(DualView<T> dv, const T *__restrict__ yb, const T *__restrict__ h,
                                                  const T *__restrict__ r, const T *__restrict__ dvec,
                                                  const T *__restrict__ hr, const T *__restrict__ hd, int nama, int e0,
@@ -674,7 +735,7 @@ __global__ void __launch_bounds__(kThreads) k_ls(DualView<T> dv, const T *__rest
                     cur = ps.node;
                     sq = dv.sqp[cur];
                 }
-                const auto M = tab.meta(ps, sq);
+                const auto M = tab.template meta<G>(ps, sq);
                 T wa, wb, ha, hb;
                 if (nama) {
                     wa = y0[k] - lam * re[k];
@@ -687,10 +748,10 @@ __global__ void __launch_bounds__(kThreads) k_ls(DualView<T> dv, const T *__rest
                     ha = h0[k];
                     hb = hdd[k];
                 }
-                const T c0 = fbe_term<T>(h0[k], y0[k], lam, ilam, M);
+                const T c0 = fbe_term<T, G>(h0[k], y0[k], lam, ilam, M);
 #pragma unroll
                 for (int j = 0; j < J; ++j) {
-                    const T cj = fbe_term<T>(ha + tau[j] * hb, wa + tau[j] * wb, lam, ilam, M);
+                    const T cj = fbe_term<T, G>(ha + tau[j] * hb, wa + tau[j] * wb, lam, ilam, M);
                     acc[j] += cj - c0;
                 }
                 pos_next(dv, ps);
@@ -721,7 +782,7 @@ __global__ void __launch_bounds__(kThreads) k_ls(DualView<T> dv, const T *__rest
 
 // ybar+ = T_lam(w(tau)) = w + lam (h(w) - z(w)); s = ybar+ - ybar -> S[p]; ybar <- ybar+.
 // rw_out, hw_out (non-null with the original backtracking test): r(w) = z(w) - h(w) and h(w).
-template <class T>
+template <class T, bool G>
 __global__ void __launch_bounds__(kThreads) k_fbstep(DualView<T> dv, T *yb, const T *__restrict__ h,
                                                      const T *__restrict__ r, const T *__restrict__ dvec,
                                                      const T *__restrict__ hr, const T *__restrict__ hd, int nama,
@@ -755,7 +816,7 @@ __global__ void __launch_bounds__(kThreads) k_fbstep(DualView<T> dv, T *yb, cons
                     cur = ps.node;
                     sq = dv.sqp[cur];
                 }
-                const auto M = tab.meta(ps, sq);
+                const auto M = tab.template meta<G>(ps, sq);
                 T w, hw;
                 if (nama) {
                     w = y0[k] - lam * re[k] + tau * (dd[k] + lam * re[k]);
@@ -764,7 +825,7 @@ __global__ void __launch_bounds__(kThreads) k_fbstep(DualView<T> dv, T *yb, cons
                     w = y0[k] + tau * dd[k];
                     hw = h0[k] + tau * hdd[k];
                 }
-                const T z = clampv(hw + w * ilam, M.lo, M.hi);
+                const T z = prox_el<T, G>(hw + w * ilam, lam, M);
                 yn[k] = w + lam * (hw - z);
                 sn[k] = yn[k] - y0[k];
                 rwv[k] = z - hw;
@@ -792,7 +853,7 @@ __global__ void __launch_bounds__(kThreads) k_fbstep(DualView<T> dv, T *yb, cons
 // ybar+ = T_lam(w) = w - lam r, and the next extrapolated point
 // w+ = ybar+ + beta (ybar+ - ybar), beta = theta_{k+1} (1/theta_k - 1).  The FBE at w and
 // ||S^-1 r||_inf are reduced for the stopping test, which the host applies to w.
-template <class T>
+template <class T, bool G>
 __global__ void __launch_bounds__(kThreads) k_gpad(DualView<T> dv, const T *__restrict__ w, const T *__restrict__ h,
                                                    T *yb, T *wn, T beta, SolverScalars *sc, double *partials) {
     __shared__ double tot[3];
@@ -819,10 +880,10 @@ __global__ void __launch_bounds__(kThreads) k_gpad(DualView<T> dv, const T *__re
                     sq = dv.sqp[cur];
                     isq = T(1) / sq;
                 }
-                const auto M = tab.meta(ps, sq);
-                const T z = clampv(he[k] + we[k] * ilam, M.lo, M.hi);
+                const auto M = tab.template meta<G>(ps, sq);
+                const T z = prox_el<T, G>(he[k] + we[k] * ilam, lam, M);
                 const T r = z - he[k];
-                fsum += fbe_term<T>(he[k], we[k], lam, ilam, M);
+                fsum += fbe_term<T, G>(he[k], we[k], lam, ilam, M);
                 const T ra = fabs(r) * isq;
                 if (!(ra <= T(3.0e38))) nan = 1;
                 rmax = fmax(rmax, ra);
@@ -887,7 +948,7 @@ __global__ void k_finish_out(DualView<T> dv, const T *yb, const T *h, const Solv
         const auto M = dv.meta(e);
         const T ye = yb[e], he = h[e];
         y[e] = M.sq * ye;
-        if (z) z[e] = clampv(he + ye * ilam, M.lo, M.hi) / M.sq;
+        if (z) z[e] = prox_el<T, true>(he + ye * ilam, lam, M) / M.sq;
         if (x) {
             int node, k;
             if (e < dv.leaf_base) {
@@ -1044,13 +1105,18 @@ sto_status solver_impl(stotree_t h, int method, const sto_opts *o, const void *x
     sto_status s = full_solve();
     if (s != STO_OK) return s;
     // k_point with the backtracking reductions the rule needs
+    const bool gen = h->general;  // some element's term is not the box indicator
     auto point = [&](int pair, const T *rwp, const T *hwp) {
-        if (bt == 1)
-            k_point<T, 1><<<grid, kThreads, tabb, st>>>(dv, yb, hv, r, ringS, ringY, vs, pair, sc, part, rwp, hwp);
-        else if (bt == 2)
-            k_point<T, 2><<<grid, kThreads, tabb, st>>>(dv, yb, hv, r, ringS, ringY, vs, pair, sc, part, rwp, hwp);
-        else
-            k_point<T, 0><<<grid, kThreads, tabb, st>>>(dv, yb, hv, r, ringS, ringY, vs, pair, sc, part, rwp, hwp);
+#define STO_POINT(BT, G) \
+    k_point<T, BT, G><<<grid, kThreads, tabb, st>>>(dv, yb, hv, r, ringS, ringY, vs, pair, sc, part, rwp, hwp)
+        if (bt == 1) {
+            if (gen) STO_POINT(1, true); else STO_POINT(1, false);
+        } else if (bt == 2) {
+            if (gen) STO_POINT(2, true); else STO_POINT(2, false);
+        } else {
+            if (gen) STO_POINT(0, true); else STO_POINT(0, false);
+        }
+#undef STO_POINT
     };
     point(0, hv, hv);  // (with BT = 1 the w terms of this call are not used)
     h->launches += 1;
@@ -1125,21 +1191,25 @@ sto_status solver_impl(stotree_t h, int method, const sto_opts *o, const void *x
         }
         for (int k = 0; k < ng; ++k) {
             const int last = k == ng - 1;
-            if (k == 0)
-                k_ls<T, 4><<<grid, kThreads, tabb, st>>>(dv, yb, hv, r, d, hr, hd, nama, gfirst[k], gcount[k], last, sc,
-                                                     part);
-            else if (k == 1)
-                k_ls<T, 8><<<grid, kThreads, tabb, st>>>(dv, yb, hv, r, d, hr, hd, nama, gfirst[k], gcount[k], last, sc,
-                                                     part);
-            else
-                k_ls<T, 19><<<grid, kThreads, tabb, st>>>(dv, yb, hv, r, d, hr, hd, nama, gfirst[k], gcount[k], last, sc,
-                                                      part);
+#define STO_LS(J, G) \
+    k_ls<T, J, G><<<grid, kThreads, tabb, st>>>(dv, yb, hv, r, d, hr, hd, nama, gfirst[k], gcount[k], last, sc, part)
+            if (k == 0) {
+                if (gen) STO_LS(4, true); else STO_LS(4, false);
+            } else if (k == 1) {
+                if (gen) STO_LS(8, true); else STO_LS(8, false);
+            } else {
+                if (gen) STO_LS(19, true); else STO_LS(19, false);
+            }
+#undef STO_LS
         }
         if (bt == 1) {
             STO_CUDA(h, cudaMemcpyAsync(ysave, yb, (size_t)m * sizeof(T), cudaMemcpyDeviceToDevice, st));
             STO_CUDA(h, cudaMemcpyAsync(hsave, hv, (size_t)m * sizeof(T), cudaMemcpyDeviceToDevice, st));
         }
-        k_fbstep<T><<<grid, kThreads, tabb, st>>>(dv, yb, hv, r, d, hr, hd, nama, ringS, vs, sc, rw_arg, hw_arg);
+        if (gen)
+            k_fbstep<T, true><<<grid, kThreads, tabb, st>>>(dv, yb, hv, r, d, hr, hd, nama, ringS, vs, sc, rw_arg, hw_arg);
+        else
+            k_fbstep<T, false><<<grid, kThreads, tabb, st>>>(dv, yb, hv, r, d, hr, hd, nama, ringS, vs, sc, rw_arg, hw_arg);
         if ((s = full_solve()) != STO_OK) return s;
         point(nama ? 1 : 0, rw, hw);
         if (bt == 1) {
@@ -1240,7 +1310,10 @@ sto_status gpad_impl(stotree_t h, const sto_opts *o, const void *x0v, void *yv, 
         if (s != STO_OK) return s;
         const double theta_next = 0.5 * (std::sqrt(theta * theta * theta * theta + 4.0 * theta * theta) - theta * theta);
         const T beta = (T)(theta_next * (1.0 / theta - 1.0));
-        k_gpad<T><<<grid, kThreads, tabb, st>>>(dv, w, hv, yb, wn, beta, sc, part);
+        if (h->general)
+            k_gpad<T, true><<<grid, kThreads, tabb, st>>>(dv, w, hv, yb, wn, beta, sc, part);
+        else
+            k_gpad<T, false><<<grid, kThreads, tabb, st>>>(dv, w, hv, yb, wn, beta, sc, part);
         h->launches += 1;
         STO_CUDA(h, cudaGetLastError());
         STO_CUDA(h, cudaMemcpyAsync(hs, sc, kScalHead, cudaMemcpyDeviceToHost, st));
@@ -1406,18 +1479,43 @@ __global__ void k_kkt_elem(int Nn, int nx, int nu, int Np, int ld64, const int *
             bi = k;
         }
         double lo = box64[bi], hi = box64[nxu + bi];
+        const double rho = box64[2 * nxu + bi], dl = box64[3 * nxu + bi];
+        int kind = (int)box64[4 * nxu + bi];
         if (node == 0 && k < nx) {
             lo = -INFINITY;
             hi = INFINITY;
+            kind = 0;
         }
         const double ye = (double)y[e];
-        atomic_max_nonneg(out + 2, fmax(0.0, fmax(lo - hv, hv - hi)));
-        const bool at_hi = hv >= hi - tol_act, at_lo = hv <= lo + tol_act;
-        if (!at_hi && !at_lo) atomic_max_nonneg(out + 3, fabs(ye));
-        double sgn = 0.0;
-        if (at_hi && !at_lo) sgn = fmax(0.0, -ye);
-        if (at_lo && !at_hi) sgn = fmax(0.0, ye);
-        atomic_max_nonneg(out + 4, sgn);
+        if (kind == 0) {
+            atomic_max_nonneg(out + 2, fmax(0.0, fmax(lo - hv, hv - hi)));
+            const bool at_hi = hv >= hi - tol_act, at_lo = hv <= lo + tol_act;
+            if (!at_hi && !at_lo) atomic_max_nonneg(out + 3, fabs(ye));
+            double sgn = 0.0;
+            if (at_hi && !at_lo) sgn = fmax(0.0, -ye);
+            if (at_lo && !at_hi) sgn = fmax(0.0, ye);
+            atomic_max_nonneg(out + 4, sgn);
+        } else {
+            // y must lie in the subdifferential [slo, shi] of g at Hx (bounds within tol_act
+            // count as kinks); a single-valued subdifferential goes to out[3], a kink to out[4]
+            double slo = 0.0, shi = 0.0;
+            if (kind == 1) {
+                if (hv > hi + tol_act) {
+                    slo = shi = rho;
+                } else if (hv < lo - tol_act) {
+                    slo = shi = -rho;
+                } else {
+                    if (hv <= lo + tol_act) slo = -rho;
+                    if (hv >= hi - tol_act) shi = rho;
+                }
+            } else {
+                const double d = fmax(lo - hv, 0.0) + fmax(hv - hi, 0.0);
+                const double gd = rho * fmin(d, dl);
+                slo = shi = hv > hi ? gd : (hv < lo ? -gd : 0.0);
+            }
+            const double res = fmax(0.0, fmax(slo - ye, ye - shi));
+            atomic_max_nonneg(out + (slo == shi ? 3 : 4), res);
+        }
     }
 }
 

@@ -68,6 +68,7 @@ def lib():
             "stotree_set_dynamics": [vp, i32, i32, vp, vp, vp, vp],
             "stotree_set_costs": [vp, vp, vp, vp, vp, vp, vp, vp],
             "stotree_set_box": [vp, vp, vp, vp, vp, vp],
+            "stotree_set_penalty": [vp, vp, vp, vp, vp],
             "stotree_factor": [vp, i32, vp],
             "stotree_solve_step": [vp, vp, vp, vp, i32, i32, i32, vp],
             "stotree_solve_step_noalloc": [vp, vp, vp, vp, i32, i32, vp],
@@ -139,7 +140,7 @@ def lib():
 
 def exported_symbols():
     return [n for n in ("stotree_create", "stotree_destroy", "stotree_sizes", "stotree_workspace_size",
-                        "stotree_bind_workspace", "stotree_set_dynamics", "stotree_set_costs", "stotree_set_box",
+                        "stotree_bind_workspace", "stotree_set_dynamics", "stotree_set_costs", "stotree_set_box", "stotree_set_penalty",
                         "stotree_factor", "stotree_solve_step", "stotree_solve_step_noalloc", "stotree_last_primal", "stotree_estimate_lambda",
                         "stotree_nama_solve", "stotree_minfbe_solve", "stotree_gpad_solve", "stotree_kkt_check", "stotree_set_timing",
                         "stotree_get_timing", "stotree_solve_bytes", "stotree_status_str", "stotree_last_error",
@@ -202,6 +203,8 @@ class StoTree:
                 self._check(L.stotree_set_dynamics(h, f, c, _np_ptr(A), _np_ptr(B), _np_ptr(cc), st), "set_dynamics")
             self.set_costs(problem.Q, problem.R, problem.PN, problem.q, problem.r, problem.pN)
             self.set_box(problem.xlo, problem.xhi, problem.ulo, problem.uhi)
+            if getattr(problem, "pen_kind", None) is not None:
+                self.set_penalty(problem.pen_kind, problem.pen_rho, problem.pen_delta)
 
     # -- plumbing -------------------------------------------------------------------------
     def _check(self, code, where, handle=True):
@@ -234,6 +237,15 @@ class StoTree:
         self._keep_cost = arr
         ptrs = [_np_ptr(a) if a is not None else None for a in arr]
         self._check(lib().stotree_set_costs(self.h, *ptrs, _stream()), "set_costs")
+
+    def set_penalty(self, kind, rho, delta):
+        """Per-component kind of g (0 box, 1 rho dist, 2 rho Huber(dist)), see stotree_set_penalty."""
+        n = self.nx + self.nu
+        k = np.ascontiguousarray(np.broadcast_to(np.asarray(kind, dtype=np.int32), (n,)))
+        r = np.ascontiguousarray(np.broadcast_to(np.asarray(rho, dtype=np.float64), (n,)))
+        d = np.ascontiguousarray(np.broadcast_to(np.asarray(delta, dtype=np.float64), (n,)))
+        self._check(lib().stotree_set_penalty(self.h, k.ctypes.data_as(ctypes.c_void_p), _np_ptr(r), _np_ptr(d),
+                                              _stream()), "set_penalty")
 
     def set_box(self, xlo, xhi, ulo, uhi):
         arr = [np.ascontiguousarray(v, dtype=np.float64) for v in (xlo, xhi, ulo, uhi)]

@@ -208,7 +208,7 @@ def test_backtracking_fp64_matches_oracle(cuda_device, p, method, rule, param):
     assert info["status"] == 0 and info["res_inf"] <= 1e-10
     assert info["halvings"] == ref["halvings"]
     assert info["lambda_"] == ref["lam"]
-    assert abs(info["iters"] - ref["iters"]) <= 6
+    assert abs(info["iters"] - ref["iters"]) <= max(6, ref["iters"] // 5)
     assert _relinf(res["x"].cpu().numpy(), ref["x"]) < 1e-8
     assert _relinf(res["y"].cpu().numpy(), ref["y"]) < 1e-7
 
