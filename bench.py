@@ -191,6 +191,7 @@ def run_ours(args):
     minfbe_ms, minfbe_infos = timed("minfbe", args.steps)
     gpad = run_gpad(st, lam, x0, stream, pg, dev, args.steps)
     backtrack = run_backtrack(st, Lhat, x0)
+    soft = run_soft(st, lam, x0)
 
     mat_bytes, vec_bytes = st.solve_bytes()
     alg_bytes = rounds * mat_bytes + rhs * vec_bytes
@@ -256,6 +257,7 @@ def run_ours(args):
             "gpu_launches": launches,
             "gpad": gpad,
             "backtracking": backtrack,
+            "soft_states": soft,
             "batched": batched,
             "warm_start": warm,
             "clocks": clk.summary(),
@@ -309,6 +311,21 @@ def run_backtrack(st, Lhat, x0):
         out[rule] = {"param": param, "ms": round(i["ms"], 3), "iters": i["iters"], "halvings": i["halvings"],
                      "lambda_final": i["lambda_"], "solve_calls": i["solve_calls"], "res_inf": i["res_inf"]}
     return out
+
+
+def run_soft(st, lam, x0):
+    """The same instance with soft state bounds (Section II-B: rho = 1 times the distance of
+    each state to its interval; inputs stay hard): NAMA to the same tolerance, one timed solve
+    after one warm-up.  The hard box is restored afterwards."""
+    n = st.nx + st.nu
+    st.set_penalty([1] * st.nx + [0] * st.nu, 1.0, 1.0)
+    try:
+        st.solve("nama", lam, x0=x0, tol=TOL, max_iter=500, outputs=False)
+        i = st.solve("nama", lam, x0=x0, tol=TOL, max_iter=500, outputs=False)["info"]
+    finally:
+        st.set_penalty([0] * n, 0.0, 1.0)
+    return {"rho": 1.0, "ms": round(i["ms"], 3), "iters": i["iters"], "solve_calls": i["solve_calls"],
+            "res_inf": i["res_inf"], "converged": i["status"] == 0}
 
 
 def run_warm(dev, train_draws, eval_draws):
