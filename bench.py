@@ -192,6 +192,7 @@ def run_ours(args):
     gpad = run_gpad(st, lam, x0, stream, pg, dev, args.steps)
     backtrack = run_backtrack(st, Lhat, x0)
     soft = run_soft(st, lam, x0)
+    spring = run_spring_mass(dev) if args.spring_mass else None
 
     mat_bytes, vec_bytes = st.solve_bytes()
     alg_bytes = rounds * mat_bytes + rhs * vec_bytes
@@ -258,6 +259,7 @@ def run_ours(args):
             "gpad": gpad,
             "backtracking": backtrack,
             "soft_states": soft,
+            "spring_mass": spring,
             "batched": batched,
             "warm_start": warm,
             "clocks": clk.summary(),
@@ -326,6 +328,42 @@ def run_soft(st, lam, x0):
         st.set_penalty([0] * n, 0.0, 1.0)
     return {"rho": 1.0, "ms": round(i["ms"], 3), "iters": i["iters"], "solve_calls": i["solve_calls"],
             "res_inf": i["res_inf"], "converged": i["status"] == 0}
+
+
+def run_spring_mass(dev):
+    """The experiment of Section IV-A: 300 initial states of the spring-mass array (stored, uniform
+    on the problem's domain), each solved from y0 = 0 to ||z - Hx||_inf <= 5e-4 by NAMA, MINFBE
+    (L-BFGS memory 5) and GPAD on the FP32 path; the oracle calls (right-hand sides through
+    Algorithm 3/4) per problem, summarised as in the paper: the share solved within 50 calls
+    and the median.  One tree and factor serve every initial state (x0 enters only the solve)."""
+    import torch
+    from paper_2107_01745_b300 import workloads as W
+    from paper_2107_01745_b300.stotree import StoTree
+    X, meta = W.spring_mass_x0s()
+    p = W.spring_mass(X[0], p_max=meta["p_max"])
+    st = StoTree(p, precision="fp32", device=dev)
+    st.factor()
+    r0 = torch.as_tensor(np.random.default_rng(0).standard_normal(st.m), dtype=torch.float32, device=dev)
+    lam, _ = st.estimate_lambda(r0, iters=50, safety=0.9)
+    x0s = [st.to_dev(x) for x in X]
+    out = {"problems": len(X), "tol": 5e-4, "lambda": lam, "p_max": meta["p_max"],
+           "paper": {"share_le50_calls_nama_minfbe": 0.84, "gpad_median_calls": 188}}
+    for method in ("nama", "minfbe", "gpad"):
+        st.solve(method, lam, x0=x0s[0], tol=5e-4, max_iter=5000, outputs=False)  # warm-up
+        calls, iters, ms, bad = [], [], [], 0
+        for x in x0s:
+            i = st.solve(method, lam, x0=x, tol=5e-4, max_iter=5000, outputs=False)["info"]
+            calls.append(i["solve_calls"])
+            iters.append(i["iters"])
+            ms.append(i["ms"])
+            bad += i["status"] != 0
+        calls = np.asarray(calls)
+        out[method] = {"share_le50_calls": round(float(np.mean(calls <= 50)), 4),
+                       "median_calls": float(np.median(calls)), "mean_iters": round(float(np.mean(iters)), 2),
+                       "mean_ms": round(float(np.mean(ms)), 3), "total_s": round(float(np.sum(ms)) / 1e3, 3),
+                       "not_converged": int(bad)}
+    st.close()
+    return out
 
 
 def run_warm(dev, train_draws, eval_draws):
@@ -498,6 +536,8 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--warm-train-draws", type=int, default=8192,
                     help="training draws of the learned warm start (0 skips it)")
+    ap.add_argument("--spring-mass", type=int, default=1,
+                    help="run the 300-problem spring-mass experiment of Section IV-A (0 skips it)")
     ap.add_argument("--profile", choices=["nama", "minfbe"], default=None,
                     help="run one solve inside a profiler range (no JSON benchmark line)")
     args = ap.parse_args()

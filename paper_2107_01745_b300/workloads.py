@@ -556,3 +556,97 @@ def largest(seed: int = 5) -> Problem:
     p = largest_unboxed(seed)
     xmax, umax = load_box("largest")
     return with_box(p, xmax, umax)
+
+
+# ------------------------------------------------------------------------------------------
+# Spring-mass-damper array (Section IV-A): M = 5 masses of 5 kg between two walls, M + 1
+# springs (1 N/m) and dampers (0.1 Ns/m), M - 1 actuators between neighbouring masses,
+# zero-order hold at T_s = 0.5 s; a two-mode Markov disturbance (c = 0 in mode 1, c = 0.1 in
+# mode 2) over a horizon of 11 stages.
+# ------------------------------------------------------------------------------------------
+
+SPRING_MASS = dict(masses=5, mass=5.0, k_s=1.0, b_d=0.1, u_max=2.0, v_max=5.0, p_max=5.0, Ts=0.5, horizon=11,
+                   p_c=(0.5, 0.5), P_c=((0.1, 0.9), (0.9, 0.1)), c_mode=(0.0, 0.1), Q=5.0, R=2.0, QN=100.0)
+
+
+def spring_mass_continuous(masses: int = 5, mass: float = 5.0, k_s: float = 1.0, b_d: float = 0.1):
+    """Newton's second law for the array, state x = (p_1..p_M, v_1..v_M), input u_j = force of
+    the actuator between masses j and j+1 (pushing j back by u_j and j+1 forward by u_j).
+    Each mass is tied to its neighbours (walls at both ends) by a spring and a damper."""
+    M = masses
+    Lap = 2.0 * np.eye(M) - np.eye(M, k=1) - np.eye(M, k=-1)   # spring / damper coupling
+    Ac = np.zeros((2 * M, 2 * M))
+    Ac[:M, M:] = np.eye(M)
+    Ac[M:, :M] = -(k_s / mass) * Lap
+    Ac[M:, M:] = -(b_d / mass) * Lap
+    Bc = np.zeros((2 * M, M - 1))
+    for j in range(M - 1):
+        Bc[M + j, j] = -1.0 / mass
+        Bc[M + j + 1, j] = 1.0 / mass
+    return Ac, Bc
+
+
+def zoh(Ac: np.ndarray, Bc: np.ndarray, Ts: float):
+    """Zero-order-hold discretisation: expm([[Ac, Bc], [0, 0]] Ts) = [[A, B], [0, I]]."""
+    import scipy.linalg
+    n, m = Bc.shape
+    E = np.zeros((n + m, n + m))
+    E[:n, :n], E[:n, n:] = Ac, Bc
+    F = scipy.linalg.expm(E * Ts)
+    return F[:n, :n].copy(), F[:n, n:].copy()
+
+
+def markov_tree(horizon: int, p_c, P_c) -> tuple[Tree, np.ndarray]:
+    """Scenario tree of a Markov chain with len(p_c) modes, branching at every stage: the root's
+    children are the modes of w_0 with probabilities p_c, a node in mode a has one child per
+    mode b with conditional probability P_c[a][b].  Returns the tree and each node's mode
+    (the root's entry is -1)."""
+    nm = len(p_c)
+    cond = [list(p_c)]
+    modes = [-1]
+    frontier = [-1]
+    for t in range(horizon):
+        nxt = []
+        for a in frontier:
+            for b in range(nm):
+                nxt.append(b)
+        if t < horizon - 1:
+            cond.extend([list(P_c[b]) for b in nxt])
+        modes.extend(nxt)
+        frontier = nxt
+    tree = tree_from_branching([nm] * horizon, cond_probs=cond)
+    return tree, np.asarray(modes, dtype=np.int64)
+
+
+def spring_mass(x0: np.ndarray | None = None, p_max: float | None = None) -> Problem:
+    """The spring-mass stochastic optimal control problem with initial state x0 (default 0).
+    The cost is x'Qx + u'Ru per stage and x'Q_N x at the leaves (Section IV-A's weights);
+    |u| <= u_max, |v| <= v_max, |p| <= p_max (the position bound is not stated in the paper)."""
+    S = SPRING_MASS
+    M = S["masses"]
+    Ac, Bc = spring_mass_continuous(M, S["mass"], S["k_s"], S["b_d"])
+    A, B = zoh(Ac, Bc, S["Ts"])
+    tree, modes = markov_tree(S["horizon"], S["p_c"], S["P_c"])
+    nn = tree.num_nodes
+    nx, nu = 2 * M, M - 1
+    An = np.broadcast_to(A, (nn, nx, nx)).copy()
+    Bn = np.broadcast_to(B, (nn, nx, nu)).copy()
+    An[0], Bn[0] = 0.0, 0.0
+    c = np.zeros((nn, nx))
+    c[1:] = np.asarray(S["c_mode"])[modes[1:]][:, None]
+    pm = S["p_max"] if p_max is None else p_max
+    xmax = np.concatenate([np.full(M, pm), np.full(M, S["v_max"])])
+    p = Problem(tree=tree, nx=nx, nu=nu, A=An, B=Bn, c=c, Q=np.full(nx, S["Q"]), R=np.full(nu, S["R"]),
+                PN=np.full(nx, S["QN"]), q=np.zeros(nx), r=np.zeros(nu), pN=np.zeros(nx),
+                xlo=-xmax, xhi=xmax.copy(), ulo=np.full(nu, -S["u_max"]), uhi=np.full(nu, S["u_max"]),
+                x0=np.zeros(nx) if x0 is None else np.asarray(x0, dtype=np.float64), name="spring_mass")
+    return p
+
+
+def spring_mass_x0s():
+    """The stored initial states: uniform on the problem's domain (rejection from the state box
+    with an LP feasibility test), written by oracle/make_spring_mass.py."""
+    path = os.path.join(os.path.dirname(os.path.abspath(__file__)), "data", "spring_mass_x0.json")
+    with open(path) as f:
+        d = json.load(f)
+    return np.asarray(d["x0"], dtype=np.float64), d
