@@ -333,26 +333,28 @@ def run_soft(st, lam, x0):
 def run_spring_mass(dev):
     """The experiment of Section IV-A: 300 initial states of the spring-mass array (stored, uniform
     on the problem's domain), each solved from y0 = 0 to ||z - Hx||_inf <= 5e-4 by NAMA, MINFBE
-    (L-BFGS memory 5) and GPAD on the FP32 path; the oracle calls (right-hand sides through
-    Algorithm 3/4) per problem, summarised as in the paper: the share solved within 50 calls
-    and the median.  One tree and factor serve every initial state (x0 enters only the solve)."""
+    (L-BFGS memory 5) and GPAD; the oracle calls (right-hand sides through Algorithm 3/4) per
+    problem, summarised as in the paper: the share solved within 50 calls and the median.  One
+    tree and factor serve every initial state (x0 enters only the solve).  FP64 path: the duals
+    are of order 100 and near the tolerance the steps fall below FP32's resolution of them."""
     import torch
     from paper_2107_01745_b300 import workloads as W
     from paper_2107_01745_b300.stotree import StoTree
     X, meta = W.spring_mass_x0s()
     p = W.spring_mass(X[0], p_max=meta["p_max"])
-    st = StoTree(p, precision="fp32", device=dev)
+    st = StoTree(p, precision="fp64", device=dev)
     st.factor()
-    r0 = torch.as_tensor(np.random.default_rng(0).standard_normal(st.m), dtype=torch.float32, device=dev)
+    r0 = torch.as_tensor(np.random.default_rng(0).standard_normal(st.m), dtype=torch.float64, device=dev)
     lam, _ = st.estimate_lambda(r0, iters=50, safety=0.9)
     x0s = [st.to_dev(x) for x in X]
-    out = {"problems": len(X), "tol": 5e-4, "lambda": lam, "p_max": meta["p_max"],
+    out = {"problems": len(X), "tol": 5e-4, "lambda": lam, "p_max": meta["p_max"], "dtype": "f64",
            "paper": {"share_le50_calls_nama_minfbe": 0.84, "gpad_median_calls": 188}}
     for method in ("nama", "minfbe", "gpad"):
-        st.solve(method, lam, x0=x0s[0], tol=5e-4, max_iter=5000, outputs=False)  # warm-up
+        cap = 2000 if method == "gpad" else 1000
+        st.solve(method, lam, x0=x0s[0], tol=5e-4, max_iter=cap, outputs=False)  # warm-up
         calls, iters, ms, bad = [], [], [], 0
         for x in x0s:
-            i = st.solve(method, lam, x0=x, tol=5e-4, max_iter=5000, outputs=False)["info"]
+            i = st.solve(method, lam, x0=x, tol=5e-4, max_iter=cap, outputs=False, allow_not_converged=True)["info"]
             calls.append(i["solve_calls"])
             iters.append(i["iters"])
             ms.append(i["ms"])
@@ -361,7 +363,7 @@ def run_spring_mass(dev):
         out[method] = {"share_le50_calls": round(float(np.mean(calls <= 50)), 4),
                        "median_calls": float(np.median(calls)), "mean_iters": round(float(np.mean(iters)), 2),
                        "mean_ms": round(float(np.mean(ms)), 3), "total_s": round(float(np.sum(ms)) / 1e3, 3),
-                       "not_converged": int(bad)}
+                       "not_converged": int(bad), "max_iter": cap}
     st.close()
     return out
 
