@@ -5,6 +5,7 @@
 #include <cstring>
 
 #include <map>
+#include <tuple>
 #include <mutex>
 
 #include "internal.h"
@@ -196,6 +197,30 @@ cudaError_t raise_smem_cap(const void *func, size_t bytes) {
     e = cudaFuncSetAttribute(func, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
     if (e == cudaSuccess) cap = bytes;
     return e;
+}
+
+int wave_grid(const void *func, int threads, size_t smem, int want) {
+    static std::mutex mu;
+    static std::map<std::tuple<int, const void *, int, size_t>, int> cache;
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess) return want;
+    std::lock_guard<std::mutex> lock(mu);
+    auto key = std::make_tuple(dev, func, threads, smem);
+    auto it = cache.find(key);
+    int full = 0;
+    if (it != cache.end()) {
+        full = it->second;
+    } else {
+        int per_sm = 0, sms = 0;
+        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, func, threads, smem) != cudaSuccess ||
+            cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) {
+            cudaGetLastError();
+            return want;
+        }
+        full = per_sm * sms;
+        cache[key] = full;
+    }
+    return full > 0 && full < want ? full : want;
 }
 
 // Tree conventions (Section II-A with the numbering of the boundary): root 0 with probability 1,

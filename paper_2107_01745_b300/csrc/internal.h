@@ -135,6 +135,9 @@ sto_status cuda_fail(stotree_t h, cudaError_t e, const char *what);
 // Raise (never lower) a kernel's dynamic shared-memory cap on the current device.  A cap that a
 // later, smaller launch lowered would sit below the size recorded in an earlier captured graph.
 cudaError_t raise_smem_cap(const void *func, size_t bytes);
+// Blocks that one wave of `func` holds on this device (occupancy x SMs), capped at `want`:
+// a grid-stride pass launched with more blocks than one wave leaves a partial second wave.
+int wave_grid(const void *func, int threads, size_t smem, int want);
 sto_status validate_tree(const int32_t *parent, const double *prob, int Nn, int horizon, std::vector<int32_t> &stage,
                          std::vector<int32_t> &ccnt, std::vector<int32_t> &cbeg);
 #define STO_CUDA(h, call)                                       \

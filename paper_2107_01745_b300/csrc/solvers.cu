@@ -676,8 +676,10 @@ __global__ void __launch_bounds__(kThreads) k_lb_dir(int m, const T *__restrict_
 template <class T, int MEM>
 void lb_direction_t(int grid, cudaStream_t st, int m, const T *g, const T *ringS, const T *ringY, long long vs,
                     SolverScalars *sc, double *part, T *d) {
-    k_lb_dots<T, MEM><<<grid, kThreads, 0, st>>>(m, g, ringS, ringY, vs, sc, part);
-    k_lb_dir<T, MEM><<<grid, kThreads, 0, st>>>(m, g, ringS, ringY, vs, sc, d);
+    const int g1 = wave_grid((const void *)k_lb_dots<T, MEM>, kThreads, 0, grid);
+    const int g2 = wave_grid((const void *)k_lb_dir<T, MEM>, kThreads, 0, grid);
+    k_lb_dots<T, MEM><<<g1, kThreads, 0, st>>>(m, g, ringS, ringY, vs, sc, part);
+    k_lb_dir<T, MEM><<<g2, kThreads, 0, st>>>(m, g, ringS, ringY, vs, sc, d);
 }
 
 template <class T>
