@@ -133,6 +133,17 @@ def _dist():
     return world, rank, local
 
 
+def _max_over_ranks(pg, value: float, device) -> float:
+    """The largest of every rank's value (the job's time is its slowest rank's); pg = None or
+    torch.distributed with an initialised process group (NCCL on GPUs, gloo on CPU)."""
+    if pg is None:
+        return value
+    import torch
+    t = torch.tensor([value], dtype=torch.float64, device=device)
+    pg.all_reduce(t, op=pg.ReduceOp.MAX)
+    return float(t.item())
+
+
 def run_ours(args):
     import torch
     from paper_2107_01745_b300 import workloads as W
@@ -176,11 +187,7 @@ def run_ours(args):
         e1.record(stream)
         torch.cuda.synchronize()
         ms = e0.elapsed_time(e1) / k
-        if pg is not None:
-            t = torch.tensor([ms], device=dev)
-            pg.all_reduce(t, op=pg.ReduceOp.MAX)
-            ms = float(t.item())
-        return ms, infos
+        return _max_over_ranks(pg, ms, dev), infos
 
     st.set_timing(True)
     st.get_timing()  # reset counters
@@ -222,10 +229,7 @@ def run_ours(args):
     e1.record(stream)
     torch.cuda.synchronize()
     e2e_ms = e0.elapsed_time(e1) / args.steps
-    if pg is not None:
-        t = torch.tensor([e2e_ms], device=dev)
-        pg.all_reduce(t, op=pg.ReduceOp.MAX)
-        e2e_ms = float(t.item())
+    e2e_ms = _max_over_ranks(pg, e2e_ms, dev)
     h2d = 4 * (st.nx + st.m)
     d2h = 4 * (st.m + st.Nn * st.nx + st.Np * st.nu)
 
