@@ -160,6 +160,7 @@ def run_ours(args):
     p = W.paper_scale(2)
     st = StoTree(p, precision="fp32", device=dev)
     st.factor()
+    factor = run_factor(st, p)
     r0 = torch.as_tensor(np.random.default_rng(7).standard_normal(st.m), dtype=torch.float32, device=dev)
     lam, Lhat = st.estimate_lambda(r0, iters=50, safety=0.9)
     x0 = st.to_dev(p.x0)
@@ -260,6 +261,7 @@ def run_ours(args):
             "solve_step_gbs": round(achieved, 1),
             "e2e": {"value": round(e2e_ms, 4), "unit": "ms", "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
             "gpu_launches": launches,
+            "factor": factor,
             "gpad": gpad,
             "backtracking": backtrack,
             "soft_states": soft,
@@ -273,6 +275,42 @@ def run_ours(args):
         pg.barrier()
         pg.destroy_process_group()
     return line
+
+
+def run_factor(st, p):
+    """The offline factor (Section III-D) of the paper-scale instance, FP64 on the device: its
+    time (set-up, not part of the headline), an operation count of its products, and the
+    FP64 rate of a cuBLAS DGEMM on this GPU for comparison (the factor is bound by the FP64
+    pipe).  Flops counted: per child j, P^j [A^j | B^j] and [A^j | B^j]' (P^j [A^j | B^j]);
+    per parent, the Cholesky factor of Rbar, K = -Rbar^-1 M and the update M' K."""
+    import torch
+    nx, nu = p.nx, p.nu
+    t = p.tree
+    nc, npn = t.num_nodes - 1, t.num_nonleaf
+    flops = nc * (2.0 * nx * nx * (nx + nu) + 2.0 * (nx + nu) ** 2 * nx) + \
+        npn * (nu ** 3 / 3.0 + 2.0 * nu * nu * nx + 2.0 * nx * nx * nu)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    stream = torch.cuda.current_stream()
+    ms = []
+    for _ in range(3):
+        torch.cuda.synchronize()
+        e0.record(stream)
+        st.factor()
+        e1.record(stream)
+        torch.cuda.synchronize()
+        ms.append(e0.elapsed_time(e1))
+    fac_ms = min(ms)
+    a = torch.randn(4096, 4096, dtype=torch.float64, device=st.device)
+    torch.matmul(a, a)
+    torch.cuda.synchronize()
+    e0.record(stream)
+    for _ in range(5):
+        torch.matmul(a, a)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    dgemm_tf = 5 * 2.0 * 4096 ** 3 / (e0.elapsed_time(e1) * 1e-3) / 1e12
+    return {"ms": round(fac_ms, 2), "gflop": round(flops / 1e9, 1), "tflops": round(flops / (fac_ms * 1e-3) / 1e12, 3),
+            "fp64_dgemm_tflops_measured": round(dgemm_tf, 3), "frac_of_dgemm": round(flops / (fac_ms * 1e-3) / 1e12 / dgemm_tf, 3)}
 
 
 def run_gpad(st, lam, x0, stream, pg, dev, steps):
