@@ -557,7 +557,19 @@ def run_profile(method):
     cudaProfilerStart/Stop (for ncu --profile-from-start off)."""
     import torch
     from paper_2107_01745_b300 import workloads as W
-    from paper_2107_01745_b300.stotree import StoTree
+    from paper_2107_01745_b300.stotree import StoBatch, StoTree
+    if method == "batched":
+        sb = StoBatch(W.batched_uneven(3))
+        sb.factor()
+        lams = sb.group_lambdas()
+        sb.nama(lams, tol=TOL, max_iter=500)
+        torch.cuda.synchronize()
+        torch.cuda.cudart().cudaProfilerStart()
+        res = sb.nama(lams, tol=TOL, max_iter=500, outputs=False)
+        torch.cuda.synchronize()
+        torch.cuda.cudart().cudaProfilerStop()
+        print(json.dumps({"profiled": method, "max_iters": int(max(i["iters"] for i in res["infos"]))}))
+        return
     p = W.paper_scale(2)
     st = StoTree(p, precision="fp32")
     st.factor()
@@ -582,7 +594,7 @@ def main():
                     help="training draws of the learned warm start (0 skips it)")
     ap.add_argument("--spring-mass", type=int, default=1,
                     help="run the 300-problem spring-mass experiment of Section IV-A (0 skips it)")
-    ap.add_argument("--profile", choices=["nama", "minfbe"], default=None,
+    ap.add_argument("--profile", choices=["nama", "minfbe", "batched"], default=None,
                     help="run one solve inside a profiler range (no JSON benchmark line)")
     args = ap.parse_args()
     if args.profile:
