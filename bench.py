@@ -87,10 +87,16 @@ class ClockSampler:
         os.close(fd)
         try:
             self.proc = subprocess.Popen(["nvidia-smi", f"--id={self.gpu}", f"--query-gpu={self.FIELDS}",
-                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                          "--format=csv,noheader,nounits", "-lms", "50"],
                                          stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
         except OSError:
             self.proc = None
+        # start timing only once the sampler is running (its first line is written)
+        t0 = time.time()
+        while self.proc is not None and time.time() - t0 < 3.0:
+            if os.path.getsize(self.path) > 0:
+                break
+            time.sleep(0.01)
         return self
 
     def __exit__(self, *exc):
@@ -194,9 +200,9 @@ def run_ours(args):
     st.get_timing()  # reset counters
     with ClockSampler(local) as clk:
         nama_ms, nama_infos = timed("nama", args.steps)
-    solve_ms, rounds, rhs = st.get_timing()
-    st.set_timing(False)
-    minfbe_ms, minfbe_infos = timed("minfbe", args.steps)
+        solve_ms, rounds, rhs = st.get_timing()
+        st.set_timing(False)
+        minfbe_ms, minfbe_infos = timed("minfbe", args.steps)
     gpad = run_gpad(st, lam, x0, stream, pg, dev, args.steps)
     backtrack = run_backtrack(st, Lhat, x0)
     soft = run_soft(st, lam, x0)
@@ -235,7 +241,7 @@ def run_ours(args):
     d2h = 4 * (st.m + st.Nn * st.nx + st.Np * st.nu)
 
     batched = run_batched(dev, max(1, min(args.steps, 3)))
-    warm = run_warm(dev, args.warm_train_draws, 512) if args.warm_train_draws > 0 else None
+    warm = run_warm(dev, args.warm_train_draws, args.warm_eval_draws) if args.warm_train_draws > 0 else None
     line = None
     if rank == 0:
         cpu = cpu_baseline(p, lam, nama_infos[0]["iters"])
@@ -454,7 +460,10 @@ def run_warm(dev, train_draws, eval_draws):
             "warm_infer_ms": round(r["warm_infer_ms"], 2), "warm_fallback_test_ms": round(r["warm_fallback_test_ms"], 2),
             "cold_iters_mean": r["cold_iters_mean"], "warm_iters_mean": r["warm_iters_mean"],
             "cold_iters_max": r["cold_iters_max"], "warm_iters_max": r["warm_iters_max"],
-            "fallbacks": r["fallbacks"], "all_converged": r["converged"]}
+            "fallbacks": r["fallbacks"], "all_converged": r["converged"],
+            "warm_direct_ms": round(r["direct_ms"], 2), "warm_direct_iters_mean": r["direct_iters_mean"],
+            "warm_direct_iters_max": r["direct_iters_max"],
+            "warm_direct_speedup": round(r["cold_ms"] / r["direct_ms"], 3)}
 
 
 def run_batched(dev, steps):
@@ -590,8 +599,10 @@ def main():
     ap.add_argument("--steps", type=int, default=5)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--warm-train-draws", type=int, default=8192,
+    ap.add_argument("--warm-train-draws", type=int, default=50000,
                     help="training draws of the learned warm start (0 skips it)")
+    ap.add_argument("--warm-eval-draws", type=int, default=5000,
+                    help="held-out draws the learned warm start is evaluated on")
     ap.add_argument("--spring-mass", type=int, default=1,
                     help="run the 300-problem spring-mass experiment of Section IV-A (0 skips it)")
     ap.add_argument("--profile", choices=["nama", "minfbe", "batched"], default=None,

@@ -171,7 +171,8 @@ __global__ void __launch_bounds__(kBT) k_bbwd(RoundArgs<NR> a, int task0) {
     const int bt = t < g.s ? g.b : 1;
     const bool leaf_children = t + 1 == g.N;
     load_cols(a, g, tk, n_t, ci);
-    __syncthreads();
+    // a tile whose instances have all converged writes nothing: leave it
+    if (!__syncthreads_or(threadIdx.x < kTC ? ci.ok[threadIdx.x] : 0)) return;
     // S[k][r][col] = sum over the children of the column's node
     for (int e = threadIdx.x; e < NR * nx * kTC; e += kBT) {
         const int k = e / (nx * kTC), rem = e - k * nx * kTC, col = rem / nx, r = rem - col * nx;
@@ -320,7 +321,8 @@ __global__ void __launch_bounds__(kBT) k_bfwd(RoundArgs<NR> a, int task0) {
         for (int e = threadIdx.x; e < nu * nx; e += kBT) Ks[e] = g.Kt[(size_t)t * nu * nx + e];
     const int n_t = g.soff[t + 1] - g.soff[t];
     load_cols(a, g, tk, n_t, ci);
-    __syncthreads();
+    // a tile whose instances have all converged writes nothing: leave it
+    if (!__syncthreads_or(threadIdx.x < kTC ? ci.ok[threadIdx.x] : 0)) return;
     for (int e = threadIdx.x; e < NR * nx * kTC; e += kBT) {
         const int k = e / (nx * kTC), rem = e - k * nx * kTC, col = rem / nx, r = rem - col * nx;
         float val = 0.f;

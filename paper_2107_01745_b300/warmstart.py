@@ -139,7 +139,8 @@ def choose_start(ev: EvalSet, y0: torch.Tensor):
 
 def warm_vs_cold(starter: WarmStarter, ev: EvalSet, tol=1e-4):
     """Batched NAMA on the evaluation draws from y0 = 0 and from the learned start; the warm time
-    includes inference and the fallback test."""
+    includes inference and the fallback test.  The learned start is also timed without the
+    fallback test ("direct": inference and the solve from every prediction)."""
     torch.cuda.synchronize()
     e0, e1 = _events()
     e0.record()
@@ -157,11 +158,20 @@ def warm_vs_cold(starter: WarmStarter, ev: EvalSet, tol=1e-4):
     y_warm, warm = ev.nama(start, tol=tol)
     e3.record()
     torch.cuda.synchronize()
+    # the same start taken without the fallback test (every draw from its prediction)
+    e4, e5 = _events()
+    e4.record()
+    y1 = starter.predict(ev.x0, ev.c)
+    _, direct = ev.nama(y1, tol=tol)
+    e5.record()
+    torch.cuda.synchronize()
     ci = np.array([i["iters"] for i in cold])
     wi = np.array([i["iters"] for i in warm])
-    ok = all(i["status"] == 0 for i in cold + warm)
+    di = np.array([i["iters"] for i in direct])
+    ok = all(i["status"] == 0 for i in cold + warm + direct)
     return dict(draws=ev.D, cold_ms=cold_ms, warm_ms=e0.elapsed_time(e3), warm_infer_ms=e0.elapsed_time(e1),
                 warm_fallback_test_ms=e1.elapsed_time(e2), warm_solve_ms=e2.elapsed_time(e3),
                 cold_iters_mean=float(ci.mean()), warm_iters_mean=float(wi.mean()), cold_iters_max=int(ci.max()),
                 warm_iters_max=int(wi.max()), fallbacks=fallbacks, converged=ok, y_warm=y_warm, y_cold=y_cold,
-                y0=y0)
+                y0=y0, direct_ms=e4.elapsed_time(e5), direct_iters_mean=float(di.mean()),
+                direct_iters_max=int(di.max()))
