@@ -150,6 +150,26 @@ __device__ __forceinline__ void load_cols(const RoundArgs<NR> &a, const GroupDev
     }
 }
 
+// e = (k * kTC + col) * R + r over [threadIdx.x, NR * kTC * R) in steps of kBT, r fastest (so that
+// a warp's global accesses to a column's R consecutive reals coalesce), with the (k, col, r)
+// of each step advanced from the previous one instead of divided out per element.
+template <int NR, class F>
+__device__ __forceinline__ void for_kcr(int R, F f) {
+    const int tot = NR * kTC * R;
+    int e = threadIdx.x;
+    int kc = e / R, r = e - kc * R;
+    const int dq = kBT / R, dr = kBT - dq * R;
+    for (; e < tot; e += kBT) {
+        f(kc / kTC, kc % kTC, r);
+        r += dr;
+        kc += dq;
+        if (r >= R) {
+            r -= R;
+            ++kc;
+        }
+    }
+}
+
 // Backward: parents of stage t.  S = sum_children s, o = [A | B]' S, v = y_u/2 + o_B + gu,
 // ubar = -(1/pi_t) R~^-1 v, s = y_x/2 + o_A + K_t' v + gx.
 template <int NR>
@@ -174,8 +194,7 @@ __global__ void __launch_bounds__(kBT) k_bbwd(RoundArgs<NR> a, int task0) {
     // a tile whose instances have all converged writes nothing: leave it
     if (!__syncthreads_or(threadIdx.x < kTC ? ci.ok[threadIdx.x] : 0)) return;
     // S[k][r][col] = sum over the children of the column's node
-    for (int e = threadIdx.x; e < NR * nx * kTC; e += kBT) {
-        const int k = e / (nx * kTC), rem = e - k * nx * kTC, col = rem / nx, r = rem - col * nx;
+    for_kcr<NR>(nx, [&](int k, int col, int r) {
         float acc = 0.f;
         if (ci.ok[col]) {
             const int i = ci.node[col];
@@ -190,7 +209,7 @@ __global__ void __launch_bounds__(kBT) k_bbwd(RoundArgs<NR> a, int task0) {
             }
         }
         S[(k * 64 + r) * kTP + col] = acc;
-    }
+    });
     __syncthreads();
     const int cg = threadIdx.x % kCG, rg = threadIdx.x / kCG;
     const int mr = (nxu + kRG - 1) / kRG, r0 = rg * mr;
@@ -232,13 +251,12 @@ __global__ void __launch_bounds__(kBT) k_bbwd(RoundArgs<NR> a, int task0) {
     __syncthreads();
     {
         const float sc = a.scaled ? g.sq[t] : 1.f;
-        for (int e = threadIdx.x; e < NR * nu * kTC; e += kBT) {
-            const int k = e / (nu * kTC), rem = e - k * nu * kTC, col = rem / nu, aa = rem - col * nu;
+        for_kcr<NR>(nu, [&](int k, int col, int aa) {
             if (ci.ok[col]) {
                 const long long o = ci.elem[col] + doff(g, ci.node[col]) + nx + aa;
                 V[(k * 32 + aa) * kTP + col] += 0.5f * sc * a.y[k][o] + (a.homog ? 0.f : a.gam[o]);
             }
-        }
+        });
     }
     __syncthreads();
     // rows c < nx: s = o_A + K' v; rows c = nx + a: ubar = -(1/pi_t) R~^-1 v
@@ -284,22 +302,20 @@ __global__ void __launch_bounds__(kBT) k_bbwd(RoundArgs<NR> a, int task0) {
     }
     __syncthreads();
     // coalesced write-out: ubar, and s = y_x/2 + (o_A + K'v) + gx
-    for (int e = threadIdx.x; e < NR * nu * kTC; e += kBT) {
-        const int k = e / (nu * kTC), rem = e - k * nu * kTC, col = rem / nu, aa = rem - col * nu;
+    for_kcr<NR>(nu, [&](int k, int col, int aa) {
         if (ci.ok[col])
             a.ubar[k * a.u_stride + ci.ub[col] + (long long)ci.node[col] * nu + aa] = V[(k * 32 + aa) * kTP + col];
-    }
+    });
     {
         const float sc = a.scaled ? g.sq[t] : 1.f;
-        for (int e = threadIdx.x; e < NR * nx * kTC; e += kBT) {
-            const int k = e / (nx * kTC), rem = e - k * nx * kTC, col = rem / nx, r = rem - col * nx;
+        for_kcr<NR>(nx, [&](int k, int col, int r) {
             if (ci.ok[col]) {
                 const int i = ci.node[col];
                 const long long o = ci.elem[col] + doff(g, i) + r;
                 a.s[k * a.s_stride + ci.sb[col] + (long long)i * nx + r] =
                     S[(k * 64 + r) * kTP + col] + 0.5f * sc * a.y[k][o] + (a.homog ? 0.f : a.gam[o]);
             }
-        }
+        });
     }
 }
 
@@ -323,8 +339,7 @@ __global__ void __launch_bounds__(kBT) k_bfwd(RoundArgs<NR> a, int task0) {
     load_cols(a, g, tk, n_t, ci);
     // a tile whose instances have all converged writes nothing: leave it
     if (!__syncthreads_or(threadIdx.x < kTC ? ci.ok[threadIdx.x] : 0)) return;
-    for (int e = threadIdx.x; e < NR * nx * kTC; e += kBT) {
-        const int k = e / (nx * kTC), rem = e - k * nx * kTC, col = rem / nx, r = rem - col * nx;
+    for_kcr<NR>(nx, [&](int k, int col, int r) {
         float val = 0.f;
         if (ci.ok[col]) {
             if (t == 0) {
@@ -335,7 +350,7 @@ __global__ void __launch_bounds__(kBT) k_bfwd(RoundArgs<NR> a, int task0) {
             }
         }
         X[(k * kMaxXU + r) * kTP + col] = val;
-    }
+    });
     __syncthreads();
     const int cg = threadIdx.x % kCG, rg = threadIdx.x / kCG;
     const float sc = a.scaled ? g.sq[t] : 1.f;
@@ -376,18 +391,16 @@ __global__ void __launch_bounds__(kBT) k_bfwd(RoundArgs<NR> a, int task0) {
                     *reinterpret_cast<float4 *>(X + (k * kMaxXU + nx + a0 + m) * kTP + cg * 4) =
                         make_float4(u[k][m][0], u[k][m][1], u[k][m][2], u[k][m][3]);
         __syncthreads();
-        for (int e = threadIdx.x; e < NR * nu * kTC; e += kBT) {
-            const int k = e / (nu * kTC), rem = e - k * nu * kTC, col = rem / nu, aa = rem - col * nu;
+        for_kcr<NR>(nu, [&](int k, int col, int aa) {
             if (ci.ok[col])
                 X[(k * kMaxXU + nx + aa) * kTP + col] +=
                     a.ubar[k * a.u_stride + ci.ub[col] + (long long)ci.node[col] * nu + aa];
-        }
+        });
         __syncthreads();
     }
     // h for the stage's nodes, primal scratch
     const int rows = leaf ? nx : nxu;
-    for (int e = threadIdx.x; e < NR * rows * kTC; e += kBT) {
-        const int k = e / (rows * kTC), rem = e - k * rows * kTC, col = rem / rows, r = rem - col * rows;
+    for_kcr<NR>(rows, [&](int k, int col, int r) {
         if (ci.ok[col]) {
             const int i = ci.node[col];
             const float val = X[(k * kMaxXU + r) * kTP + col];
@@ -397,7 +410,7 @@ __global__ void __launch_bounds__(kBT) k_bfwd(RoundArgs<NR> a, int task0) {
             else
                 a.us[k * a.u_stride + ci.ub[col] + (long long)i * nu + r - nx] = val;
         }
-    }
+    });
     if (leaf) return;
     // children: x^j = [A | B][x; u] + c^j (rows r of x over the row groups)
     const int mx = (nx + kRG - 1) / kRG, x0r = rg * mx;
@@ -436,8 +449,7 @@ __global__ void __launch_bounds__(kBT) k_bfwd(RoundArgs<NR> a, int task0) {
                     make_float4(acc[k][m][0], acc[k][m][1], acc[k][m][2], acc[k][m][3]);
     __syncthreads();
     const int bt = t < g.s ? g.b : 1;
-    for (int e = threadIdx.x; e < NR * nx * kTC; e += kBT) {
-        const int k = e / (nx * kTC), rem = e - k * nx * kTC, col = rem / nx, r = rem - col * nx;
+    for_kcr<NR>(nx, [&](int k, int col, int r) {
         if (ci.ok[col]) {
             const int i = ci.node[col];
             const int j0 = g.soff[t + 1] + (i - g.soff[t]) * bt;
@@ -447,7 +459,7 @@ __global__ void __launch_bounds__(kBT) k_bfwd(RoundArgs<NR> a, int task0) {
                 a.xs[k * a.s_stride + ci.sb[col] + (long long)j * nx + r] = xv + cj;
             }
         }
-    }
+    });
 }
 
 // gamma^i = pi_{t+1} [A | B]' P~_{t+1} sum_j c^j for every nonleaf node and instance (set-up).
