@@ -150,6 +150,26 @@ __device__ __forceinline__ void load_cols(const RoundArgs<NR> &a, const GroupDev
     }
 }
 
+// acc[q] += sum_u w_u x[u][q] for the four weights w of a 16-byte load and four column vectors.
+__device__ __forceinline__ void fma4x4(const float4 w, const float4 *x, float *acc) {
+    acc[0] = fmaf(w.x, x[0].x, acc[0]);
+    acc[1] = fmaf(w.x, x[0].y, acc[1]);
+    acc[2] = fmaf(w.x, x[0].z, acc[2]);
+    acc[3] = fmaf(w.x, x[0].w, acc[3]);
+    acc[0] = fmaf(w.y, x[1].x, acc[0]);
+    acc[1] = fmaf(w.y, x[1].y, acc[1]);
+    acc[2] = fmaf(w.y, x[1].z, acc[2]);
+    acc[3] = fmaf(w.y, x[1].w, acc[3]);
+    acc[0] = fmaf(w.z, x[2].x, acc[0]);
+    acc[1] = fmaf(w.z, x[2].y, acc[1]);
+    acc[2] = fmaf(w.z, x[2].z, acc[2]);
+    acc[3] = fmaf(w.z, x[2].w, acc[3]);
+    acc[0] = fmaf(w.w, x[3].x, acc[0]);
+    acc[1] = fmaf(w.w, x[3].y, acc[1]);
+    acc[2] = fmaf(w.w, x[3].z, acc[2]);
+    acc[3] = fmaf(w.w, x[3].w, acc[3]);
+}
+
 // e = (k * kTC + col) * R + r over [threadIdx.x, NR * kTC * R) in steps of kBT, r fastest (so that
 // a warp's global accesses to a column's R consecutive reals coalesce), with the (k, col, r)
 // of each step advanced from the previous one instead of divided out per element.
@@ -422,7 +442,26 @@ __global__ void __launch_bounds__(kBT) k_bfwd(RoundArgs<NR> a, int task0) {
         for (int m = 0; m < kMX; ++m)
 #pragma unroll
             for (int q = 0; q < 4; ++q) acc[k][m][q] = 0.f;
-    for (int qq = 0; qq < nxu; ++qq) {
+    int qq = 0;
+    if ((nxu & 3) == 0) {
+        // four inputs per step: one 16-byte load of each G row, four of the column tile
+        for (; qq + 4 <= nxu; qq += 4) {
+            float4 x4[NR][4];
+#pragma unroll
+            for (int k = 0; k < NR; ++k)
+#pragma unroll
+                for (int u = 0; u < 4; ++u)
+                    x4[k][u] = *reinterpret_cast<const float4 *>(X + (k * kMaxXU + qq + u) * kTP + cg * 4);
+#pragma unroll
+            for (int m = 0; m < kMX; ++m)
+                if (m < mx && x0r + m < nx) {
+                    const float4 g4 = *reinterpret_cast<const float4 *>(Gs + (x0r + m) * nxu + qq);
+#pragma unroll
+                    for (int k = 0; k < NR; ++k) fma4x4(g4, x4[k], acc[k][m]);
+                }
+        }
+    }
+    for (; qq < nxu; ++qq) {
         float4 x4[NR];
 #pragma unroll
         for (int k = 0; k < NR; ++k) x4[k] = *reinterpret_cast<const float4 *>(X + (k * kMaxXU + qq) * kTP + cg * 4);
