@@ -567,6 +567,21 @@ def run_profile(method):
     import torch
     from paper_2107_01745_b300 import workloads as W
     from paper_2107_01745_b300.stotree import StoBatch, StoTree
+    if method == "warm":
+        from paper_2107_01745_b300 import warmstart as WS
+        system = W.warm_start_system(4)
+        lam = WS.batch_lambda(system)
+        data = WS.make_dataset(system, W.WARM_TRAIN_SEED, 64, lam)
+        starter = WS.WarmStarter(system, hidden=256, batch=8192, seed=0)
+        starter.net.set_draws(data["x0"], data["c"], data["y"])
+        starter.net.train(5)
+        torch.cuda.synchronize()
+        torch.cuda.cudart().cudaProfilerStart()
+        hist = starter.net.train(3)
+        torch.cuda.synchronize()
+        torch.cuda.cudart().cudaProfilerStop()
+        print(json.dumps({"profiled": method, "train_steps": 3, "loss": float(hist[-1])}))
+        return
     if method == "batched":
         sb = StoBatch(W.batched_uneven(3))
         sb.factor()
@@ -605,7 +620,7 @@ def main():
                     help="held-out draws the learned warm start is evaluated on")
     ap.add_argument("--spring-mass", type=int, default=1,
                     help="run the 300-problem spring-mass experiment of Section IV-A (0 skips it)")
-    ap.add_argument("--profile", choices=["nama", "minfbe", "batched"], default=None,
+    ap.add_argument("--profile", choices=["nama", "minfbe", "batched", "warm"], default=None,
                     help="run one solve inside a profiler range (no JSON benchmark line)")
     args = ap.parse_args()
     if args.profile:
