@@ -490,6 +490,20 @@ def run_batched(dev, steps):
     infos = res["infos"]
     if not all(i["status"] == 0 and i["res_inf"] <= TOL for i in infos):
         raise RuntimeError("batched NAMA: some instance did not reach the tolerance")
+    # algorithmic vector bytes of the solve rounds: every right-hand side an active instance
+    # pushes through Algorithm 3/4 reads y and writes Hx (m reals each) and writes and reads the
+    # per-node scratch s, ubar, x, u once; NAMA pushes 1 + 3 k right-hand sides in k iterations
+    vec_bytes = 0.0
+    inst = 0
+    for g in groups:
+        t = g.tree()
+        m_i = t.num_nonleaf * (g.nx + g.nu) + t.num_leaves * g.nx
+        per_rhs = 4.0 * (2 * m_i + 2 * (g.nu * t.num_nonleaf + g.nx * t.num_nodes))
+        for _ in range(g.num_instances):
+            vec_bytes += per_rhs * (1 + 3 * infos[inst]["iters"])
+            inst += 1
+    peak, peak_kind = _peaks()
+    rounds_gbs = vec_bytes / (batched_ms * 1e-3) / 1e9
     plain_ms, sample = 0.0, 0
     for gi, g in enumerate(groups):
         st = StoTree(g.instance(0), precision="fp32", device=dev)
@@ -512,7 +526,12 @@ def run_batched(dev, steps):
             "max_iters": int(max(i["iters"] for i in infos)),
             "plain_sequential_ms": round(plain_ms, 1),
             "plain_sample": f"{sample} instances (one per group) timed with the single-instance path, x32",
-            "speedup": round(plain_ms / batched_ms, 2)}
+            "speedup": round(plain_ms / batched_ms, 2),
+            "roofline": {"bound": "hbm", "achieved": round(rounds_gbs, 1), "peak": peak, "unit": "GB/s",
+                         "frac": round(rounds_gbs / peak, 4), "peak_source": peak_kind,
+                         "algorithmic_bytes": vec_bytes,
+                         "note": "vector bytes of the solve rounds over the whole batched solve time "
+                                 "(elementwise passes included in the time, not in the bytes)"}}
 
 
 def cpu_baseline(p, lam, gpu_iters):
