@@ -524,6 +524,8 @@ def run_batched(dev, steps):
                         "group, own x0 ~ U[-3,3] and w ~ N(0, 0.05^2) per instance, seed 3; NAMA to 1e-4",
             "instances": sb.ninst, "dual_variables": sb.M, "batched_ms": round(batched_ms, 3),
             "max_iters": int(max(i["iters"] for i in infos)),
+            "mean_iters": round(float(np.mean([i["iters"] for i in infos])), 3),
+            "instances_needing_iterations": int(sum(i["iters"] > 0 for i in infos)),
             "plain_sequential_ms": round(plain_ms, 1),
             "plain_sample": f"{sample} instances (one per group) timed with the single-instance path, x32",
             "speedup": round(plain_ms / batched_ms, 2),
