@@ -204,15 +204,16 @@ __global__ void __launch_bounds__(kBT) k_bbwd(RoundArgs<NR> a, int task0) {
     float *Rs = Ks + 32 * 64;        // R~_t^-1 [a][b]
     float *S = Rs + 32 * 32;         // [k][r][col]; afterwards s (without y_x/2 + gx)
     float *V = S + NR * 64 * kTP;    // [k][a][col]: v; afterwards ubar
-    for (int e = threadIdx.x; e < nx * nxu; e += kBT) Gs[e] = g.G[e];
-    for (int e = threadIdx.x; e < nu * nx; e += kBT) Ks[e] = g.Kt[(size_t)t * nu * nx + e];
-    for (int e = threadIdx.x; e < nu * nu; e += kBT) Rs[e] = g.Ri[(size_t)t * nu * nu + e];
     const int n_t = g.soff[t + 1] - g.soff[t];
     const int bt = t < g.s ? g.b : 1;
     const bool leaf_children = t + 1 == g.N;
     load_cols(a, g, tk, n_t, ci);
-    // a tile whose instances have all converged writes nothing: leave it
+    // a tile whose instances have all converged writes nothing: leave it (before its matrices
+    // are staged; the barrier after the gather below orders their stores before any use)
     if (!__syncthreads_or(threadIdx.x < kTC ? ci.ok[threadIdx.x] : 0)) return;
+    for (int e = threadIdx.x; e < nx * nxu; e += kBT) Gs[e] = g.G[e];
+    for (int e = threadIdx.x; e < nu * nx; e += kBT) Ks[e] = g.Kt[(size_t)t * nu * nx + e];
+    for (int e = threadIdx.x; e < nu * nu; e += kBT) Rs[e] = g.Ri[(size_t)t * nu * nu + e];
     // S[k][r][col] = sum over the children of the column's node
     for_kcr<NR>(nx, [&](int k, int col, int r) {
         float acc = 0.f;
@@ -352,13 +353,14 @@ __global__ void __launch_bounds__(kBT) k_bfwd(RoundArgs<NR> a, int task0) {
     float *Ks = Gs + 64 * kMaxXU;
     float *X = Ks + 32 * 64;  // [k][row][col]: x then u per column
     const bool leaf = t == g.N;
+    const int n_t = g.soff[t + 1] - g.soff[t];
+    load_cols(a, g, tk, n_t, ci);
+    // a tile whose instances have all converged writes nothing: leave it (before its matrices
+    // are staged; the barrier after the gather below orders their stores before any use)
+    if (!__syncthreads_or(threadIdx.x < kTC ? ci.ok[threadIdx.x] : 0)) return;
     for (int e = threadIdx.x; e < nx * nxu; e += kBT) Gs[e] = g.G[e];
     if (!leaf)
         for (int e = threadIdx.x; e < nu * nx; e += kBT) Ks[e] = g.Kt[(size_t)t * nu * nx + e];
-    const int n_t = g.soff[t + 1] - g.soff[t];
-    load_cols(a, g, tk, n_t, ci);
-    // a tile whose instances have all converged writes nothing: leave it
-    if (!__syncthreads_or(threadIdx.x < kTC ? ci.ok[threadIdx.x] : 0)) return;
     for_kcr<NR>(nx, [&](int k, int col, int r) {
         float val = 0.f;
         if (ci.ok[col]) {
