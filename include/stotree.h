@@ -85,7 +85,9 @@ typedef struct {
     const double *prob;
 } sto_tree_desc;
 
-/* Options of Algorithms 1 and 2. */
+/* Options of Algorithms 1 and 2 (stotree_nama_solve, stotree_minfbe_solve), of GPAD
+ * (stotree_gpad_solve: lambda, tol, max_iter) and of the batched NAMA (stobatch_nama_solve: no
+ * backtracking, the step comes per group). */
 typedef struct {
     double lambda;      /* step, in (0, 1/L) (Algorithm 1 input); see stotree_estimate_lambda */
     double tol;         /* stop when ||z - Hx||_inf <= tol (unscaled residual, Section III-B) */
