@@ -79,10 +79,16 @@ def make_dataset(system: W.Group, first_seed: int, count: int, lam: float, chunk
 
 
 class WarmStarter:
-    def __init__(self, system: W.Group, hidden=256, batch=8192, seed=0, device="cuda:0"):
+    def __init__(self, system: W.Group, hidden=256, batch=8192, seed=0, device="cuda:0", infer_batch=65536):
         self.system = system
         self.tree = system.tree()
         self.net = StoWarm(self.tree, system.nx, system.nu, hidden=hidden, batch=batch, seed=seed, device=device)
+        # inference runs the trained weights in a second network with a larger row batch: each
+        # product is then large enough to keep the tensor cores busy (training keeps its batch)
+        self._infer_args = dict(hidden=hidden, batch=max(batch, infer_batch), seed=seed, device=device)
+        self._infer = None
+        self._infer_version = -1
+        self._version = 0
 
     def fit(self, data: dict, epochs=10, lr=1e-3, shuffle_seed=0):
         self.net.set_draws(data["x0"], data["c"], data["y"])
@@ -94,11 +100,20 @@ class WarmStarter:
         hist = self.net.train(steps, lr=lr, seed=shuffle_seed)
         e1.record()
         torch.cuda.synchronize()
+        self._version += 1
         return dict(loss=hist.cpu().numpy(), steps=steps, ms=e0.elapsed_time(e1))
 
     def predict(self, x0: torch.Tensor, c: torch.Tensor) -> torch.Tensor:
-        self.net.set_draws(x0, c)
-        return self.net.predict(0, x0.shape[0])
+        net = self.net
+        if self._infer_args["batch"] > self.net.batch:
+            if self._infer is None:
+                self._infer = StoWarm(self.tree, self.system.nx, self.system.nu, **self._infer_args)
+            if self._infer_version != self._version:
+                self._infer.set_params(self.net.params())
+                self._infer_version = self._version
+            net = self._infer
+        net.set_draws(x0, c)
+        return net.predict(0, x0.shape[0])
 
 
 class EvalSet:
