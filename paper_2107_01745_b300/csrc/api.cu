@@ -319,6 +319,9 @@ sto_status stotree_create(const sto_tree_desc *t, int32_t precision, stotree_t *
     if (cudaMallocHost(&h->host_scal, sizeof(SolverScalars)) != cudaSuccess) {
         h->host_scal = new SolverScalars();
     }
+    if (cudaMallocHost(&h->host_scal2, sizeof(SolverScalars)) != cudaSuccess) {
+        h->host_scal2 = new SolverScalars();
+    }
     *out = h;
     return STO_OK;
 }
@@ -328,6 +331,9 @@ void stotree_destroy(stotree_t h) {
     for (auto e : h->ev_pool) cudaEventDestroy(e);
     if (h->host_scal) {
         if (cudaFreeHost(h->host_scal) != cudaSuccess) delete h->host_scal;
+    }
+    if (h->host_scal2) {
+        if (cudaFreeHost(h->host_scal2) != cudaSuccess) delete h->host_scal2;
     }
     delete h;
 }

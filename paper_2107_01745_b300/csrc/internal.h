@@ -124,6 +124,7 @@ struct stotree_s {
     int grid_ctas[5] = {0, 0, 0, 0, 0};  // CTAs of the persistent solve kernel, per nrhs
     // pinned host mirror of the device scalars
     sto::SolverScalars *host_scal = nullptr;
+    sto::SolverScalars *host_scal2 = nullptr;  // second header buffer (GPAD look-ahead)
 
     template <class T>
     T *at(size_t off) const { return reinterpret_cast<T *>(ws + off); }

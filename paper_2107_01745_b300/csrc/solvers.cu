@@ -857,8 +857,10 @@ __global__ void __launch_bounds__(kThreads) k_fbstep(DualView<T> dv, T *yb, cons
 // ||S^-1 r||_inf are reduced for the stopping test, which the host applies to w.
 template <class T, bool G>
 __global__ void __launch_bounds__(kThreads) k_gpad(DualView<T> dv, const T *__restrict__ w, const T *__restrict__ h,
-                                                   T *yb, T *wn, T beta, SolverScalars *sc, double *partials) {
+                                                   T *yb, T *wn, T beta, int it, int max_iter, SolverScalars *sc,
+                                                   double *partials) {
     __shared__ double tot[3];
+    if (sc->status) return;  // an earlier step stopped the run: this (look-ahead) step does nothing
     extern __shared__ __align__(16) unsigned char tab_raw[];
     CompTab<T> tab;
     tab.load(dv, reinterpret_cast<T *>(tab_raw));
@@ -903,6 +905,8 @@ __global__ void __launch_bounds__(kThreads) k_gpad(DualView<T> dv, const T *__re
         sc->phi = -tot[0];
         sc->res_inf = tot[2];
         if (tot[1] > 0.0 || !(tot[0] == tot[0])) sc->nan_flag = 1;
+        // stop: converged at w, NaN, or the iteration cap (the host returns w of this step)
+        if (sc->nan_flag || tot[2] <= sc->tol || it >= max_iter) sc->status = 1;
     }
 }
 
@@ -1288,7 +1292,6 @@ sto_status gpad_impl(stotree_t h, const sto_opts *o, const void *x0v, void *yv, 
     STO_CUDA(h, cudaEventCreate(&e0));
     STO_CUDA(h, cudaEventCreate(&e1));
     STO_CUDA(h, cudaEventRecord(e0, st));
-    const int64_t calls0 = h->solve_calls;
     const int64_t launches0 = h->launches;
 
     SolverScalars *hs = h->host_scal;
@@ -1302,38 +1305,61 @@ sto_status gpad_impl(stotree_t h, const sto_opts *o, const void *x0v, void *yv, 
     k_scale_in<T><<<grid, kThreads, 0, st>>>(dv, static_cast<const T *>(yv), yb);
     STO_CUDA(h, cudaMemcpyAsync(w, yb, (size_t)dv.m * sizeof(T), cudaMemcpyDeviceToDevice, st));
     h->launches += 1;
+    // One step of look-ahead: step k + 1 is enqueued before the host reads step k's residual,
+    // so the GPU does not idle on the host's decision.  w and S H x(w) alternate between two
+    // buffers; once a step stops the run (device flag), the look-ahead step leaves the
+    // buffers of the stopped step alone.
+    T *wb[2] = {w, wn}, *hb[2] = {hv, V + 11 * vs};
+    SolverScalars *hbuf[2] = {hs, h->host_scal2};
+    cudaEvent_t ev[2];
+    STO_CUDA(h, cudaEventCreateWithFlags(&ev[0], cudaEventDisableTiming));
+    STO_CUDA(h, cudaEventCreateWithFlags(&ev[1], cudaEventDisableTiming));
     double theta = 1.0;
-    sto_status result = STO_OK;
-    int iters = 0;
-    while (true) {
-        const void *ys[1] = {w};
-        void *hs_[1] = {hv};
-        const sto_status s = solve_round(h, ys, x0v, hs_, 1, false, true, st);
-        if (s != STO_OK) return s;
+    auto enqueue = [&](int k) -> sto_status {
         const double theta_next = 0.5 * (std::sqrt(theta * theta * theta * theta + 4.0 * theta * theta) - theta * theta);
         const T beta = (T)(theta_next * (1.0 / theta - 1.0));
+        theta = theta_next;
+        const void *ys[1] = {wb[k & 1]};
+        void *hs_[1] = {hb[k & 1]};
+        const sto_status s = solve_round(h, ys, x0v, hs_, 1, false, true, st);
+        if (s != STO_OK) return s;
         if (h->general)
-            k_gpad<T, true><<<grid, kThreads, tabb, st>>>(dv, w, hv, yb, wn, beta, sc, part);
+            k_gpad<T, true><<<grid, kThreads, tabb, st>>>(dv, wb[k & 1], hb[k & 1], yb, wb[(k + 1) & 1], beta, k,
+                                                          o->max_iter, sc, part);
         else
-            k_gpad<T, false><<<grid, kThreads, tabb, st>>>(dv, w, hv, yb, wn, beta, sc, part);
+            k_gpad<T, false><<<grid, kThreads, tabb, st>>>(dv, wb[k & 1], hb[k & 1], yb, wb[(k + 1) & 1], beta, k,
+                                                           o->max_iter, sc, part);
         h->launches += 1;
         STO_CUDA(h, cudaGetLastError());
-        STO_CUDA(h, cudaMemcpyAsync(hs, sc, kScalHead, cudaMemcpyDeviceToHost, st));
-        STO_CUDA(h, cudaStreamSynchronize(st));
-        if (hs->nan_flag) {
+        STO_CUDA(h, cudaMemcpyAsync(hbuf[k & 1], sc, kScalHead, cudaMemcpyDeviceToHost, st));
+        STO_CUDA(h, cudaEventRecord(ev[k & 1], st));
+        return STO_OK;
+    };
+    sto_status result = STO_OK;
+    int iters = 0;
+    sto_status s = enqueue(0);
+    while (s == STO_OK) {
+        if (iters + 1 <= o->max_iter && (s = enqueue(iters + 1)) != STO_OK) break;
+        STO_CUDA(h, cudaEventSynchronize(ev[iters & 1]));
+        const SolverScalars *hk = hbuf[iters & 1];
+        if (hk->nan_flag) {
             result = STO_ERR_NUMERICAL;
             h->err = "NaN or Inf in the residual";
             break;
         }
-        if (hs->res_inf <= o->tol) break;
+        if (hk->res_inf <= o->tol) break;
         if (iters >= o->max_iter) {
             result = STO_NOT_CONVERGED;
             break;
         }
-        std::swap(w, wn);
-        theta = theta_next;
         ++iters;
     }
+    cudaEventDestroy(ev[0]);
+    cudaEventDestroy(ev[1]);
+    if (s != STO_OK) return s;
+    const double res_final = hbuf[iters & 1]->res_inf, phi_final = hbuf[iters & 1]->phi;
+    w = wb[iters & 1];
+    hv = hb[iters & 1];
     h->launches += 1;
     k_finish_out<T><<<grid, kThreads, 0, st>>>(dv, w, hv, sc, static_cast<T *>(yv), static_cast<T *>(zv),
                                                static_cast<T *>(xv), static_cast<T *>(uv));
@@ -1351,11 +1377,11 @@ sto_status gpad_impl(stotree_t h, const sto_opts *o, const void *x0v, void *yv, 
     cudaEventDestroy(e1);
     if (info) {
         info->iters = iters;
-        info->solve_calls = (int32_t)(h->solve_calls - calls0);
+        info->solve_calls = iters + 1;  // the look-ahead solve is not one of the method's calls
         info->status = result;
         info->ls_zero = 0;
-        info->res_inf = hs->res_inf;
-        info->fbe = hs->phi;
+        info->res_inf = res_final;
+        info->fbe = phi_final;
         info->ms = ms;
         info->launches = (int32_t)(h->launches - launches0);
         info->halvings = 0;
