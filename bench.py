@@ -9,6 +9,12 @@ timed beside it.  The solve rounds (Algorithm 3/4) are timed inside the library 
 events on the launching stream for the roofline line.
 
     python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
+                    [--warm-train-draws D] [--warm-eval-draws E] [--spring-mass 0|1]
+                    [--profile nama|minfbe|batched|warm]
+
+Beside the headline the line carries the batched workload (512 instances), the learned warm
+start (training, inference, warm vs cold), the factor, GPAD (warm start and to tolerance), the
+step-size backtracking rules, soft state bounds and the spring-mass experiment of Section IV-A.
 
 Under torchrun each rank solves its own replica of the instance (independent problems, no
 collective on the data path; scaling "weak"); rank 0 prints one JSON line.
