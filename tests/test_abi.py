@@ -89,3 +89,12 @@ def test_create_rejects_bad_sizes(libso):
     assert _create(libso, t.parent, t.prob, nx=400, nu=200)[0] == 1
     assert _create(libso, t.parent, t.prob, nx=200, nu=100, prec=0)[0] == 1
     assert _create(libso, t.parent, t.prob, nx=200, nu=100, prec=1)[0] == 0
+
+
+def test_missing_library_fails_loudly(monkeypatch):
+    """No silent fallback: without the built library the binding raises before any work."""
+    import paper_2107_01745_b300.stotree as S
+    monkeypatch.setattr(S, "LIB_PATH", "/nonexistent/libstotree.so")
+    monkeypatch.setattr(S, "_lib", None)
+    with pytest.raises(RuntimeError, match="missing"):
+        S.lib()
