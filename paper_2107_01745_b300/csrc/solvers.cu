@@ -6,9 +6,9 @@
 // block order and takes the algorithm's decision on the device):
 //   k_point   z = proj_{SY}(h + ybar/lam), r = z - h, FBE, ||S^-1 r||_inf          (Section II-D, III-A)
 //   k_grad    g = r + lam S H x_lin(r) = grad FBE                                  (Section III-A)
-//   k_lb_dots / k_lb_dir   L-BFGS direction d = -B g, compact form               (Alg. 1 line 3, Alg. 2 line 5)
-//   k_ls      FBE at up to 19 step sizes tau = 2^-k in one pass                    (Alg. 1 line 4, Alg. 2 line 6)
-//   k_fbstep  ybar+ = T_lam(w), s = ybar+ - ybar                                   (Alg. 1 line 5, Alg. 2 lines 7-8)
+//   k_lb_dots / k_lb_dir   L-BFGS direction d = -B g, compact form               (Alg. 1, 2: quasi-Newton direction)
+//   k_ls      FBE at up to 19 step sizes tau = 2^-k in one pass                    (Alg. 1, 2: line search)
+//   k_fbstep  ybar+ = T_lam(w), s = ybar+ - ybar                                   (Alg. 1, 2: forward-backward update)
 //   k_gpad    GPAD step ybar+ = T_lam(w), next extrapolated point                 (Section III-F, Section IV)
 //
 // Readings of the text used here:
@@ -24,7 +24,7 @@
 //     entries of S Hx.  The line search sums the per-entry change against the current point.
 //   * Termination uses the unscaled residual ||z - Hx||_inf (Section III-B).
 //   * L-BFGS: H0 = gamma I with gamma = <s,q>/<q,q> of the newest pair, lam I while empty;
-//     pairs are kept when <s,q> > eps' ||s||^2 ||g||^2 (Alg. 1 line 7, Alg. 2 line 10).
+//     pairs are kept when <s,q> > eps' ||s||^2 ||g||^2 (Algorithms 1, 2: the curvature test).
 #include <cmath>
 #include <cstring>
 #include <utility>

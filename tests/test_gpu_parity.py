@@ -186,6 +186,77 @@ BT_BOXED = [D.boxed_problem(12, horizon=3, nx=3, nu=2), D.boxed_problem(17, hori
             D.boxed_problem(16, horizon=3, nx=5, nu=3, frac=0.9)]
 
 
+@pytest.mark.parametrize("method", ["nama", "minfbe"])
+@pytest.mark.parametrize("p", BT_BOXED, ids=lambda p: f"{p.name}-nx{p.nx}")
+def test_solver_fp64_follows_oracle_iterates(cuda_device, p, method):
+    """FP64 Algorithms 1 and 2 with a fixed step on problems whose box binds: after K
+    iterations the GPU's iterate, its proximal point z, the primal x(y), the residual and the
+    FBE value equal the oracle's after K iterations, so every iteration's L-BFGS direction,
+    line-search step and forward-backward step match one at a time.  Over these first ten
+    iterations every FBE comparison of the line search is decided by a margin of at least
+    7e-9 relative, far above FP64 rounding."""
+    o = O.LQOracle(p)
+    lam, _ = O.power_lambda(o, np.random.default_rng(0).standard_normal(o.m))
+    fn = O.nama if method == "nama" else O.minfbe
+    st = _st()(p, precision="fp64")
+    st.factor()
+    for K in (0, 1, 2, 3, 5, 10):
+        ref = fn(o, lam, tol=0.0, max_iter=K)
+        assert ref["iters"] == K and ref["status"] == "not_converged"
+        res = st.solve(method, lam, tol=1e-300, max_iter=K, allow_not_converged=True)
+        info = res["info"]
+        assert info["status"] == 7 and info["iters"] == K
+        assert _relinf(res["y"].cpu().numpy(), ref["y"]) < 1e-9, K
+        assert _relinf(res["z"].cpu().numpy(), ref["z"]) < 1e-9, K
+        assert _relinf(res["x"].cpu().numpy(), ref["x"]) < 1e-9, K
+        assert _relinf(res["u"].cpu().numpy(), ref["u"]) < 1e-9, K
+        assert abs(info["res_inf"] - ref["res_inf"]) <= 1e-9 * max(1.0, ref["res_inf"]), K
+        assert abs(info["fbe"] - ref["phi"][-1]) <= 1e-10 * max(1.0, abs(ref["phi"][-1])), K
+
+
+@pytest.mark.parametrize("method", ["nama", "minfbe"])
+@pytest.mark.parametrize("p", BT_BOXED, ids=lambda p: f"{p.name}-nx{p.nx}")
+def test_solver_fp64_binding_box_to_tolerance(cuda_device, p, method):
+    """The same runs to 1e-10: the solution is the oracle's to 1e-8 with certified KKT
+    conditions.  The iterates agree to rounding until the residual nears the tolerance, where
+    FBE comparisons at rounding level can go either way, so the counts may differ by a few."""
+    o = O.LQOracle(p)
+    lam, _ = O.power_lambda(o, np.random.default_rng(0).standard_normal(o.m))
+    ref = (O.nama if method == "nama" else O.minfbe)(o, lam, tol=1e-10, max_iter=2000)
+    assert ref["status"] == "converged"
+    st = _st()(p, precision="fp64")
+    st.factor()
+    res = st.solve(method, lam, tol=1e-10, max_iter=2000)
+    info = res["info"]
+    assert info["status"] == 0 and info["res_inf"] <= 1e-10
+    assert abs(info["iters"] - ref["iters"]) <= max(6, ref["iters"] // 5)
+    assert _relinf(res["x"].cpu().numpy(), ref["x"]) < 1e-8
+    assert _relinf(res["u"].cpu().numpy(), ref["u"]) < 1e-8
+    assert _relinf(res["y"].cpu().numpy(), ref["y"]) < 1e-7
+    kkt = st.kkt_check(st.to_dev(p.x0), res["x"], res["u"], res["y"], tol_active=1e-7)
+    assert kkt["dynamics"] < 1e-12 and kkt["stationarity"] < 1e-9
+    assert kkt["feasibility"] < 1e-9 and kkt["sign"] < 1e-7
+
+
+@pytest.mark.parametrize("prec,tol", [("fp64", 1e-12), ("fp32", 2e-5)])
+@pytest.mark.parametrize("p", BT_BOXED, ids=lambda p: f"{p.name}-nx{p.nx}")
+def test_prox_and_fbe_at_a_point_hard_box(cuda_device, p, prec, tol):
+    """Zero iterations from a given y with the hard box (the indicator g of Section II-B):
+    z_lambda(y) and phi_lambda(y) as the oracle computes them."""
+    o = O.LQOracle(p)
+    st = _st()(p, precision=prec)
+    st.factor()
+    rng = np.random.default_rng(9)
+    for lam in (0.05, 0.4):
+        y = rng.standard_normal(o.m) * rng.choice([0.05, 3.0], o.m)
+        y[:p.nx] = 0.0
+        pt = O.fb_point(o, y / o.sq, lam)
+        res = st.solve("nama", lam, y0=st.to_dev(y), tol=1e-300, max_iter=0, allow_not_converged=True)
+        assert _relinf(res["z"].double().cpu().numpy(), pt["z"] / o.sq) < tol
+        assert abs(res["info"]["fbe"] - pt["phi"]) <= tol * max(1.0, abs(pt["phi"])) * 10
+        assert abs(res["info"]["res_inf"] - pt["res_inf"]) <= tol * max(1.0, pt["res_inf"]) * 10
+
+
 @pytest.mark.parametrize("rule,param", [("original", 0.1), ("simple", 0.25)])
 @pytest.mark.parametrize("method", ["nama", "minfbe"])
 @pytest.mark.parametrize("p", BT_BOXED, ids=lambda p: f"{p.name}-nx{p.nx}")
