@@ -151,11 +151,11 @@ enum Epi { EPI_F32 = 0, EPI_GELU = 1, EPI_OUT = 2, EPI_DGELU = 3, EPI_PART = 4, 
 struct EpiArgs {
     int M, N;                     // valid rows / columns (EPI_F32)
     const float *bias;            // [N] (GELU, OUT, PRED)
-    float *C;                     // FP32 output: EPI_F32 [M][ldc]; EPI_PART [split][.][ldc]; GELU: Z; OUT: Y
+    float *C;                     // FP32 output: EPI_F32 [M][ldc]; EPI_PART [split][.][ldc]; GELU: Z (or null); OUT: Y
     long long ldc, split_stride;
     __nv_bfloat16 *A;             // BF16 row-major copy (GELU: activation, OUT: dY, DGELU: dZ), may be null
     long long lda;
-    __nv_bfloat16 *AT;            // BF16 transposed copy [col][ldat]
+    __nv_bfloat16 *AT;            // BF16 transposed copy [col][ldat] (GELU: may be null)
     long long ldat;
     const float *Zin;             // DGELU: pre-activation, row-major [row][ldzin]
     long long ldzin;
@@ -249,7 +249,7 @@ __global__ void __launch_bounds__(kThreads, 1)
 #pragma unroll
                 for (int j = 0; j < 16; j += 4) *reinterpret_cast<float4 *>(dst + j) = make_float4(v[j], v[j + 1], v[j + 2], v[j + 3]);
             } else if (EPI == EPI_GELU) {
-                float *z = ep.C + (long long)row * ep.ldc + nb;
+                // Z and the transposed copy feed only the backward pass: null when predicting
                 __align__(16) __nv_bfloat16 a[16];
 #pragma unroll
                 for (int j = 0; j < 16; ++j) {
@@ -257,13 +257,18 @@ __global__ void __launch_bounds__(kThreads, 1)
                     v[j] = zz;
                     a[j] = __float2bfloat16_rn(gelu_f(zz));
                 }
+                if (ep.C) {
+                    float *z = ep.C + (long long)row * ep.ldc + nb;
 #pragma unroll
-                for (int j = 0; j < 16; j += 4) *reinterpret_cast<float4 *>(z + j) = make_float4(v[j], v[j + 1], v[j + 2], v[j + 3]);
+                    for (int j = 0; j < 16; j += 4)
+                        *reinterpret_cast<float4 *>(z + j) = make_float4(v[j], v[j + 1], v[j + 2], v[j + 3]);
+                }
                 uint4 *ad = reinterpret_cast<uint4 *>(ep.A + (long long)row * ep.lda + nb);
                 ad[0] = reinterpret_cast<uint4 *>(a)[0];
                 ad[1] = reinterpret_cast<uint4 *>(a)[1];
+                if (ep.AT)
 #pragma unroll
-                for (int j = 0; j < 16; ++j) ep.AT[(long long)(nb + j) * ep.ldat + row] = a[j];
+                    for (int j = 0; j < 16; ++j) ep.AT[(long long)(nb + j) * ep.ldat + row] = a[j];
             } else if (EPI == EPI_DGELU) {
                 const float *z = ep.Zin + (long long)row * ep.ldzin + nb;
                 __align__(16) __nv_bfloat16 d[16];
@@ -422,10 +427,11 @@ __host__ __device__ inline long long w3_off(const NetDev &n) { return b2_off(n) 
 __host__ __device__ inline long long b3_off(const NetDev &n) { return w3_off(n) + (long long)n.DO * n.H; }
 __host__ __device__ inline long long nparam_padded(const NetDev &n) { return b3_off(n) + n.DO; }
 
-// Batch rows of (draw, node) samples: features, target and valid count; one warp per row, 32
-// rows per block, the transposed copy staged in shared memory so both copies are written in
-// contiguous runs.  mode 0: training sample from the permutation of the current epoch; mode 1:
-// sample index base + b (prediction).  Past the end of the samples a row is zeros, nvalid 0.
+// Batch rows of (draw, node) samples: features, target and valid count; one warp per row, 16
+// rows per block, the transposed copy (training only) staged in shared memory so both copies
+// are written in contiguous runs.  mode 0: training sample from the permutation of the current
+// epoch; mode 1: sample index base + b (prediction).  Past the end of the samples a row is
+// zeros, nvalid 0.
 constexpr int kGatherRows = 16;
 __global__ void __launch_bounds__(256) k_gather(NetDev n, const float *x0, const float *c, const float *y,
                                                 long long num_samples, long long base, long long steps_per_epoch,
@@ -474,7 +480,7 @@ __global__ void __launch_bounds__(256) k_gather(NetDev n, const float *x0, const
                 }
                 const __nv_bfloat16 bv = __float2bfloat16_rn(v);
                 n.X[(long long)b * n.D0 + f] = bv;
-                tile[f][rr] = bv;
+                if (mode == 0) tile[f][rr] = bv;
             }
             if (y)
                 for (int k = lane; k < n.DO; k += 32)
@@ -482,7 +488,7 @@ __global__ void __launch_bounds__(256) k_gather(NetDev n, const float *x0, const
         } else {
             for (int f = lane; f < n.D0; f += 32) {
                 n.X[(long long)b * n.D0 + f] = __float2bfloat16_rn(0.f);
-                tile[f][rr] = __float2bfloat16_rn(0.f);
+                if (mode == 0) tile[f][rr] = __float2bfloat16_rn(0.f);
             }
             for (int k = lane; k < n.DO; k += 32) n.T[(long long)b * n.DO + k] = 0.f;
         }
@@ -494,10 +500,12 @@ __global__ void __launch_bounds__(256) k_gather(NetDev n, const float *x0, const
         }
     }
     __syncthreads();
-    for (int e = threadIdx.x; e < n.D0 * kGatherRows; e += blockDim.x) {
-        const int f = e / kGatherRows, rr = e % kGatherRows;
-        n.XT[(long long)f * n.B + b0 + rr] = tile[f][rr];
-    }
+    // the transposed copy feeds only the first layer's weight gradient: training batches only
+    if (mode == 0)
+        for (int e = threadIdx.x; e < n.D0 * kGatherRows; e += blockDim.x) {
+            const int f = e / kGatherRows, rr = e % kGatherRows;
+            n.XT[(long long)f * n.B + b0 + rr] = tile[f][rr];
+        }
     if (threadIdx.x == 0) atomicAdd(n.count, cnt);   // integer sums: order-independent
 }
 
@@ -784,18 +792,19 @@ EpiArgs epi0(stowarm_t h) {
 sto_status run_net(stowarm_t h, bool train, bool predict, float *yout, cudaStream_t st) {
     NetDev &n = h->n;
     EpiArgs e = epi0(h);
+    // a prediction keeps only the BF16 activations the next layer reads
     e.bias = n.W + b1_off(n);
-    e.C = n.Z1;
+    e.C = predict ? nullptr : n.Z1;
     e.ldc = n.H;
     e.A = n.A1;
     e.lda = n.H;
-    e.AT = n.A1T;
+    e.AT = predict ? nullptr : n.A1T;
     e.ldat = n.B;
     WCUDA(h, run_gemm<EPI_GELU>(h->g_l1, e, st));
     e.bias = n.W + b2_off(n);
-    e.C = n.Z2;
+    e.C = predict ? nullptr : n.Z2;
     e.A = n.A2;
-    e.AT = n.A2T;
+    e.AT = predict ? nullptr : n.A2T;
     WCUDA(h, run_gemm<EPI_GELU>(h->g_l2, e, st));
     e = epi0(h);
     e.bias = n.W + b3_off(n);
