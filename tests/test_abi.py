@@ -98,3 +98,50 @@ def test_missing_library_fails_loudly(monkeypatch):
     monkeypatch.setattr(S, "_lib", None)
     with pytest.raises(RuntimeError, match="missing"):
         S.lib()
+
+
+def test_warm_create_validates_arguments(libso):
+    """stowarm_create refuses bad sizes and trees before touching the device."""
+    from paper_2107_01745_b300 import workloads as W
+    from paper_2107_01745_b300.stotree import _WarmDesc
+    t = W.tree_from_branching([2, 2])
+    parent = np.ascontiguousarray(t.parent, dtype=np.int32)
+    prob = np.ascontiguousarray(t.prob, dtype=np.float64)
+    bad = prob.copy()
+    bad[1] = 0.7  # children of the root no longer sum to 1
+
+    def create(**kw):
+        a = dict(num_nodes=len(parent), horizon=2, nx=3, nu=2, parent=parent.ctypes.data, prob=prob.ctypes.data,
+                 hidden=256, batch=8192, seed=0)
+        a.update(kw)
+        h = ctypes.c_void_p()
+        return libso.stowarm_create(ctypes.byref(_WarmDesc(**a)), ctypes.byref(h))
+
+    # hidden width not a whole number of 128-row tiles; batch outside [256, 65536] or not a
+    # multiple of the 256-row weight-gradient split; empty state; 4 nx + 1 features above 256
+    for kw in (dict(hidden=192), dict(batch=128), dict(batch=131072), dict(batch=8000), dict(nx=0),
+               dict(nx=64, nu=1), dict(parent=None)):
+        assert create(**kw) == 1, kw
+    assert create(prob=bad.ctypes.data) == 2
+
+
+def test_batch_create_validates_groups(libso):
+    """stobatch_create refuses groups outside the batched engine's shapes before touching the device."""
+    from paper_2107_01745_b300.stotree import _GroupDesc
+    nx, nu = 4, 2
+    arrs = dict(A=np.eye(nx), B=np.ones((nx, nu)), Q=np.ones(nx), R=np.ones(nu), PN=np.ones(nx),
+                xlo=-np.ones(nx), xhi=np.ones(nx), ulo=-np.ones(nu), uhi=np.ones(nu))
+
+    def create(n=1, **kw):
+        a = dict(horizon=3, branching=2, branch_stages=2, nx=nx, nu=nu, num_instances=2)
+        a.update({k: v.ctypes.data for k, v in arrs.items()})
+        a.update(kw)
+        g = (_GroupDesc * 1)(_GroupDesc(**a))
+        h = ctypes.c_void_p()
+        return libso.stobatch_create(g, n, ctypes.byref(h))
+
+    # nx <= 64, nu <= 32, horizon in [1, 64], branch_stages <= horizon, instances >= 1, data given
+    for kw in (dict(nx=0), dict(nx=65), dict(nu=33), dict(horizon=0), dict(horizon=65), dict(branch_stages=4),
+               dict(branching=0), dict(num_instances=0), dict(A=None), dict(uhi=None)):
+        assert create(**kw) == 1, kw
+    assert create(n=0) == 1
