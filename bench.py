@@ -10,7 +10,7 @@ events on the launching stream for the roofline line.
 
     python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
                     [--warm-train-draws D] [--warm-eval-draws E] [--spring-mass 0|1]
-                    [--profile nama|minfbe|batched|warm]
+                    [--profile nama|minfbe|batched|warm|infer]
 
 Beside the headline the line carries the batched workload (512 instances), the learned warm
 start (training, inference, warm vs cold), the factor, GPAD (warm start and to tolerance), the
@@ -609,6 +609,22 @@ def run_profile(method):
         torch.cuda.cudart().cudaProfilerStop()
         print(json.dumps({"profiled": method, "train_steps": 3, "loss": float(hist[-1])}))
         return
+    if method == "infer":
+        from paper_2107_01745_b300 import warmstart as WS
+        system = W.warm_start_system(4)
+        ev = W.warm_start_draws(system, W.WARM_EVAL_SEED, 500, dtype=np.float32)
+        x0 = torch.as_tensor(ev.x0, dtype=torch.float32, device="cuda")
+        c = torch.as_tensor(ev.c, dtype=torch.float32, device="cuda")
+        starter = WS.WarmStarter(system, hidden=256, batch=8192, seed=0)
+        starter.predict(x0, c)
+        torch.cuda.synchronize()
+        torch.cuda.cudart().cudaProfilerStart()
+        y = starter.predict(x0, c)
+        torch.cuda.synchronize()
+        torch.cuda.cudart().cudaProfilerStop()
+        print(json.dumps({"profiled": method, "draws": 500, "rows": 500 * system.tree().num_nodes,
+                          "outputs": int(y.numel())}))
+        return
     if method == "batched":
         sb = StoBatch(W.batched_uneven(3))
         sb.factor()
@@ -647,7 +663,7 @@ def main():
                     help="held-out draws the learned warm start is evaluated on")
     ap.add_argument("--spring-mass", type=int, default=1,
                     help="run the 300-problem spring-mass experiment of Section IV-A (0 skips it)")
-    ap.add_argument("--profile", choices=["nama", "minfbe", "batched", "warm"], default=None,
+    ap.add_argument("--profile", choices=["nama", "minfbe", "batched", "warm", "infer"], default=None,
                     help="run one solve inside a profiler range (no JSON benchmark line)")
     args = ap.parse_args()
     if args.profile:
