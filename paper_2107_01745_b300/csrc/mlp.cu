@@ -390,7 +390,8 @@ cudaError_t run_gemm(const Gemm &g, const EpiArgs &ep, cudaStream_t st) {
 // Warm-start network state and the non-GEMM kernels
 // ------------------------------------------------------------------------------------------
 struct NodeInfo {
-    int parent, stage, nvalid, pad;
+    int parent, stage, nvalid;
+    int grand;        // parent's parent when both are below the root, else -1 (feature gather)
     long long doff;   // first dual entry of the node
     float sq;         // sqrt(pi)
     float pad2;
@@ -465,7 +466,7 @@ __global__ void __launch_bounds__(256) k_gather(NetDev n, const float *x0, const
             sq = ni.sq;
             off = (d - (mode == 1 ? draw0 : 0)) * n.m + ni.doff;
             const int anc1 = i > 0 ? ni.parent : -1;
-            const int anc2 = anc1 > 0 ? n.nodes[anc1].parent : -1;
+            const int anc2 = ni.grand;  // stored, so no dependent load of the parent's record
             // features: x0 | t/N | c^i | c^anc | c^anc^2 (zeros for the root and missing ancestors)
             for (int f = lane; f < n.D0; f += 32) {
                 float v = 0.f;
@@ -899,7 +900,8 @@ STO_API sto_status stowarm_create(const sto_warm_desc *d, stowarm_t *out) {
         ni.parent = d->parent[i];
         ni.stage = stage[i];
         ni.nvalid = ccnt[i] > 0 ? d->nx + d->nu : d->nx;
-        ni.pad = 0;
+        const int par = d->parent[i];
+        ni.grand = (i > 0 && par > 0) ? d->parent[par] : -1;
         ni.doff = off;
         ni.sq = (float)std::sqrt(d->prob[i]);
         ni.pad2 = 0.f;
