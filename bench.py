@@ -87,14 +87,16 @@ class ClockSampler:
         self.gpu = gpu_index
         self.proc = None
         self.path = None
+        self._out = None
 
     def __enter__(self):
         fd, self.path = tempfile.mkstemp(suffix=".csv")
         os.close(fd)
+        self._out = open(self.path, "w")
         try:
             self.proc = subprocess.Popen(["nvidia-smi", f"--id={self.gpu}", f"--query-gpu={self.FIELDS}",
                                           "--format=csv,noheader,nounits", "-lms", "50"],
-                                         stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+                                         stdout=self._out, stderr=subprocess.DEVNULL)
         except OSError:
             self.proc = None
         # start timing only once the sampler is running (its first line is written)
@@ -112,6 +114,8 @@ class ClockSampler:
                 self.proc.wait(timeout=5)
             except subprocess.TimeoutExpired:
                 self.proc.kill()
+                self.proc.wait(timeout=5)
+        self._out.close()
 
     def summary(self):
         if not self.path or not os.path.exists(self.path):
