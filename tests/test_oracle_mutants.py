@@ -1,0 +1,223 @@
+"""Mutation check of the oracle's pins (CPU only).
+
+The pins in test_oracle_pins.py, test_gpad_oracle.py and test_penalty_oracle.py tie the
+oracle to facts outside it (dense KKT solves, closed forms, brute force, Riccati).  This
+file plants one plausible mistake at a time in a private copy of the oracle -- a dropped
+probability weight or factor 1/2, a flipped sign, a transposed operand, an overwritten
+child sum, the paper's garbled signs and extrapolation taken literally -- and checks that
+the unchanged pins reject every copy.  A mistake they let through is a gap in the pins.
+
+C mistakes go into a copy of stotree_oracle.c compiled into its own library, which the
+oracle module then calls; Python mistakes go into a copy of oracle.py executed as a
+separate module, which the pin modules then import in place of the real one.  Nothing
+here touches the installed oracle or the CUDA path, and each planted text must occur
+exactly once in the source, so an edit of the oracle that moves a line makes this file
+fail loudly instead of silently testing nothing.
+"""
+import ctypes
+import inspect
+import itertools
+import subprocess
+import types
+
+import numpy as np
+import pytest
+from _pytest.mark.structures import ParameterSet
+
+from oracle import oracle as O
+from tests import test_gpad_oracle, test_oracle_pins, test_penalty_oracle
+
+PIN_MODULES = [test_oracle_pins, test_gpad_oracle, test_penalty_oracle]
+
+# (id, mistake, text in the source, planted text)
+C_MUTANTS = [
+    ("leaf_P_no_pi", "leaf P^l without the probability pi^l",
+     "Pl[k * nx + k] = p->prob[l] * p->PN[k];", "Pl[k * nx + k] = p->PN[k];"),
+    ("Rbar_no_pi", "pi^i dropped from Rbar = pi R + sum B'PB",
+     "Rb[a * nu + a] = pi * p->R[a];", "Rb[a * nu + a] = p->R[a];"),
+    ("gu_no_half", "factor 1/2 dropped from the linear input cost in gu",
+     "gui[a] = 0.5 * pi * p->r[a];", "gui[a] = pi * p->r[a];"),
+    ("gx_no_pi", "pi^i dropped from the linear state cost in gx",
+     "gxi[a] = 0.5 * pi * p->q[a];", "gxi[a] = 0.5 * p->q[a];"),
+    ("M_transposed_PA", "M = sum B'(PA)' instead of B'PA",
+     "s += Bj[k * nu + a] * PA[k * nx + b];", "s += Bj[k * nu + a] * PA[b * nx + k];"),
+    ("K_sign", "K = +Rbar^-1 M",
+     "Ki[a * nx + b] = -sol[a];", "Ki[a * nx + b] = sol[a];"),
+    ("P_minus_MK", "P = pi Q + sum A'PA - M'K",
+     "s += M[k * nx + a] * Ki[k * nx + b];", "s -= M[k * nx + a] * Ki[k * nx + b];"),
+    ("chol_back_sub", "back substitution reads the (zero) upper triangle of L",
+     "for (int k = i + 1; k < n; ++k) s -= L[k * n + i] * x[k];",
+     "for (int k = i + 1; k < n; ++k) s -= L[i * n + k] * x[k];"),
+    ("leaf_s_no_half", "leaf s^l = y^l instead of y^l / 2",
+     "s[(size_t)l * nx + a] = 0.5 * yl[a] +", "s[(size_t)l * nx + a] = yl[a] +"),
+    ("leaf_s_pN_no_half", "leaf s^l with pi^l p_N instead of pi^l p_N / 2",
+     "0.5 * p->prob[l] * p->pN[a]", "p->prob[l] * p->pN[a]"),
+    ("v_no_half", "v^i = y_u^i + ... instead of y_u^i / 2 + ...",
+     "v[a] = 0.5 * yi[nx + a]", "v[a] = yi[nx + a]"),
+    ("child_sum_overwrites", "child sum assigned, not accumulated (Algorithm 3 read literally)",
+     "v[a] += acc;", "v[a] = acc;"),
+    ("backward_A_not_transposed", "backward child sum with A^j instead of A^j'",
+     "acc += Aj[k * nx + a] * sj[k];", "acc += Aj[a * nx + k] * sj[k];"),
+    ("backward_minus_Kv", "s^i with -K'v instead of +K'v",
+     "for (int k = 0; k < nu; ++k) acc += Ki[k * nx + a] * v[k];",
+     "for (int k = 0; k < nu; ++k) acc -= Ki[k * nx + a] * v[k];"),
+    ("ubar_sign", "ubar = +Rbar^-1 v",
+     "for (int a = 0; a < nu; ++a) ub[a] = -ub[a];", "for (int a = 0; a < nu; ++a) ub[a] = ub[a];"),
+    ("backward_skips_root", "backward loop stops before the root stage",
+     "for (int t = p->N - 1; t >= 0; --t) {\n        const int first = p->soff[t], last = p->soff[t + 1];\n"
+     "#pragma omp parallel for schedule(static)",
+     "for (int t = p->N - 1; t >= 1; --t) {\n        const int first = p->soff[t], last = p->soff[t + 1];\n"
+     "#pragma omp parallel for schedule(static)"),
+    ("forward_no_c", "disturbance c^j dropped from the rollout",
+     "double acc = homogeneous ? 0.0 : p->c[(size_t)j * nx + a];", "double acc = 0.0;"),
+    ("forward_open_loop_u", "rollout with ubar^i in place of u^i = K x + ubar",
+     "for (int k = 0; k < nu; ++k) acc += Bj[a * nu + k] * ui[k];",
+     "for (int k = 0; k < nu; ++k) acc += Bj[a * nu + k] * ubar[(size_t)i * nu + k];"),
+    ("forward_root_zero", "x^0 = 0 instead of p in Algorithm 3",
+     "for (int a = 0; a < nx; ++a) x[a] = homogeneous ? 0.0 : x0[a];",
+     "for (int a = 0; a < nx; ++a) x[a] = 0.0;"),
+    ("forward_skips_last_stage", "rollout stops one stage early (leaves never set)",
+     "for (int t = 0; t < p->N; ++t) {", "for (int t = 0; t < p->N - 1; ++t) {"),
+]
+
+PY_MUTANTS = [
+    ("proj_unscaled", "box projection on Y instead of the scaled box S Y",
+     "return np.minimum(np.maximum(v, o.sq * o.lo), o.sq * o.hi)",
+     "return np.minimum(np.maximum(v, o.lo), o.hi)"),
+    ("prox_unscaled", "z_lambda clamps v instead of v / sqrt(pi)",
+     "t = v / s\n", "t = v\n"),
+    ("residual_sign", "R = Hx - z instead of z - Hx",
+     "r = z - h\n", "r = h - z\n"),
+    ("T_sign", "T(y) = y + lam R (the sign of the forward-backward map taken literally)",
+     "T=yb - lam * r", "T=yb + lam * r"),
+    ("fbe_no_half", "FBE with lam ||Hx - z||^2 instead of lam / 2",
+     "0.5 * lam * float(np.dot(h - z, h - z))", "lam * float(np.dot(h - z, h - z))"),
+    ("fbe_no_g", "FBE without the g(z) term (matters for soft terms)",
+     "phi = -(f + g_val(o, z) +", "phi = -(f +"),
+    ("fbe_grad_sign", "grad phi = R - lam Hbar x_lin(R)",
+     'return pt["r"] + lam * hbar_lin(o, pt["r"])', 'return pt["r"] - lam * hbar_lin(o, pt["r"])'),
+    ("sigma_swapped", "support function with lo and hi swapped",
+     "out[pos] = hi[pos] * y[pos]\n    out[neg] = lo[neg] * y[neg]",
+     "out[pos] = lo[pos] * y[pos]\n    out[neg] = hi[neg] * y[neg]"),
+    ("huber_prox_threshold", "Huber prox switching at delta instead of delta (1 + a rho)",
+     "np.where(e <= o.delta * (1.0 + ar), e / (1.0 + ar), e - ar * o.delta)",
+     "np.where(e <= o.delta, e / (1.0 + ar), e - ar * o.delta)"),
+    ("lbfgs_gamma", "L-BFGS H0 = <s,q>/<s,s> I instead of <s,q>/<q,q> I",
+     "gamma = float(np.dot(s_new, y_new)) / float(np.dot(y_new, y_new))",
+     "gamma = float(np.dot(s_new, y_new)) / float(np.dot(s_new, s_new))"),
+    ("lbfgs_keeps_oldest", "L-BFGS memory drops the newest pair instead of the oldest",
+     "self.S.pop(0)\n            self.Y.pop(0)", "self.S.pop()\n            self.Y.pop()"),
+    ("lbfgs_alpha_order", "second loop of the two-loop recursion pairs the alphas in push order",
+     "zip(zip(self.S, self.Y, rhos), reversed(alphas))", "zip(zip(self.S, self.Y, rhos), alphas)"),
+    ("power_lambda_inverted", "step size lam = 0.9 L instead of 0.9 / L",
+     "return safety / L, L", "return safety * L, L"),
+    ("nama_literal_extrapolation", "NAMA's w = y + tau d + (1 - tau) R (Algorithm 2 read literally)",
+     'pt["y"] + tau * d + (1.0 - tau) * fb_dir', 'pt["y"] + tau * d + (1.0 - tau) * pt["r"]'),
+    ("gpad_theta_sign", "GPAD's theta recurrence with + theta^2",
+     "th_prev, th = th, 0.5 * (np.sqrt(th ** 4 + 4.0 * th * th) - th * th)",
+     "th_prev, th = th, 0.5 * (np.sqrt(th ** 4 + 4.0 * th * th) + th * th)"),
+    ("gpad_extrapolation_sign", "GPAD extrapolates backwards",
+     "(yb - y_prev)", "(y_prev - yb)"),
+]
+
+
+def _plant(src: str, old: str, new: str) -> str:
+    assert src.count(old) == 1, f"planted text must occur exactly once in the oracle: {old!r}"
+    return src.replace(old, new)
+
+
+def _cases(mod):
+    """(name, function, kwargs) for every pin of a module whose arguments all come from its
+    parametrize marks (pins that need fixtures are left out)."""
+    for name, fn in vars(mod).items():
+        if not name.startswith("test_") or not inspect.isfunction(fn):
+            continue
+        axes = []
+        for m in getattr(fn, "pytestmark", []):
+            if m.name != "parametrize":
+                continue
+            names = m.args[0]
+            names = [a.strip() for a in names.split(",")] if isinstance(names, str) else list(names)
+            axes.append((names, list(m.args[1])))
+        covered = {a for names, _ in axes for a in names}
+        if set(inspect.signature(fn).parameters) - covered:
+            continue
+        for combo in itertools.product(*[vals for _, vals in axes]):
+            kw = {}
+            for (names, _), v in zip(axes, combo):
+                vals = v.values if isinstance(v, ParameterSet) else (v if len(names) > 1 else (v,))
+                kw.update(zip(names, vals))
+            yield f"{mod.__name__.split('.')[-1]}::{name}", fn, kw
+
+
+ALL_CASES = [c for mod in PIN_MODULES for c in _cases(mod)]
+
+
+def _first_failing_pin():
+    """Run the pins in order; return the first that fails (or None).  Overflow in a diverging
+    copy is expected and not reported as a warning."""
+    for name, fn, kw in ALL_CASES:
+        try:
+            with np.errstate(over="ignore", invalid="ignore", divide="ignore"):
+                fn(**kw)
+        except pytest.skip.Exception:
+            continue
+        except Exception as e:  # an assertion, a refused factor, a non-finite value ...
+            return f"{name}({', '.join(f'{k}={getattr(v, 'name', v)}' for k, v in kw.items())}): {type(e).__name__}"
+    return None
+
+
+def _load_c(src: str, tmp_path) -> ctypes.CDLL:
+    c_file, so_file = tmp_path / "mutant.c", tmp_path / "libmutant.so"
+    c_file.write_text(src)
+    subprocess.check_call(["gcc", "-O2", "-fopenmp", "-fPIC", "-shared", "-std=c11",
+                           str(c_file), "-o", str(so_file), "-lm"])
+    lib = ctypes.CDLL(str(so_file))
+    lib.orc_factor.restype = ctypes.c_int
+    lib.orc_solve.restype = ctypes.c_int
+    lib.orc_num_threads.restype = ctypes.c_int
+    return lib
+
+
+def _load_py(src: str) -> types.ModuleType:
+    mod = types.ModuleType("oracle_mutant")
+    mod.__file__ = O.__file__
+    exec(compile(src, O.__file__, "exec"), mod.__dict__)
+    return mod
+
+
+def test_harness_collects_the_pins():
+    names = {n for n, _, _ in ALL_CASES}
+    assert len(ALL_CASES) >= 60 and len(names) >= 25
+
+
+def test_unmodified_copies_pass_every_pin(tmp_path, monkeypatch):
+    """The harness itself: a compiled copy of the C oracle and an executed copy of oracle.py,
+    both unmodified, pass every pin, so a failure below comes from the planted mistake."""
+    with open(O._SRC) as f:
+        lib = _load_c(f.read(), tmp_path)
+    with open(O.__file__) as f:
+        copy = _load_py(f.read())
+    copy._lib_handle = lib
+    for mod in PIN_MODULES:
+        monkeypatch.setattr(mod, "O", copy)
+    assert _first_failing_pin() is None
+
+
+@pytest.mark.parametrize("mid,what,old,new", C_MUTANTS, ids=[m[0] for m in C_MUTANTS])
+def test_pins_reject_planted_c_mistake(mid, what, old, new, tmp_path, monkeypatch):
+    with open(O._SRC) as f:
+        src = _plant(f.read(), old, new)
+    monkeypatch.setattr(O, "_lib_handle", _load_c(src, tmp_path))
+    caught = _first_failing_pin()
+    assert caught is not None, f"no pin rejects: {what}"
+
+
+@pytest.mark.parametrize("mid,what,old,new", PY_MUTANTS, ids=[m[0] for m in PY_MUTANTS])
+def test_pins_reject_planted_python_mistake(mid, what, old, new, monkeypatch):
+    with open(O.__file__) as f:
+        mutant = _load_py(_plant(f.read(), old, new))
+    for mod in PIN_MODULES:
+        monkeypatch.setattr(mod, "O", mutant)
+    caught = _first_failing_pin()
+    assert caught is not None, f"no pin rejects: {what}"

@@ -99,10 +99,15 @@ def test_hessian_symmetric_psd_and_dense(p):
     assert _rel(Hs, np.stack(cols, axis=1)) < 1e-10
 
 
-def test_prox_moreau_and_brute_force():
-    """prox_{lam g*} via Moreau equals the two-sided shrink and a scalar brute-force minimisation."""
-    p = W.random_problem(7, box_scale=0.5)
+@pytest.mark.parametrize("p_branch", [0.6, 1.0])
+def test_prox_moreau_and_brute_force(p_branch):
+    """prox_{lam g*} via Moreau equals the two-sided shrink and a scalar brute-force minimisation.
+    The box is the preconditioned S Y (Section III-E); with p_branch = 1 every node branches, so
+    sqrt(pi) < 1 below the root and a projection on the unscaled Y fails the identity."""
+    p = W.random_problem(7, box_scale=0.5, p_branch=p_branch)
     o = O.LQOracle(p)
+    if p_branch == 1.0:
+        assert np.min(o.sq) < 0.75
     lam = 0.7
     rng = np.random.default_rng(8)
     v = 3.0 * rng.standard_normal(o.m)
@@ -230,6 +235,24 @@ def test_solver_reaches_certified_qp_solution(solver, p):
     dual_val = O.fhat(o, yb) + O.g_conj(o, yb)
     primal_val = o.cost(res["x"], res["u"])
     assert abs(primal_val + dual_val) < 1e-7 * max(1.0, abs(primal_val))
+
+
+@pytest.mark.parametrize("p", BOXED[:1] + [D.boxed_problem(s, horizon=4, nx=3, nu=2) for s in (19, 26)],
+                         ids=lambda p: p.name)
+def test_nama_line_search_reaches_the_forward_backward_step(p):
+    """Algorithm 2's trial point w(tau) = ybar + tau d + (1 - tau)(T(ybar) - ybar) tends to the
+    forward-backward step T(ybar) as tau -> 0, and for lam < 1/L that step lowers the FBE by
+    at least (1 - lam L) lam / 2 ||R||^2 (Section III-A).  So while the residual is far from
+    zero some halving is accepted and the tau = 0 fallback is never used; reading the
+    extrapolation literally as ybar + tau d + (1 - tau) R makes the small trials approach
+    ybar + R instead, where the test can fail at every halving."""
+    o = O.LQOracle(p)
+    lam, _ = O.power_lambda(o, np.random.default_rng(0).standard_normal(o.m))
+    res = O.nama(o, lam, tol=1e-10, max_iter=500)
+    assert res["status"] == "converged"
+    taus, before = np.array(res["tau"]), np.array(res["res"][:-1])
+    assert np.any(taus < 1.0), "the line search never halves on this problem: no evidence"
+    assert not np.any((taus == 0.0) & (before > 1e-6))
 
 
 def test_loose_box_stops_at_iteration_zero():
