@@ -1,15 +1,17 @@
 """Mutation check of the oracle's pins (CPU only).
 
-The pins in test_oracle_pins.py, test_gpad_oracle.py and test_penalty_oracle.py tie the
-oracle to facts outside it (dense KKT solves, closed forms, brute force, Riccati).  This
+The pins in test_oracle_pins.py, test_gpad_oracle.py, test_penalty_oracle.py,
+test_mlp_oracle.py and test_stream_kkt.py tie the oracle to facts outside it (dense KKT
+solves, closed forms, brute force, Riccati, PyTorch's autograd, Adam and BF16 cast).  This
 file plants one plausible mistake at a time in a private copy of the oracle -- a dropped
 probability weight or factor 1/2, a flipped sign, a transposed operand, an overwritten
 child sum, the paper's garbled signs and extrapolation taken literally -- and checks that
 the unchanged pins reject every copy.  A mistake they let through is a gap in the pins.
 
 C mistakes go into a copy of stotree_oracle.c compiled into its own library, which the
-oracle module then calls; Python mistakes go into a copy of oracle.py executed as a
-separate module, which the pin modules then import in place of the real one.  Nothing
+oracle module then calls; Python mistakes go into a copy of oracle.py, mlp.py or
+stream_kkt.py executed as a separate module, which the pin modules then use in place of
+the real one.  Nothing
 here touches the installed oracle or the CUDA path, and each planted text must occur
 exactly once in the source, so an edit of the oracle that moves a line makes this file
 fail loudly instead of silently testing nothing.
@@ -24,10 +26,18 @@ import numpy as np
 import pytest
 from _pytest.mark.structures import ParameterSet
 
+from oracle import mlp as M
 from oracle import oracle as O
-from tests import test_gpad_oracle, test_oracle_pins, test_penalty_oracle
+from oracle import stream_kkt as SK
+from tests import test_gpad_oracle, test_mlp_oracle, test_oracle_pins, test_penalty_oracle, test_stream_kkt
 
 PIN_MODULES = [test_oracle_pins, test_gpad_oracle, test_penalty_oracle]
+# Python parts of the oracle: (module, the name the pin modules import it under, pin modules)
+TARGETS = {
+    "oracle": (O, "O", PIN_MODULES),
+    "mlp": (M, "M", [test_mlp_oracle]),
+    "stream": (SK, "SK", [test_stream_kkt]),
+}
 
 # (id, mistake, text in the source, planted text)
 C_MUTANTS = [
@@ -120,6 +130,49 @@ PY_MUTANTS = [
      "(yb - y_prev)", "(y_prev - yb)"),
 ]
 
+# the warm-start network (oracle/mlp.py) and the streamed optimality check (oracle/stream_kkt.py)
+MLP_MUTANTS = [
+    ("gelu_cubic_coefficient", "tanh-GELU cubic coefficient 0.0447 instead of 0.044715",
+     "GELU_A = 0.044715", "GELU_A = 0.0447"),
+    ("gelu_grad_chain", "GELU derivative without the factor 3 of the cubic term",
+     "(1.0 + 3.0 * GELU_A * z * z)", "(1.0 + GELU_A * z * z)"),
+    ("bf16_truncates", "BF16 storage by truncation instead of rounding",
+     "r = ((u + 0x7FFF + lsb) >> 16) << 16", "r = (u >> 16) << 16"),
+    ("bf16_ties_up", "BF16 ties rounded up instead of to even",
+     "r = ((u + 0x7FFF + lsb) >> 16) << 16", "r = ((u + 0x8000) >> 16) << 16"),
+    ("loss_unmasked", "loss over the padded outputs too",
+     'diff = (f["Y"] - T) * mask', 'diff = (f["Y"] - T)'),
+    ("loss_mean_over_all", "loss averaged over every output instead of the valid ones",
+     "count = mask.sum()", "count = float(mask.size)"),
+    ("grad_W2_transposed", "weight gradient of the hidden layer transposed",
+     'g["W2"] = dZ2.T @ f["A1"]', 'g["W2"] = f["A1"].T @ dZ2'),
+    ("backprop_W2_transposed", "data gradient through the hidden layer with W2' instead of W2",
+     'dA1 = dZ2 @ f["W2"]', 'dA1 = dZ2 @ f["W2"].T'),
+    ("adam_no_bias_correction", "Adam without the first moment's bias correction",
+     "mh = m / (1.0 - beta1 ** t)", "mh = m"),
+    ("adam_eps_inside_sqrt", "Adam with eps under the square root",
+     "(np.sqrt(vh) + eps)", "np.sqrt(vh + eps)"),
+    ("feature_stage_unscaled", "stage feature t instead of t / N",
+     "out[r, nx] = stage[i] / horizon", "out[r, nx] = stage[i]"),
+]
+
+STREAM_MUTANTS = [
+    ("leaf_multiplier_no_2", "leaf multiplier without the factor 2 of the quadratic cost",
+     "mu[j] = 2.0 * prob[j] * PN * x[j]", "mu[j] = prob[j] * PN * x[j]"),
+    ("child_A_not_transposed", "parents collect A^c mu^c instead of A^c' mu^c",
+     'np.add.at(accA, pp, np.einsum("nij,ni->nj", A, mu[b0:b1]))',
+     'np.add.at(accA, pp, np.einsum("nij,nj->ni", A, mu[b0:b1]))'),
+    ("dynamics_no_c", "dynamics residual without the disturbance",
+     "res = x[b0:b1] - ax - bu - hom * c", "res = x[b0:b1] - ax - bu"),
+    ("u_equation_no_r", "u equations without the linear input cost",
+     "+ prob[:npn, None] * r[None, :] + yu + accB", "+ yu + accB"),
+    ("root_not_checked", "the root state is not compared with the parameter",
+     "return {\"dynamics\": max(dyn_res, root_res)", "return {\"dynamics\": dyn_res"),
+]
+
+PY_ALL = ([("oracle",) + m for m in PY_MUTANTS] + [("mlp",) + m for m in MLP_MUTANTS]
+          + [("stream",) + m for m in STREAM_MUTANTS])
+
 
 def _plant(src: str, old: str, new: str) -> str:
     assert src.count(old) == 1, f"planted text must occur exactly once in the oracle: {old!r}"
@@ -151,12 +204,13 @@ def _cases(mod):
 
 
 ALL_CASES = [c for mod in PIN_MODULES for c in _cases(mod)]
+TARGET_CASES = {k: [c for mod in mods for c in _cases(mod)] for k, (_, _, mods) in TARGETS.items()}
 
 
-def _first_failing_pin():
+def _first_failing_pin(cases=ALL_CASES):
     """Run the pins in order; return the first that fails (or None).  Overflow in a diverging
     copy is expected and not reported as a warning."""
-    for name, fn, kw in ALL_CASES:
+    for name, fn, kw in cases:
         try:
             with np.errstate(over="ignore", invalid="ignore", divide="ignore"):
                 fn(**kw)
@@ -179,10 +233,10 @@ def _load_c(src: str, tmp_path) -> ctypes.CDLL:
     return lib
 
 
-def _load_py(src: str) -> types.ModuleType:
-    mod = types.ModuleType("oracle_mutant")
-    mod.__file__ = O.__file__
-    exec(compile(src, O.__file__, "exec"), mod.__dict__)
+def _load_py(src: str, like: types.ModuleType = O) -> types.ModuleType:
+    mod = types.ModuleType(like.__name__ + "_mutant")
+    mod.__file__ = like.__file__
+    exec(compile(src, like.__file__, "exec"), mod.__dict__)
     return mod
 
 
@@ -202,6 +256,13 @@ def test_unmodified_copies_pass_every_pin(tmp_path, monkeypatch):
     for mod in PIN_MODULES:
         monkeypatch.setattr(mod, "O", copy)
     assert _first_failing_pin() is None
+    for key in ("mlp", "stream"):
+        target, attr, mods = TARGETS[key]
+        with open(target.__file__) as f:
+            other = _load_py(f.read(), target)
+        for mod in mods:
+            monkeypatch.setattr(mod, attr, other)
+        assert _first_failing_pin(TARGET_CASES[key]) is None
 
 
 @pytest.mark.parametrize("mid,what,old,new", C_MUTANTS, ids=[m[0] for m in C_MUTANTS])
@@ -213,11 +274,12 @@ def test_pins_reject_planted_c_mistake(mid, what, old, new, tmp_path, monkeypatc
     assert caught is not None, f"no pin rejects: {what}"
 
 
-@pytest.mark.parametrize("mid,what,old,new", PY_MUTANTS, ids=[m[0] for m in PY_MUTANTS])
-def test_pins_reject_planted_python_mistake(mid, what, old, new, monkeypatch):
-    with open(O.__file__) as f:
-        mutant = _load_py(_plant(f.read(), old, new))
-    for mod in PIN_MODULES:
-        monkeypatch.setattr(mod, "O", mutant)
-    caught = _first_failing_pin()
+@pytest.mark.parametrize("key,mid,what,old,new", PY_ALL, ids=[f"{m[0]}-{m[1]}" for m in PY_ALL])
+def test_pins_reject_planted_python_mistake(key, mid, what, old, new, monkeypatch):
+    target, attr, mods = TARGETS[key]
+    with open(target.__file__) as f:
+        mutant = _load_py(_plant(f.read(), old, new), target)
+    for mod in mods:
+        monkeypatch.setattr(mod, attr, mutant)
+    caught = _first_failing_pin(TARGET_CASES[key])
     assert caught is not None, f"no pin rejects: {what}"

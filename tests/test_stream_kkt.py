@@ -1,6 +1,8 @@
 """Pins of the streamed optimality check (oracle/stream_kkt.py) and of the block-generated
 largest instance: the independent dense KKT solution has zero residuals, a perturbation shows
 up exactly where the equations say, and block generation is the same however it is sliced."""
+import copy
+
 import numpy as np
 import pytest
 
@@ -33,6 +35,28 @@ def test_perturbation_is_detected_where_it_enters():
     res = SK.solve_step_residuals(p, y, x, u2)
     assert abs(res["u_eq"] - 2.0 * p.tree.prob[i] * p.R[k] * delta) < 1e-12
     assert res["dynamics"] > 0.1 * delta * np.min(np.abs(p.B[p.tree.child_begin[i]][:, k]).max())
+
+
+@pytest.mark.parametrize("homogeneous", [False, True])
+def test_root_state_is_checked_against_the_parameter(homogeneous):
+    """x^0 is the parameter p (zero in Algorithm 4): a candidate whose root state is off by
+    delta while every other equation is rebuilt around it (the solve step of the changed
+    parameter) still violates x^0 = p by exactly delta."""
+    p = PROBLEMS[1]
+    y = W.random_dual(p, 6)
+    delta = 2.5e-3
+    shifted = copy.copy(p)
+    shifted.x0 = np.asarray(p.x0, dtype=float) + delta * (np.arange(p.nx) == 1)
+    if homogeneous:
+        # Algorithm 4 has x^0 = 0: the solution for x^0 = delta e_1 solves the inhomogeneous
+        # problem with c, q, r, p_N zero
+        shifted.c = np.zeros_like(p.c)
+        shifted.q, shifted.r, shifted.pN = np.zeros(p.nx), np.zeros(p.nu), np.zeros(p.nx)
+        shifted.x0 = delta * (np.arange(p.nx) == 1)
+    x, u = D.dense_solve(shifted, y)
+    res = SK.solve_step_residuals(p, y, x, u, homogeneous=homogeneous, block=3)
+    assert abs(res["dynamics"] - delta) < 1e-12
+    assert res["u_eq"] <= 1e-10 * max(1.0, res["u_scale"])
 
 
 def test_largest_blocks_are_slice_independent():
