@@ -1,7 +1,7 @@
 """Mutation check of the oracle's pins (CPU only).
 
 The pins in test_oracle_pins.py, test_gpad_oracle.py, test_penalty_oracle.py,
-test_mlp_oracle.py and test_stream_kkt.py tie the oracle to facts outside it (dense KKT
+test_backtrack_oracle.py, test_mlp_oracle.py and test_stream_kkt.py tie the oracle to facts outside it (dense KKT
 solves, closed forms, brute force, Riccati, PyTorch's autograd, Adam and BF16 cast).  This
 file plants one plausible mistake at a time in a private copy of the oracle -- a dropped
 probability weight or factor 1/2, a flipped sign, a transposed operand, an overwritten
@@ -29,9 +29,10 @@ from _pytest.mark.structures import ParameterSet
 from oracle import mlp as M
 from oracle import oracle as O
 from oracle import stream_kkt as SK
-from tests import test_gpad_oracle, test_mlp_oracle, test_oracle_pins, test_penalty_oracle, test_stream_kkt
+from tests import (test_backtrack_oracle, test_gpad_oracle, test_mlp_oracle, test_oracle_pins,
+                   test_penalty_oracle, test_stream_kkt)
 
-PIN_MODULES = [test_oracle_pins, test_gpad_oracle, test_penalty_oracle]
+PIN_MODULES = [test_oracle_pins, test_gpad_oracle, test_backtrack_oracle, test_penalty_oracle]
 # Python parts of the oracle: (module, the name the pin modules import it under, pin modules)
 TARGETS = {
     "oracle": (O, "O", PIN_MODULES),
@@ -128,6 +129,14 @@ PY_MUTANTS = [
      "th_prev, th = th, 0.5 * (np.sqrt(th ** 4 + 4.0 * th * th) + th * th)"),
     ("gpad_extrapolation_sign", "GPAD extrapolates backwards",
      "(yb - y_prev)", "(y_prev - yb)"),
+    ("original_rule_no_beta", "original backtracking test without the factor (1 - beta)",
+     "> (1.0 - beta) * float(np.dot(R, R))", "> float(np.dot(R, R))"),
+    ("original_rule_half_curvature", "original backtracking test with lam / 2 <R, grad^2 fhat R>",
+     "return lam * float(np.dot(R, HR)) >", "return 0.5 * lam * float(np.dot(R, HR)) >"),
+    ("simple_rule_no_lambda", "simple backtracking test without lam on the gradient difference",
+     'lhs = lam * float(np.linalg.norm(-hT + pt["h"]))', 'lhs = float(np.linalg.norm(-hT + pt["h"]))'),
+    ("halving_doubles", "NAMA's backtracking doubles lambda",
+     "nonlocal lam, pt\n        lam *= 0.5", "nonlocal lam, pt\n        lam *= 2.0"),
 ]
 
 # the warm-start network (oracle/mlp.py) and the streamed optimality check (oracle/stream_kkt.py)
@@ -179,9 +188,31 @@ def _plant(src: str, old: str, new: str) -> str:
     return src.replace(old, new)
 
 
+class _BacktrackCase:
+    """Stands for the module fixture `case` of test_backtrack_oracle.py (problem, oracle, L of
+    the dense Hessian), built when the pin runs so that its oracle is the copy under test."""
+    dense_L = {}
+
+    def __init__(self, idx):
+        self.idx = idx
+        self.name = test_backtrack_oracle.BOXED[idx].name
+
+    def build(self):
+        T = test_backtrack_oracle
+        p = T.BOXED[self.idx]
+        o = T.O.LQOracle(p)
+        assert T.O.fb_point(o, np.zeros(o.m), 0.1)["res_inf"] > 0.1
+        if self.idx not in self.dense_L:
+            self.dense_L[self.idx] = T._dense_L(p)
+        return p, o, self.dense_L[self.idx]
+
+
+FIXTURES = {(test_backtrack_oracle, "case"): [_BacktrackCase(i) for i in range(len(test_backtrack_oracle.BOXED))]}
+
+
 def _cases(mod):
     """(name, function, kwargs) for every pin of a module whose arguments all come from its
-    parametrize marks (pins that need fixtures are left out)."""
+    parametrize marks or from FIXTURES (other fixtures are left out)."""
     for name, fn in vars(mod).items():
         if not name.startswith("test_") or not inspect.isfunction(fn):
             continue
@@ -192,6 +223,9 @@ def _cases(mod):
             names = m.args[0]
             names = [a.strip() for a in names.split(",")] if isinstance(names, str) else list(names)
             axes.append((names, list(m.args[1])))
+        for arg in inspect.signature(fn).parameters:
+            if (mod, arg) in FIXTURES:
+                axes.append(([arg], FIXTURES[(mod, arg)]))
         covered = {a for names, _ in axes for a in names}
         if set(inspect.signature(fn).parameters) - covered:
             continue
@@ -213,7 +247,7 @@ def _first_failing_pin(cases=ALL_CASES):
     for name, fn, kw in cases:
         try:
             with np.errstate(over="ignore", invalid="ignore", divide="ignore"):
-                fn(**kw)
+                fn(**{k: v.build() if isinstance(v, _BacktrackCase) else v for k, v in kw.items()})
         except pytest.skip.Exception:
             continue
         except Exception as e:  # an assertion, a refused factor, a non-finite value ...
