@@ -145,3 +145,58 @@ def test_batch_create_validates_groups(libso):
                dict(branching=0), dict(num_instances=0), dict(A=None), dict(uhi=None)):
         assert create(**kw) == 1, kw
     assert create(n=0) == 1
+
+
+def test_noalloc_refusals_need_no_device(libso):
+    """stotree_solve_step_noalloc checks its arguments, its fixed scratch limit and the factor
+    before it looks up the scratch array, so these refusals come back on a host without a GPU.
+    The limit is the one its declaration states: s, ubar, x and u of one right-hand side
+    (each part rounded up to 256 bytes) plus the round's flags must fit 32 MiB.  On a star
+    tree (a root with K leaves, nx = 100, nu = 50, FP32) the largest K that fits is accepted
+    as far as the factor check, and K + 1 is refused with a message."""
+    L = libso
+    L.stotree_solve_step_noalloc.argtypes = [ctypes.c_void_p] * 4 + [ctypes.c_int32] * 2 + [ctypes.c_void_p]
+    L.stotree_last_error.argtypes = [ctypes.c_void_p]
+    L.stotree_last_error.restype = ctypes.c_char_p
+    L.stotree_destroy.argtypes = [ctypes.c_void_p]
+    fake = ctypes.c_void_p(4096)  # never dereferenced: each call below is refused first
+    nx, nu = 100, 50
+
+    def a256(v):
+        return (v + 255) // 256 * 256
+
+    def need(k):
+        nn = k + 1
+        return 2 * (a256(4 * nn * nx) + a256(4 * nu)) + a256(8 * nn) + 256
+
+    kmax = 1
+    while need(kmax + 1) <= 32 << 20:
+        kmax += 1
+
+    def star(k):
+        parent = np.zeros(k + 1, dtype=np.int32)
+        parent[0] = -1
+        prob = np.full(k + 1, 1.0 / k)
+        prob[0] = 1.0
+        d = _Desc(k + 1, 1, nx, nu, parent.ctypes.data, prob.ctypes.data)
+        h = ctypes.c_void_p()
+        assert L.stotree_create(ctypes.byref(d), 1, ctypes.byref(h)) == 0
+        return h
+
+    h = star(kmax)
+    try:
+        assert L.stotree_solve_step_noalloc(None, fake, fake, fake, 0, 0, None) == 1
+        assert L.stotree_solve_step_noalloc(h, None, fake, fake, 0, 0, None) == 1
+        assert L.stotree_solve_step_noalloc(h, fake, fake, None, 0, 0, None) == 1
+        assert L.stotree_solve_step_noalloc(h, fake, None, fake, 0, 0, None) == 1  # x0 needed
+        assert L.stotree_solve_step_noalloc(h, fake, None, fake, 1, 0, None) == 3  # not factored
+        assert L.stotree_solve_step_noalloc(h, fake, fake, fake, 0, 1, None) == 3
+    finally:
+        L.stotree_destroy(h)
+    h = star(kmax + 1)
+    try:
+        assert L.stotree_solve_step_noalloc(h, fake, fake, fake, 0, 0, None) == 1
+        msg = L.stotree_last_error(h)
+        assert b"scratch" in msg and str(need(kmax + 1)).encode() in msg
+    finally:
+        L.stotree_destroy(h)
