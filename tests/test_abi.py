@@ -200,3 +200,43 @@ def test_noalloc_refusals_need_no_device(libso):
         assert b"scratch" in msg and str(need(kmax + 1)).encode() in msg
     finally:
         L.stotree_destroy(h)
+
+
+_CTYPE_OF = {
+    "int32_t": ctypes.c_int32, "int64_t": ctypes.c_int64, "uint64_t": ctypes.c_uint64,
+    "size_t": ctypes.c_size_t, "double": ctypes.c_double, "float": ctypes.c_float, "sto_status": ctypes.c_int,
+}
+_HANDLES = {"stotree_t", "stobatch_t", "stowarm_t", "sto_stream_t"}
+
+
+def _expected_ctype(ctype: str):
+    ctype = ctype.replace("const ", "").strip()
+    if ctype.endswith("*") or ctype in _HANDLES:
+        return ctypes.c_void_p
+    return _CTYPE_OF[ctype]
+
+
+def test_binding_prototypes_match_the_header():
+    """Every entry point declared in include/stotree.h has a ctypes prototype in the binding with
+    the same number of arguments, each of the declared width and kind, and the declared result
+    type.  Without one, ctypes would pass a 64-bit pointer as a 32-bit int, or a float as a
+    double, and the call would read shifted or truncated arguments."""
+    from paper_2107_01745_b300 import stotree
+    L = stotree.lib()
+    src = open(os.path.join(ROOT, "include", "stotree.h")).read()
+    decls = re.findall(r"STO_API\s+([^;]*?)\b(sto(?:tree|batch|warm)_\w+)\s*\(([^)]*)\)\s*;", src, re.S)
+    assert len(decls) == len(_declared())
+    for ret, name, params in decls:
+        fn = getattr(L, name)
+        params = " ".join(params.split())
+        decl = [p.strip() for p in params.split(",") if p.strip() and p.strip() != "void"]
+        want = [_expected_ctype(re.match(r"(.*?)\w+$", p).group(1)) for p in decl]
+        assert fn.argtypes is not None, f"{name}: no prototype"
+        assert len(fn.argtypes) == len(want), f"{name}: {len(fn.argtypes)} arguments bound, {len(want)} declared"
+        for k, (got, exp) in enumerate(zip(fn.argtypes, want)):
+            assert got is exp or (exp is ctypes.c_void_p and got is ctypes.c_char_p), f"{name} argument {k}: {got} vs {exp}"
+        ret = " ".join(ret.split())
+        want_ret = {"void": None, "const char *": ctypes.c_char_p}.get(ret, ctypes.c_int)
+        if ret == "sto_status":
+            want_ret = ctypes.c_int
+        assert fn.restype is want_ret, f"{name}: result {fn.restype} vs {ret}"
