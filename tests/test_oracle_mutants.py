@@ -24,7 +24,6 @@ import types
 
 import numpy as np
 import pytest
-from _pytest.mark.structures import ParameterSet
 
 from oracle import mlp as M
 from oracle import oracle as O
@@ -181,6 +180,9 @@ STREAM_MUTANTS = [
 
 PY_ALL = ([("oracle",) + m for m in PY_MUTANTS] + [("mlp",) + m for m in MLP_MUTANTS]
           + [("stream",) + m for m in STREAM_MUTANTS])
+
+
+ParameterSet = type(pytest.param(None))  # what pytest.param returns
 
 
 def _plant(src: str, old: str, new: str) -> str:
