@@ -1,25 +1,27 @@
 """Mutation check of the oracle's pins (CPU only).
 
-The pins in test_oracle_pins.py, test_gpad_oracle.py, test_penalty_oracle.py,
-test_backtrack_oracle.py, test_mlp_oracle.py and test_stream_kkt.py tie the oracle to facts outside it (dense KKT
-solves, closed forms, brute force, Riccati, PyTorch's autograd, Adam and BF16 cast).  This
-file plants one plausible mistake at a time in a private copy of the oracle -- a dropped
-probability weight or factor 1/2, a flipped sign, a transposed operand, an overwritten
-child sum, the paper's garbled signs and extrapolation taken literally -- and checks that
-the unchanged pins reject every copy.  A mistake they let through is a gap in the pins.
+The pins in test_oracle_pins.py, test_gpad_oracle.py, test_backtrack_oracle.py,
+test_penalty_oracle.py, test_mlp_oracle.py, test_stream_kkt.py and test_spring_mass.py tie
+the oracle and the spring-mass inputs to facts outside them (dense KKT solves, closed forms,
+brute force, Riccati, PyTorch's autograd, Adam and BF16 cast, scipy's hold discretisation,
+Newton's law).  This file plants one plausible mistake at a time in a private copy -- a
+dropped probability weight or factor 1/2, a flipped sign, a transposed operand, an
+overwritten child sum, the paper's garbled signs and extrapolation taken literally -- and
+checks that the unchanged pins reject every copy.  A mistake they let through is a gap in
+the pins.
 
 C mistakes go into a copy of stotree_oracle.c compiled into its own library, which the
-oracle module then calls; Python mistakes go into a copy of oracle.py, mlp.py or
-stream_kkt.py executed as a separate module, which the pin modules then use in place of
-the real one.  Nothing
-here touches the installed oracle or the CUDA path, and each planted text must occur
-exactly once in the source, so an edit of the oracle that moves a line makes this file
-fail loudly instead of silently testing nothing.
+oracle module then calls; Python mistakes go into a copy of oracle.py, mlp.py,
+stream_kkt.py or workloads.py executed as a separate module, which the pin modules then use
+in place of the real one.  Nothing here touches the installed oracle or the CUDA path, and
+each planted text must occur exactly once in its source, so an edit that moves a line makes
+this file fail loudly instead of silently testing nothing.
 """
 import ctypes
 import inspect
 import itertools
 import subprocess
+import sys
 import types
 
 import numpy as np
@@ -28,8 +30,9 @@ import pytest
 from oracle import mlp as M
 from oracle import oracle as O
 from oracle import stream_kkt as SK
+from paper_2107_01745_b300 import workloads as W
 from tests import (test_backtrack_oracle, test_gpad_oracle, test_mlp_oracle, test_oracle_pins,
-                   test_penalty_oracle, test_stream_kkt)
+                   test_penalty_oracle, test_spring_mass, test_stream_kkt)
 
 PIN_MODULES = [test_oracle_pins, test_gpad_oracle, test_backtrack_oracle, test_penalty_oracle]
 # Python parts of the oracle: (module, the name the pin modules import it under, pin modules)
@@ -37,6 +40,8 @@ TARGETS = {
     "oracle": (O, "O", PIN_MODULES),
     "mlp": (M, "M", [test_mlp_oracle]),
     "stream": (SK, "SK", [test_stream_kkt]),
+    # the spring-mass generator of the shared input module, pinned by physics and probability
+    "inputs": (W, "W", [test_spring_mass]),
 }
 
 # (id, mistake, text in the source, planted text)
@@ -186,8 +191,21 @@ STREAM_MUTANTS = [
      "return {\"dynamics\": max(dyn_res, root_res)", "return {\"dynamics\": dyn_res"),
 ]
 
+INPUT_MUTANTS = [
+    ("actuator_sign", "actuator pushes both masses forward",
+     "Bc[M + j, j] = -1.0 / mass", "Bc[M + j, j] = 1.0 / mass"),
+    ("dampers_to_ground", "dampers tie each mass to the ground instead of its neighbours",
+     "Ac[M:, M:] = -(b_d / mass) * Lap", "Ac[M:, M:] = -(b_d / mass) * np.eye(M)"),
+    ("euler_input_matrix", "input matrix by Euler (Bc Ts) instead of the exact hold",
+     "return F[:n, :n].copy(), F[:n, n:].copy()", "return F[:n, :n].copy(), Bc * Ts"),
+    ("markov_ignores_mode", "every node branches with the first mode's conditional probabilities",
+     "cond.extend([list(P_c[b]) for b in nxt])", "cond.extend([list(P_c[0]) for b in nxt])"),
+    ("disturbance_modes_swapped", "disturbance of mode 0 given to mode 1 and back",
+     'c[1:] = np.asarray(S["c_mode"])[modes[1:]][:, None]', 'c[1:] = np.asarray(S["c_mode"])[1 - modes[1:]][:, None]'),
+]
+
 PY_ALL = ([("oracle",) + m for m in PY_MUTANTS] + [("mlp",) + m for m in MLP_MUTANTS]
-          + [("stream",) + m for m in STREAM_MUTANTS])
+          + [("stream",) + m for m in STREAM_MUTANTS] + [("inputs",) + m for m in INPUT_MUTANTS])
 
 
 ParameterSet = type(pytest.param(None))  # what pytest.param returns
@@ -225,6 +243,8 @@ def _cases(mod):
     parametrize marks or from FIXTURES (other fixtures are left out)."""
     for name, fn in vars(mod).items():
         if not name.startswith("test_") or not inspect.isfunction(fn):
+            continue
+        if any(m.name == "slow" for m in getattr(fn, "pytestmark", [])):
             continue
         axes = []
         for m in getattr(fn, "pytestmark", []):
@@ -283,7 +303,11 @@ def _load_c(src: str, tmp_path) -> ctypes.CDLL:
 def _load_py(src: str, like: types.ModuleType = O) -> types.ModuleType:
     mod = types.ModuleType(like.__name__ + "_mutant")
     mod.__file__ = like.__file__
-    exec(compile(src, like.__file__, "exec"), mod.__dict__)
+    sys.modules[mod.__name__] = mod  # dataclasses look their module up while the class is built
+    try:
+        exec(compile(src, like.__file__, "exec"), mod.__dict__)
+    finally:
+        del sys.modules[mod.__name__]
     return mod
 
 
@@ -303,7 +327,7 @@ def test_unmodified_copies_pass_every_pin(tmp_path, monkeypatch):
     for mod in PIN_MODULES:
         monkeypatch.setattr(mod, "O", copy)
     assert _first_failing_pin() is None
-    for key in ("mlp", "stream"):
+    for key in ("mlp", "stream", "inputs"):
         target, attr, mods = TARGETS[key]
         with open(target.__file__) as f:
             other = _load_py(f.read(), target)
