@@ -136,6 +136,11 @@ PY_MUTANTS = [
      "return safety / L, L", "return safety * L, L"),
     ("nama_literal_extrapolation", "NAMA's w = y + tau d + (1 - tau) R (Algorithm 2 read literally)",
      'pt["y"] + tau * d + (1.0 - tau) * fb_dir', 'pt["y"] + tau * d + (1.0 - tau) * pt["r"]'),
+    ("minfbe_no_fb_step", "MINFBE's update y+ = w instead of T(w)",
+     'new = fb_point(o, wp["T"], lam)\n        if backtrack == "original" and original_backtrack_fails(o, wp, new, lam, bt_beta):'
+     '\n            halve()\n            continue\n        g_new',
+     'new = fb_point(o, wp["y"], lam)\n        if backtrack == "original" and original_backtrack_fails(o, wp, new, lam, bt_beta):'
+     '\n            halve()\n            continue\n        g_new'),
     ("gpad_theta_sign", "GPAD's theta recurrence with + theta^2",
      "th_prev, th = th, 0.5 * (np.sqrt(th ** 4 + 4.0 * th * th) - th * th)",
      "th_prev, th = th, 0.5 * (np.sqrt(th ** 4 + 4.0 * th * th) + th * th)"),
