@@ -123,7 +123,9 @@ typedef struct {
     double lambda;        /* the step at return (opts->lambda unless backtracking halved it) */
 } sto_info;
 
-/* Validate the tree and create a handle.  No device work.
+/* Validate the tree and create a handle.  No device work.  The tree is the scenario tree of
+ * Section II-A: every node's probability is the sum of its children's, and the probabilities
+ * of each stage add up to one.
  * Errors: STO_ERR_INVALID_ARG (null pointer, nx < 1, nu < 1, m >= 2^31, or a padded row width
  * above the solve kernel's register tiling: max(pad(nx + nu), pad(nx) + pad(nu)) > 512 for FP32
  * or > 256 for FP64, pad = round up to 16 bytes), STO_ERR_TREE. */
@@ -305,12 +307,13 @@ STO_API sto_status stobatch_sizes(stobatch_t b, int64_t *total_dual, int32_t *nu
 STO_API sto_status stobatch_workspace_size(stobatch_t b, size_t *bytes);
 STO_API sto_status stobatch_bind_workspace(stobatch_t b, void *dev_ptr, size_t bytes, sto_stream_t stream);
 
-/* Instance data: x0 [nx] and disturbances c [Nn][nx] of the group's tree (row 0 unused), host
- * FP64.  Invalidates the factor. */
+/* Instance data: x0 [nx] and disturbances c [Nn][nx] of the group's tree (row 0 unused; the
+ * parameter p and the c^j of eq. system_dynamics_tree), host FP64.  Invalidates the factor. */
 STO_API sto_status stobatch_set_instance(stobatch_t b, int32_t group, int32_t instance, const double *x0,
                                          const double *c, sto_stream_t stream);
 
-/* FP64 stage factor of every group and the affine terms of every instance.  Synchronises;
+/* FP64 stage factor of every group (the recursion of Section III-D, one matrix set per stage)
+ * and the affine terms of every instance.  Synchronises;
  * STO_ERR_NUMERICAL if some R + B'PB is not positive definite. */
 STO_API sto_status stobatch_factor(stobatch_t b, sto_stream_t stream);
 
@@ -319,7 +322,7 @@ STO_API sto_status stobatch_factor(stobatch_t b, sto_stream_t stream);
 STO_API sto_status stobatch_solve_step(stobatch_t b, const void *y, void *hx, int32_t homogeneous, int32_t scaled,
                                        sto_stream_t stream);
 
-/* NAMA for every instance (opts.lbfgs_mem <= 8).  lambdas [ngroups] host.  y (device float batch
+/* NAMA (Algorithm 2) for every instance (opts.lbfgs_mem <= 8).  lambdas [ngroups] host.  y (device float batch
  * vector, unscaled; zeros for a cold start) receives the final duals, z and hx (may be NULL) the
  * z_lambda and Hx of each instance's final iterate; infos [num_instances] (may be NULL).  An
  * instance stops at its own tolerance; the call returns STO_NOT_CONVERGED if some instance hit
