@@ -91,6 +91,8 @@ C_MUTANTS = [
     ("forward_root_zero", "x^0 = 0 instead of p in Algorithm 3",
      "for (int a = 0; a < nx; ++a) x[a] = homogeneous ? 0.0 : x0[a];",
      "for (int a = 0; a < nx; ++a) x[a] = 0.0;"),
+    ("dual_offset_nonleaf", "nonleaf dual blocks at i nx instead of i (nx + nu) (reads stay inside y)",
+     "return i < p->Np ? (size_t)i * (p->nx + p->nu)", "return i < p->Np ? (size_t)i * p->nx"),
     ("forward_skips_last_stage", "rollout stops one stage early (leaves never set)",
      "for (int t = 0; t < p->N; ++t) {", "for (int t = 0; t < p->N - 1; ++t) {"),
 ]
