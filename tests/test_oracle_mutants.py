@@ -1,7 +1,8 @@
 """Mutation check of the oracle's pins (CPU only).
 
 The pins in test_oracle_pins.py, test_gpad_oracle.py, test_backtrack_oracle.py,
-test_penalty_oracle.py, test_mlp_oracle.py, test_stream_kkt.py and test_spring_mass.py tie
+test_penalty_oracle.py, test_mlp_oracle.py, test_stream_kkt.py, test_kkt_oracle.py and
+test_spring_mass.py tie
 the oracle and the spring-mass inputs to facts outside them (dense KKT solves, closed forms,
 brute force, Riccati, PyTorch's autograd, Adam and BF16 cast, scipy's hold discretisation,
 Newton's law).  This file plants one plausible mistake at a time in a private copy -- a
@@ -12,7 +13,7 @@ the pins.
 
 C mistakes go into a copy of stotree_oracle.c compiled into its own library, which the
 oracle module then calls; Python mistakes go into a copy of oracle.py, mlp.py,
-stream_kkt.py or workloads.py executed as a separate module, which the pin modules then use
+stream_kkt.py, kkt_check.py or workloads.py executed as a separate module, which the pin modules then use
 in place of the real one.  Nothing here touches the installed oracle or the CUDA path, and
 each planted text must occur exactly once in its source, so an edit that moves a line makes
 this file fail loudly instead of silently testing nothing.
@@ -29,9 +30,10 @@ import pytest
 
 from oracle import mlp as M
 from oracle import oracle as O
+from oracle import kkt_check as KC
 from oracle import stream_kkt as SK
 from paper_2107_01745_b300 import workloads as W
-from tests import (test_backtrack_oracle, test_gpad_oracle, test_mlp_oracle, test_oracle_pins,
+from tests import (test_backtrack_oracle, test_gpad_oracle, test_kkt_oracle, test_mlp_oracle, test_oracle_pins,
                    test_penalty_oracle, test_spring_mass, test_stream_kkt)
 
 PIN_MODULES = [test_oracle_pins, test_gpad_oracle, test_backtrack_oracle, test_penalty_oracle]
@@ -40,6 +42,8 @@ TARGETS = {
     "oracle": (O, "O", PIN_MODULES),
     "mlp": (M, "M", [test_mlp_oracle]),
     "stream": (SK, "SK", [test_stream_kkt]),
+    # the optimality residuals that the library's FP64 check is compared with
+    "kkt": (KC, "KC", [test_kkt_oracle]),
     # the spring-mass generator of the shared input module, pinned by physics and probability
     "inputs": (W, "W", [test_spring_mass]),
 }
@@ -198,6 +202,24 @@ STREAM_MUTANTS = [
      "return {\"dynamics\": max(dyn_res, root_res)", "return {\"dynamics\": dyn_res"),
 ]
 
+KKT_MUTANTS = [
+    ("kkt_leaf_costate_no_2", "leaf costate without the factor 2 of the quadratic cost",
+     "mu[j] = 2.0 * prob[j] * PN * x[j]", "mu[j] = prob[j] * PN * x[j]"),
+    ("kkt_child_A_not_transposed", "parents collect A^c mu^c instead of A^c' mu^c",
+     "sumA[parent[j]] += p.A[j].T @ mu[j]", "sumA[parent[j]] += p.A[j] @ mu[j]"),
+    ("kkt_no_dual_in_u_equation", "u equation without the dual's input part",
+     "+ prob[j] * r + y[o + nx:o + nx + nu] + sumB[j]", "+ prob[j] * r + sumB[j]"),
+    ("kkt_dynamics_no_c", "dynamics residual without the disturbance",
+     "p.B[j] @ u[i] + p.c[j])", "p.B[j] @ u[i])"),
+    ("kkt_sign_at_upper_bound", "multiplier at an upper bound required to be <= 0",
+     "elif at_hi and not at_lo:\n                    sign = max(sign, -yk)",
+     "elif at_hi and not at_lo:\n                    sign = max(sign, yk)"),
+    ("kkt_soft_kink_one_sided", "soft term's subdifferential at the upper bound taken as {0}",
+     "rho[k] if hk >= hi[k] - tol_active else 0.0", "0.0"),
+    ("kkt_huber_unsaturated", "Huber derivative rho d without the cap at delta",
+     "gd = rho[k] * min(d, delta[k])", "gd = rho[k] * d"),
+]
+
 INPUT_MUTANTS = [
     ("actuator_sign", "actuator pushes both masses forward",
      "Bc[M + j, j] = -1.0 / mass", "Bc[M + j, j] = 1.0 / mass"),
@@ -212,7 +234,8 @@ INPUT_MUTANTS = [
 ]
 
 PY_ALL = ([("oracle",) + m for m in PY_MUTANTS] + [("mlp",) + m for m in MLP_MUTANTS]
-          + [("stream",) + m for m in STREAM_MUTANTS] + [("inputs",) + m for m in INPUT_MUTANTS])
+          + [("stream",) + m for m in STREAM_MUTANTS] + [("kkt",) + m for m in KKT_MUTANTS]
+          + [("inputs",) + m for m in INPUT_MUTANTS])
 
 
 ParameterSet = type(pytest.param(None))  # what pytest.param returns
@@ -242,7 +265,25 @@ class _BacktrackCase:
         return p, o, self.dense_L[self.idx]
 
 
-FIXTURES = {(test_backtrack_oracle, "case"): [_BacktrackCase(i) for i in range(len(test_backtrack_oracle.BOXED))]}
+class _SolvedCase:
+    """Stands for the module fixture `solved` of test_kkt_oracle.py: a problem and its certified
+    QP solution, which come from the oracle's solver and the dense KKT system, not from the
+    module under test, so they are computed once."""
+    cache = {}
+
+    def __init__(self, idx):
+        self.idx = idx
+        self.name = test_kkt_oracle.PROBS[idx].name
+
+    def build(self):
+        if self.idx not in self.cache:
+            p = test_kkt_oracle.PROBS[self.idx]
+            self.cache[self.idx] = (p,) + test_kkt_oracle._solution(p)
+        return self.cache[self.idx]
+
+
+FIXTURES = {(test_backtrack_oracle, "case"): [_BacktrackCase(i) for i in range(len(test_backtrack_oracle.BOXED))],
+            (test_kkt_oracle, "solved"): [_SolvedCase(i) for i in range(len(test_kkt_oracle.PROBS))]}
 
 
 def _cases(mod):
@@ -287,7 +328,7 @@ def _first_failing_pin(cases=ALL_CASES):
     for name, fn, kw in cases:
         try:
             with np.errstate(over="ignore", invalid="ignore", divide="ignore"):
-                fn(**{k: v.build() if isinstance(v, _BacktrackCase) else v for k, v in kw.items()})
+                fn(**{k: v.build() if isinstance(v, (_BacktrackCase, _SolvedCase)) else v for k, v in kw.items()})
         except pytest.skip.Exception:
             continue
         except Exception as e:  # an assertion, a refused factor, a non-finite value ...
@@ -334,7 +375,7 @@ def test_unmodified_copies_pass_every_pin(tmp_path, monkeypatch):
     for mod in PIN_MODULES:
         monkeypatch.setattr(mod, "O", copy)
     assert _first_failing_pin() is None
-    for key in ("mlp", "stream", "inputs"):
+    for key in ("mlp", "stream", "kkt", "inputs"):
         target, attr, mods = TARGETS[key]
         with open(target.__file__) as f:
             other = _load_py(f.read(), target)
