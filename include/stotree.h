@@ -190,26 +190,49 @@ STO_API sto_status stotree_factor(stotree_t h, int32_t sync, sto_stream_t stream
  *   x0   device real [nx], the root state p (ignored when homogeneous).
  *   hx   device real [nrhs][m]: Hx(y) laid out like y; with scaled = 1 the output is
  *        sqrt(pi) Hx per block.  The root block holds [x0; u^0] ([0; u^0] if homogeneous).
- * Asynchronous.  Errors: STO_ERR_INVALID_ARG, STO_ERR_NOT_READY. */
+ * Asynchronous; a dependency wait that gives up is reported by stotree_round_status.
+ * Errors: STO_ERR_INVALID_ARG, STO_ERR_NOT_READY. */
 STO_API sto_status stotree_solve_step(stotree_t h, const void *y, const void *x0, void *hx, int32_t nrhs,
                               int32_t homogeneous, int32_t scaled, sto_stream_t stream);
 
 /* stotree_solve_step for one right-hand side without any allocation (the paper has no
  * counterpart).  For callers that cannot call cudaMalloc, or any allocator, while they run a
  * solve: e.g. a controller whose device-memory plan is frozen after start-up.  The handle must
- * be set up and factored beforehand; a call then touches only y, hx, the factor arrays in the
- * bound workspace and a fixed 32 MiB scratch array compiled into the library, which every GPU
- * that loads the library holds until the process exits.
+ * be set up and factored beforehand (stotree_factor also sets up this call's launch, so even
+ * the handle's first solve needs no host-side set-up); a call then touches only y, hx, the
+ * factor arrays in the bound workspace and a fixed 32 MiB scratch array compiled into the
+ * library, which every GPU that loads the library holds until the process exits.  Solve-step
+ * timing (stotree_set_timing) does not cover this call.
  *   y, x0, hx, homogeneous, scaled: as stotree_solve_step with nrhs = 1.
- * Limit: the round needs 2 (Nn nx + Np nu) reals of scratch (each part 256-byte aligned); larger
+ * Limit: with esz = sizeof(real) and a256(v) = v rounded up to a multiple of 256, the call
+ * needs 2 (a256(Nn nx esz) + a256(Np nu esz)) + a256(8 Nn) + 256 bytes of scratch (s, ubar,
+ * x, u, the round's dependency flags and its work counter), at most 33554432 (32 MiB); larger
  * problems get STO_ERR_INVALID_ARG and a message in stotree_last_error.  The first call on a
  * device looks the array's address up (cudaGetSymbolAddress) with that device current; make
  * that first call before any stream capture.  All calls share the one array: calls that
  * overlap on the GPU (other streams, other handles) race and give wrong results.  The
- * primal trajectory stays in the array, so stotree_last_primal does not report it.
+ * primal trajectory stays in the array, so stotree_last_primal keeps reporting the last
+ * round of stotree_solve_step.  A dependency wait that gives up is reported by
+ * stotree_round_status.
  * Asynchronous.  Errors: STO_ERR_INVALID_ARG, STO_ERR_NOT_READY, STO_ERR_CUDA. */
 STO_API sto_status stotree_solve_step_noalloc(stotree_t h, const void *y, const void *x0, void *hx,
                                               int32_t homogeneous, int32_t scaled, sto_stream_t stream);
+
+/* Limit of each dependency wait inside a solve round (a node waiting for the round's work on
+ * its children in the backward pass, or on its parent in the forward pass), in seconds, from 0
+ * to 60; default 1.5.  Waits that give up let the round finish without them (its output is then
+ * wrong) and are reported as STO_ERR_TIMEOUT by the next synchronising call or by
+ * stotree_round_status.  0 gives up at the first check that finds the dependency unfinished.
+ * Copy waits inside the round keep their fixed 1.5 s limit.  Host only. */
+STO_API sto_status stotree_set_wait_limit(stotree_t h, double seconds);
+
+/* Status of the solve rounds enqueued since the last synchronising call (stotree_solve_step,
+ * stotree_solve_step_noalloc): synchronises the stream and returns STO_ERR_TIMEOUT if a bounded
+ * wait inside one of them gave up (the results of those rounds are wrong), else STO_OK.  On
+ * STO_ERR_TIMEOUT the round state (dependency flags, work counter, error word) is reset, so the
+ * next round runs normally.  The *_solve calls and stotree_estimate_lambda check this themselves.
+ * Errors: STO_ERR_INVALID_ARG, STO_ERR_NOT_READY, STO_ERR_CUDA, STO_ERR_TIMEOUT. */
+STO_API sto_status stotree_round_status(stotree_t h, sto_stream_t stream);
 
 /* Primal trajectory of the last solve round's first right-hand side: x [Nn][nx],
  * u [Np][nu] (device real).  Asynchronous. */

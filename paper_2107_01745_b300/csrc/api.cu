@@ -514,6 +514,8 @@ sto_status stotree_factor(stotree_t h, int32_t sync, sto_stream_t stream) {
     cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
     sto_status s = factor_run(h, st);
     if (s != STO_OK) return s;
+    s = prepare_round(h);
+    if (s != STO_OK) return s;
     h->factored = true;
     if (sync) {
         int flag = 0;
@@ -541,6 +543,18 @@ sto_status stotree_solve_step(stotree_t h, const void *y, const void *x0, void *
     }
     return solve_round(h, ys, x0, hs, nrhs, homogeneous != 0, scaled != 0,
                        reinterpret_cast<cudaStream_t>(stream));
+}
+
+sto_status stotree_set_wait_limit(stotree_t h, double seconds) {
+    if (!h || !(seconds >= 0.0 && seconds <= 60.0)) return STO_ERR_INVALID_ARG;
+    h->wait_ns = (unsigned long long)(seconds * 1e9);
+    return STO_OK;
+}
+
+sto_status stotree_round_status(stotree_t h, sto_stream_t stream) {
+    if (!h) return STO_ERR_INVALID_ARG;
+    if (!h->ws) return STO_ERR_NOT_READY;
+    return check_round_error(h, reinterpret_cast<cudaStream_t>(stream));
 }
 
 sto_status stotree_last_primal(stotree_t h, void *x, void *u, sto_stream_t stream) {

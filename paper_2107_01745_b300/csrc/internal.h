@@ -122,6 +122,7 @@ struct stotree_s {
     unsigned epoch = 0;                 // last epoch written to the flags
     unsigned long long ticket_base = 0;  // value of the ticket counter before the next round
     int grid_ctas[5] = {0, 0, 0, 0, 0};  // CTAs of the persistent solve kernel, per nrhs
+    unsigned long long wait_ns = 1500000000ull;  // limit of each dependency wait in a solve round
     // pinned host mirror of the device scalars
     sto::SolverScalars *host_scal = nullptr;
     sto::SolverScalars *host_scal2 = nullptr;  // second header buffer (GPAD look-ahead)
@@ -160,6 +161,10 @@ struct SolveScratch {
 };
 sto_status solve_round(stotree_t h, const void *const *y, const void *x0, void *const *hx, int nrhs,
                        bool homogeneous, bool scaled, cudaStream_t st, const SolveScratch *scratch = nullptr);
+
+// Grid and shared-memory caps of the one-right-hand-side round, set up ahead of its first launch
+// (called when the factor is computed, so that later rounds do no host-side set-up work).
+sto_status prepare_round(stotree_t h);
 
 sto_status check_round_error(stotree_t h, cudaStream_t st);
 

@@ -188,19 +188,20 @@ __device__ __forceinline__ unsigned ld_acquire(const unsigned *p) {
 __device__ __forceinline__ void st_release(unsigned *p, unsigned v) {
     asm volatile("st.release.gpu.global.u32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
 }
-// Bounded wait until *f == epoch.  Gives up at once when the error flag is already raised.
-__device__ __forceinline__ void wait_flag(const unsigned *f, unsigned epoch, int *err) {
+// Bounded wait until *f == epoch, for at most `limit` ns (the handle's dependency-wait limit;
+// 0 gives up at the first check that finds the flag unset).  Gives up without a new error when
+// the error flag is already raised; the first cause recorded is kept.
+__device__ __forceinline__ void wait_flag(const unsigned *f, unsigned epoch, int *err, unsigned long long limit) {
     if (ld_acquire(f) == epoch) return;
     const unsigned long long t0 = now_ns();
-    for (;;) {
+    while (now_ns() - t0 < limit) {
         for (int it = 0; it < 32; ++it) {
             if (ld_acquire(f) == epoch) return;
             __nanosleep(32);
         }
         if (*(volatile int *)err) return;
-        if (now_ns() - t0 > kWaitNs) break;
     }
-    atomicExch(err, 1);
+    atomicCAS(err, 0, 1);
 }
 // Asynchronous element copies global -> shared (the small per-node vectors); the issuing thread
 // waits for its own copies with cp_async_wait, a named barrier then publishes them.
@@ -235,6 +236,7 @@ struct TreeArgs {
     unsigned *flags;        // [2][Nn]
     unsigned long long *ticket;
     int *err;
+    unsigned long long wait_ns;  // limit of each dependency wait
     int homog, scaled;
     int rpcG, rpcRK, rpcGt, rpcKt;  // rows per ring slot
 };
@@ -480,7 +482,7 @@ struct Consumer {
                             s_in[e] = T(0.5) * scj * a.y[k][o + r] + cj * a.pN[r];
                         }
                     } else {
-                        if (tid == 0) wait_flag(a.flags + j, epoch, a.err);
+                        if (tid == 0) wait_flag(a.flags + j, epoch, a.err, a.wait_ns);
                         cbar();
                         for (int e = tid; e < NR * nx; e += kCW * 32) {
                             const int k = e / nx, r = e - k * nx;
@@ -547,7 +549,7 @@ struct Consumer {
                         }
                     } else {
                         const int i = a.parent[j];
-                        if (tid == 0) wait_flag(a.flags + a.Nn + i, epoch, a.err);
+                        if (tid == 0) wait_flag(a.flags + a.Nn + i, epoch, a.err, a.wait_ns);
                         cbar();
                         for (int e = tid; e < NR * a.ldg; e += kCW * 32) {
                             const int k = e / a.ldg, cc = e - k * a.ldg;
@@ -597,7 +599,7 @@ struct Consumer {
                 // u^j = K^j x^j + ubar^j, axpy form over the rows of K^j'
                 const int j = md.node;
                 if ((f & F_FIRST) && (f & F_ROOT)) {
-                    if (tid == 0) wait_flag(a.flags + 0, epoch, a.err);  // backward pass finished
+                    if (tid == 0) wait_flag(a.flags + 0, epoch, a.err, a.wait_ns);  // backward pass finished
                     cbar();
                     for (int k = 0; k < NR; ++k) prefetch(nx + k * nu, a.ubar + k * a.u_stride, nu);
                     cp_async_commit();
@@ -722,6 +724,14 @@ void launch_tree_kv(stotree_t h, const TreeArgs<T> &a, unsigned epoch, unsigned 
     }
 }
 
+// Raise the shared-memory caps of both passes' kernels and return the occupancy of one CTA.
+template <class T, int NR, int KV>
+cudaError_t tree_caps(size_t smem, int *per_sm) {
+    raise_smem_cap((const void *)k_tree<T, NR, KV, 0>, smem);
+    raise_smem_cap((const void *)k_tree<T, NR, KV, 1>, smem);
+    return cudaOccupancyMaxActiveBlocksPerMultiprocessor(per_sm, k_tree<T, NR, KV, 0>, kThreadsT, smem);
+}
+
 // CTAs of the persistent kernel: every CTA must be resident at once (items wait on earlier ones).
 template <class T, int NR>
 int tree_grid(const TreeArgs<T> &a) {
@@ -732,24 +742,18 @@ int tree_grid(const TreeArgs<T> &a) {
     const int kv = (a.lda / V16<T>::n + 31) / 32;
     cudaError_t e;
     switch (kv) {
-        case 1: raise_smem_cap((const void *)k_tree<T, NR, 1, 0>, smem);
-                e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_tree<T, NR, 1, 0>, kThreadsT, smem); break;
-        case 2: raise_smem_cap((const void *)k_tree<T, NR, 2, 0>, smem);
-                e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_tree<T, NR, 2, 0>, kThreadsT, smem); break;
-        case 3: raise_smem_cap((const void *)k_tree<T, NR, 3, 0>, smem);
-                e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_tree<T, NR, 3, 0>, kThreadsT, smem); break;
-        default: raise_smem_cap((const void *)k_tree<T, NR, 4, 0>, smem);
-                 e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_tree<T, NR, 4, 0>, kThreadsT, smem); break;
+        case 1: e = tree_caps<T, NR, 1>(smem, &per_sm); break;
+        case 2: e = tree_caps<T, NR, 2>(smem, &per_sm); break;
+        case 3: e = tree_caps<T, NR, 3>(smem, &per_sm); break;
+        default: e = tree_caps<T, NR, 4>(smem, &per_sm); break;
     }
     if (e != cudaSuccess || per_sm < 1) return 0;
     return sms * (per_sm < kCtasPerSm ? per_sm : kCtasPerSm);
 }
 
+// Row widths and item counts of a round (the part of TreeArgs the grid and caps depend on).
 template <class T>
-sto_status solve_impl(stotree_t h, const void *const *y, const void *x0, void *const *hx, int nrhs, bool homog,
-                      bool scaled, cudaStream_t st, const SolveScratch *scratch) {
-    const Layout &L = h->L;
-    TreeArgs<T> a;
+void tree_dims(stotree_t h, TreeArgs<T> &a) {
     a.nx = h->nx;
     a.nu = h->nu;
     a.ldg = h->ldg;
@@ -757,6 +761,26 @@ sto_status solve_impl(stotree_t h, const void *const *y, const void *x0, void *c
     a.ldr = h->ldr;
     a.ldrk = h->ldrk;
     a.lda = h->ldrk > h->ldg ? h->ldrk : h->ldg;
+}
+
+template <class T>
+sto_status prepare_impl(stotree_t h) {
+    TreeArgs<T> a;
+    tree_dims(h, a);
+    if (h->grid_ctas[1] <= 0) h->grid_ctas[1] = tree_grid<T, 1>(a);
+    if (h->grid_ctas[1] <= 0) {
+        h->err = "solve kernel does not fit on this device";
+        return STO_ERR_CUDA;
+    }
+    return STO_OK;
+}
+
+template <class T>
+sto_status solve_impl(stotree_t h, const void *const *y, const void *x0, void *const *hx, int nrhs, bool homog,
+                      bool scaled, cudaStream_t st, const SolveScratch *scratch) {
+    const Layout &L = h->L;
+    TreeArgs<T> a;
+    tree_dims(h, a);
     a.Np = h->Np;
     a.Nn = h->Nn;
     a.nxu = h->nx + h->nu;
@@ -793,6 +817,7 @@ sto_status solve_impl(stotree_t h, const void *const *y, const void *x0, void *c
     a.rpcGt = kChunk / (h->ldk * (int)sizeof(T));
     a.rpcKt = kChunk / (h->ldr * (int)sizeof(T));
     a.err = h->at<int>(L.fstatus) + 8;
+    a.wait_ns = h->wait_ns;
     unsigned epoch;
     unsigned long long tbase;
     int &grid = h->grid_ctas[nrhs];
@@ -835,8 +860,9 @@ sto_status solve_impl(stotree_t h, const void *const *y, const void *x0, void *c
         // every CTA's producer draws one ticket past the last item
         h->ticket_base += (unsigned long long)(a.Tb + a.Tf + 2 * grid);
     }
-    cudaEvent_t ev;
-    timing_begin(h, st, &ev);
+    // the scratch (no-allocation) path is never timed: timing may create events
+    cudaEvent_t ev = nullptr;
+    if (!scratch) timing_begin(h, st, &ev);
     switch (nrhs) {
         case 1: launch_tree_kv<T, 1>(h, a, epoch, tbase, grid, st); break;
         case 2: launch_tree_kv<T, 2>(h, a, epoch, tbase, grid, st); break;
@@ -851,6 +877,10 @@ sto_status solve_impl(stotree_t h, const void *const *y, const void *x0, void *c
 }
 
 }  // namespace
+
+sto_status prepare_round(stotree_t h) {
+    return h->prec == STO_FP64 ? prepare_impl<double>(h) : prepare_impl<float>(h);
+}
 
 sto_status solve_round(stotree_t h, const void *const *y, const void *x0, void *const *hx, int nrhs, bool homog,
                        bool scaled, cudaStream_t st, const SolveScratch *scratch) {

@@ -73,6 +73,8 @@ def lib():
             "stotree_solve_step": [vp, vp, vp, vp, i32, i32, i32, vp],
             "stotree_solve_step_noalloc": [vp, vp, vp, vp, i32, i32, vp],
             "stotree_last_primal": [vp, vp, vp, vp],
+            "stotree_set_wait_limit": [vp, dbl],
+            "stotree_round_status": [vp, vp],
             "stotree_estimate_lambda": [vp, vp, i32, dbl, vp, vp, vp],
             "stotree_nama_solve": [vp, vp, vp, vp, vp, vp, vp, vp, vp],
             "stotree_minfbe_solve": [vp, vp, vp, vp, vp, vp, vp, vp, vp],
@@ -141,7 +143,8 @@ def lib():
 def exported_symbols():
     return [n for n in ("stotree_create", "stotree_destroy", "stotree_sizes", "stotree_workspace_size",
                         "stotree_bind_workspace", "stotree_set_dynamics", "stotree_set_costs", "stotree_set_box", "stotree_set_penalty",
-                        "stotree_factor", "stotree_solve_step", "stotree_solve_step_noalloc", "stotree_last_primal", "stotree_estimate_lambda",
+                        "stotree_factor", "stotree_solve_step", "stotree_solve_step_noalloc", "stotree_set_wait_limit",
+                        "stotree_round_status", "stotree_last_primal", "stotree_estimate_lambda",
                         "stotree_nama_solve", "stotree_minfbe_solve", "stotree_gpad_solve", "stotree_kkt_check", "stotree_set_timing",
                         "stotree_get_timing", "stotree_solve_bytes", "stotree_status_str", "stotree_last_error",
                         "stobatch_create", "stobatch_destroy", "stobatch_sizes", "stobatch_workspace_size",
@@ -274,6 +277,15 @@ class StoTree:
                                                      1 if homogeneous else 0, 1 if scaled else 0, _stream()),
                     "solve_step_noalloc")
         return out
+
+    def set_wait_limit(self, seconds):
+        """stotree_set_wait_limit: limit of each dependency wait inside a solve round."""
+        self._check(lib().stotree_set_wait_limit(self.h, float(seconds)), "set_wait_limit")
+
+    def round_status(self):
+        """stotree_round_status: raises StoError (timeout) if a wait of the rounds since the last
+        synchronising call gave up."""
+        self._check(lib().stotree_round_status(self.h, _stream()), "round_status")
 
     def last_primal(self):
         x = torch.empty((self.Nn, self.nx), dtype=self.dtype, device=self.device)

@@ -280,10 +280,13 @@ def paper_scale(seed: int = 2) -> Problem:
 
 
 def random_problem(seed: int, horizon: int = 3, nx: int = 3, nu: int = 2, max_branch: int = 3,
-                   box_scale: float = 1.0, linear_terms: bool = True, p_branch: float = 0.6) -> Problem:
-    """Small ragged problem with per-node dynamics, for parity cases and pins."""
+                   box_scale: float = 1.0, linear_terms: bool = True, p_branch: float = 0.6,
+                   tree: Tree | None = None) -> Problem:
+    """Small ragged problem with per-node dynamics, for parity cases and pins.  With `tree`
+    given, that tree is used and no tree is drawn (horizon, max_branch, p_branch unused)."""
     rng = np.random.default_rng(seed)
-    tree = random_tree(rng, horizon, max_branch=max_branch, p_branch=p_branch)
+    if tree is None:
+        tree = random_tree(rng, horizon, max_branch=max_branch, p_branch=p_branch)
     nn = tree.num_nodes
     A0 = spectral_rescale(rng.standard_normal((nx, nx)), 0.95)
     A = np.empty((nn, nx, nx))
@@ -556,6 +559,19 @@ def largest(seed: int = 5) -> Problem:
     p = largest_unboxed(seed)
     xmax, umax = load_box("largest")
     return with_box(p, xmax, umax)
+
+
+def largest_truncated(seed: int = 5, horizon: int = 14) -> Problem:
+    """The largest instance's recipe cut at a smaller horizon: the same generator, sizes, box and
+    binary stages (the first `horizon` stages of the tree), small enough for an FP64 host solve.
+    Node data comes in the same seeded 512-node blocks, so every full block equals the full
+    instance's; the last, partial block is drawn for its own size."""
+    p = largest_unboxed(seed, tree=largest_tree(horizon=horizon,
+                                                branch_stages=min(horizon, LARGEST_SHAPE["branch_stages"])))
+    xmax, umax = load_box("largest")
+    p = with_box(p, xmax, umax)
+    p.name = f"largest_h{horizon}"
+    return p
 
 
 # ------------------------------------------------------------------------------------------

@@ -240,3 +240,27 @@ def test_binding_prototypes_match_the_header():
         if ret == "sto_status":
             want_ret = ctypes.c_int
         assert fn.restype is want_ret, f"{name}: result {fn.restype} vs {ret}"
+
+
+def test_wait_limit_and_round_status_refusals_need_no_device(libso):
+    """stotree_set_wait_limit accepts 0..60 s and refuses anything else; stotree_round_status
+    needs a handle with a bound workspace.  Both answer on a host without a GPU."""
+    L = libso
+    L.stotree_set_wait_limit.argtypes = [ctypes.c_void_p, ctypes.c_double]
+    L.stotree_round_status.argtypes = [ctypes.c_void_p, ctypes.c_void_p]
+    L.stotree_destroy.argtypes = [ctypes.c_void_p]
+    parent = np.array([-1, 0, 0], dtype=np.int32)
+    prob = np.array([1.0, 0.5, 0.5])
+    d = _Desc(3, 1, 2, 1, parent.ctypes.data, prob.ctypes.data)
+    h = ctypes.c_void_p()
+    assert L.stotree_create(ctypes.byref(d), 1, ctypes.byref(h)) == 0
+    try:
+        for bad in (-1e-9, 60.5, float("nan"), float("inf")):
+            assert L.stotree_set_wait_limit(h, bad) == 1, bad
+        for ok in (0.0, 1e-6, 1.5, 60.0):
+            assert L.stotree_set_wait_limit(h, ok) == 0, ok
+        assert L.stotree_set_wait_limit(None, 1.0) == 1
+        assert L.stotree_round_status(None, None) == 1
+        assert L.stotree_round_status(h, None) == 3  # no workspace bound
+    finally:
+        L.stotree_destroy(h)

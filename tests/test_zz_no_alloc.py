@@ -41,6 +41,31 @@ def test_noalloc_matches_solve_step_twice(cuda_device, prec, tol):
         assert _rel2(out, ref) < tol, f"call {call}"
 
 
+@pytest.mark.parametrize("prec,tol", [("fp64", 1e-11), ("fp32", 1e-5)])
+def test_noalloc_as_the_first_solve_of_a_handle(cuda_device, prec, tol):
+    """A freshly factored handle whose first solve is the no-allocation call: the factor has set
+    up the launch, so the result equals a later ordinary solve step.  The no-allocation call
+    leaves stotree_last_primal on the last ordinary round."""
+    from paper_2107_01745_b300.stotree import StoTree
+    p = W.random_problem(52, horizon=5, nx=9, nu=4, max_branch=3)
+    st = StoTree(p, precision=prec)
+    st.factor()
+    x0 = st.to_dev(p.x0)
+    y1 = st.to_dev(W.random_dual(p, 11))
+    first = st.solve_step_noalloc(y1, x0=x0)
+    torch.cuda.synchronize()
+    st.round_status()
+    ref = st.solve_step(y1, x0=x0)
+    assert _rel2(first, ref) < tol
+    x1, u1 = st.last_primal()
+    y2 = st.to_dev(W.random_dual(p, 12))
+    second = st.solve_step_noalloc(y2, x0=x0)
+    x2, u2 = st.last_primal()
+    torch.cuda.synchronize()
+    assert torch.equal(x1, x2) and torch.equal(u1, u2)
+    assert _rel2(second, st.solve_step(y2, x0=x0)) < tol
+
+
 def test_noalloc_paper_scale_and_limit(cuda_device):
     """The paper-scale tree fits the fixed scratch; a problem needing more is refused with a message."""
     from paper_2107_01745_b300.stotree import StoTree, _stream, _t_ptr
