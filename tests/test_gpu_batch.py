@@ -65,7 +65,7 @@ def test_batched_nama_matches_oracle(cuda_device, small):
             ref = O.nama(o, lams[gi], tol=1e-5, max_iter=400)
             sl = slice(sb.offsets[k], sb.offsets[k] + sb.sizes[k])
             assert _relinf(hx[sl], ref["h"]) < 1e-4
-            assert _relinf(y[sl], ref["y"]) < 1e-3
+            assert _relinf(y[sl], ref["y"]) < 1e-4
             k += 1
 
 
@@ -88,4 +88,5 @@ def test_batched_uneven_workload(cuda_device):
         o = O.LQOracle(g.instance(k_local))
         ref = O.nama(o, lams[gi], tol=1e-4, max_iter=500)
         sl = slice(sb.offsets[k], sb.offsets[k] + sb.sizes[k])
-        assert _relinf(hx[sl], ref["h"]) < 2e-3
+        assert _relinf(hx[sl], ref["h"]) < 1e-4
+        assert _relinf(res["y"].cpu().numpy()[sl], ref["y"]) < 1e-4

@@ -2,8 +2,10 @@
 
 Tolerances: FP64 handles within 1e-11 relative on the solve step (rounding only); FP32
 handles within 1e-5 relative (2-norm) on the dual gradient, the bound stated for the
-FP32 path; solver results at the same stopping tolerance within 1e-4 relative (FP32) or
-1e-8 (FP64)."""
+FP32 path; solver results at the same stopping tolerance within 1e-4 relative (FP32: x, u
+and y, against the oracle at the same tolerance and run to 1e-10) or 1e-8 (FP64).  At paper
+scale the dual's bound is derived from the spread the stopping test itself allows (see
+test_paper_scale_solver)."""
 import numpy as np
 import pytest
 import torch
@@ -112,21 +114,30 @@ def test_solver_fp64_matches_oracle(cuda_device, p, method):
     assert kkt["feasibility"] < 1e-9 and kkt["sign"] < 1e-12
 
 
+FP32_CASES = BOXED[1:] + [D.boxed_problem(12, horizon=3, nx=3, nu=2), D.boxed_problem(17, horizon=4, nx=4, nu=2, frac=0.9),
+                          D.boxed_problem(16, horizon=3, nx=5, nu=3, frac=0.9)]
+
+
 @pytest.mark.parametrize("method", ["nama", "minfbe"])
-@pytest.mark.parametrize("p", BOXED[1:], ids=lambda p: p.name)
+@pytest.mark.parametrize("p", FP32_CASES, ids=lambda p: p.name)
 def test_solver_fp32_matches_oracle(cuda_device, p, method):
-    """FP32 Algorithms 1 and 2 reach the stopping tolerance; the solution matches the
-    oracle's at the same tolerance within 1e-4 relative."""
+    """FP32 Algorithms 1 and 2 reach the stopping tolerance; the primal x, u and the dual y match
+    the oracle's at the same tolerance within 1e-4 relative (the stated bound for the final
+    solution), and the oracle's solution run to 1e-10 within the same bound.  The last three
+    problems have binding boxes (active duals), the first three do not."""
     o = O.LQOracle(p)
     lam, _ = O.power_lambda(o, np.random.default_rng(0).standard_normal(o.m))
-    ref = (O.nama if method == "nama" else O.minfbe)(o, lam, tol=1e-5, max_iter=500)
+    fn = O.nama if method == "nama" else O.minfbe
+    ref = fn(o, lam, tol=1e-5, max_iter=500)
+    star = fn(o, lam, tol=1e-10, max_iter=5000)
     st = _st()(p, precision="fp32")
     st.factor()
     res = st.solve(method, lam, tol=1e-5, max_iter=500)
     assert res["info"]["res_inf"] <= 1e-5
-    assert _relinf(res["x"].cpu().numpy(), ref["x"]) < 1e-4
-    assert _relinf(res["u"].cpu().numpy(), ref["u"]) < 1e-4
-    assert _relinf(res["y"].cpu().numpy(), ref["y"]) < 1e-3
+    for k in ("x", "u", "y"):
+        got = res[k].double().cpu().numpy()
+        assert _relinf(got, ref[k]) < 1e-4, k
+        assert _relinf(got, star[k]) < 1e-4, k
 
 
 @pytest.mark.parametrize("p", BOXED, ids=lambda p: p.name)
@@ -361,17 +372,31 @@ def test_paper_scale_solve_step(cuda_device, paper_scale):
 @pytest.mark.parametrize("method", ["nama", "minfbe"])
 def test_paper_scale_solver(cuda_device, paper_scale, method):
     """Full-size FP32 MINFBE / NAMA to ||z - Hx||_inf <= 1e-4 against the FP64 oracle run to
-    the same tolerance, plus the FP64 KKT check of the GPU result."""
+    the same tolerance and to 1e-7, plus the FP64 KKT check of the GPU result.
+
+    x and u: within 1e-4 relative of both oracle runs.  y: the stopping test bounds the
+    residual, not the distance to the dual solution, and on this instance the oracle itself,
+    stopped at 1e-4, lies 2-3e-4 (relative, infinity norm) from its 1e-7 solution; the FP32 run
+    stops at another point of the same residual ball.  The bound is therefore derived from
+    that spread: ||y - y*|| <= 1e-4 + 3 ||y_oracle(1e-4) - y*|| (relative), y* the oracle's
+    1e-7 dual."""
     p, o = paper_scale
     r0 = np.random.default_rng(7).standard_normal(o.m)
     lam, _ = O.power_lambda(o, r0)
-    ref = (O.nama if method == "nama" else O.minfbe)(o, lam, tol=1e-4, max_iter=300)
+    fn = O.nama if method == "nama" else O.minfbe
+    ref = fn(o, lam, tol=1e-4, max_iter=300)
+    star = fn(o, lam, tol=1e-7, max_iter=1000)
     st = _st()(p, precision="fp32")
     st.factor()
     res = st.solve(method, lam, tol=1e-4, max_iter=300)
     assert res["info"]["res_inf"] <= 1e-4
-    assert _relinf(res["x"].cpu().numpy(), ref["x"]) < 1e-3
-    assert _relinf(res["u"].cpu().numpy(), ref["u"]) < 1e-3
+    got = {k: res[k].double().cpu().numpy() for k in ("x", "u", "y")}
+    for k in ("x", "u"):
+        assert _relinf(got[k], ref[k]) < 1e-4, k
+        assert _relinf(got[k], star[k]) < 1e-4, k
+    spread = _relinf(ref["y"], star["y"])
+    print(f"paper-scale {method}: y vs 1e-7 oracle {_relinf(got['y'], star['y']):.2e}, oracle(1e-4) spread {spread:.2e}")
+    assert _relinf(got["y"], star["y"]) <= 1e-4 + 3.0 * spread
     kkt = st.kkt_check(st.to_dev(p.x0), res["x"], res["u"], res["y"], tol_active=1e-3)
     assert kkt["dynamics"] < 1e-4 and kkt["feasibility"] < 2e-4
 
