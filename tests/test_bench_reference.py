@@ -23,3 +23,19 @@ def test_reference_line_has_the_contract_keys(monkeypatch):
     assert cb["kind"] == "oracle" and cb["value"] == line["value"] and cb["cores"] >= 1 and cb["sample"]
     assert line["e2e"] == {"value": line["value"], "unit": "ms", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}
     assert line["config"]["workload"] == bench.WORKLOAD
+    assert line["steps_measured"] == 2 and "all 2" in line["steps_note"]
+    # both arms print the same workload description
+    p = W.tiny_fp64(0)
+    n = p.tree.num_nonleaf * p.nu + (p.tree.num_nodes - 1) * p.nx
+    assert line["config"] == bench._config(1, p.num_dual, n)
+
+
+def test_reference_arm_stops_measuring_at_its_budget(monkeypatch):
+    monkeypatch.setattr(W, "paper_scale", lambda seed: W.tiny_fp64(0))
+    monkeypatch.setattr(bench, "REF_BUDGET_S", 0.0)
+
+    class Args:
+        warmup, steps = 3, 4
+
+    line = bench.run_reference(Args)
+    assert line["steps_measured"] == 1 and "budget" in line["steps_note"]

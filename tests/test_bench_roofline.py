@@ -81,6 +81,12 @@ def test_traffic_reported_only_for_the_profiled_source(tmp_path, monkeypatch):
         os.makedirs(tmp_path / os.path.dirname(rel), exist_ok=True)
         shutil.copy(os.path.join(src_root, rel), tmp_path / rel)
     monkeypatch.setattr(bench, "ROOT", str(tmp_path))
+    # the copy of the summary names the copied source's hash (the committed summary may be older
+    # than the source, in which case bench.py reports no traffic, as checked at the end)
+    import hashlib
+    src_hash = hashlib.sha256((tmp_path / "paper_2107_01745_b300/csrc/solve.cu").read_bytes()).hexdigest()
+    md = tmp_path / "profiles/k_tree_paper_scale.md"
+    md.write_text(re.sub(r"sha256 `[0-9a-f]{64}`", f"sha256 `{src_hash}`", md.read_text(), count=1))
     text = (tmp_path / "profiles/k_tree_paper_scale.md").read_text()
     t1 = int(re.search(r"traffic_bytes_per_round_1rhs: (\d+)", text).group(1))
     t2 = int(re.search(r"traffic_bytes_per_round_2rhs: (\d+)", text).group(1))
