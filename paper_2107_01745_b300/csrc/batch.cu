@@ -1597,7 +1597,7 @@ STO_API sto_status stobatch_nama_solve(stobatch_t b, const sto_opts *o, const do
             infos[i].ls_zero = b->hs[i].ls_zero;
             infos[i].launches = 0;
             infos[i].halvings = 0;
-            infos[i].lambda = lambdas[i];
+            infos[i].lambda = lambdas[b->insts[i].group];  // the step is per group
             infos[i].res_inf = b->hs[i].res_inf;
             infos[i].fbe = b->hs[i].phi;
             infos[i].ms = ms;

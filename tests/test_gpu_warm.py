@@ -16,22 +16,23 @@ from paper_2107_01745_b300 import workloads as W
 
 pytestmark = pytest.mark.gpu
 
-NX, NU, H, BATCH = 3, 2, 128, 256
+NX, NU, BATCH = 3, 2, 256
+WIDTHS = [128, 256]  # both hidden widths the kernels tile (256 is the configured one)
 
 
 def _tree():
     return W.tree_from_branching([2, 2, 1])
 
 
-def _params(seed, d_in=4 * NX + 1, d_out=NX + NU):
+def _params(seed, H, d_in=4 * NX + 1, d_out=NX + NU):
     p = M.init_params(np.random.default_rng(seed), d_in, H, d_out)
     return {k: v.astype(np.float32).astype(np.float64) for k, v in p.items()}
 
 
-@pytest.fixture(scope="module")
-def net(cuda_device):
+@pytest.fixture(scope="module", params=WIDTHS, ids=lambda h: f"hidden{h}")
+def net(cuda_device, request):
     from paper_2107_01745_b300.stotree import StoWarm
-    return StoWarm(_tree(), NX, NU, hidden=H, batch=BATCH, seed=1)
+    return StoWarm(_tree(), NX, NU, hidden=request.param, batch=BATCH, seed=1)
 
 
 def _rows(seed, rows, d_in=4 * NX + 1, d_out=NX + NU):
@@ -59,7 +60,7 @@ def test_gemm_bf16_matches_fp64(cuda_device, M_, N_, K_):
 
 @pytest.mark.parametrize("rows", [BATCH, 200])
 def test_forward_matches_oracle(net, rows):
-    p = _params(2)
+    p = _params(2, net.hidden)
     net.set_params(net.flatten(p))
     X, _, _ = _rows(3, rows)
     Y = net.forward(_dev(X)).cpu().numpy().astype(np.float64)
@@ -70,14 +71,14 @@ def test_forward_matches_oracle(net, rows):
 
 
 def test_params_round_trip(net):
-    p = net.flatten(_params(4)).astype(np.float32)
+    p = net.flatten(_params(4, net.hidden)).astype(np.float32)
     net.set_params(p)
     assert np.array_equal(net.params(), p)
 
 
 @pytest.mark.parametrize("rows", [BATCH, 137])
 def test_gradients_match_oracle(net, rows):
-    p = _params(5)
+    p = _params(5, net.hidden)
     net.set_params(net.flatten(p))
     X, T, nv = _rows(6, rows)
     g, loss = net.gradients(_dev(X), _dev(T), _dev(nv))
@@ -92,7 +93,7 @@ def test_adam_steps_match_oracle(net):
     """Three Adam steps on one batch.  An Adam step moves each weight by about lr times the sign
     of its gradient, so weights whose gradient is within the gradient tolerance of zero may move
     the other way; all others must agree closely."""
-    p = _params(7)
+    p = _params(7, net.hidden)
     net.set_params(net.flatten(p))
     X, T, nv = _rows(8, BATCH)
     lr, steps = 1e-3, 3
@@ -113,7 +114,7 @@ def test_predict_matches_oracle_features(net):
     """Feature gather (x0, t/N, c of the node and two ancestors), forward pass and the scatter of
     sqrt(pi) ybar into the dual layout, for every node of three draws."""
     tree = _tree()
-    p = _params(9)
+    p = _params(9, net.hidden)
     net.set_params(net.flatten(p))
     rng = np.random.default_rng(10)
     D = 3
@@ -142,7 +143,7 @@ def test_training_reduces_loss(net):
     rng = np.random.default_rng(11)
     g = W.make_group(rng, 3, 2, 2, NX, NU, 64)
     y = np.stack([O.LQOracle(g.instance(k)).hx(np.zeros(net.m)) for k in range(64)])
-    net.set_params(net.flatten(_params(12)))
+    net.set_params(net.flatten(_params(12, net.hidden)))
     net.set_draws(_dev(g.x0.astype(np.float32)), _dev(g.c.astype(np.float32)), _dev(y.astype(np.float32)))
     assert g.tree().num_nodes == tree.num_nodes
     hist = net.train(300, lr=2e-3, seed=5).cpu().numpy()
@@ -155,4 +156,4 @@ def test_rejects_bad_sizes(cuda_device):
     with pytest.raises(StoError):
         StoWarm(_tree(), NX, NU, hidden=64, batch=BATCH)
     with pytest.raises(StoError):
-        StoWarm(_tree(), NX, NU, hidden=H, batch=300)
+        StoWarm(_tree(), NX, NU, hidden=128, batch=300)
