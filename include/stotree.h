@@ -341,7 +341,10 @@ STO_API sto_status stobatch_set_instance(stobatch_t b, int32_t group, int32_t in
 STO_API sto_status stobatch_factor(stobatch_t b, sto_stream_t stream);
 
 /* One batched solve round (Algorithm 3 / 4, one right-hand side per instance): y, hx device
- * float batch vectors; scaled as in stotree_solve_step.  Asynchronous. */
+ * float batch vectors, 16-byte aligned (else STO_ERR_INVALID_ARG); scaled as in stotree_solve_step.  The round is one persistent launch that
+ * hands out tiles of (node, instance) columns of one (group, stage) in dependency order; each
+ * tile waits, bounded, for the tiles of the stage it reads.  Asynchronous; a wait that gives up
+ * is reported by stobatch_round_status (or by the next stobatch_nama_solve). */
 STO_API sto_status stobatch_solve_step(stobatch_t b, const void *y, void *hx, int32_t homogeneous, int32_t scaled,
                                        sto_stream_t stream);
 
@@ -352,6 +355,30 @@ STO_API sto_status stobatch_solve_step(stobatch_t b, const void *y, void *hx, in
  * max_iter.  Synchronises the stream. */
 STO_API sto_status stobatch_nama_solve(stobatch_t b, const sto_opts *opts, const double *lambdas, void *y, void *z,
                                        void *hx, sto_info *infos, sto_stream_t stream);
+/* Status of the batched rounds enqueued since the last synchronising call: synchronises and
+ * returns STO_ERR_TIMEOUT if a dependency wait inside one of them gave up (their results are
+ * wrong; the error word is cleared), else STO_OK.  Errors: STO_ERR_INVALID_ARG, STO_ERR_NOT_READY,
+ * STO_ERR_CUDA, STO_ERR_TIMEOUT. */
+STO_API sto_status stobatch_round_status(stobatch_t b, sto_stream_t stream);
+
+/* The round configuration chosen by the batch's tuner, which stobatch_factor runs once per batch
+ * (the paper has no counterpart).  It times one round of each candidate -- the tile kernel with 32
+ * columns on 128-thread CTAs, 32 columns on 256-thread CTAs and 64 columns on 256-thread CTAs
+ * (each thread a block of rows and columns of the stage products), and the column kernel with
+ * one column per thread on 128-thread CTAs (only when every group has nx <= 32 and nu <= 16) --
+ * and keeps the fastest, separately for one and two right-hand sides.  For nrhs = 1 or 2: the
+ * chosen tile width in columns, the threads per CTA, the CTAs of the persistent launch (0 before
+ * a round of that variant was set up) and the measured round time of each candidate in the order
+ * above (host double[4], may be NULL; -1 for a candidate that does not apply), in milliseconds.
+ * Host only. */
+STO_API sto_status stobatch_round_config(stobatch_t b, int32_t nrhs, int32_t *tile_cols, int32_t *cta_threads,
+                                         int32_t *ctas, double *tuned_ms);
+
+/* Override the tuner's choice for rounds with nrhs = 1 or 2 right-hand sides: variant 0..3 in the
+ * order of stobatch_round_config's candidates.  Every variant computes the same round.  Errors:
+ * STO_ERR_INVALID_ARG (bad nrhs or variant, or the column kernel for a batch with nx > 32 or
+ * nu > 16).  Host only. */
+STO_API sto_status stobatch_set_round_variant(stobatch_t b, int32_t nrhs, int32_t variant);
 STO_API const char *stobatch_last_error(stobatch_t b);
 
 /* ---------------------------------------------------------------------------------------------

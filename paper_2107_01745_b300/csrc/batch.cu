@@ -30,7 +30,6 @@
 namespace sto {
 namespace {
 
-constexpr int kTC = 64;        // columns per solve tile
 constexpr int kBT = 256;       // threads per block
 constexpr int kChunkE = 2048;  // elements per block of the elementwise passes
 constexpr int kMaxStages = 64;
@@ -49,6 +48,8 @@ struct GroupDev {
     const float *box;           // [lo x | lo u][hi x | hi u]
     const float *W;             // [Q | R | P_N]
     const float *sqn;           // sqrt(pi) per node
+    int al_d, al_s, al_u;       // widest vector (4, 2 or 1 floats) that every instance's dual blocks,
+                                // state rows (s, x, c) and input rows (ubar) are aligned to
 };
 
 struct InstDev {
@@ -85,66 +86,135 @@ __device__ __forceinline__ long long doff(const GroupDev &g, int i) {
 }
 
 // ---------------------------------------------------------------------------------------------
-// Solve rounds.  A task is a tile of up to kTC columns of one (group, stage); column c of a stage
-// with n nodes is instance c / n, node soff_t + c % n.
+// Solve rounds.  A tile is up to TC (node, instance) columns of one (group, stage) and one pass;
+// column c of a stage with n nodes is instance c / n, node soff_t + c % n.  A round is one
+// persistent launch (one wave of CTAs) that hands the tiles out in ticket order: the backward
+// tiles by height (stage N_g - 1 - p of every group g, for p = 0, 1, ...), then the forward tiles
+// by depth.  A tile first waits (bounded) until every tile of the (group, stage, pass) it reads
+// is done: backward (g, t) on backward (g, t + 1) (the leaves' s comes from y), forward (g, t) on
+// forward (g, t - 1), forward (g, 0) on backward (g, 0).  Those tiles hold earlier tickets and
+// every CTA is resident, so every wait ends; a wait that gives up raises an error word, and the
+// round runs to its end without that input.  Data other CTAs write during the round (s, ubar,
+// x) is read through L2.
 // ---------------------------------------------------------------------------------------------
-struct Task {
+struct Task {  // set-up passes (gamma): a tile of kGC columns of one (group, stage)
     int group, stage, col0, ncols;
+};
+constexpr int kGC = 64;
+
+struct RTask {
+    int group, stage, col0, ncols;
+    int pass;       // 0 backward, 1 forward
+    int wait_ctr;   // counter to wait on (-1: none)
+    int wait_need;  // tiles that counter must reach
+    int done_ctr;   // counter this tile increments when done
 };
 
 template <int NR>
 struct RoundArgs {
     const GroupDev *groups;
     const InstDev *insts;
-    const Task *tasks;
+    const RTask *tasks;
+    int ntasks;
     const float *y[2];
     float *h[2];
     const float *gam;     // gamma in the dual layout (x-part, u-part)
     const float *c;       // disturbances [instance][Nn][nx] (scratch layout of s)
     const float *x0;      // [instance][64]
-    float *s, *ubar, *xs, *us;  // scratch; second right-hand side at +stride
+    float *s, *ubar, *xs;  // scratch; second right-hand side at +stride
     long long s_stride, u_stride;
     const int *active;    // per instance (null: all active)
+    unsigned *ctrs;       // tiles done per (group, stage, pass)
+    unsigned *ticket;     // next tile to hand out
+    int *err;             // raised by a dependency wait that gave up
     int homog, scaled;
 };
 
-constexpr int kMaxXU = 96;   // nx + nu <= 96 in the batched engine (nx <= 64)
-constexpr int kTP = kTC + 4; // row stride of the column tiles in shared memory (16-byte aligned)
-constexpr int kCG = kTC / 4; // column groups of 4 (one per thread of a row group)
-constexpr int kRG = kBT / kCG;  // row groups
-constexpr int kMR = (kMaxXU + kRG - 1) / kRG;  // output rows per thread, at most
+constexpr unsigned long long kBWaitNs = 1500000000ull;  // bounded waits: 1.5 s of wall time
 
-// Stage products as register-blocked FP32 GEMMs: thread (rg, cg) owns up to kMR consecutive
-// output rows and four columns of a tile, so each step of the inner dimension loads one float4 of
-// the tile and kMR matrix entries for 4 kMR fused multiply-adds per right-hand side.
-template <int NR>
-constexpr size_t bwd_smem() {  // G [nx][nxu], K [nu][nx], R~^-1 [nu][nu], S [NR][64][kTP], V [NR][32][kTP]
-    return sizeof(float) * (64 * kMaxXU + 32 * 64 + 32 * 32 + NR * 64 * kTP + NR * 32 * kTP);
-}
-template <int NR>
-constexpr size_t fwd_smem() {  // G [nx][nxu], K [nu][nx], X [NR][kMaxXU][kTP]
-    return sizeof(float) * (64 * kMaxXU + 32 * 64 + NR * kMaxXU * kTP);
-}
-
-// Columns of a task: instance data and node of each column, and whether its instance is active.
-struct ColInfo {
-    long long elem[kTC], sb[kTC], ub[kTC];
-    int node[kTC], ok[kTC];
+// Tile geometry for TC columns and nx + nu <= XU (XU = 48: nx <= 32, nu <= 16; XU = 96: nx <= 64,
+// nu <= 32).  Stage products are register-blocked FP32 GEMMs: thread (rg, cg) owns up to MR
+// consecutive output rows and four columns of the tile.
+template <int TC, int XU, int NT>
+struct Cfg {
+    static constexpr int NXM = XU * 2 / 3, NUM = XU / 3;
+    static constexpr int TP = TC + 4;                 // row stride of the column tiles (16-byte aligned)
+    static constexpr int CG = TC / 4;                 // column groups of 4
+    static constexpr int RG = NT / CG;                // row groups
+    static constexpr int MR = (XU + RG - 1) / RG;     // rows of [x; u] per thread
+    static constexpr int MU = (NUM + RG - 1) / RG;    // rows of u per thread
+    static constexpr int MX = (NXM + RG - 1) / RG;    // rows of x per thread
+    static constexpr int MAT = NXM * XU + NUM * NXM + NUM * NUM;  // G, K, R~^-1
 };
-template <int NR>
-__device__ __forceinline__ void load_cols(const RoundArgs<NR> &a, const GroupDev &g, const Task &tk, int n_t,
-                                          ColInfo &ci) {
-    if (threadIdx.x < kTC) {
+template <int NR, int TC, int XU, int NT>
+constexpr size_t round_smem() {
+    // matrices, then backward S [NR][NXM][TP], V [NR][NUM][TP], Wb [NR][XU][TP]
+    // or forward X [NR][XU][TP], UB [NR][NUM][TP], CB [NR][NXM][TP]
+    using C = Cfg<TC, XU, NT>;
+    return sizeof(float) * (C::MAT + 2 * NR * XU * C::TP);
+}
+
+// What a tile needs of its group and stage, loaded into registers once per tile (the group record
+// sits in global memory, and stores inside the tile would otherwise force its fields to be
+// re-read in every loop).
+struct Geo {
+    int nx, nu, nxu, Np, Nn, m, s0, s1, n_t, bt, inst0;
+    long long elem0, sbase, ubase;
+    float sq_t, sq_t1, pi_t;
+    const float *G, *Kt, *Ri;
+    int al_d, al_s, al_u;
+};
+__device__ __forceinline__ Geo load_geo(const GroupDev &g, int t) {
+    Geo q;
+    q.nx = g.nx;
+    q.nu = g.nu;
+    q.nxu = g.nxu;
+    q.Np = g.Np;
+    q.Nn = g.Nn;
+    q.m = g.m;
+    q.s0 = g.soff[t];
+    q.s1 = g.soff[t + 1];
+    q.n_t = q.s1 - q.s0;
+    q.bt = t < g.s ? g.b : 1;
+    q.inst0 = g.inst0;
+    q.elem0 = g.elem0;
+    q.sbase = g.sbase;
+    q.ubase = g.ubase;
+    q.sq_t = g.sq[t];
+    q.sq_t1 = t < g.N ? g.sq[t + 1] : 1.f;
+    q.pi_t = g.pi[t];
+    q.G = g.G;
+    q.Kt = g.Kt;
+    q.Ri = g.Ri;
+    q.al_d = g.al_d;
+    q.al_s = g.al_s;
+    q.al_u = g.al_u;
+    return q;
+}
+__device__ __forceinline__ long long doff(const Geo &q, int i) {
+    return i < q.Np ? (long long)i * q.nxu : (long long)q.Np * q.nxu + (long long)(i - q.Np) * q.nx;
+}
+
+// Columns of a tile: instance data and node of each column, and whether its instance is active.
+// A group's instances lie one after another in every batch array, so their offsets follow from
+// the instance index (no per-instance record is read).
+template <int TC>
+struct ColInfo {
+    long long elem[TC], sb[TC], ub[TC];
+    int node[TC], ok[TC];
+};
+template <int NR, int TC>
+__device__ __forceinline__ void load_cols(const RoundArgs<NR> &a, const Geo &q, const RTask &tk, ColInfo<TC> &ci) {
+    if (threadIdx.x < TC) {
         const int col = threadIdx.x;
         int ok = 0;
         if (col < tk.ncols) {
-            const int cc = tk.col0 + col, inst = cc / n_t;
-            const InstDev &in = a.insts[g.inst0 + inst];
-            ci.elem[col] = in.elem0;
-            ci.sb[col] = in.sbase;
-            ci.ub[col] = in.ubase;
-            ci.node[col] = g.soff[tk.stage] + cc % n_t;
-            ok = !a.active || a.active[g.inst0 + inst];
+            const int cc = tk.col0 + col, inst = cc / q.n_t;
+            ci.elem[col] = q.elem0 + (long long)inst * q.m;
+            ci.sb[col] = q.sbase + (long long)inst * q.Nn * q.nx;
+            ci.ub[col] = q.ubase + (long long)inst * q.Np * q.nu;
+            ci.node[col] = q.s0 + cc - inst * q.n_t;
+            ok = !a.active || a.active[q.inst0 + inst];
         }
         ci.ok[col] = ok;
     }
@@ -170,17 +240,17 @@ __device__ __forceinline__ void fma4x4(const float4 w, const float4 *x, float *a
     acc[3] = fmaf(w.w, x[3].w, acc[3]);
 }
 
-// e = (k * kTC + col) * R + r over [threadIdx.x, NR * kTC * R) in steps of kBT, r fastest (so that
+// e = (k * TC + col) * R + r over [threadIdx.x, NR * TC * R) in steps of NT, r fastest (so that
 // a warp's global accesses to a column's R consecutive reals coalesce), with the (k, col, r)
 // of each step advanced from the previous one instead of divided out per element.
-template <int NR, class F>
+template <int NR, int TC, int NT, class F>
 __device__ __forceinline__ void for_kcr(int R, F f) {
-    const int tot = NR * kTC * R;
+    const int tot = NR * TC * R;
     int e = threadIdx.x;
     int kc = e / R, r = e - kc * R;
-    const int dq = kBT / R, dr = kBT - dq * R;
-    for (; e < tot; e += kBT) {
-        f(kc / kTC, kc % kTC, r);
+    const int dq = NT / R, dr = NT - dq * R;
+    for (; e < tot; e += NT) {
+        f(kc / TC, kc % TC, r);
         r += dr;
         kc += dq;
         if (r >= R) {
@@ -190,64 +260,133 @@ __device__ __forceinline__ void for_kcr(int R, F f) {
     }
 }
 
-// Backward: parents of stage t.  S = sum_children s, o = [A | B]' S, v = y_u/2 + o_B + gu,
-// ubar = -(1/pi_t) R~^-1 v, s = y_x/2 + o_A + K_t' v + gx.
-template <int NR>
-__global__ void __launch_bounds__(kBT) k_bbwd(RoundArgs<NR> a, int task0) {
-    const Task tk = a.tasks[task0 + blockIdx.x];
-    const GroupDev &g = a.groups[tk.group];
-    const int nx = g.nx, nu = g.nu, nxu = g.nxu, t = tk.stage;
-    extern __shared__ __align__(16) float bsm[];
-    __shared__ ColInfo ci;
-    float *Gs = bsm;                 // [r][c], r < nx, c < nx + nu
-    float *Ks = Gs + 64 * kMaxXU;    // K_t [a][c]
-    float *Rs = Ks + 32 * 64;        // R~_t^-1 [a][b]
-    float *S = Rs + 32 * 32;         // [k][r][col]; afterwards s (without y_x/2 + gx)
-    float *V = S + NR * 64 * kTP;    // [k][a][col]: v; afterwards ubar
-    const int n_t = g.soff[t + 1] - g.soff[t];
-    const int bt = t < g.s ? g.b : 1;
-    const bool leaf_children = t + 1 == g.N;
-    load_cols(a, g, tk, n_t, ci);
-    // a tile whose instances have all converged writes nothing: leave it (before its matrices
-    // are staged; the barrier after the gather below orders their stores before any use)
-    if (!__syncthreads_or(threadIdx.x < kTC ? ci.ok[threadIdx.x] : 0)) return;
-    for (int e = threadIdx.x; e < nx * nxu; e += kBT) Gs[e] = g.G[e];
-    for (int e = threadIdx.x; e < nu * nx; e += kBT) Ks[e] = g.Kt[(size_t)t * nu * nx + e];
-    for (int e = threadIdx.x; e < nu * nu; e += kBT) Rs[e] = g.Ri[(size_t)t * nu * nu + e];
-    // S[k][r][col] = sum over the children of the column's node
-    for_kcr<NR>(nx, [&](int k, int col, int r) {
-        float acc = 0.f;
-        if (ci.ok[col]) {
-            const int i = ci.node[col];
-            const int j0 = g.soff[t + 1] + (i - g.soff[t]) * bt;
-            for (int j = j0; j < j0 + bt; ++j) {
-                if (leaf_children) {
-                    const float sc = a.scaled ? g.sq[t + 1] : 1.f;
-                    acc += 0.5f * sc * a.y[k][ci.elem[col] + doff(g, j) + r];
-                } else {
-                    acc += a.s[k * a.s_stride + ci.sb[col] + (long long)j * nx + r];
-                }
+// gather: v = load(k, col, r) for every (k, col, r) of for_kcr's enumeration, U elements per
+// thread at a time with their loads issued together, then store(k, col, r, v).
+template <int NR, int TC, int NT, int U, class L, class S>
+__device__ __forceinline__ void gather_kcr(int R, L load, S store) {
+    const int tot = NR * TC * R;
+    int e = threadIdx.x;
+    int kc = e / R, r = e - kc * R;
+    const int dq = NT / R, dr = NT - dq * R;
+    while (e < tot) {
+        float v[U];
+        int kk[U], cc[U], rr[U];
+#pragma unroll
+        for (int u = 0; u < U; ++u) {
+            kk[u] = e < tot ? kc / TC : -1;
+            cc[u] = kc % TC;
+            rr[u] = r;
+            v[u] = kk[u] >= 0 ? load(kk[u], cc[u], rr[u]) : 0.f;
+            e += NT;
+            r += dr;
+            kc += dq;
+            if (r >= R) {
+                r -= R;
+                ++kc;
             }
         }
-        S[(k * 64 + r) * kTP + col] = acc;
-    });
+#pragma unroll
+        for (int u = 0; u < U; ++u)
+            if (kk[u] >= 0) store(kk[u], cc[u], rr[u], v[u]);
+    }
+}
+
+__device__ __forceinline__ unsigned ld_acq(const unsigned *p) {
+    unsigned v;
+    asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+    return v;
+}
+__device__ __forceinline__ unsigned long long gtimer() {
+    unsigned long long t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return t;
+}
+// Bounded wait until *c >= need; on expiry the error word is raised and the wait gives up.
+__device__ void wait_count(const unsigned *c, unsigned need, int *err) {
+    if (ld_acq(c) >= need) return;
+    const unsigned long long t0 = gtimer();
+    while (gtimer() - t0 < kBWaitNs) {
+        for (int it = 0; it < 32; ++it) {
+            if (ld_acq(c) >= need) return;
+            __nanosleep(64);
+        }
+        if (*(volatile int *)err) return;
+    }
+    atomicCAS(err, 0, 1);
+}
+
+// Backward tile: parents of stage t.  S = sum_children s, o = [A | B]' S, v = y_u/2 + o_B + gu,
+// ubar = -(1/pi_t) R~^-1 v, s = y_x/2 + o_A + K_t' v + gx.  Every global read of the tile (the
+// children's s, or the leaves' y, and the column's y and gamma block) is issued in one gather.
+template <int NR, int TC, int XU, int NT>
+__device__ __forceinline__ void bwd_tile(const RoundArgs<NR> &a, const RTask &tk, float *sm, ColInfo<TC> &ci,
+                                         int &staged) {
+    using C = Cfg<TC, XU, NT>;
+    const int t = tk.stage;
+    const Geo q = load_geo(a.groups[tk.group], t);
+    const int nx = q.nx, nu = q.nu, nxu = q.nxu;
+    float *Gs = sm;                      // [r][c], r < nx, c < nx + nu
+    float *Ks = Gs + C::NXM * XU;        // K_t [a][c]
+    float *Rs = Ks + C::NUM * C::NXM;    // R~_t^-1 [a][b]
+    float *S = sm + C::MAT;              // [k][r][col]; afterwards s (without y_x/2 + gx)
+    float *V = S + NR * C::NXM * C::TP;  // [k][a][col]: v; afterwards ubar
+    float *Wb = V + NR * C::NUM * C::TP; // [k][c][col]: y/2 (scaled) + gamma of the column's block
+    const int bt = q.bt;
+    const bool leaf_children = q.s1 >= q.Np;  // the children of stage t are leaves
+    load_cols<NR, TC>(a, q, tk, ci);
+    // a tile whose instances have all converged reads and writes nothing (the barrier after the
+    // gather below orders the matrices' staging stores before any use)
+    if (!__syncthreads_or(threadIdx.x < TC ? ci.ok[threadIdx.x] : 0)) return;
+    const int key = 2 * (tk.group * (kMaxStages + 1) + t);
+    if (staged != key) {
+        for (int e = threadIdx.x; e < nx * nxu; e += NT) Gs[e] = q.G[e];
+        for (int e = threadIdx.x; e < nu * nx; e += NT) Ks[e] = q.Kt[(size_t)t * nu * nx + e];
+        for (int e = threadIdx.x; e < nu * nu; e += NT) Rs[e] = q.Ri[(size_t)t * nu * nu + e];
+        staged = key;
+    }
+    {
+        const float sc = a.scaled ? q.sq_t : 1.f, scc = a.scaled ? q.sq_t1 : 1.f;
+        // rows r < nx: S; rows nx + c: the block's entry c
+        gather_kcr<NR, TC, NT, 4>(
+            nx + nxu,
+            [&](int k, int col, int r) -> float {
+                if (!ci.ok[col]) return 0.f;
+                const int i = ci.node[col];
+                if (r < nx) {
+                    const int j0 = q.s1 + (i - q.s0) * bt;
+                    float acc = 0.f;
+                    for (int j = j0; j < j0 + bt; ++j)
+                        acc += leaf_children ? 0.5f * scc * a.y[k][ci.elem[col] + doff(q, j) + r]
+                                             : __ldcg(a.s + k * a.s_stride + ci.sb[col] + (long long)j * nx + r);
+                    return acc;
+                }
+                const long long o = ci.elem[col] + doff(q, i) + (r - nx);
+                return 0.5f * sc * a.y[k][o] + (a.homog ? 0.f : a.gam[o]);
+            },
+            [&](int k, int col, int r, float v) {
+                if (r < nx)
+                    S[(k * C::NXM + r) * C::TP + col] = v;
+                else
+                    Wb[(k * XU + r - nx) * C::TP + col] = v;
+            });
+    }
     __syncthreads();
-    const int cg = threadIdx.x % kCG, rg = threadIdx.x / kCG;
-    const int mr = (nxu + kRG - 1) / kRG, r0 = rg * mr;
-    float acc[NR][kMR][4];
+    const int cg = threadIdx.x % C::CG, rg = threadIdx.x / C::CG;
+    const int mr = (nxu + C::RG - 1) / C::RG, r0 = rg * mr;
+    float acc[NR][C::MR][4];
 #pragma unroll
     for (int k = 0; k < NR; ++k)
 #pragma unroll
-        for (int m = 0; m < kMR; ++m)
+        for (int m = 0; m < C::MR; ++m)
 #pragma unroll
             for (int q = 0; q < 4; ++q) acc[k][m][q] = 0.f;
     // o = [A | B]' S
     for (int r = 0; r < nx; ++r) {
         float4 s4[NR];
 #pragma unroll
-        for (int k = 0; k < NR; ++k) s4[k] = *reinterpret_cast<const float4 *>(S + (k * 64 + r) * kTP + cg * 4);
+        for (int k = 0; k < NR; ++k) s4[k] = *reinterpret_cast<const float4 *>(S + (k * C::NXM + r) * C::TP + cg * 4);
 #pragma unroll
-        for (int m = 0; m < kMR; ++m)
+        for (int m = 0; m < C::MR; ++m)
             if (m < mr && r0 + m < nxu) {
                 const float gv = Gs[r * nxu + r0 + m];
 #pragma unroll
@@ -259,30 +398,22 @@ __global__ void __launch_bounds__(kBT) k_bbwd(RoundArgs<NR> a, int task0) {
                 }
             }
     }
-    // o_B rows -> V; then v = o_B + y_u/2 + gu
+    // v = o_B + y_u/2 + gu -> V
 #pragma unroll
-    for (int m = 0; m < kMR; ++m) {
+    for (int m = 0; m < C::MR; ++m) {
         const int c = r0 + m;
         if (m < mr && c >= nx && c < nxu)
 #pragma unroll
-            for (int k = 0; k < NR; ++k)
-                *reinterpret_cast<float4 *>(V + (k * 32 + c - nx) * kTP + cg * 4) =
-                    make_float4(acc[k][m][0], acc[k][m][1], acc[k][m][2], acc[k][m][3]);
-    }
-    __syncthreads();
-    {
-        const float sc = a.scaled ? g.sq[t] : 1.f;
-        for_kcr<NR>(nu, [&](int k, int col, int aa) {
-            if (ci.ok[col]) {
-                const long long o = ci.elem[col] + doff(g, ci.node[col]) + nx + aa;
-                V[(k * 32 + aa) * kTP + col] += 0.5f * sc * a.y[k][o] + (a.homog ? 0.f : a.gam[o]);
+            for (int k = 0; k < NR; ++k) {
+                const float4 w = *reinterpret_cast<const float4 *>(Wb + (k * XU + c) * C::TP + cg * 4);
+                *reinterpret_cast<float4 *>(V + (k * C::NUM + c - nx) * C::TP + cg * 4) =
+                    make_float4(acc[k][m][0] + w.x, acc[k][m][1] + w.y, acc[k][m][2] + w.z, acc[k][m][3] + w.w);
             }
-        });
     }
     __syncthreads();
     // rows c < nx: s = o_A + K' v; rows c = nx + a: ubar = -(1/pi_t) R~^-1 v
 #pragma unroll
-    for (int m = 0; m < kMR; ++m)
+    for (int m = 0; m < C::MR; ++m)
         if (r0 + m >= nx)
 #pragma unroll
             for (int k = 0; k < NR; ++k)
@@ -291,9 +422,9 @@ __global__ void __launch_bounds__(kBT) k_bbwd(RoundArgs<NR> a, int task0) {
     for (int aa = 0; aa < nu; ++aa) {
         float4 v4[NR];
 #pragma unroll
-        for (int k = 0; k < NR; ++k) v4[k] = *reinterpret_cast<const float4 *>(V + (k * 32 + aa) * kTP + cg * 4);
+        for (int k = 0; k < NR; ++k) v4[k] = *reinterpret_cast<const float4 *>(V + (k * C::NUM + aa) * C::TP + cg * 4);
 #pragma unroll
-        for (int m = 0; m < kMR; ++m) {
+        for (int m = 0; m < C::MR; ++m) {
             const int c = r0 + m;
             if (m < mr && c < nxu) {
                 const float cf = c < nx ? Ks[aa * nx + c] : Rs[(c - nx) * nu + aa];
@@ -307,93 +438,113 @@ __global__ void __launch_bounds__(kBT) k_bbwd(RoundArgs<NR> a, int task0) {
             }
         }
     }
-    __syncthreads();  // every thread is done with S and V
-    const float ipi = 1.f / g.pi[t];
+    // results in place: s = o_A + K'v + y_x/2 + gx over S (read only before the barrier above),
+    // ubar over the u rows of Wb (consumed into V before it); this thread alone reads the Wb
+    // entries it overwrites
+    const float ipi = 1.f / q.pi_t;
 #pragma unroll
-    for (int m = 0; m < kMR; ++m) {
+    for (int m = 0; m < C::MR; ++m) {
         const int c = r0 + m;
         if (m < mr && c < nxu)
 #pragma unroll
             for (int k = 0; k < NR; ++k) {
-                float *dst = c < nx ? S + (k * 64 + c) * kTP + cg * 4 : V + (k * 32 + c - nx) * kTP + cg * 4;
-                const float f = c < nx ? 1.f : -ipi;
-                *reinterpret_cast<float4 *>(dst) =
-                    make_float4(f * acc[k][m][0], f * acc[k][m][1], f * acc[k][m][2], f * acc[k][m][3]);
+                float4 *wp = reinterpret_cast<float4 *>(Wb + (k * XU + c) * C::TP + cg * 4);
+                if (c < nx) {
+                    const float4 w = *wp;
+                    *reinterpret_cast<float4 *>(S + (k * C::NXM + c) * C::TP + cg * 4) =
+                        make_float4(acc[k][m][0] + w.x, acc[k][m][1] + w.y, acc[k][m][2] + w.z, acc[k][m][3] + w.w);
+                } else {
+                    *wp = make_float4(-ipi * acc[k][m][0], -ipi * acc[k][m][1], -ipi * acc[k][m][2], -ipi * acc[k][m][3]);
+                }
             }
     }
     __syncthreads();
-    // coalesced write-out: ubar, and s = y_x/2 + (o_A + K'v) + gx
-    for_kcr<NR>(nu, [&](int k, int col, int aa) {
-        if (ci.ok[col])
-            a.ubar[k * a.u_stride + ci.ub[col] + (long long)ci.node[col] * nu + aa] = V[(k * 32 + aa) * kTP + col];
+    // coalesced write-out of ubar and s
+    for_kcr<NR, TC, NT>(nxu, [&](int k, int col, int c) {
+        if (!ci.ok[col]) return;
+        const int i = ci.node[col];
+        if (c < nx)
+            a.s[k * a.s_stride + ci.sb[col] + (long long)i * nx + c] = S[(k * C::NXM + c) * C::TP + col];
+        else
+            a.ubar[k * a.u_stride + ci.ub[col] + (long long)i * nu + c - nx] = Wb[(k * XU + c) * C::TP + col];
     });
-    {
-        const float sc = a.scaled ? g.sq[t] : 1.f;
-        for_kcr<NR>(nx, [&](int k, int col, int r) {
-            if (ci.ok[col]) {
-                const int i = ci.node[col];
-                const long long o = ci.elem[col] + doff(g, i) + r;
-                a.s[k * a.s_stride + ci.sb[col] + (long long)i * nx + r] =
-                    S[(k * 64 + r) * kTP + col] + 0.5f * sc * a.y[k][o] + (a.homog ? 0.f : a.gam[o]);
-            }
-        });
-    }
 }
 
-// Forward: nodes of stage t.  x from the parent's pass (or x0 at the root); u = K x + ubar;
-// h = S [x; u]; every child j gets x^j = A x + B u + c^j.  Leaves (t = N) only write h.
-template <int NR>
-__global__ void __launch_bounds__(kBT) k_bfwd(RoundArgs<NR> a, int task0) {
-    const Task tk = a.tasks[task0 + blockIdx.x];
-    const GroupDev &g = a.groups[tk.group];
-    const int nx = g.nx, nu = g.nu, nxu = g.nxu, t = tk.stage;
-    extern __shared__ __align__(16) float bsm[];
-    __shared__ ColInfo ci;
-    float *Gs = bsm;
-    float *Ks = Gs + 64 * kMaxXU;
-    float *X = Ks + 32 * 64;  // [k][row][col]: x then u per column
-    const bool leaf = t == g.N;
-    const int n_t = g.soff[t + 1] - g.soff[t];
-    load_cols(a, g, tk, n_t, ci);
-    // a tile whose instances have all converged writes nothing: leave it (before its matrices
-    // are staged; the barrier after the gather below orders their stores before any use)
-    if (!__syncthreads_or(threadIdx.x < kTC ? ci.ok[threadIdx.x] : 0)) return;
-    for (int e = threadIdx.x; e < nx * nxu; e += kBT) Gs[e] = g.G[e];
-    if (!leaf)
-        for (int e = threadIdx.x; e < nu * nx; e += kBT) Ks[e] = g.Kt[(size_t)t * nu * nx + e];
-    for_kcr<NR>(nx, [&](int k, int col, int r) {
-        float val = 0.f;
-        if (ci.ok[col]) {
-            if (t == 0) {
-                const int inst = (tk.col0 + col) / n_t;
-                val = a.homog ? 0.f : a.x0[(long long)(g.inst0 + inst) * 64 + r];
-            } else {
-                val = a.xs[k * a.s_stride + ci.sb[col] + (long long)ci.node[col] * nx + r];
-            }
-        }
-        X[(k * kMaxXU + r) * kTP + col] = val;
-    });
+// Forward tile: nodes of stage t.  x from the parent's tile (or x0 at the root); u = K x + ubar;
+// h = S [x; u]; every child j gets x^j = A x + B u + c^j.  Leaves (t = N) only write h.  Every
+// global read (x, ubar, and the only child's c on non-branching stages) is one gather.
+template <int NR, int TC, int XU, int NT>
+__device__ __forceinline__ void fwd_tile(const RoundArgs<NR> &a, const RTask &tk, float *sm, ColInfo<TC> &ci,
+                                         int &staged) {
+    using C = Cfg<TC, XU, NT>;
+    const int t = tk.stage;
+    const Geo q = load_geo(a.groups[tk.group], t);
+    const int nx = q.nx, nu = q.nu, nxu = q.nxu;
+    float *Gs = sm;
+    float *Ks = Gs + C::NXM * XU;
+    float *X = sm + C::MAT;                 // [k][row][col]: x then u per column
+    float *UB = X + NR * XU * C::TP;        // [k][a][col]: ubar
+    float *CB = UB + NR * C::NUM * C::TP;   // [k][r][col]: c of the only child (one child per node)
+    const bool leaf = q.s0 >= q.Np;
+    const int bt = q.bt;
+    const bool one_child = !leaf && bt == 1 && !a.homog;
+    load_cols<NR, TC>(a, q, tk, ci);
+    if (!__syncthreads_or(threadIdx.x < TC ? ci.ok[threadIdx.x] : 0)) return;
+    const int key = 2 * (tk.group * (kMaxStages + 1) + t) + 1;
+    if (staged != key) {
+        for (int e = threadIdx.x; e < nx * nxu; e += NT) Gs[e] = q.G[e];
+        if (!leaf)
+            for (int e = threadIdx.x; e < nu * nx; e += NT) Ks[e] = q.Kt[(size_t)t * nu * nx + e];
+        staged = key;
+    }
+    {
+        // rows r < nx: x; nx <= r < nx + nu: ubar (nonleaf); nx + nu <= r: c of the only child
+        const int R = leaf ? nx : (one_child ? nxu + nx : nxu);
+        gather_kcr<NR, TC, NT, 4>(
+            R,
+            [&](int k, int col, int r) -> float {
+                if (!ci.ok[col]) return 0.f;
+                const int i = ci.node[col];
+                if (r < nx) {
+                    if (t == 0) {
+                        const int inst = (tk.col0 + col) / q.n_t;
+                        return a.homog ? 0.f : a.x0[(long long)(q.inst0 + inst) * 64 + r];
+                    }
+                    return __ldcg(a.xs + k * a.s_stride + ci.sb[col] + (long long)i * nx + r);
+                }
+                if (r < nxu) return __ldcg(a.ubar + k * a.u_stride + ci.ub[col] + (long long)i * nu + r - nx);
+                const int j = q.s1 + (i - q.s0);
+                return a.c[ci.sb[col] + (long long)j * nx + r - nxu];
+            },
+            [&](int k, int col, int r, float v) {
+                if (r < nx)
+                    X[(k * XU + r) * C::TP + col] = v;
+                else if (r < nxu)
+                    UB[(k * C::NUM + r - nx) * C::TP + col] = v;
+                else
+                    CB[(k * C::NXM + r - nxu) * C::TP + col] = v;
+            });
+    }
     __syncthreads();
-    const int cg = threadIdx.x % kCG, rg = threadIdx.x / kCG;
-    const float sc = a.scaled ? g.sq[t] : 1.f;
+    const int cg = threadIdx.x % C::CG, rg = threadIdx.x / C::CG;
+    const float sc = a.scaled ? q.sq_t : 1.f;
     if (!leaf) {
-        // u = K x (rows a of u over the row groups), then + ubar
-        const int mu = (nu + kRG - 1) / kRG, a0 = rg * mu;
-        constexpr int kMU = (32 + kRG - 1) / kRG;
-        float u[NR][kMU][4];
+        // u = K x + ubar (rows a of u over the row groups)
+        const int mu = (nu + C::RG - 1) / C::RG, a0 = rg * mu;
+        float u[NR][C::MU][4];
 #pragma unroll
         for (int k = 0; k < NR; ++k)
 #pragma unroll
-            for (int m = 0; m < kMU; ++m)
+            for (int m = 0; m < C::MU; ++m)
 #pragma unroll
                 for (int q = 0; q < 4; ++q) u[k][m][q] = 0.f;
         for (int r = 0; r < nx; ++r) {
             float4 x4[NR];
 #pragma unroll
             for (int k = 0; k < NR; ++k)
-                x4[k] = *reinterpret_cast<const float4 *>(X + (k * kMaxXU + r) * kTP + cg * 4);
+                x4[k] = *reinterpret_cast<const float4 *>(X + (k * XU + r) * C::TP + cg * 4);
 #pragma unroll
-            for (int m = 0; m < kMU; ++m)
+            for (int m = 0; m < C::MU; ++m)
                 if (m < mu && a0 + m < nu) {
                     const float kv = Ks[(a0 + m) * nx + r];
 #pragma unroll
@@ -406,42 +557,29 @@ __global__ void __launch_bounds__(kBT) k_bfwd(RoundArgs<NR> a, int task0) {
                 }
         }
 #pragma unroll
-        for (int m = 0; m < kMU; ++m)
+        for (int m = 0; m < C::MU; ++m)
             if (m < mu && a0 + m < nu)
 #pragma unroll
-                for (int k = 0; k < NR; ++k)
-                    *reinterpret_cast<float4 *>(X + (k * kMaxXU + nx + a0 + m) * kTP + cg * 4) =
-                        make_float4(u[k][m][0], u[k][m][1], u[k][m][2], u[k][m][3]);
-        __syncthreads();
-        for_kcr<NR>(nu, [&](int k, int col, int aa) {
-            if (ci.ok[col])
-                X[(k * kMaxXU + nx + aa) * kTP + col] +=
-                    a.ubar[k * a.u_stride + ci.ub[col] + (long long)ci.node[col] * nu + aa];
-        });
+                for (int k = 0; k < NR; ++k) {
+                    const float4 w = *reinterpret_cast<const float4 *>(UB + (k * C::NUM + a0 + m) * C::TP + cg * 4);
+                    *reinterpret_cast<float4 *>(X + (k * XU + nx + a0 + m) * C::TP + cg * 4) =
+                        make_float4(u[k][m][0] + w.x, u[k][m][1] + w.y, u[k][m][2] + w.z, u[k][m][3] + w.w);
+                }
         __syncthreads();
     }
-    // h for the stage's nodes, primal scratch
+    // h for the stage's nodes
     const int rows = leaf ? nx : nxu;
-    for_kcr<NR>(rows, [&](int k, int col, int r) {
-        if (ci.ok[col]) {
-            const int i = ci.node[col];
-            const float val = X[(k * kMaxXU + r) * kTP + col];
-            a.h[k][ci.elem[col] + doff(g, i) + r] = sc * val;
-            if (r < nx)
-                a.xs[k * a.s_stride + ci.sb[col] + (long long)i * nx + r] = val;
-            else
-                a.us[k * a.u_stride + ci.ub[col] + (long long)i * nu + r - nx] = val;
-        }
+    for_kcr<NR, TC, NT>(rows, [&](int k, int col, int r) {
+        if (ci.ok[col]) a.h[k][ci.elem[col] + doff(q, ci.node[col]) + r] = sc * X[(k * XU + r) * C::TP + col];
     });
     if (leaf) return;
     // children: x^j = [A | B][x; u] + c^j (rows r of x over the row groups)
-    const int mx = (nx + kRG - 1) / kRG, x0r = rg * mx;
-    constexpr int kMX = (64 + kRG - 1) / kRG;
-    float acc[NR][kMX][4];
+    const int mx = (nx + C::RG - 1) / C::RG, x0r = rg * mx;
+    float acc[NR][C::MX][4];
 #pragma unroll
     for (int k = 0; k < NR; ++k)
 #pragma unroll
-        for (int m = 0; m < kMX; ++m)
+        for (int m = 0; m < C::MX; ++m)
 #pragma unroll
             for (int q = 0; q < 4; ++q) acc[k][m][q] = 0.f;
     int qq = 0;
@@ -453,9 +591,9 @@ __global__ void __launch_bounds__(kBT) k_bfwd(RoundArgs<NR> a, int task0) {
             for (int k = 0; k < NR; ++k)
 #pragma unroll
                 for (int u = 0; u < 4; ++u)
-                    x4[k][u] = *reinterpret_cast<const float4 *>(X + (k * kMaxXU + qq + u) * kTP + cg * 4);
+                    x4[k][u] = *reinterpret_cast<const float4 *>(X + (k * XU + qq + u) * C::TP + cg * 4);
 #pragma unroll
-            for (int m = 0; m < kMX; ++m)
+            for (int m = 0; m < C::MX; ++m)
                 if (m < mx && x0r + m < nx) {
                     const float4 g4 = *reinterpret_cast<const float4 *>(Gs + (x0r + m) * nxu + qq);
 #pragma unroll
@@ -466,9 +604,9 @@ __global__ void __launch_bounds__(kBT) k_bfwd(RoundArgs<NR> a, int task0) {
     for (; qq < nxu; ++qq) {
         float4 x4[NR];
 #pragma unroll
-        for (int k = 0; k < NR; ++k) x4[k] = *reinterpret_cast<const float4 *>(X + (k * kMaxXU + qq) * kTP + cg * 4);
+        for (int k = 0; k < NR; ++k) x4[k] = *reinterpret_cast<const float4 *>(X + (k * XU + qq) * C::TP + cg * 4);
 #pragma unroll
-        for (int m = 0; m < kMX; ++m)
+        for (int m = 0; m < C::MX; ++m)
             if (m < mx && x0r + m < nx) {
                 const float gv = Gs[(x0r + m) * nxu + qq];
 #pragma unroll
@@ -480,27 +618,390 @@ __global__ void __launch_bounds__(kBT) k_bfwd(RoundArgs<NR> a, int task0) {
                 }
             }
     }
-    __syncthreads();  // every thread is done with X
+    // the children's states over CB (this thread alone reads the CB entries it overwrites)
 #pragma unroll
-    for (int m = 0; m < kMX; ++m)
+    for (int m = 0; m < C::MX; ++m)
         if (m < mx && x0r + m < nx)
 #pragma unroll
-            for (int k = 0; k < NR; ++k)
-                *reinterpret_cast<float4 *>(X + (k * kMaxXU + x0r + m) * kTP + cg * 4) =
-                    make_float4(acc[k][m][0], acc[k][m][1], acc[k][m][2], acc[k][m][3]);
+            for (int k = 0; k < NR; ++k) {
+                float4 *cp = reinterpret_cast<float4 *>(CB + (k * C::NXM + x0r + m) * C::TP + cg * 4);
+                float4 v = make_float4(acc[k][m][0], acc[k][m][1], acc[k][m][2], acc[k][m][3]);
+                if (one_child) {
+                    const float4 w = *cp;
+                    v.x += w.x;
+                    v.y += w.y;
+                    v.z += w.z;
+                    v.w += w.w;
+                }
+                *cp = v;
+            }
     __syncthreads();
-    const int bt = t < g.s ? g.b : 1;
-    for_kcr<NR>(nx, [&](int k, int col, int r) {
+    for_kcr<NR, TC, NT>(nx, [&](int k, int col, int r) {
         if (ci.ok[col]) {
             const int i = ci.node[col];
-            const int j0 = g.soff[t + 1] + (i - g.soff[t]) * bt;
-            const float xv = X[(k * kMaxXU + r) * kTP + col];
-            for (int j = j0; j < j0 + bt; ++j) {
-                const float cj = a.homog ? 0.f : a.c[ci.sb[col] + (long long)j * nx + r];
-                a.xs[k * a.s_stride + ci.sb[col] + (long long)j * nx + r] = xv + cj;
+            const int j0 = q.s1 + (i - q.s0) * bt;
+            const float xv = CB[(k * C::NXM + r) * C::TP + col];
+            if (one_child || a.homog) {
+                a.xs[k * a.s_stride + ci.sb[col] + (long long)j0 * nx + r] = xv;
+                for (int j = j0 + 1; j < j0 + bt; ++j) a.xs[k * a.s_stride + ci.sb[col] + (long long)j * nx + r] = xv;
+            } else {
+                for (int j = j0; j < j0 + bt; ++j)
+                    a.xs[k * a.s_stride + ci.sb[col] + (long long)j * nx + r] = xv + a.c[ci.sb[col] + (long long)j * nx + r];
             }
         }
     });
+}
+
+// One solve round as one persistent launch over the round's tiles (see above).  Thread 0 draws the
+// next ticket while the CTA works on the current tile; a CTA that holds a drawn ticket is working
+// on a lower one, so the holder of the lowest unfinished ticket is always working on it.
+template <int NR, int TC, int XU, int NT>
+__global__ void __launch_bounds__(NT) k_bround(RoundArgs<NR> a) {
+    extern __shared__ __align__(16) float bsm[];
+    __shared__ ColInfo<TC> ci;
+    __shared__ int s_tick[2];
+    int staged = -1;  // (group, stage, pass) whose matrices sit in shared memory
+    if (threadIdx.x == 0) s_tick[0] = (int)atomicAdd(a.ticket, 1u);
+    __syncthreads();
+    for (int it = 0;; ++it) {
+        const int k = s_tick[it & 1];
+        if (k >= a.ntasks) return;
+        const RTask tk = a.tasks[k];
+        if (threadIdx.x == 0) {
+            s_tick[(it + 1) & 1] = (int)atomicAdd(a.ticket, 1u);
+            if (tk.wait_ctr >= 0) wait_count(a.ctrs + tk.wait_ctr, (unsigned)tk.wait_need, a.err);
+        }
+        __syncthreads();
+        if (tk.pass == 0)
+            bwd_tile<NR, TC, XU, NT>(a, tk, bsm, ci, staged);
+        else
+            fwd_tile<NR, TC, XU, NT>(a, tk, bsm, ci, staged);
+        // every thread's stores of the tile precede thread 0's fence and count
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            __threadfence();
+            atomicAdd(a.ctrs + tk.done_ctr, 1u);
+        }
+    }
+}
+
+// Row access of the column kernel: n (runtime, at most N) consecutive floats at p, with 16- or
+// 8-byte vector accesses when al = 4 or 2 (p aligned to al floats and al dividing n); the entries
+// of d beyond n are zero.  cg: read through L2 (data other CTAs write during the round).
+template <int N>
+__device__ __forceinline__ void row_load(float (&d)[N], const float *p, int n, int al, bool cg) {
+    if (al == 4) {
+#pragma unroll
+        for (int q = 0; q < N / 4; ++q) {
+            float4 v = make_float4(0.f, 0.f, 0.f, 0.f);
+            if (4 * q < n) v = cg ? __ldcg(reinterpret_cast<const float4 *>(p) + q) : reinterpret_cast<const float4 *>(p)[q];
+            d[4 * q] = v.x;
+            d[4 * q + 1] = v.y;
+            d[4 * q + 2] = v.z;
+            d[4 * q + 3] = v.w;
+        }
+    } else if (al == 2) {
+#pragma unroll
+        for (int q = 0; q < N / 2; ++q) {
+            float2 v = make_float2(0.f, 0.f);
+            if (2 * q < n) v = cg ? __ldcg(reinterpret_cast<const float2 *>(p) + q) : reinterpret_cast<const float2 *>(p)[q];
+            d[2 * q] = v.x;
+            d[2 * q + 1] = v.y;
+        }
+    } else {
+#pragma unroll
+        for (int r = 0; r < N; ++r) d[r] = r < n ? (cg ? __ldcg(p + r) : p[r]) : 0.f;
+    }
+}
+template <int N>
+__device__ __forceinline__ void row_store(float *p, const float (&v)[N], int n, int al) {
+    if (al == 4) {
+#pragma unroll
+        for (int q = 0; q < N / 4; ++q)
+            if (4 * q < n) reinterpret_cast<float4 *>(p)[q] = make_float4(v[4 * q], v[4 * q + 1], v[4 * q + 2], v[4 * q + 3]);
+    } else if (al == 2) {
+#pragma unroll
+        for (int q = 0; q < N / 2; ++q)
+            if (2 * q < n) reinterpret_cast<float2 *>(p)[q] = make_float2(v[2 * q], v[2 * q + 1]);
+    } else {
+#pragma unroll
+        for (int r = 0; r < N; ++r)
+            if (r < n) p[r] = v[r];
+    }
+}
+
+// Column kernel: one (node, instance) column per thread, for batches whose groups all have
+// nx <= NXP and nu <= NUP (NXP, NUP compile-time).  The stage matrices sit in shared memory
+// zero-padded to the compile-time widths (A columns at [0, NXP), B columns at [NXP, NXP + NUP)),
+// so every product runs over registers with fixed indices; all threads read the same matrix
+// entry at once (a broadcast).  A thread loads its own column's vectors, so a tile needs no
+// barrier beyond the matrices' staging.  Tiles and their ticket order are those of k_bround
+// with NT columns per tile.
+template <int NXP, int NUP>
+__device__ __forceinline__ void col_stage(const Geo &q, int t, bool leaf, float *Gp, float *Kp, float *Rp, int NT) {
+    const int nx = q.nx, nu = q.nu, nxu = q.nxu;
+    for (int e = threadIdx.x; e < NXP * (NXP + NUP); e += NT) {
+        const int r = e / (NXP + NUP), c = e - r * (NXP + NUP);
+        float v = 0.f;
+        if (r < nx) {
+            if (c < NXP) {
+                if (c < nx) v = q.G[r * nxu + c];
+            } else if (c - NXP < nu) {
+                v = q.G[r * nxu + nx + c - NXP];
+            }
+        }
+        Gp[e] = v;
+    }
+    if (!leaf) {
+        for (int e = threadIdx.x; e < NUP * NXP; e += NT) {
+            const int aa = e / NXP, c = e - aa * NXP;
+            Kp[e] = (aa < nu && c < nx) ? q.Kt[(size_t)t * nu * nx + aa * nx + c] : 0.f;
+        }
+        for (int e = threadIdx.x; e < NUP * NUP; e += NT) {
+            const int aa = e / NUP, bb = e - aa * NUP;
+            Rp[e] = (aa < nu && bb < nu) ? q.Ri[(size_t)t * nu * nu + aa * nu + bb] : 0.f;
+        }
+    }
+}
+
+template <int NR, int NXP, int NUP>
+__device__ __forceinline__ void col_bwd(const RoundArgs<NR> &a, const Geo &q, int t, int inst, int i,
+                                        const float *Gp, const float *Kp, const float *Rp) {
+    constexpr int NXU = NXP + NUP;
+    const int nx = q.nx, nu = q.nu;
+    const long long elem = q.elem0 + (long long)inst * q.m;
+    const long long sb = q.sbase + (long long)inst * q.Nn * nx;
+    const long long ub = q.ubase + (long long)inst * q.Np * nu;
+    const bool leaf_children = q.s1 >= q.Np;
+    const int j0 = q.s1 + (i - q.s0) * q.bt;
+    const float sc = a.scaled ? q.sq_t : 1.f, scc = a.scaled ? q.sq_t1 : 1.f;
+    const float ipi = 1.f / q.pi_t;
+    const long long oi = elem + doff(q, i);
+#pragma unroll 1
+    for (int k = 0; k < NR; ++k) {
+        // S = sum of the children's s (or the leaves' y / 2), then o = [A | B]' S
+        float S[NXP];
+        if (leaf_children) {
+            row_load<NXP>(S, a.y[k] + elem + doff(q, j0), nx, q.al_d, false);
+#pragma unroll
+            for (int r = 0; r < NXP; ++r) S[r] *= 0.5f * scc;
+        } else {
+            row_load<NXP>(S, a.s + k * a.s_stride + sb + (long long)j0 * nx, nx, q.al_s, true);
+        }
+        for (int j = j0 + 1; j < j0 + q.bt; ++j) {
+            float Sj[NXP];
+            if (leaf_children) {
+                row_load<NXP>(Sj, a.y[k] + elem + doff(q, j), nx, q.al_d, false);
+#pragma unroll
+                for (int r = 0; r < NXP; ++r) S[r] += 0.5f * scc * Sj[r];
+            } else {
+                row_load<NXP>(Sj, a.s + k * a.s_stride + sb + (long long)j * nx, nx, q.al_s, true);
+#pragma unroll
+                for (int r = 0; r < NXP; ++r) S[r] += Sj[r];
+            }
+        }
+        float o[NXU];
+#pragma unroll
+        for (int c = 0; c < NXU; ++c) o[c] = 0.f;
+#pragma unroll
+        for (int r = 0; r < NXP; ++r) {
+            const float sr = S[r];
+#pragma unroll
+            for (int c4 = 0; c4 < NXU / 4; ++c4) {
+                const float4 g = *reinterpret_cast<const float4 *>(Gp + r * NXU + 4 * c4);
+                o[4 * c4 + 0] = fmaf(g.x, sr, o[4 * c4 + 0]);
+                o[4 * c4 + 1] = fmaf(g.y, sr, o[4 * c4 + 1]);
+                o[4 * c4 + 2] = fmaf(g.z, sr, o[4 * c4 + 2]);
+                o[4 * c4 + 3] = fmaf(g.w, sr, o[4 * c4 + 3]);
+            }
+        }
+        // v = o_B + y_u/2 + gu
+        const float *yi = a.y[k] + oi;
+        const float *gi = a.gam + oi;
+        float v[NUP], w[NUP];
+        row_load<NUP>(v, yi + nx, nu, q.al_d, false);
+        if (!a.homog) row_load<NUP>(w, gi + nx, nu, q.al_d, false);
+#pragma unroll
+        for (int aa = 0; aa < NUP; ++aa) v[aa] = o[NXP + aa] + 0.5f * sc * v[aa] + (a.homog ? 0.f : w[aa]);
+        // ubar = -(1/pi) R~^-1 v
+        {
+            float ubv[NUP];
+#pragma unroll
+            for (int aa = 0; aa < NUP; ++aa) {
+                float acc = 0.f;
+#pragma unroll
+                for (int b4 = 0; b4 < NUP / 4; ++b4) {
+                    const float4 rr = *reinterpret_cast<const float4 *>(Rp + aa * NUP + 4 * b4);
+                    acc = fmaf(rr.x, v[4 * b4 + 0], acc);
+                    acc = fmaf(rr.y, v[4 * b4 + 1], acc);
+                    acc = fmaf(rr.z, v[4 * b4 + 2], acc);
+                    acc = fmaf(rr.w, v[4 * b4 + 3], acc);
+                }
+                ubv[aa] = -ipi * acc;
+            }
+            row_store<NUP>(a.ubar + k * a.u_stride + ub + (long long)i * nu, ubv, nu, q.al_u);
+        }
+        // s = o_A + K'v + y_x/2 + gx
+#pragma unroll
+        for (int aa = 0; aa < NUP; ++aa) {
+            const float va = v[aa];
+#pragma unroll
+            for (int c4 = 0; c4 < NXP / 4; ++c4) {
+                const float4 kk = *reinterpret_cast<const float4 *>(Kp + aa * NXP + 4 * c4);
+                o[4 * c4 + 0] = fmaf(kk.x, va, o[4 * c4 + 0]);
+                o[4 * c4 + 1] = fmaf(kk.y, va, o[4 * c4 + 1]);
+                o[4 * c4 + 2] = fmaf(kk.z, va, o[4 * c4 + 2]);
+                o[4 * c4 + 3] = fmaf(kk.w, va, o[4 * c4 + 3]);
+            }
+        }
+        {
+            float wx[NXP], gx[NXP];
+            row_load<NXP>(wx, yi, nx, q.al_d, false);
+            if (!a.homog) row_load<NXP>(gx, gi, nx, q.al_d, false);
+#pragma unroll
+            for (int r = 0; r < NXP; ++r) wx[r] = o[r] + 0.5f * sc * wx[r] + (a.homog ? 0.f : gx[r]);
+            row_store<NXP>(a.s + k * a.s_stride + sb + (long long)i * nx, wx, nx, q.al_s);
+        }
+    }
+}
+
+template <int NR, int NXP, int NUP>
+__device__ __forceinline__ void col_fwd(const RoundArgs<NR> &a, const Geo &q, int t, int inst, int i,
+                                        const float *Gp, const float *Kp) {
+    constexpr int NXU = NXP + NUP;
+    const int nx = q.nx, nu = q.nu;
+    const long long elem = q.elem0 + (long long)inst * q.m;
+    const long long sb = q.sbase + (long long)inst * q.Nn * nx;
+    const long long ub = q.ubase + (long long)inst * q.Np * nu;
+    const bool leaf = q.s0 >= q.Np;
+    const float sc = a.scaled ? q.sq_t : 1.f;
+    const long long oi = elem + doff(q, i);
+#pragma unroll 1
+    for (int k = 0; k < NR; ++k) {
+        float x[NXP], u[NUP];
+        if (t == 0) {
+            if (a.homog) {
+#pragma unroll
+                for (int r = 0; r < NXP; ++r) x[r] = 0.f;
+            } else {
+                row_load<NXP>(x, a.x0 + (long long)(q.inst0 + inst) * 64, nx, (nx & 3) == 0 ? 4 : 1, false);
+            }
+        } else {
+            row_load<NXP>(x, a.xs + k * a.s_stride + sb + (long long)i * nx, nx, q.al_s, true);
+        }
+        float *hi = a.h[k] + oi;
+        if (leaf) {
+            float hx[NXP];
+#pragma unroll
+            for (int r = 0; r < NXP; ++r) hx[r] = sc * x[r];
+            row_store<NXP>(hi, hx, nx, q.al_d);
+            continue;
+        }
+        row_load<NUP>(u, a.ubar + k * a.u_stride + ub + (long long)i * nu, nu, q.al_u, true);
+        // u = K x + ubar
+#pragma unroll
+        for (int aa = 0; aa < NUP; ++aa) {
+            float acc = u[aa];
+#pragma unroll
+            for (int c4 = 0; c4 < NXP / 4; ++c4) {
+                const float4 kk = *reinterpret_cast<const float4 *>(Kp + aa * NXP + 4 * c4);
+                acc = fmaf(kk.x, x[4 * c4 + 0], acc);
+                acc = fmaf(kk.y, x[4 * c4 + 1], acc);
+                acc = fmaf(kk.z, x[4 * c4 + 2], acc);
+                acc = fmaf(kk.w, x[4 * c4 + 3], acc);
+            }
+            u[aa] = aa < nu ? acc : 0.f;
+        }
+        {
+            float hx[NXP], hu[NUP];
+#pragma unroll
+            for (int r = 0; r < NXP; ++r) hx[r] = sc * x[r];
+#pragma unroll
+            for (int aa = 0; aa < NUP; ++aa) hu[aa] = sc * u[aa];
+            row_store<NXP>(hi, hx, nx, q.al_d);
+            row_store<NUP>(hi + nx, hu, nu, q.al_d);
+        }
+        // children: x^j = [A | B][x; u] + c^j
+        float xc[NXP];
+#pragma unroll
+        for (int r = 0; r < NXP; ++r) {
+            float acc = 0.f;
+#pragma unroll
+            for (int c4 = 0; c4 < NXP / 4; ++c4) {
+                const float4 g = *reinterpret_cast<const float4 *>(Gp + r * NXU + 4 * c4);
+                acc = fmaf(g.x, x[4 * c4 + 0], acc);
+                acc = fmaf(g.y, x[4 * c4 + 1], acc);
+                acc = fmaf(g.z, x[4 * c4 + 2], acc);
+                acc = fmaf(g.w, x[4 * c4 + 3], acc);
+            }
+#pragma unroll
+            for (int a4 = 0; a4 < NUP / 4; ++a4) {
+                const float4 g = *reinterpret_cast<const float4 *>(Gp + r * NXU + NXP + 4 * a4);
+                acc = fmaf(g.x, u[4 * a4 + 0], acc);
+                acc = fmaf(g.y, u[4 * a4 + 1], acc);
+                acc = fmaf(g.z, u[4 * a4 + 2], acc);
+                acc = fmaf(g.w, u[4 * a4 + 3], acc);
+            }
+            xc[r] = acc;
+        }
+        const int j0 = q.s1 + (i - q.s0) * q.bt;
+        for (int j = j0; j < j0 + q.bt; ++j) {
+            float xj[NXP];
+            if (a.homog) {
+#pragma unroll
+                for (int r = 0; r < NXP; ++r) xj[r] = xc[r];
+            } else {
+                row_load<NXP>(xj, a.c + sb + (long long)j * nx, nx, q.al_s, false);
+#pragma unroll
+                for (int r = 0; r < NXP; ++r) xj[r] += xc[r];
+            }
+            row_store<NXP>(a.xs + k * a.s_stride + sb + (long long)j * nx, xj, nx, q.al_s);
+        }
+    }
+}
+
+template <int NR, int NXP, int NUP, int NT>
+__global__ void __launch_bounds__(NT, 4) k_bcol(RoundArgs<NR> a) {
+    __shared__ __align__(16) float Gp[NXP * (NXP + NUP)];
+    __shared__ __align__(16) float Kp[NUP * NXP];
+    __shared__ __align__(16) float Rp[NUP * NUP];
+    __shared__ int s_tick[2];
+    int staged = -1;
+    if (threadIdx.x == 0) s_tick[0] = (int)atomicAdd(a.ticket, 1u);
+    __syncthreads();
+    for (int it = 0;; ++it) {
+        const int k = s_tick[it & 1];
+        if (k >= a.ntasks) return;
+        const RTask tk = a.tasks[k];
+        if (threadIdx.x == 0) {
+            s_tick[(it + 1) & 1] = (int)atomicAdd(a.ticket, 1u);
+            if (tk.wait_ctr >= 0) wait_count(a.ctrs + tk.wait_ctr, (unsigned)tk.wait_need, a.err);
+        }
+        const int t = tk.stage;
+        const Geo q = load_geo(a.groups[tk.group], t);
+        const int key = 2 * (tk.group * (kMaxStages + 1) + t) + tk.pass;
+        if (staged != key) {
+            __syncthreads();  // every thread is done with the previous matrices
+            col_stage<NXP, NUP>(q, t, q.s0 >= q.Np, Gp, Kp, Rp, NT);
+            staged = key;
+        }
+        __syncthreads();  // the matrices, the next ticket and the dependency wait
+        const int col = threadIdx.x;
+        if (col < tk.ncols) {
+            const int cc = tk.col0 + col, inst = cc / q.n_t, i = q.s0 + cc - inst * q.n_t;
+            if (!a.active || a.active[q.inst0 + inst]) {
+                if (tk.pass == 0)
+                    col_bwd<NR, NXP, NUP>(a, q, t, inst, i, Gp, Kp, Rp);
+                else
+                    col_fwd<NR, NXP, NUP>(a, q, t, inst, i, Gp, Kp);
+            }
+        }
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            __threadfence();
+            atomicAdd(a.ctrs + tk.done_ctr, 1u);
+        }
+    }
 }
 
 // gamma^i = pi_{t+1} [A | B]' P~_{t+1} sum_j c^j for every nonleaf node and instance (set-up).
@@ -1057,19 +1558,38 @@ __global__ void k_bscale(ElemArgs a, const float *y, float *yb, int dir) {
 // =============================================================================================
 using namespace sto;
 
+// Tile variants: 0-2 the tile kernel (k_bround) with 32 columns on 128 or 256 threads or 64 columns
+// on 256 threads; 3 the column kernel (k_bcol, one column per thread, 128 columns per tile), for
+// batches whose groups all have nx <= 32 and nu <= 16.
+constexpr int kTileVars = 4;
+constexpr int kTileCols[kTileVars] = {32, 32, 64, 128};         // columns per tile of each variant
+constexpr int kTileThreads[kTileVars] = {128, 256, 256, 128};   // threads per CTA of each variant
+constexpr int kColVar = 3;
+
 struct stobatch_s {
     std::vector<sto_group_desc> desc;
     std::vector<GroupDev> groups;   // host copies (device pointers filled at bind)
     std::vector<InstDev> insts;
     std::vector<int> blk_inst;
-    std::vector<Task> tasks;
+    std::vector<Task> tasks;                // set-up (gamma) tiles
     std::vector<int> bwd_phase, fwd_phase;  // task offsets per phase (size phases + 1)
     std::vector<int> gam_phase;
+    // solve rounds: tiles of kTileCols[v] columns (tile variant v) in ticket order, and the
+    // number of per-(group, stage, pass) counters they wait on
+    std::vector<RTask> rtasks[kTileVars];
+    int nctr = 0;
+    int xu = 96;                          // shape class: 48 if every group has nx <= 32, nu <= 16
+    int nxp = 32, nup = 16;               // the column kernel's padded widths (when xu == 48)
+    int tile_var[3] = {1, 1, 1};          // variant per right-hand-side count (set by the tuner)
+    double tuned_ms[3][kTileVars] = {};   // round time of each variant, measured by the tuner
+    int grid[3][kTileVars] = {};          // CTAs of one wave per (right-hand sides, variant)
+    bool tuned = false;
+    size_t o_rtask[kTileVars] = {}, o_ctr = 0;
     int maxN = 0, ninst = 0, nblocks = 0;
     long long M = 0, vpad = 0, Ssz = 0, Usz = 0;  // vector length, padded stride, scratch sizes
     // layout (byte offsets)
     size_t o_groups, o_insts, o_blk, o_tasks, o_G, o_K, o_R, o_box, o_W, o_AB64, o_P64, o_scr, o_off, o_gam, o_c,
-        o_x0, o_s, o_ub, o_xs, o_us, o_vec, o_ringS, o_ringY, o_part, o_sc, o_active, o_nact, o_status, o_sqn, total;
+        o_x0, o_s, o_ub, o_xs, o_vec, o_ringS, o_ringY, o_part, o_sc, o_active, o_nact, o_status, o_sqn, total;
     std::vector<long long> aboff, ptoff, scoff;
     char *ws = nullptr;
     bool factored = false;
@@ -1083,6 +1603,10 @@ struct stobatch_s {
 };
 
 static size_t ru(size_t v, size_t a) { return (v + a - 1) / a * a; }
+
+namespace {
+sto_status tune_rounds(stobatch_t b, cudaStream_t st);
+}
 
 static sto_status bfail(stobatch_t b, cudaError_t e, const char *what) {
     b->err = std::string(what) + ": " + cudaGetErrorString(e);
@@ -1170,12 +1694,74 @@ STO_API sto_status stobatch_create(const sto_group_desc *groups, int32_t ngroups
     b->vpad = (long long)ru((size_t)elem, 64);
     b->Ssz = sb;
     b->Usz = ub;
-    // tasks: backward phase p = stage N_g - 1 - p, forward phase p = stage p, gamma = stages 0..N-1
+    // widest vector access every instance's rows allow (the arrays start 256-byte aligned)
+    auto widest = [](std::initializer_list<long long> vals) {
+        for (int p : {4, 2}) {
+            bool ok = true;
+            for (long long v : vals) ok = ok && v % p == 0;
+            if (ok) return p;
+        }
+        return 1;
+    };
+    for (auto &g : b->groups) {
+        g.al_d = widest({g.nx, g.nu, (long long)g.m, g.elem0, b->vpad});
+        g.al_s = widest({g.nx, g.sbase, (long long)g.Nn * g.nx, sb});
+        g.al_u = widest({g.nu, g.ubase, (long long)g.Np * g.nu, ub});
+    }
+    // set-up tiles: backward phase p = stage N_g - 1 - p (gamma covers every nonleaf stage)
     auto add_tasks = [&](int gi, int t) {
         const GroupDev &g = b->groups[gi];
         const int cols = (g.soff[t + 1] - g.soff[t]) * g.I;
-        for (int c0 = 0; c0 < cols; c0 += kTC) b->tasks.push_back(Task{gi, t, c0, std::min(kTC, cols - c0)});
+        for (int c0 = 0; c0 < cols; c0 += kGC) b->tasks.push_back(Task{gi, t, c0, std::min(kGC, cols - c0)});
     };
+    // solve-round tiles in ticket order, per tile variant: backward by height, then forward by
+    // depth; counter (g, t, pass) = cbase[g] + pass (N_g + 1) + t
+    std::vector<int> cbase(ngroups);
+    b->nctr = 0;
+    b->xu = 48;
+    int maxnx = 0, maxnu = 0;
+    for (int gi = 0; gi < ngroups; ++gi) {
+        cbase[gi] = b->nctr;
+        b->nctr += 2 * (b->groups[gi].N + 1);
+        if (b->groups[gi].nx > 32 || b->groups[gi].nu > 16) b->xu = 96;
+        maxnx = std::max(maxnx, b->groups[gi].nx);
+        maxnu = std::max(maxnu, b->groups[gi].nu);
+    }
+    b->nxp = maxnx <= 16 ? 16 : (maxnx <= 24 ? 24 : 32);
+    b->nup = maxnu <= 8 ? 8 : 16;
+    for (int v = 0; v < kTileVars; ++v) {
+        const int tc = kTileCols[v];
+        auto ntiles = [&](int gi, int t) {
+            const GroupDev &g = b->groups[gi];
+            return ((g.soff[t + 1] - g.soff[t]) * g.I + tc - 1) / tc;
+        };
+        auto add = [&](int gi, int t, int pass, int wctr, int wneed) {
+            const GroupDev &g = b->groups[gi];
+            const int cols = (g.soff[t + 1] - g.soff[t]) * g.I;
+            const int done = cbase[gi] + pass * (g.N + 1) + t;
+            for (int c0 = 0; c0 < cols; c0 += tc)
+                b->rtasks[v].push_back(RTask{gi, t, c0, std::min(tc, cols - c0), pass, wctr, wneed, done});
+        };
+        for (int p = 0; p < b->maxN; ++p)
+            for (int gi = 0; gi < ngroups; ++gi) {
+                const GroupDev &g = b->groups[gi];
+                if (g.N <= p) continue;
+                const int t = g.N - 1 - p;
+                if (t + 1 < g.N)
+                    add(gi, t, 0, cbase[gi] + t + 1, ntiles(gi, t + 1));
+                else
+                    add(gi, t, 0, -1, 0);
+            }
+        for (int p = 0; p <= b->maxN; ++p)
+            for (int gi = 0; gi < ngroups; ++gi) {
+                const GroupDev &g = b->groups[gi];
+                if (g.N < p) continue;
+                if (p == 0)
+                    add(gi, 0, 1, cbase[gi] + 0, ntiles(gi, 0));  // the backward pass of stage 0
+                else
+                    add(gi, p, 1, cbase[gi] + (g.N + 1) + p - 1, ntiles(gi, p - 1));
+            }
+    }
     for (int p = 0; p < b->maxN; ++p) {
         b->bwd_phase.push_back((int)b->tasks.size());
         for (int gi = 0; gi < ngroups; ++gi)
@@ -1200,6 +1786,8 @@ STO_API sto_status stobatch_create(const sto_group_desc *groups, int32_t ngroups
     b->o_insts = add(b->ninst * sizeof(InstDev));
     b->o_blk = add(b->nblocks * 4);
     b->o_tasks = add(b->tasks.size() * sizeof(Task));
+    for (int v = 0; v < kTileVars; ++v) b->o_rtask[v] = add(b->rtasks[v].size() * sizeof(RTask));
+    b->o_ctr = add((size_t)(b->nctr + 1) * 4);  // the counters, then the ticket
     size_t gsz = 0, ksz = 0, rsz = 0, absz = 0, psz = 0, scsz = 0;
     for (auto &g : b->groups) {
         gsz += (size_t)g.nx * g.nxu;
@@ -1227,7 +1815,6 @@ STO_API sto_status stobatch_create(const sto_group_desc *groups, int32_t ngroups
     b->o_s = add(2 * b->Ssz * 4);
     b->o_ub = add(2 * b->Usz * 4);
     b->o_xs = add(2 * b->Ssz * 4);
-    b->o_us = add(2 * b->Usz * 4);
     b->o_vec = add(8 * b->vpad * 4);
     b->o_ringS = add((kBMaxMem + 1) * b->vpad * 4);
     b->o_ringY = add((kBMaxMem + 1) * b->vpad * 4);
@@ -1324,6 +1911,9 @@ STO_API sto_status stobatch_bind_workspace(stobatch_t b, void *dev, size_t bytes
     BCUDA(b, cudaMemcpyAsync(b->ws + b->o_blk, b->blk_inst.data(), b->blk_inst.size() * 4, cudaMemcpyHostToDevice, st));
     BCUDA(b, cudaMemcpyAsync(b->ws + b->o_tasks, b->tasks.data(), b->tasks.size() * sizeof(Task),
                              cudaMemcpyHostToDevice, st));
+    for (int v = 0; v < kTileVars; ++v)
+        BCUDA(b, cudaMemcpyAsync(b->ws + b->o_rtask[v], b->rtasks[v].data(), b->rtasks[v].size() * sizeof(RTask),
+                                 cudaMemcpyHostToDevice, st));
     BCUDA(b, cudaMemcpyAsync(b->ws + b->o_G, Gh.data(), Gh.size() * 4, cudaMemcpyHostToDevice, st));
     BCUDA(b, cudaMemcpyAsync(b->ws + b->o_AB64, ABh.data(), ABh.size() * 8, cudaMemcpyHostToDevice, st));
     BCUDA(b, cudaMemcpyAsync(b->ws + b->o_box, boxh.data(), boxh.size() * 4, cudaMemcpyHostToDevice, st));
@@ -1383,6 +1973,44 @@ STO_API sto_status stobatch_factor(stobatch_t b, sto_stream_t stream) {
         return STO_ERR_NUMERICAL;
     }
     b->factored = true;
+    if (!b->tuned) {  // the round's tile shape, once per batch (shapes do not change)
+        const sto_status s = tune_rounds(b, st);
+        if (s != STO_OK) return s;
+        b->tuned = true;
+    }
+    return STO_OK;
+}
+
+STO_API sto_status stobatch_round_status(stobatch_t b, sto_stream_t stream) {
+    if (!b) return STO_ERR_INVALID_ARG;
+    if (!b->ws) return STO_ERR_NOT_READY;
+    cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
+    int err = 0;
+    BCUDA(b, cudaMemcpyAsync(&err, b->at<int>(b->o_nact) + 1, 4, cudaMemcpyDeviceToHost, st));
+    BCUDA(b, cudaStreamSynchronize(st));
+    if (!err) return STO_OK;
+    BCUDA(b, cudaMemsetAsync(b->at<int>(b->o_nact) + 1, 0, 4, st));
+    BCUDA(b, cudaStreamSynchronize(st));
+    b->err = "a batched solve round gave up waiting for a dependency";
+    return STO_ERR_TIMEOUT;
+}
+
+STO_API sto_status stobatch_set_round_variant(stobatch_t b, int32_t nrhs, int32_t variant) {
+    if (!b || nrhs < 1 || nrhs > 2 || variant < 0 || variant >= kTileVars) return STO_ERR_INVALID_ARG;
+    if (variant == kColVar && b->xu == 96) return STO_ERR_INVALID_ARG;
+    b->tile_var[nrhs] = variant;
+    return STO_OK;
+}
+
+STO_API sto_status stobatch_round_config(stobatch_t b, int32_t nrhs, int32_t *tile_cols, int32_t *cta_threads,
+                                         int32_t *ctas, double *tuned_ms) {
+    if (!b || nrhs < 1 || nrhs > 2) return STO_ERR_INVALID_ARG;
+    const int v = b->tile_var[nrhs];
+    if (tile_cols) *tile_cols = kTileCols[v];
+    if (cta_threads) *cta_threads = kTileThreads[v];
+    if (ctas) *ctas = b->grid[nrhs][v];
+    if (tuned_ms)
+        for (int k = 0; k < kTileVars; ++k) tuned_ms[k] = b->tuned_ms[nrhs][k];
     return STO_OK;
 }
 
@@ -1391,64 +2019,152 @@ STO_API sto_status stobatch_factor(stobatch_t b, sto_stream_t stream) {
 namespace {
 
 template <int NR>
-void launch_round(stobatch_t b, const RoundArgs<NR> &a, cudaStream_t st) {
-    raise_smem_cap((const void *)k_bbwd<NR>, bwd_smem<NR>());
-    raise_smem_cap((const void *)k_bfwd<NR>, fwd_smem<NR>());
-    for (size_t p = 0; p + 1 < b->bwd_phase.size(); ++p) {
-        const int t0 = b->bwd_phase[p], nt = b->bwd_phase[p + 1] - t0;
-        if (nt > 0) k_bbwd<NR><<<nt, kBT, bwd_smem<NR>(), st>>>(a, t0);
-    }
-    for (size_t p = 0; p + 1 < b->fwd_phase.size(); ++p) {
-        const int t0 = b->fwd_phase[p], nt = b->fwd_phase[p + 1] - t0;
-        if (nt > 0) k_bfwd<NR><<<nt, kBT, fwd_smem<NR>(), st>>>(a, t0);
+RoundArgs<NR> round_args(stobatch_t b, const float *y0, const float *y1, float *h0, float *h1, bool homog,
+                         bool scaled, const int *active, int var) {
+    RoundArgs<NR> a;
+    a.groups = b->at<GroupDev>(b->o_groups);
+    a.insts = b->at<InstDev>(b->o_insts);
+    a.tasks = b->at<RTask>(b->o_rtask[var]);
+    a.ntasks = (int)b->rtasks[var].size();
+    a.y[0] = y0;
+    a.y[1] = y1 ? y1 : y0;
+    a.h[0] = h0;
+    a.h[1] = h1 ? h1 : h0;
+    a.gam = b->at<float>(b->o_gam);
+    a.c = b->at<float>(b->o_c);
+    a.x0 = b->at<float>(b->o_x0);
+    a.s = b->at<float>(b->o_s);
+    a.ubar = b->at<float>(b->o_ub);
+    a.xs = b->at<float>(b->o_xs);
+    a.s_stride = b->Ssz;
+    a.u_stride = b->Usz;
+    a.active = active;
+    a.ctrs = b->at<unsigned>(b->o_ctr);
+    a.ticket = a.ctrs + b->nctr;
+    a.err = b->at<int>(b->o_nact) + 1;
+    a.homog = homog ? 1 : 0;
+    a.scaled = scaled ? 1 : 0;
+    return a;
+}
+
+// One wave of the round kernel (every CTA resident: tiles wait only on earlier tickets).
+template <int NR, int TC, int XU, int NT>
+int round_grid(int ntasks) {
+    const size_t smem = round_smem<NR, TC, XU, NT>();
+    raise_smem_cap((const void *)k_bround<NR, TC, XU, NT>, smem);
+    int dev = 0, sms = 0, per_sm = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_bround<NR, TC, XU, NT>, NT, smem) != cudaSuccess ||
+        per_sm < 1)
+        return 0;
+    return std::max(1, std::min(per_sm * sms, ntasks));
+}
+
+template <int NR, int TC, int XU, int NT>
+void round_launch(const RoundArgs<NR> &a, int grid, cudaStream_t st) {
+    k_bround<NR, TC, XU, NT><<<grid, NT, round_smem<NR, TC, XU, NT>(), st>>>(a);
+}
+
+template <int NR, int NXP, int NUP>
+int col_grid(int ntasks) {
+    int dev = 0, sms = 0, per_sm = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_bcol<NR, NXP, NUP, 128>, 128, 0) != cudaSuccess ||
+        per_sm < 1)
+        return 0;
+    return std::max(1, std::min(per_sm * sms, ntasks));
+}
+template <int NR>
+int col_grid_for(int nxp, int nup, int ntasks) {
+    if (nup == 8) return nxp == 16 ? col_grid<NR, 16, 8>(ntasks) : (nxp == 24 ? col_grid<NR, 24, 8>(ntasks) : col_grid<NR, 32, 8>(ntasks));
+    return nxp == 16 ? col_grid<NR, 16, 16>(ntasks) : (nxp == 24 ? col_grid<NR, 24, 16>(ntasks) : col_grid<NR, 32, 16>(ntasks));
+}
+template <int NR>
+void col_launch_for(int nxp, int nup, const RoundArgs<NR> &a, int grid, cudaStream_t st) {
+    if (nup == 8) {
+        if (nxp == 16) k_bcol<NR, 16, 8, 128><<<grid, 128, 0, st>>>(a);
+        else if (nxp == 24) k_bcol<NR, 24, 8, 128><<<grid, 128, 0, st>>>(a);
+        else k_bcol<NR, 32, 8, 128><<<grid, 128, 0, st>>>(a);
+    } else {
+        if (nxp == 16) k_bcol<NR, 16, 16, 128><<<grid, 128, 0, st>>>(a);
+        else if (nxp == 24) k_bcol<NR, 24, 16, 128><<<grid, 128, 0, st>>>(a);
+        else k_bcol<NR, 32, 16, 128><<<grid, 128, 0, st>>>(a);
     }
 }
 
-// One solve round for nrhs (1 or 2) right-hand sides, replayed from a cached CUDA graph.
+// The kernel of tile variant v (kTileCols[v] columns, kTileThreads[v] threads) for the batch's
+// shape class: grid of one wave, or a launch.
+template <int NR, int XU>
+int variant_grid(int v, int ntasks) {
+    switch (v) {
+        case 0: return round_grid<NR, 32, XU, 128>(ntasks);
+        case 1: return round_grid<NR, 32, XU, 256>(ntasks);
+        default: return round_grid<NR, 64, XU, 256>(ntasks);
+    }
+}
+template <int NR, int XU>
+void variant_launch(int v, const RoundArgs<NR> &a, int grid, cudaStream_t st) {
+    switch (v) {
+        case 0: round_launch<NR, 32, XU, 128>(a, grid, st); break;
+        case 1: round_launch<NR, 32, XU, 256>(a, grid, st); break;
+        default: round_launch<NR, 64, XU, 256>(a, grid, st); break;
+    }
+}
+
+// The round's counters and ticket start at zero, then one persistent launch.
+template <int NR>
+sto_status launch_round(stobatch_t b, const RoundArgs<NR> &a, int var, cudaStream_t st) {
+    int &grid = b->grid[NR][var];
+    const bool big = b->xu == 96;
+    if (var == kColVar && big) {
+        b->err = "the column kernel needs nx <= 32 and nu <= 16 in every group";
+        return STO_ERR_INVALID_ARG;
+    }
+    if (grid == 0) {
+        if (var == kColVar)
+            grid = col_grid_for<NR>(b->nxp, b->nup, a.ntasks);
+        else
+            grid = big ? variant_grid<NR, 96>(var, a.ntasks) : variant_grid<NR, 48>(var, a.ntasks);
+        if (grid <= 0) {
+            b->err = "batched round kernel does not fit on this device";
+            return STO_ERR_CUDA;
+        }
+    }
+    BCUDA(b, cudaMemsetAsync(a.ctrs, 0, (size_t)(b->nctr + 1) * 4, st));
+    if (var == kColVar)
+        col_launch_for<NR>(b->nxp, b->nup, a, grid, st);
+    else if (big)
+        variant_launch<NR, 96>(var, a, grid, st);
+    else
+        variant_launch<NR, 48>(var, a, grid, st);
+    return STO_OK;
+}
+
+// One solve round for nrhs (1 or 2) right-hand sides with the tuned tile variant, replayed from
+// a cached CUDA graph (the counters' reset and the persistent launch).
 sto_status bround(stobatch_t b, const float *y0, const float *y1, float *h0, float *h1, int nrhs, bool homog,
                   bool scaled, const int *active, cudaStream_t st) {
+    const int var = b->tile_var[nrhs];
     auto key = std::make_tuple((const void *)y0, (const void *)y1, (const void *)h0, (const void *)h1,
-                               (const void *)active, nrhs, (int)homog, (int)scaled);
+                               (const void *)active, nrhs * 8 + var, (int)homog, (int)scaled);
     auto it = b->graphs.find(key);
     if (it == b->graphs.end()) {
         cudaStream_t cap;
         BCUDA(b, cudaStreamCreateWithFlags(&cap, cudaStreamNonBlocking));
         cudaGraph_t graph;
         BCUDA(b, cudaStreamBeginCapture(cap, cudaStreamCaptureModeThreadLocal));
-        auto fill = [&](auto &a) {
-            a.groups = b->at<GroupDev>(b->o_groups);
-            a.insts = b->at<InstDev>(b->o_insts);
-            a.tasks = b->at<Task>(b->o_tasks);
-            a.y[0] = y0;
-            a.y[1] = y1 ? y1 : y0;
-            a.h[0] = h0;
-            a.h[1] = h1 ? h1 : h0;
-            a.gam = b->at<float>(b->o_gam);
-            a.c = b->at<float>(b->o_c);
-            a.x0 = b->at<float>(b->o_x0);
-            a.s = b->at<float>(b->o_s);
-            a.ubar = b->at<float>(b->o_ub);
-            a.xs = b->at<float>(b->o_xs);
-            a.us = b->at<float>(b->o_us);
-            a.s_stride = b->Ssz;
-            a.u_stride = b->Usz;
-            a.active = active;
-            a.homog = homog ? 1 : 0;
-            a.scaled = scaled ? 1 : 0;
-        };
-        if (nrhs == 1) {
-            RoundArgs<1> a;
-            fill(a);
-            launch_round<1>(b, a, cap);
-        } else {
-            RoundArgs<2> a;
-            fill(a);
-            launch_round<2>(b, a, cap);
-        }
+        sto_status ls;
+        if (nrhs == 1)
+            ls = launch_round<1>(b, round_args<1>(b, y0, y1, h0, h1, homog, scaled, active, var), var, cap);
+        else
+            ls = launch_round<2>(b, round_args<2>(b, y0, y1, h0, h1, homog, scaled, active, var), var, cap);
         cudaError_t e = cudaStreamEndCapture(cap, &graph);
-        if (e != cudaSuccess) {
+        if (ls != STO_OK || e != cudaSuccess) {
+            if (e == cudaSuccess) cudaGraphDestroy(graph);
             cudaStreamDestroy(cap);
-            return bfail(b, e, "capture of a batched solve round");
+            return ls != STO_OK ? ls : bfail(b, e, "capture of a batched solve round");
         }
         cudaGraphExec_t exec;
         e = cudaGraphInstantiate(&exec, graph, 0);
@@ -1458,6 +2174,62 @@ sto_status bround(stobatch_t b, const float *y0, const float *y1, float *h0, flo
         it = b->graphs.emplace(key, exec).first;
     }
     BCUDA(b, cudaGraphLaunch(it->second, st));
+    return STO_OK;
+}
+
+// Round tuner: times a homogeneous round of every tile variant that fits the batch's shapes, for
+// one and for two right-hand sides, on zeroed scratch vectors (one launch to warm up, then the
+// mean of three) and keeps the fastest per right-hand-side count.
+sto_status tune_rounds(stobatch_t b, cudaStream_t st) {
+    const long long vs = b->vpad;
+    float *V = b->at<float>(b->o_vec);
+    float *y = V + 6 * vs, *h0 = V + 7 * vs, *h1 = V + 5 * vs;
+    BCUDA(b, cudaMemsetAsync(y, 0, (size_t)vs * 4, st));
+    cudaEvent_t e0, e1;
+    BCUDA(b, cudaEventCreate(&e0));
+    BCUDA(b, cudaEventCreate(&e1));
+    sto_status s = STO_OK;
+    for (int nr = 1; nr <= 2 && s == STO_OK; ++nr) {
+        double best = 1e30;
+        for (int v = 0; v < kTileVars && s == STO_OK; ++v) {
+            if (v == kColVar && b->xu == 96) {
+                b->tuned_ms[nr][v] = -1.0;  // not applicable to this batch's shapes
+                continue;
+            }
+            for (int rep = 0; rep < 4 && s == STO_OK; ++rep) {
+                if (rep == 1) cudaEventRecord(e0, st);
+                if (nr == 1)
+                    s = launch_round<1>(b, round_args<1>(b, y, nullptr, h0, nullptr, true, true, nullptr, v), v, st);
+                else
+                    s = launch_round<2>(b, round_args<2>(b, y, y, h0, h1, true, true, nullptr, v), v, st);
+            }
+            if (s != STO_OK) break;
+            cudaEventRecord(e1, st);
+            cudaError_t e = cudaEventSynchronize(e1);
+            float ms = 0.f;
+            if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, e0, e1);
+            if (e != cudaSuccess) {
+                s = bfail(b, e, "timing a batched round");
+                break;
+            }
+            b->tuned_ms[nr][v] = ms / 3.0;
+            if (ms / 3.0 < best) {
+                best = ms / 3.0;
+                b->tile_var[nr] = v;
+            }
+        }
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    if (s != STO_OK) return s;
+    int err = 0;
+    BCUDA(b, cudaMemcpyAsync(&err, b->at<int>(b->o_nact) + 1, 4, cudaMemcpyDeviceToHost, st));
+    BCUDA(b, cudaStreamSynchronize(st));
+    if (err) {
+        BCUDA(b, cudaMemsetAsync(b->at<int>(b->o_nact) + 1, 0, 4, st));
+        b->err = "a batched solve round gave up waiting for a dependency";
+        return STO_ERR_TIMEOUT;
+    }
     return STO_OK;
 }
 
@@ -1477,6 +2249,7 @@ extern "C" {
 STO_API sto_status stobatch_solve_step(stobatch_t b, const void *y, void *hx, int32_t homogeneous, int32_t scaled,
                                        sto_stream_t stream) {
     if (!b || !y || !hx) return STO_ERR_INVALID_ARG;
+    if ((reinterpret_cast<uintptr_t>(y) | reinterpret_cast<uintptr_t>(hx)) & 15) return STO_ERR_INVALID_ARG;
     if (!b->factored) return STO_ERR_NOT_READY;
     cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
     sto_status s = bround(b, static_cast<const float *>(y), nullptr, static_cast<float *>(hx), nullptr, 1,
@@ -1548,12 +2321,21 @@ STO_API sto_status stobatch_nama_solve(stobatch_t b, const sto_opts *o, const do
     if (s != STO_OK) return s;
     k_bpoint<<<nb, kBT, 0, st>>>(ea, yb, h, r, ringS, ringY, 0);
     k_bstep_done<<<(ninst + 127) / 128, 128, 0, st>>>(sc, ninst, o->tol, active, nact, 0);
-    int iters = 0, nleft = ninst;
+    int iters = 0;
+    int head[2] = {ninst, 0};  // active instances, round error word
     sto_status result = STO_OK;
     while (true) {
-        BCUDA(b, cudaMemcpyAsync(&nleft, nact, 4, cudaMemcpyDeviceToHost, st));
+        BCUDA(b, cudaMemcpyAsync(head, nact, 8, cudaMemcpyDeviceToHost, st));
         BCUDA(b, cudaStreamSynchronize(st));
-        if (nleft == 0) break;
+        if (head[1]) {
+            BCUDA(b, cudaMemsetAsync(nact + 1, 0, 4, st));
+            BCUDA(b, cudaStreamSynchronize(st));
+            cudaEventDestroy(e0);
+            cudaEventDestroy(e1);
+            b->err = "a batched solve round gave up waiting for a dependency";
+            return STO_ERR_TIMEOUT;
+        }
+        if (head[0] == 0) break;
         if (iters >= o->max_iter) {
             result = STO_NOT_CONVERGED;
             break;

@@ -103,6 +103,9 @@ def lib():
             "stobatch_factor": [vp, vp],
             "stobatch_solve_step": [vp, vp, vp, i32, i32, vp],
             "stobatch_nama_solve": [vp, vp, vp, vp, vp, vp, vp, vp],
+            "stobatch_round_status": [vp, vp],
+            "stobatch_round_config": [vp, i32, vp, vp, vp, vp],
+            "stobatch_set_round_variant": [vp, i32, i32],
         }
         for name, args in bsigs.items():
             fn = getattr(L, name)
@@ -149,7 +152,8 @@ def exported_symbols():
                         "stotree_get_timing", "stotree_solve_bytes", "stotree_status_str", "stotree_last_error",
                         "stobatch_create", "stobatch_destroy", "stobatch_sizes", "stobatch_workspace_size",
                         "stobatch_bind_workspace", "stobatch_set_instance", "stobatch_factor",
-                        "stobatch_solve_step", "stobatch_nama_solve", "stobatch_last_error",
+                        "stobatch_solve_step", "stobatch_nama_solve", "stobatch_round_status",
+                        "stobatch_round_config", "stobatch_set_round_variant", "stobatch_last_error",
                         "stowarm_create", "stowarm_destroy", "stowarm_dims", "stowarm_workspace_size",
                         "stowarm_bind_workspace", "stowarm_set_params", "stowarm_get_params", "stowarm_forward",
                         "stowarm_gradients", "stowarm_train_batch", "stowarm_set_draws", "stowarm_train",
@@ -446,6 +450,25 @@ class StoBatch:
         if code != 0 and not (allow_not_converged and code == STO_NOT_CONVERGED):
             self._check(code, "nama")
         return dict(y=y, z=z, hx=hx, infos=[i.as_dict() for i in infos])
+
+    def round_status(self):
+        """stobatch_round_status: raises StoError (timeout) if a wait of the rounds since the last
+        synchronising call gave up."""
+        self._check(lib().stobatch_round_status(self.h, _stream()), "round_status")
+
+    def round_config(self, nrhs=1):
+        """stobatch_round_config: the tuned tile (columns, CTA threads), the persistent launch's
+        CTAs and the tuner's measured round time per candidate (-1: not applicable)."""
+        tc, nt, ctas = ctypes.c_int32(), ctypes.c_int32(), ctypes.c_int32()
+        ms = (ctypes.c_double * 4)()
+        self._check(lib().stobatch_round_config(self.h, nrhs, ctypes.byref(tc), ctypes.byref(nt), ctypes.byref(ctas),
+                                                ms), "round_config")
+        return dict(tile_cols=tc.value, cta_threads=nt.value, ctas=ctas.value,
+                    tuned_ms={"tile32x128": ms[0], "tile32x256": ms[1], "tile64x256": ms[2], "column128": ms[3]})
+
+    def set_round_variant(self, nrhs, variant):
+        """stobatch_set_round_variant: fix the round kernel variant (0-3) instead of the tuner's."""
+        self._check(lib().stobatch_set_round_variant(self.h, nrhs, variant), "set_round_variant")
 
     def group_lambdas(self, iters=50, safety=0.9, seed=7):
         """lambda per group from the single-instance power iteration on the group's first instance

@@ -28,9 +28,15 @@ def small():
     return groups, sb, oracles
 
 
-def test_batched_solve_step_matches_oracle(cuda_device, small):
-    """One batched round of Algorithm 3 / 4 equals the oracle's solve of every instance."""
+VARIANTS = [0, 1, 2, 3]  # the round kernels the tuner chooses from (stobatch_round_config order)
+
+
+@pytest.mark.parametrize("variant", VARIANTS)
+def test_batched_solve_step_matches_oracle(cuda_device, small, variant):
+    """One batched round of Algorithm 3 / 4 equals the oracle's solve of every instance, with
+    every round kernel variant."""
     groups, sb, oracles = small
+    sb.set_round_variant(1, variant)
     ys = [W.random_dual(g.instance(k), 50 + 10 * gi + k) for gi, g in enumerate(groups) for k in range(g.num_instances)]
     flat = [o for row in oracles for o in row]
     y = sb.pack(ys)
@@ -46,10 +52,14 @@ def test_batched_solve_step_matches_oracle(cuda_device, small):
         assert _rel2(hs[sb.offsets[k]:sb.offsets[k] + sb.sizes[k]], o.sq * o.hx(yk)) < 1e-5
 
 
-def test_batched_nama_matches_oracle(cuda_device, small):
+@pytest.mark.parametrize("variant", VARIANTS)
+def test_batched_nama_matches_oracle(cuda_device, small, variant):
     """Batched NAMA reaches the tolerance for every instance; each solution matches the
-    oracle's NAMA on that instance at the same tolerance and step size."""
+    oracle's NAMA on that instance at the same tolerance and step size (rounds of one and two
+    right-hand sides with every round kernel variant)."""
     groups, sb, oracles = small
+    sb.set_round_variant(1, variant)
+    sb.set_round_variant(2, variant)
     lams = []
     for row in oracles:
         lam, _ = O.power_lambda(row[0], np.random.default_rng(0).standard_normal(row[0].m))
@@ -67,6 +77,44 @@ def test_batched_nama_matches_oracle(cuda_device, small):
             assert _relinf(hx[sl], ref["h"]) < 1e-4
             assert _relinf(y[sl], ref["y"]) < 1e-4
             k += 1
+
+
+@pytest.mark.parametrize("variant", VARIANTS)
+def test_batched_round_at_the_column_kernel_limits(cuda_device, variant):
+    """Shapes at the column kernel's padded widths (nx = 32, nu = 16; nx = 20, nu = 10, the
+    learned-warm-start family's) with branching and chain stages: one round with each variant
+    against the oracle, and the tuner's measurements reported."""
+    from paper_2107_01745_b300.stotree import StoBatch
+    rng = np.random.default_rng(33)
+    groups = [W.make_group(rng, 5, 2, 3, 32, 16, 2), W.make_group(rng, 6, 4, 2, 20, 10, 3)]
+    sb = StoBatch(groups)
+    sb.factor()
+    cfg = sb.round_config(1)
+    assert cfg["tile_cols"] in (32, 64, 128) and all(v > 0 for v in cfg["tuned_ms"].values())
+    sb.set_round_variant(1, variant)
+    ys, flat = [], []
+    for gi, g in enumerate(groups):
+        for k in range(g.num_instances):
+            ys.append(W.random_dual(g.instance(k), 70 + 10 * gi + k))
+            flat.append(O.LQOracle(g.instance(k)))
+    y = sb.pack(ys)
+    for homog in (False, True):
+        h = sb.solve_step(y, homogeneous=homog).cpu().numpy()
+        sb.round_status()
+        for k, (o, yk) in enumerate(zip(flat, ys)):
+            hk = h[sb.offsets[k]:sb.offsets[k] + sb.sizes[k]]
+            assert _rel2(hk, o.hx(yk, homogeneous=homog)) < 1e-5, (homog, k)
+
+
+def test_column_kernel_refused_for_wide_shapes(cuda_device):
+    from paper_2107_01745_b300.stotree import StoBatch, StoError
+    rng = np.random.default_rng(34)
+    sb = StoBatch([W.make_group(rng, 3, 2, 2, 40, 8, 2)])
+    sb.factor()
+    assert sb.round_config(1)["tuned_ms"]["column128"] == -1.0
+    with pytest.raises(StoError) as ei:
+        sb.set_round_variant(1, 3)
+    assert ei.value.code == 1
 
 
 @pytest.mark.slow
