@@ -46,7 +46,7 @@ import time
 
 import numpy as np
 
-from paper_2107_01745_b300.workloads import Problem, dual_offsets
+from paper_2107_01745_b300.workloads import Problem, dual_offsets, problem_offsets
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
 _SRC = os.path.join(_HERE, "stotree_oracle.c")
@@ -135,24 +135,35 @@ class LQOracle:
             raise np.linalg.LinAlgError(f"Rbar not positive definite at node {-st - 1}")
         self._s = np.zeros((self.Nn, nx))
         self._ubar = np.zeros((self.Np, nu))
-        self.off = dual_offsets(t, nx, nu)
+        # the [x; u] layout of Algorithms 3 and 4, and the dual layout (the same unless the problem
+        # has general constraint maps z = F x + G u, Section II-C)
+        self.sel_off = dual_offsets(t, nx, nu)
+        self.sel_m = int(self.sel_off[-1])
+        self.general = p.general
+        self.off = problem_offsets(p)
         self.m = int(self.off[-1])
         self.solve_calls = 0
-        # per dual element: sqrt(pi) of its node, unscaled box (root state block unbounded)
+        # per dual element: sqrt(pi) of its node, unscaled box (selection: root state unbounded)
         node_of = np.repeat(np.arange(self.Nn), np.diff(self.off))
         self.node_of = node_of
         self.sq = np.sqrt(t.prob[node_of])
         lo = np.empty(self.m)
         hi = np.empty(self.m)
         for i in range(self.Nn):
-            o = self.off[i]
+            o, o1 = self.off[i], self.off[i + 1]
+            if self.general:
+                lo[o:o1], hi[o:o1] = (p.zlo, p.zhi) if i < self.Np else (p.zNlo, p.zNhi)
+                continue
             lo[o:o + nx], hi[o:o + nx] = p.xlo, p.xhi
             if i < self.Np:
                 lo[o + nx:o + nx + nu], hi[o + nx:o + nx + nu] = p.ulo, p.uhi
-        lo[:nx], hi[:nx] = -np.inf, np.inf
+        if not self.general:
+            lo[:nx], hi[:nx] = -np.inf, np.inf
         self.lo, self.hi = lo, hi
         # the nonsmooth term per element (Section II-B): kind, rho, delta of its component
         kind, rho, dl = np.zeros(self.m, dtype=np.int32), np.zeros(self.m), np.ones(self.m)
+        if p.pen_kind is not None and self.general:
+            raise ValueError("soft terms are per component of [x; u]: not with general constraint maps")
         if p.pen_kind is not None:
             comp = np.empty(self.m, dtype=np.int64)
             for i in range(self.Nn):
@@ -168,10 +179,28 @@ class LQOracle:
     def Rbar(self) -> np.ndarray:
         return np.einsum("iab,icb->iac", self.Lc, self.Lc)
 
+    def ht(self, y: np.ndarray) -> np.ndarray:
+        """H'y in the [x; u] layout: per nonleaf node [F'y^i; G'y^i], per leaf FN'y^l (the
+        selection: y itself)."""
+        if not self.general:
+            return y
+        p, npl, nx = self.p, self.Np, self.nx
+        nc, ncn = p.F.shape[0], p.FN.shape[0]
+        Yn = y[:npl * nc].reshape(npl, nc)
+        Yl = y[npl * nc:].reshape(self.Nn - npl, ncn)
+        out = np.empty(self.sel_m)
+        blk = out[:npl * (nx + self.nu)].reshape(npl, nx + self.nu)
+        blk[:, :nx] = Yn @ p.F
+        blk[:, nx:] = Yn @ p.G
+        out[npl * (nx + self.nu):] = (Yl @ p.FN).reshape(-1)
+        return out
+
     def solve(self, y: np.ndarray, homogeneous: bool = False):
-        """x(y) by Algorithm 3 (or Algorithm 4 if homogeneous).  y is unscaled, dual-sized."""
+        """x(y) by Algorithm 3 (or Algorithm 4 if homogeneous): the minimiser of f(x) + <y, Hx>,
+        i.e. Algorithm 3 with H'y in the [x; u] layout.  y is unscaled, dual-sized."""
         y = np.ascontiguousarray(y, dtype=np.float64)
         assert y.shape == (self.m,)
+        y = np.ascontiguousarray(self.ht(y))
         x = np.zeros((self.Nn, self.nx))
         u = np.zeros((self.Np, self.nu))
         x0 = np.ascontiguousarray(self.p.x0, dtype=np.float64)
@@ -182,14 +211,22 @@ class LQOracle:
         return x, u
 
     def stack(self, x: np.ndarray, u: np.ndarray) -> np.ndarray:
-        """Hx laid out like y: nonleaf [x^i; u^i], leaf x^l."""
+        """Hx laid out like y: nonleaf [x^i; u^i], leaf x^l; with general constraint maps
+        F x^i + G u^i and FN x^l (x[0] is the root state)."""
         npl, nx, nu = self.Np, self.nx, self.nu
         h = np.empty(self.m)
+        if self.general:
+            p = self.p
+            nc = p.F.shape[0]
+            h[:npl * nc] = (x[:npl] @ p.F.T + u @ p.G.T).reshape(-1)
+            h[npl * nc:] = (x[npl:] @ p.FN.T).reshape(-1)
+            return h
         h[:npl * (nx + nu)] = np.concatenate([x[:npl], u], axis=1).reshape(-1)
         h[npl * (nx + nu):] = x[npl:].reshape(-1)
         return h
 
     def unstack(self, h: np.ndarray):
+        assert not self.general, "H is not invertible in general"
         npl, nx, nu = self.Np, self.nx, self.nu
         blk = h[:npl * (nx + nu)].reshape(npl, nx + nu)
         x = np.concatenate([blk[:, :nx], h[npl * (nx + nu):].reshape(-1, nx)], axis=0)

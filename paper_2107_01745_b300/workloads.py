@@ -156,16 +156,50 @@ class Problem:
     pen_kind: np.ndarray | None = None   # [nx + nu] int
     pen_rho: np.ndarray | None = None    # [nx + nu]
     pen_delta: np.ndarray | None = None  # [nx + nu]
+    # General constraint maps (Section II-C): z^i = F x^i + G u^i at every nonleaf node (the root
+    # included, with x^0 = x0) and z^l = FN x^l at every leaf, shared by all nodes, with the box
+    # zlo <= z <= zhi (zNlo, zNhi at the leaves).  None: the selection z^i = [x^i; u^i], z^l = x^l
+    # with the x and u boxes above (the root's state unboxed).
+    F: np.ndarray | None = None      # [nc, nx]
+    G: np.ndarray | None = None      # [nc, nu]
+    FN: np.ndarray | None = None     # [ncN, nx]
+    zlo: np.ndarray | None = None    # [nc]
+    zhi: np.ndarray | None = None
+    zNlo: np.ndarray | None = None   # [ncN]
+    zNhi: np.ndarray | None = None
+
+    @property
+    def general(self) -> bool:
+        return self.F is not None
 
     @property
     def num_dual(self) -> int:
         t = self.tree
+        if self.general:
+            return t.num_nonleaf * self.F.shape[0] + t.num_leaves * self.FN.shape[0]
         return t.num_nonleaf * (self.nx + self.nu) + t.num_leaves * self.nx
 
     @property
     def num_primal(self) -> int:
         t = self.tree
         return t.num_nonleaf * self.nu + (t.num_nodes - 1) * self.nx
+
+
+def problem_offsets(p: "Problem") -> np.ndarray:
+    """Start of node i's block in p's dual vector: [x; u] / x (selection) or z = F x + G u / FN x."""
+    if p.general:
+        return block_offsets(p.tree, p.F.shape[0], p.FN.shape[0])
+    return dual_offsets(p.tree, p.nx, p.nu)
+
+
+def block_offsets(tree: Tree, nb: int, nbl: int) -> np.ndarray:
+    """Start of node i's block when nonleaf blocks have nb entries and leaf blocks nbl."""
+    nn, npl = tree.num_nodes, tree.num_nonleaf
+    off = np.empty(nn + 1, dtype=np.int64)
+    idx = np.arange(nn, dtype=np.int64)
+    off[:nn] = np.where(idx < npl, idx * nb, npl * nb + (idx - npl) * nbl)
+    off[nn] = npl * nb + (nn - npl) * nbl
+    return off
 
 
 def dual_offsets(tree: Tree, nx: int, nu: int) -> np.ndarray:
@@ -314,11 +348,36 @@ def random_problem(seed: int, horizon: int = 3, nx: int = 3, nu: int = 2, max_br
 
 
 def random_dual(p: Problem, seed: int, scale: float = 1.0) -> np.ndarray:
-    """A seeded dual vector (unscaled), zero on the root's state block."""
+    """A seeded dual vector (unscaled), zero on the root's state block (selection constraints:
+    the root's state is the parameter and carries no constraint)."""
     rng = np.random.default_rng(seed)
     y = scale * rng.standard_normal(p.num_dual)
-    y[:p.nx] = 0.0
+    if not p.general:
+        y[:p.nx] = 0.0
     return y
+
+
+def with_constraints(p: Problem, F, G, FN, zlo, zhi, zNlo, zNhi) -> Problem:
+    """Set general constraint maps and their boxes (see Problem)."""
+    p.F, p.G, p.FN = (np.ascontiguousarray(a, dtype=np.float64) for a in (F, G, FN))
+    p.zlo, p.zhi, p.zNlo, p.zNhi = (np.ascontiguousarray(a, dtype=np.float64) for a in (zlo, zhi, zNlo, zNhi))
+    return p
+
+
+def constrained_problem(seed: int, horizon: int = 3, nx: int = 3, nu: int = 2, nc: int = 4, ncN: int = 2,
+                        max_branch: int = 3, p_branch: float = 0.6, tree: Tree | None = None) -> Problem:
+    """A random problem of random_problem's recipe with general constraint maps: F ~ N(0,1) [nc, nx],
+    G ~ N(0,1) [nc, nu], FN ~ N(0,1) [ncN, nx] (draw order after the problem's own draws: F, G, FN),
+    boxes left unbounded (+-inf); the caller sets them (e.g. from the unconstrained solution)."""
+    p = random_problem(seed, horizon=horizon, nx=nx, nu=nu, max_branch=max_branch, p_branch=p_branch,
+                       box_scale=1e6, tree=tree)
+    rng = np.random.default_rng([seed, 7])
+    F = rng.standard_normal((nc, nx))
+    G = rng.standard_normal((nc, nu))
+    FN = rng.standard_normal((ncN, nx))
+    inf = np.inf
+    return with_constraints(p, F, G, FN, -inf * np.ones(nc), inf * np.ones(nc), -inf * np.ones(ncN),
+                            inf * np.ones(ncN))
 
 
 # --------------------------------------------------------------------------------------

@@ -18,28 +18,29 @@ def _index(p):
 
 def build_qp(p, y, homogeneous=False):
     """min 1/2 v'Gv + g'v  s.t.  E v = e  for  f(x) + <y, Hx>  under the dynamics.
-    v = (u^0..u^{Np-1}, x^1..x^{Nn-1}); y is unscaled, dual-sized."""
+    v = (u^0..u^{Np-1}, x^1..x^{Nn-1}); y is unscaled, dual-sized (the term <y, Hx> enters g
+    through the rows of H, h_rows; with general constraint maps H is F, G, FN)."""
     t = p.tree
     nn, npl, nx, nu = t.num_nodes, t.num_nonleaf, p.nx, p.nu
     pr = t.prob
     uoff, xoff, nv = _index(p)
-    from paper_2107_01745_b300.workloads import dual_offsets
-    off = dual_offsets(t, nx, nu)
     G = np.zeros((nv, nv))
     g = np.zeros(nv)
     lin = 0.0 if homogeneous else 1.0
     for i in range(npl):
         o = uoff[i]
         G[o:o + nu, o:o + nu] = 2.0 * pr[i] * np.diag(p.R)
-        g[o:o + nu] = lin * pr[i] * p.r + y[off[i] + nx:off[i] + nx + nu]
+        g[o:o + nu] = lin * pr[i] * p.r
     for j in range(1, nn):
         o = xoff[j]
         if j < npl:
             G[o:o + nx, o:o + nx] = 2.0 * pr[j] * np.diag(p.Q)
-            g[o:o + nx] = lin * pr[j] * p.q + y[off[j]:off[j] + nx]
+            g[o:o + nx] = lin * pr[j] * p.q
         else:
             G[o:o + nx, o:o + nx] = 2.0 * pr[j] * np.diag(p.PN)
-            g[o:o + nx] = lin * pr[j] * p.pN + y[off[j]:off[j] + nx]
+            g[o:o + nx] = lin * pr[j] * p.pN
+    Hm, _ = h_rows(p)
+    g = g + Hm.T @ np.asarray(y, dtype=np.float64)
     E = np.zeros(((nn - 1) * nx, nv))
     e = np.zeros((nn - 1) * nx)
     x0 = np.zeros(nx) if homogeneous else p.x0
@@ -79,15 +80,29 @@ def dense_solve(p, y, homogeneous=False):
 
 
 def h_rows(p):
-    """Selection of Hx (laid out like y) from v, plus the constant root block."""
+    """Hx (laid out like y) as Hm v + const: the selection of [x^i; u^i] / x^l, or with general
+    constraint maps F x^i + G u^i / FN x^l; the root state enters the constant."""
     t = p.tree
     nn, npl, nx, nu = t.num_nodes, t.num_nonleaf, p.nx, p.nu
     uoff, xoff, nv = _index(p)
-    from paper_2107_01745_b300.workloads import dual_offsets
-    off = dual_offsets(t, nx, nu)
+    from paper_2107_01745_b300.workloads import problem_offsets
+    off = problem_offsets(p)
     m = int(off[-1])
     Hm = np.zeros((m, nv))
     const = np.zeros(m)
+    if p.general:
+        nc, ncn = p.F.shape[0], p.FN.shape[0]
+        for i in range(nn):
+            o = off[i]
+            if i < npl:
+                if i == 0:
+                    const[o:o + nc] = p.F @ p.x0
+                else:
+                    Hm[o:o + nc, xoff[i]:xoff[i] + nx] = p.F
+                Hm[o:o + nc, uoff[i]:uoff[i] + nu] = p.G
+            else:
+                Hm[o:o + ncn, xoff[i]:xoff[i] + nx] = p.FN
+        return Hm, const
     for i in range(nn):
         o = off[i]
         if i == 0:
@@ -100,12 +115,17 @@ def h_rows(p):
 
 
 def box_vectors(p):
-    from paper_2107_01745_b300.workloads import dual_offsets
+    from paper_2107_01745_b300.workloads import dual_offsets, problem_offsets
     t = p.tree
     nx, nu = p.nx, p.nu
-    off = dual_offsets(t, nx, nu)
+    off = problem_offsets(p)
     m = int(off[-1])
     lo, hi = np.empty(m), np.empty(m)
+    if p.general:
+        for i in range(t.num_nodes):
+            o, o1 = off[i], off[i + 1]
+            lo[o:o1], hi[o:o1] = (p.zlo, p.zhi) if i < t.num_nonleaf else (p.zNlo, p.zNhi)
+        return lo, hi
     for i in range(t.num_nodes):
         o = off[i]
         lo[o:o + nx], hi[o:o + nx] = p.xlo, p.xhi
@@ -170,5 +190,24 @@ def boxed_problem(seed, frac=0.7, **kw):
         W.with_box(p, f * np.max(np.abs(x[1:]), axis=0), f * np.max(np.abs(u), axis=0))
         if feasible(p):
             p.name = f"boxed{seed}"
+            return p
+    raise RuntimeError("no feasible box")
+
+
+def constrained_boxed_problem(seed, frac=0.7, **kw):
+    """Random problem with general constraint maps z = F x + G u (FN x at the leaves) whose z box is
+    frac x the range of z along its unconstrained solution, relaxed until the LP says it is
+    feasible."""
+    from paper_2107_01745_b300 import workloads as W
+    p = W.constrained_problem(seed, **kw)
+    x, u = dense_solve(p, np.zeros(p.num_dual))
+    npl = p.tree.num_nonleaf
+    zn = x[:npl] @ p.F.T + u @ p.G.T
+    zl = x[npl:] @ p.FN.T
+    for f in (frac, frac + 0.1, frac + 0.2, 1.0):
+        zmax, zNmax = f * np.max(np.abs(zn), axis=0), f * np.max(np.abs(zl), axis=0)
+        W.with_constraints(p, p.F, p.G, p.FN, -zmax, zmax, -zNmax, zNmax)
+        if feasible(p):
+            p.name = f"fg{seed}"
             return p
     raise RuntimeError("no feasible box")

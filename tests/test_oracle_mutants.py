@@ -33,10 +33,10 @@ from oracle import oracle as O
 from oracle import kkt_check as KC
 from oracle import stream_kkt as SK
 from paper_2107_01745_b300 import workloads as W
-from tests import (test_backtrack_oracle, test_gpad_oracle, test_kkt_oracle, test_mlp_oracle, test_oracle_pins,
-                   test_penalty_oracle, test_spring_mass, test_stream_kkt)
+from tests import (test_backtrack_oracle, test_fg_oracle, test_gpad_oracle, test_kkt_oracle, test_mlp_oracle,
+                   test_oracle_pins, test_penalty_oracle, test_spring_mass, test_stream_kkt)
 
-PIN_MODULES = [test_oracle_pins, test_gpad_oracle, test_backtrack_oracle, test_penalty_oracle]
+PIN_MODULES = [test_oracle_pins, test_gpad_oracle, test_backtrack_oracle, test_penalty_oracle, test_fg_oracle]
 # Python parts of the oracle: (module, the name the pin modules import it under, pin modules)
 TARGETS = {
     "oracle": (O, "O", PIN_MODULES),
@@ -160,6 +160,13 @@ PY_MUTANTS = [
      'lhs = lam * float(np.linalg.norm(-hT + pt["h"]))', 'lhs = float(np.linalg.norm(-hT + pt["h"]))'),
     ("halving_doubles", "NAMA's backtracking doubles lambda",
      "nonlocal lam, pt\n        lam *= 0.5", "nonlocal lam, pt\n        lam *= 2.0"),
+    # general constraint maps z = F x + G u
+    ("fg_ht_drops_G", "H'y without the G'y part (the inputs never see the dual)",
+     "blk[:, nx:] = Yn @ p.G", "blk[:, nx:] = 0.0"),
+    ("fg_hx_drops_Gu", "Hx without the G u part",
+     "h[:npl * nc] = (x[:npl] @ p.F.T + u @ p.G.T).reshape(-1)", "h[:npl * nc] = (x[:npl] @ p.F.T).reshape(-1)"),
+    ("fg_leaf_dual_dropped", "the leaves' dual left out of H'y",
+     "out[npl * (nx + self.nu):] = (Yl @ p.FN).reshape(-1)", "out[npl * (nx + self.nu):] = 0.0"),
 ]
 
 # the warm-start network (oracle/mlp.py) and the streamed optimality check (oracle/stream_kkt.py)
