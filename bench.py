@@ -10,7 +10,7 @@ events on the launching stream for the roofline line.
 
     python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
                     [--warm-train-draws D] [--warm-eval-draws E] [--spring-mass 0|1]
-                    [--profile nama|minfbe|batched|warm|infer]
+                    [--profile nama|minfbe|batched|warm|infer|warm_round|warm_round_full|uneven_round]
 
 Beside the headline the line carries the batched workload (512 instances), the learned warm
 start (training, inference, warm vs cold), the factor, GPAD (warm start and to tolerance), the
@@ -483,6 +483,56 @@ def run_warm(dev, train_draws, eval_draws):
             "warm_direct_speedup": round(r["cold_ms"] / r["direct_ms"], 3)}
 
 
+def batched_round_bytes(groups, affine=True):
+    """Algorithmic bytes of one batched solve round (one right-hand side per instance, FP32): y read
+    and Hx written (m each), s and ubar of every nonleaf node written and read once, the state of
+    every non-root node written and read once, and for the affine round (Algorithm 3) the
+    disturbances c and the constant terms gamma read once.  The stage matrices (a few KB per
+    group) are not counted."""
+    total = 0.0
+    for g in groups:
+        t = g.tree()
+        nn, npl = t.num_nodes, t.num_nonleaf
+        m_i = npl * (g.nx + g.nu) + t.num_leaves * g.nx
+        per = 2 * m_i + 2 * g.nx * npl + 2 * g.nu * npl + 2 * g.nx * (nn - 1)
+        if affine:
+            per += g.nx * (nn - 1) + (g.nx + g.nu) * npl
+        total += 4.0 * per * g.num_instances
+    return total
+
+
+def time_batched_rounds(groups, dev, reps=20):
+    """Mean time of `reps` batched solve rounds (Algorithm 3, one right-hand side per instance) and
+    their HBM roofline: algorithmic bytes (batched_round_bytes) over the CUDA-event time on the
+    launching stream; the tuner's choice of round kernel beside it."""
+    import torch
+    from paper_2107_01745_b300.stotree import StoBatch
+    sb = StoBatch(groups, device=dev)
+    sb.factor()
+    stream = torch.cuda.current_stream()
+    y = torch.randn(sb.M, device=dev, generator=torch.Generator(device=dev).manual_seed(1)) * 0.01
+    for _ in range(3):
+        sb.solve_step(y)
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(reps):
+        sb.solve_step(y)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    sb.round_status()
+    ms = e0.elapsed_time(e1) / reps
+    nbytes = batched_round_bytes(groups)
+    peak, peak_kind = _peaks()
+    gbs = nbytes / (ms * 1e-3) / 1e9
+    cfg = sb.round_config(1)
+    sb.close()
+    return {"round_ms": round(ms, 4), "algorithmic_bytes": nbytes, "dual_variables": sb.M,
+            "roofline": {"bound": "hbm", "achieved": round(gbs, 1), "peak": peak, "unit": "GB/s",
+                         "frac": round(gbs / peak, 4), "peak_source": peak_kind},
+            "round_kernel": cfg}
+
+
 def run_batched(dev, steps):
     """Batched uneven workload: 512 instances (16 shape groups x 32) solved by one batched NAMA
     per step, against the plain single-instance FP32 path run instance after instance (timed on
@@ -536,9 +586,41 @@ def run_batched(dev, steps):
         plain_ms += a.elapsed_time(bb) * g.num_instances
         sample += 1
         st.close()
+    # the same groups with a binding input box (|u| <= 0.3 instead of the configured |u| <= 1), so
+    # that the instances iterate: labelled as a variant, beside the literal workload
+    import dataclasses
+    bgroups = [dataclasses.replace(g, ulo=-0.3 * np.ones(g.nu), uhi=0.3 * np.ones(g.nu)) for g in groups]
+    sbb = StoBatch(bgroups, device=dev)
+    sbb.factor()
+    blams = sbb.group_lambdas()
+    sbb.nama(blams, tol=TOL, max_iter=1000)  # warm-up (graph capture)
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    bres = sbb.nama(blams, tol=TOL, max_iter=1000, outputs=False)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    binfos = bres["infos"]
+    binding = {"workload": "the same 512 instances with the input box |u| <= 0.3 (a variant: the configured box is "
+                           "|u| <= 1, under which most instances do not iterate)",
+               "batched_ms": round(e0.elapsed_time(e1), 3),
+               "all_converged": all(i["status"] == 0 and i["res_inf"] <= TOL for i in binfos),
+               "mean_iters": round(float(np.mean([i["iters"] for i in binfos])), 3),
+               "max_iters": int(max(i["iters"] for i in binfos)),
+               "instances_needing_iterations": int(sum(i["iters"] > 0 for i in binfos))}
+    sbb.close()
+    # solve rounds alone: the literal workload (tile kernel: groups up to nx = 64) and the
+    # learned-warm-start evaluation batch, a family that iterates (column kernel)
+    rounds_uneven = time_batched_rounds(groups, dev)
+    rounds_warm = time_batched_rounds([W.warm_start_draws(W.warm_start_system(4), W.WARM_EVAL_SEED, 5000,
+                                                          dtype=np.float32)], dev)
     return {"workload": "16 shape groups x 32 instances (512): horizon U{10..30}, branching 2 or 3 for the first "
                         "stages with 64-1024 scenarios, nx in {16, 32, 64}, nu = nx/2, shared A, B, costs and box per "
                         "group, own x0 ~ U[-3,3] and w ~ N(0, 0.05^2) per instance, seed 3; NAMA to 1e-4",
+            "binding_box_variant": binding,
+            "rounds": {"uneven_512": rounds_uneven,
+                       "warm_start_eval_5000": dict(rounds_warm, workload="the learned-warm-start family (horizon 15, "
+                                                    "branching 4 for 4 stages, nx=20, nu=10), 5,000 evaluation draws")},
             "instances": sb.ninst, "dual_variables": sb.M, "batched_ms": round(batched_ms, 3),
             "max_iters": int(max(i["iters"] for i in infos)),
             "mean_iters": round(float(np.mean([i["iters"] for i in infos])), 3),
@@ -546,11 +628,11 @@ def run_batched(dev, steps):
             "plain_sequential_ms": round(plain_ms, 1),
             "plain_sample": f"{sample} instances (one per group) timed with the single-instance path, x32",
             "speedup": round(plain_ms / batched_ms, 2),
-            "roofline": {"bound": "hbm", "achieved": round(rounds_gbs, 1), "peak": peak, "unit": "GB/s",
-                         "frac": round(rounds_gbs / peak, 4), "peak_source": peak_kind,
-                         "algorithmic_bytes": vec_bytes,
-                         "note": "vector bytes of the solve rounds over the whole batched solve time "
-                                 "(elementwise passes included in the time, not in the bytes)"}}
+            "solve_vector_rate": {"achieved": round(rounds_gbs, 1), "unit": "GB/s", "algorithmic_bytes": vec_bytes,
+                                  "note": "vector bytes of the solve rounds over the whole batched NAMA time "
+                                          "(elementwise passes and host round trips in the time, not in the bytes); "
+                                          "the per-round roofline is under rounds"},
+            "roofline": rounds_warm["roofline"]}
 
 
 def cpu_baseline(p, lam, gpu_iters):
@@ -655,6 +737,31 @@ def run_profile(method):
         print(json.dumps({"profiled": method, "draws": 500, "rows": 500 * system.tree().num_nodes,
                           "outputs": int(y.numel())}))
         return
+    if method in ("warm_round", "warm_round_full", "uneven_round"):
+        # one batched solve round (Algorithm 3): 300 draws of the learned-warm-start family (the
+        # column kernel; a few GB on the device), the 5,000 evaluation draws (for single-pass
+        # counters only: about 50 GB on the device), or the 512-instance workload's 16 shape groups
+        # with 8 instances each (the tile kernel; a few GB)
+        if method == "warm_round":
+            groups = [W.warm_start_draws(W.warm_start_system(4), W.WARM_EVAL_SEED, 300, dtype=np.float32)]
+        elif method == "warm_round_full":
+            groups = [W.warm_start_draws(W.warm_start_system(4), W.WARM_EVAL_SEED, 5000, dtype=np.float32)]
+        else:
+            groups = W.batched_uneven(3, instances=8)
+        sb = StoBatch(groups)
+        sb.factor()
+        y = torch.randn(sb.M, device="cuda", generator=torch.Generator(device="cuda").manual_seed(1)) * 0.01
+        for _ in range(3):
+            sb.solve_step(y)
+        torch.cuda.synchronize()
+        torch.cuda.cudart().cudaProfilerStart()
+        sb.solve_step(y)
+        torch.cuda.synchronize()
+        torch.cuda.cudart().cudaProfilerStop()
+        sb.round_status()
+        print(json.dumps({"profiled": method, "round_kernel": sb.round_config(1),
+                          "algorithmic_bytes": batched_round_bytes(groups)}))
+        return
     if method == "batched":
         sb = StoBatch(W.batched_uneven(3))
         sb.factor()
@@ -693,7 +800,9 @@ def main():
                     help="held-out draws the learned warm start is evaluated on")
     ap.add_argument("--spring-mass", type=int, default=1,
                     help="run the 300-problem spring-mass experiment of Section IV-A (0 skips it)")
-    ap.add_argument("--profile", choices=["nama", "minfbe", "batched", "warm", "infer"], default=None,
+    ap.add_argument("--profile", choices=["nama", "minfbe", "batched", "warm", "infer", "warm_round", "warm_round_full",
+                                          "uneven_round"],
+                    default=None,
                     help="run one solve inside a profiler range (no JSON benchmark line)")
     args = ap.parse_args()
     if args.profile:

@@ -18,8 +18,8 @@ def _commands(text):
 
 
 def test_every_summary_names_its_command():
-    modes = set(re.search(r'"--profile", choices=\[([^\]]*)\]', open(os.path.join(ROOT, "bench.py")).read())
-                .group(1).replace('"', "").replace(" ", "").split(","))
+    modes = {m.strip().strip('"') for m in re.search(r'"--profile", choices=\[([^\]]*)\]',
+                                                      open(os.path.join(ROOT, "bench.py")).read()).group(1).split(",")}
     paths = sorted(glob.glob(os.path.join(ROOT, "profiles", "*.md")))
     assert paths
     for path in paths:
