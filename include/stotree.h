@@ -22,8 +22,9 @@
  *
  * Vector layouts.  A dual-sized vector (y, Hx, z; length m = Np(nx+nu) + Nl nx) has
  * one block per node: nonleaf i at offset i(nx+nu) holding [x-part (nx); u-part (nu)],
- * leaf l at offset Np(nx+nu) + (l-Np)nx holding [x-part (nx)].  Primal outputs are
- * x [Nn][nx] (x[0] = x0) and u [Np][nu].
+ * leaf l at offset Np(nx+nu) + (l-Np)nx holding [x-part (nx)].  With general constraint
+ * maps (stotree_set_constraint_maps) the blocks hold z^i = F x^i + G u^i (nc entries) and
+ * z^l = FN x^l (ncN).  Primal outputs are x [Nn][nx] (x[0] = x0) and u [Np][nu].
  *
  * Precision: a handle is created either FP64 (every device array and vector of the
  * solve path in double) or FP32 (solve step, prox and L-BFGS in float; the factor
@@ -130,6 +131,27 @@ typedef struct {
  * above the solve kernel's register tiling: max(pad(nx + nu), pad(nx) + pad(nu)) > 512 for FP32
  * or > 256 for FP64, pad = round up to 16 bytes), STO_ERR_TREE. */
 STO_API sto_status stotree_create(const sto_tree_desc *tree, int32_t precision, stotree_t *out);
+
+/* General constraint maps (Section II-C) instead of the selection of [x; u]: z^i = F x^i + G u^i at
+ * every nonleaf node (the root included, with x^0 = x0) and z^l = FN x^l at every leaf, the same
+ * F [nc][nx], G [nc][nu], FN [ncN][nx] (host FP64, row-major, copied) at every node.  The dual
+ * then has one block of nc entries per nonleaf node and of ncN per leaf (m = Np nc + Nl ncN, the
+ * same block order as the selection layout); y, Hx, z and every dual-sized argument below use
+ * that layout, and the box is the one of stotree_set_zbox (stotree_set_box is not used).  Call it
+ * after stotree_create and before stotree_workspace_size / stotree_bind_workspace (it changes m
+ * and the workspace).  A solve round then computes H'y, runs Algorithm 3/4 in the [x; u] layout
+ * and forms Hx = H [x; u]; the solvers take f(x) of the FBE from the primal of each round.  Not
+ * with soft terms (stotree_set_penalty) or the no-allocation solve step.
+ * Errors: STO_ERR_INVALID_ARG (sizes < 1 or > 1024, m >= 2^31, non-finite entries, workspace
+ * already bound). */
+STO_API sto_status stotree_set_constraint_maps(stotree_t h, int32_t nc, int32_t ncN, const double *F, const double *G,
+                                               const double *FN);
+
+/* The box zlo <= z <= zhi [nc] of the nonleaf blocks and zNlo <= z <= zNhi [ncN] of the leaf blocks
+ * (general maps; +-INFINITY allowed; host FP64).  Synchronises.  Errors: STO_ERR_INVALID_ARG
+ * (no general maps, lo > hi), STO_ERR_NOT_READY (no workspace). */
+STO_API sto_status stotree_set_zbox(stotree_t h, const double *zlo, const double *zhi, const double *zNlo,
+                                    const double *zNhi, sto_stream_t stream);
 
 /* Release the handle (host memory only; the workspace belongs to the caller). */
 STO_API void stotree_destroy(stotree_t h);

@@ -23,6 +23,11 @@ with Algorithm 1):
     rho min(d, delta) sign, d the distance, sign +1 above the box and -1 below it.
   The root's state block is the parameter and carries no term (its y must be zero).
 
+With general constraint maps (Section II-C: z^i = F x^i + G u^i, z^l = FN x^l) the same conditions
+hold with H'y in place of y in the costates and u equations (per nonleaf node F'y^i for the state
+part and G'y^i for the input part, FN'y^l at a leaf) and with the box on z, the root's block
+included (x^0 = x0).
+
 kkt_residuals returns the five numbers that stotree_kkt_check defines (largest violations, with
 points within tol_active of a bound counted as lying on it):
   dynamics, stationarity, feasibility (hard components), complementarity (hard components
@@ -43,6 +48,25 @@ def _dual_block(p, i):
     return npn * (nx + nu) + (i - npn) * nx, nx
 
 
+def _ht_blocks(p, y):
+    """H'y in the [x; u] layout (the selection maps: y itself)."""
+    if not p.general:
+        return np.asarray(y, dtype=np.float64)
+    t = p.tree
+    npn, nn, nx, nu = t.num_nonleaf, t.num_nodes, p.nx, p.nu
+    nc, ncn = p.F.shape[0], p.FN.shape[0]
+    out = np.empty(npn * (nx + nu) + (nn - npn) * nx)
+    for i in range(nn):
+        if i < npn:
+            yi = y[i * nc:(i + 1) * nc]
+            out[i * (nx + nu):i * (nx + nu) + nx] = p.F.T @ yi
+            out[i * (nx + nu) + nx:(i + 1) * (nx + nu)] = p.G.T @ yi
+        else:
+            o = npn * nc + (i - npn) * ncn
+            out[npn * (nx + nu) + (i - npn) * nx:npn * (nx + nu) + (i - npn + 1) * nx] = p.FN.T @ y[o:o + ncn]
+    return out
+
+
 def _component_terms(p):
     """Per component of [x; u]: lo, hi, kind, rho, delta (hard box when no penalty is set)."""
     lo = np.concatenate([np.asarray(p.xlo, float), np.asarray(p.ulo, float)])
@@ -61,7 +85,8 @@ def kkt_residuals(p, x0, x, u, y, tol_active):
     prob, parent = np.asarray(t.prob, float), np.asarray(t.parent)
     x = np.asarray(x, dtype=np.float64)
     u = np.asarray(u, dtype=np.float64)
-    y = np.asarray(y, dtype=np.float64)
+    y_dual = np.asarray(y, dtype=np.float64)
+    y = _ht_blocks(p, y_dual)  # the dual as it enters the costates and u equations
     x0 = np.asarray(x0, dtype=np.float64)
     Q, R, PN = (np.asarray(v, float) for v in (p.Q, p.R, p.PN))
     q, r, pN = (np.asarray(v, float) for v in (p.q, p.r, p.pN))
@@ -95,6 +120,8 @@ def kkt_residuals(p, x0, x, u, y, tol_active):
             sumA[parent[j]] += p.A[j].T @ mu[j]
             sumB[parent[j]] += p.B[j].T @ mu[j]
 
+    if p.general:
+        return {"dynamics": dyn, "stationarity": stat, **_box_on_z(p, x0, x, u, y_dual, tol_active)}
     # the nonsmooth term, component by component
     lo, hi, kind, rho, delta = _component_terms(p)
     feas = comp = sign = 0.0
@@ -135,3 +162,31 @@ def kkt_residuals(p, x0, x, u, y, tol_active):
             else:
                 sign = max(sign, viol)
     return {"dynamics": dyn, "stationarity": stat, "feasibility": feas, "complementarity": comp, "sign": sign}
+
+
+def _box_on_z(p, x0, x, u, y, tol_active):
+    """Feasibility, complementarity and sign of the box on z = F x + G u (FN x at the leaves)."""
+    t = p.tree
+    npn, nn = t.num_nonleaf, t.num_nodes
+    nc, ncn = p.F.shape[0], p.FN.shape[0]
+    feas = comp = sign = 0.0
+    for i in range(nn):
+        if i < npn:
+            z = p.F @ (x0 if i == 0 else x[i]) + p.G @ u[i]
+            yi, lo, hi = y[i * nc:(i + 1) * nc], p.zlo, p.zhi
+        else:
+            o = npn * nc + (i - npn) * ncn
+            z = p.FN @ x[i]
+            yi, lo, hi = y[o:o + ncn], p.zNlo, p.zNhi
+        for k in range(len(z)):
+            zk, yk = float(z[k]), float(yi[k])
+            feas = max(feas, lo[k] - zk, zk - hi[k], 0.0)
+            at_hi, at_lo = zk >= hi[k] - tol_active, zk <= lo[k] + tol_active
+            if not at_hi and not at_lo:
+                comp = max(comp, abs(yk))
+            elif at_hi and not at_lo:
+                sign = max(sign, -yk)
+            elif at_lo and not at_hi:
+                sign = max(sign, yk)
+    return {"feasibility": feas, "complementarity": comp, "sign": sign}
+

@@ -124,13 +124,26 @@ static void compute_layout(stotree_t h) {
     L.ringY = add((kMaxMem + 1) * mpad * es);
     L.partials = add((size_t)kRedBlocks * kRedSlots * 8);
     L.scal = add(sizeof(SolverScalars));
-    L.kkt = add((Nn * nx + Np * nu) * 8 + 64 * 8);
+    L.kkt = add((Nn * nx + Np * nu) * 8 + 64 * 8 + (h->fg ? (size_t)h->msel * 8 : 0));
     L.bstart = add(h->bstart.size() * 4);
     L.bnodes = add(h->bnodes.size() * 4);
     L.fstart = add(h->fstart.size() * 4);
     L.fnodes = add(h->fnodes.size() * 4);
     L.flags = add(2 * Nn * 4);
     L.ticket = add(64);
+    if (h->fg) {
+        const size_t nfg = (size_t)h->nc * (nx + nu) + (size_t)h->ncN * nx;
+        const size_t nzb = 5 * (size_t)(h->nc + h->ncN);
+        const size_t spad = round_up((size_t)h->msel, 64);
+        L.FG = add(nfg * es);
+        L.FG64 = add(nfg * 8);
+        L.zbox = add(nzb * es);
+        L.zbox64 = add(nzb * 8);
+        L.ht = add(kMaxRhs * spad * es);
+        L.pv = add(kMaxRhs * spad * es);
+        L.pvec = add(4 * spad * es);
+        L.zcost = add(4 * (size_t)(h->nc + h->ncN + nx + nu) * es);
+    }
     L.total = round_up(total, 256);
 }
 
@@ -338,6 +351,59 @@ void stotree_destroy(stotree_t h) {
     delete h;
 }
 
+sto_status stotree_set_constraint_maps(stotree_t h, int32_t nc, int32_t ncN, const double *F, const double *G,
+                                       const double *FN) {
+    if (!h || nc < 1 || ncN < 1 || nc > kMaxDim || ncN > kMaxDim || !F || !G || !FN) return STO_ERR_INVALID_ARG;
+    if (h->ws) return STO_ERR_INVALID_ARG;  // the dual length is part of the workspace layout
+    const int64_t m = (int64_t)h->Np * nc + (int64_t)h->Nl * ncN;
+    if (m >= (int64_t)1 << 31) return STO_ERR_INVALID_ARG;
+    for (int64_t k = 0; k < (int64_t)nc * h->nx; ++k)
+        if (!std::isfinite(F[k])) return STO_ERR_INVALID_ARG;
+    for (int64_t k = 0; k < (int64_t)nc * h->nu; ++k)
+        if (!std::isfinite(G[k])) return STO_ERR_INVALID_ARG;
+    for (int64_t k = 0; k < (int64_t)ncN * h->nx; ++k)
+        if (!std::isfinite(FN[k])) return STO_ERR_INVALID_ARG;
+    h->fg = true;
+    h->nc = nc;
+    h->ncN = ncN;
+    h->Fm.assign(F, F + (size_t)nc * h->nx);
+    h->Gm.assign(G, G + (size_t)nc * h->nu);
+    h->FNm.assign(FN, FN + (size_t)ncN * h->nx);
+    h->msel = (int64_t)h->Np * (h->nx + h->nu) + (int64_t)h->Nl * h->nx;  // the [x; u] layout of the round
+    h->m = m;
+    h->have_zbox = false;
+    compute_layout(h);
+    return STO_OK;
+}
+
+sto_status stotree_set_zbox(stotree_t h, const double *zlo, const double *zhi, const double *zNlo, const double *zNhi,
+                            sto_stream_t stream) {
+    if (!h || !zlo || !zhi || !zNlo || !zNhi) return STO_ERR_INVALID_ARG;
+    if (!h->fg) return STO_ERR_INVALID_ARG;
+    if (!h->ws) return STO_ERR_NOT_READY;
+    const int n = h->nc + h->ncN;
+    std::vector<double> b(5 * (size_t)n, 0.0);
+    for (int k = 0; k < n; ++k) {
+        const double lo = k < h->nc ? zlo[k] : zNlo[k - h->nc], hi = k < h->nc ? zhi[k] : zNhi[k - h->nc];
+        if (!(lo <= hi)) return STO_ERR_INVALID_ARG;
+        b[k] = lo;
+        b[n + k] = hi;
+        b[3 * n + k] = 1.0;  // delta (unused: hard box)
+    }
+    cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
+    STO_CUDA(h, cudaMemcpyAsync(h->ws + h->L.zbox64, b.data(), b.size() * 8, cudaMemcpyHostToDevice, st));
+    if (h->prec == STO_FP64) {
+        STO_CUDA(h, cudaMemcpyAsync(h->ws + h->L.zbox, b.data(), b.size() * 8, cudaMemcpyHostToDevice, st));
+    } else {
+        std::vector<float> bf(b.begin(), b.end());
+        STO_CUDA(h, cudaMemcpyAsync(h->ws + h->L.zbox, bf.data(), bf.size() * 4, cudaMemcpyHostToDevice, st));
+    }
+    STO_CUDA(h, cudaStreamSynchronize(st));
+    h->zboxv = b;
+    h->have_zbox = true;
+    return STO_OK;
+}
+
 sto_status stotree_sizes(stotree_t h, int64_t *m, int64_t *n, int32_t *np, int32_t *nl) {
     if (!h) return STO_ERR_INVALID_ARG;
     if (m) *m = h->m;
@@ -382,6 +448,19 @@ sto_status stotree_bind_workspace(stotree_t h, void *dev, size_t bytes, sto_stre
         std::vector<float> sq(h->Nn);
         for (int i = 0; i < h->Nn; ++i) sq[i] = (float)std::sqrt(h->prob[i]);
         STO_CUDA(h, cudaMemcpyAsync(h->ws + L.sqp, sq.data(), h->Nn * 4, cudaMemcpyHostToDevice, st));
+    }
+    if (h->fg) {
+        std::vector<double> fg64(h->Fm);
+        fg64.insert(fg64.end(), h->Gm.begin(), h->Gm.end());
+        fg64.insert(fg64.end(), h->FNm.begin(), h->FNm.end());
+        STO_CUDA(h, cudaMemcpyAsync(h->ws + L.FG64, fg64.data(), fg64.size() * 8, cudaMemcpyHostToDevice, st));
+        if (h->prec == STO_FP64) {
+            STO_CUDA(h, cudaMemcpyAsync(h->ws + L.FG, fg64.data(), fg64.size() * 8, cudaMemcpyHostToDevice, st));
+        } else {
+            std::vector<float> f32(fg64.begin(), fg64.end());
+            STO_CUDA(h, cudaMemcpyAsync(h->ws + L.FG, f32.data(), f32.size() * 4, cudaMemcpyHostToDevice, st));
+        }
+        h->have_zbox = false;
     }
     STO_CUDA(h, cudaStreamSynchronize(st));
     std::fill(h->have_dyn.begin() + 1, h->have_dyn.end(), 0);
@@ -486,6 +565,7 @@ sto_status stotree_set_box(stotree_t h, const double *xlo, const double *xhi, co
 sto_status stotree_set_penalty(stotree_t h, const int32_t *kind, const double *rho, const double *delta,
                                sto_stream_t stream) {
     if (!h) return STO_ERR_INVALID_ARG;
+    if (h->fg && kind) return STO_ERR_INVALID_ARG;  // soft terms are per component of [x; u]
     const int n = h->nx + h->nu;
     std::vector<double> pen(3 * (size_t)n, 0.0);
     for (int k = 0; k < n; ++k) {
@@ -589,7 +669,7 @@ sto_status stotree_nama_solve(stotree_t h, const sto_opts *o, const void *x0, vo
     if (!h || !x0 || !y) return STO_ERR_INVALID_ARG;
     sto_status s = check_opts(o);
     if (s != STO_OK) return s;
-    if (!h->factored || !h->have_box) return STO_ERR_NOT_READY;
+    if (!h->factored || !(h->fg ? h->have_zbox : h->have_box)) return STO_ERR_NOT_READY;
     return solver_run(h, 0, o, x0, y, x, u, z, info, reinterpret_cast<cudaStream_t>(stream));
 }
 
@@ -598,7 +678,7 @@ sto_status stotree_minfbe_solve(stotree_t h, const sto_opts *o, const void *x0, 
     if (!h || !x0 || !y) return STO_ERR_INVALID_ARG;
     sto_status s = check_opts(o);
     if (s != STO_OK) return s;
-    if (!h->factored || !h->have_box) return STO_ERR_NOT_READY;
+    if (!h->factored || !(h->fg ? h->have_zbox : h->have_box)) return STO_ERR_NOT_READY;
     return solver_run(h, 1, o, x0, y, x, u, z, info, reinterpret_cast<cudaStream_t>(stream));
 }
 
@@ -607,14 +687,14 @@ sto_status stotree_gpad_solve(stotree_t h, const sto_opts *o, const void *x0, vo
     if (!h || !x0 || !y) return STO_ERR_INVALID_ARG;
     sto_status s = check_opts(o);
     if (s != STO_OK) return s;
-    if (!h->factored || !h->have_box) return STO_ERR_NOT_READY;
+    if (!h->factored || !(h->fg ? h->have_zbox : h->have_box)) return STO_ERR_NOT_READY;
     return solver_run(h, 2, o, x0, y, x, u, z, info, reinterpret_cast<cudaStream_t>(stream));
 }
 
 sto_status stotree_kkt_check(stotree_t h, const void *x0, const void *x, const void *u, const void *y,
                              double tol_active, double *out, sto_stream_t stream) {
     if (!h || !x0 || !x || !u || !y || !out) return STO_ERR_INVALID_ARG;
-    if (!h->ws || !h->have_cost || !h->have_box) return STO_ERR_NOT_READY;
+    if (!h->ws || !h->have_cost || !(h->fg ? h->have_zbox : h->have_box)) return STO_ERR_NOT_READY;
     return kkt_run(h, x0, x, u, y, tol_active, out, reinterpret_cast<cudaStream_t>(stream));
 }
 

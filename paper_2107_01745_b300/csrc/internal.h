@@ -42,6 +42,9 @@ struct SolverScalars {
     double sq_dot, s_norm2, g_norm2_prev, g_norm2;
     // power iteration
     double pw_L, pw_inv_norm;
+    // general constraint maps: f(x) at the point (k_fcost) and the line search's f(pa) - f(p0),
+    // linear and quadratic coefficients in tau (k_fquad); zero for the selection maps
+    double f_pt, f_ls[3];
     // reduction bookkeeping
     unsigned int red_counter;
     unsigned int pad2;
@@ -77,6 +80,12 @@ struct Layout {
     size_t bstart, bnodes, fstart, fnodes;  // int: segment offsets and node lists
     size_t flags;                // unsigned [2][Nn]: backward / forward completion epochs
     size_t ticket;               // unsigned long long: work-item counter
+    // general constraint maps z = F x + G u (FN x at the leaves)
+    size_t FG, FG64;             // real / double: F [nc][nx], G [nc][nu], FN [ncN][nx]
+    size_t zbox, zbox64;         // real / double: [lo | hi | rho | delta | kind] rows of nc + ncN
+    size_t ht, pv;               // real [kMaxRhs][msel]: H'y into and the primal out of a round
+    size_t pvec;                 // real [4][msel]: the solvers' primal vectors
+    size_t zcost;                // real zeros: the (absent) cost weights of the z entries
 };
 
 constexpr int kSegMax = 4;       // nodes per path segment (work item) of a solve round
@@ -107,6 +116,14 @@ struct stotree_s {
     // [rho | delta | kind] (kind 0 = indicator of the box, 1 = rho dist, 2 = rho Huber(dist))
     std::vector<double> boxv, pen;
     bool general = false;   // some component's kind is not 0
+    // general constraint maps (Section II-C): z^i = F x^i + G u^i at nonleaf nodes, FN x^l at
+    // leaves; the dual then has nc entries per nonleaf node and ncN per leaf (m), the solve round
+    // keeps its [x; u] layout (msel entries)
+    bool fg = false;
+    int nc = 0, ncN = 0;
+    int64_t msel = 0;
+    std::vector<double> Fm, Gm, FNm, zboxv;
+    bool have_zbox = false;
     std::string err;
     // timing
     bool timing = false;
@@ -159,14 +176,23 @@ struct SolveScratch {
     void *flags;               // unsigned [2][Nn] (cleared by the round)
     void *ticket;              // unsigned long long (cleared by the round)
 };
+// With general maps the round computes H'y, runs Algorithm 3/4 in the [x; u] layout into the
+// primal vectors pout[k] (the workspace's when pout is null; msel reals, scaled like hx) and
+// writes hx = H p.
 sto_status solve_round(stotree_t h, const void *const *y, const void *x0, void *const *hx, int nrhs,
-                       bool homogeneous, bool scaled, cudaStream_t st, const SolveScratch *scratch = nullptr);
+                       bool homogeneous, bool scaled, cudaStream_t st, const SolveScratch *scratch = nullptr,
+                       void *const *pout = nullptr);
 
 // Grid and shared-memory caps of the one-right-hand-side round, set up ahead of its first launch
 // (called when the factor is computed, so that later rounds do no host-side set-up work).
 sto_status prepare_round(stotree_t h);
 
 sto_status check_round_error(stotree_t h, cudaStream_t st);
+
+// fgmap.cu: H'y into the [x; u] layout (handle precision, or FP64 for the optimality check) and
+// Hx = H p from the [x; u] layout, for general constraint maps.
+sto_status fg_ht(stotree_t h, const void *y, void *out, bool fp64_out, cudaStream_t st);
+sto_status fg_hx(stotree_t h, const void *p, void *out, cudaStream_t st);
 
 sto_status solver_run(stotree_t h, int method, const sto_opts *o, const void *x0, void *y, void *x,
                       void *u, void *z, sto_info *info, cudaStream_t st);

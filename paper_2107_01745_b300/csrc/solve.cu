@@ -883,10 +883,34 @@ sto_status prepare_round(stotree_t h) {
 }
 
 sto_status solve_round(stotree_t h, const void *const *y, const void *x0, void *const *hx, int nrhs, bool homog,
-                       bool scaled, cudaStream_t st, const SolveScratch *scratch) {
+                       bool scaled, cudaStream_t st, const SolveScratch *scratch, void *const *pout) {
     if (scratch && nrhs != 1) return STO_ERR_INVALID_ARG;
-    return h->prec == STO_FP64 ? solve_impl<double>(h, y, x0, hx, nrhs, homog, scaled, st, scratch)
-                               : solve_impl<float>(h, y, x0, hx, nrhs, homog, scaled, st, scratch);
+    if (!h->fg)
+        return h->prec == STO_FP64 ? solve_impl<double>(h, y, x0, hx, nrhs, homog, scaled, st, scratch)
+                                   : solve_impl<float>(h, y, x0, hx, nrhs, homog, scaled, st, scratch);
+    // general maps: H'y -> the round in the [x; u] layout -> Hx = H p
+    if (scratch) {
+        h->err = "the no-allocation solve step takes the selection maps only";
+        return STO_ERR_INVALID_ARG;
+    }
+    const size_t spad = (size_t)((h->msel + 63) / 64 * 64) * h->esz;
+    const void *ys[kMaxRhs];
+    void *ps[kMaxRhs];
+    for (int k = 0; k < nrhs; ++k) {
+        void *ht = h->ws + h->L.ht + k * spad;
+        const sto_status s = fg_ht(h, y[k], ht, false, st);
+        if (s != STO_OK) return s;
+        ys[k] = ht;
+        ps[k] = pout ? pout[k] : h->ws + h->L.pv + k * spad;
+    }
+    const sto_status s = h->prec == STO_FP64 ? solve_impl<double>(h, ys, x0, ps, nrhs, homog, scaled, st, nullptr)
+                                             : solve_impl<float>(h, ys, x0, ps, nrhs, homog, scaled, st, nullptr);
+    if (s != STO_OK) return s;
+    for (int k = 0; k < nrhs; ++k) {
+        const sto_status e = fg_hx(h, ps[k], hx[k], st);
+        if (e != STO_OK) return e;
+    }
+    return STO_OK;
 }
 
 }  // namespace sto

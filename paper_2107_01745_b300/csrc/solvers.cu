@@ -38,9 +38,16 @@ constexpr int kThreads = 256;
 
 template <class T>
 struct DualView {
-    int m, Np, nx, nu, nxu, leaf_base;
-    float inv_nxu, inv_nx;
-    const T *sqp, *box, *Wc;  // box = [lo x|u][hi x|u][rho][delta][kind], Wc = [Q|R|PN][q|r|pN]
+    int m, Np, nb, nbl, leaf_base;   // dual length, nonleaf nodes, nonleaf / leaf block sizes
+    float inv_nb, inv_nbl;
+    int nx, nu;                      // state and input dimensions
+    // the per-component table: tab_n entries per row, leaf components at leaf_off + c (the
+    // selection layout: the leaves' x part shares the nonleaf rows, leaf_off = 0); root_free: the
+    // root's state block is the parameter (selection layout only); has_cost: the cost weights
+    // belong to the dual entries (selection layout: Hx holds x and u), else f(x) comes from the
+    // primal separately
+    int tab_n, leaf_off, root_free, has_cost;
+    const T *sqp, *box, *Wc;  // box = [lo][hi][rho][delta][kind] rows of tab_n, Wc = [Q|R|PN][q|r|pN]
 
     // per element: sqrt(pi) of its node, scaled bounds sqrt(pi) lo, sqrt(pi) hi, cost weights,
     // and the kind of its nonsmooth term g with rho, delta (Section II-B)
@@ -51,35 +58,39 @@ struct DualView {
 
     // Scalar path (caller-facing conversions): per-entry constants read from global memory.
     __device__ __forceinline__ Meta meta(int e) const {
-        int node, comp, kind;
+        int node, comp;
+        bool leaf;
         if (e < leaf_base) {
-            node = e / nxu;
-            const int k = e - node * nxu;
-            kind = k < nx ? 0 : 1;
-            comp = k < nx ? k : k - nx;
+            node = e / nb;
+            comp = e - node * nb;
+            leaf = false;
         } else {
             const int e2 = e - leaf_base;
-            node = Np + e2 / nx;
-            comp = e2 - (node - Np) * nx;
-            kind = 2;
+            node = Np + e2 / nbl;
+            comp = e2 - (node - Np) * nbl;
+            leaf = true;
         }
         Meta M;
         M.sq = sqp[node];
-        const int bi = kind == 1 ? nx + comp : comp;
-        const int wi = kind == 0 ? comp : (kind == 1 ? nx + comp : nx + nu + comp);
-        if (node == 0 && kind == 0) {
+        const int bi = leaf ? leaf_off + comp : comp;
+        if (root_free && !leaf && node == 0 && comp < nx) {
             M.lo = -INFINITY;
             M.hi = INFINITY;
             M.kind = 0;
         } else {
             M.lo = M.sq * box[bi];
-            M.hi = M.sq * box[nxu + bi];
-            M.kind = (int)box[4 * nxu + bi];
+            M.hi = M.sq * box[tab_n + bi];
+            M.kind = (int)box[4 * tab_n + bi];
         }
-        M.rho = box[2 * nxu + bi];
-        M.delta = box[3 * nxu + bi];
-        M.w = Wc[wi];
-        M.l = M.sq * Wc[2 * nx + nu + wi];
+        M.rho = box[2 * tab_n + bi];
+        M.delta = box[3 * tab_n + bi];
+        if (has_cost) {
+            const int wi = leaf ? nx + nu + comp : comp;
+            M.w = Wc[wi];
+            M.l = M.sq * Wc[2 * nx + nu + wi];
+        } else {
+            M.w = M.l = T(0);
+        }
         return M;
     }
 };
@@ -108,10 +119,10 @@ template <class T>
 __device__ __forceinline__ Pos pos_of(const DualView<T> &dv, int e) {
     Pos p;
     if (e < dv.leaf_base) {
-        p.node = div_fix(e, dv.nxu, dv.inv_nxu, p.comp);
+        p.node = div_fix(e, dv.nb, dv.inv_nb, p.comp);
         p.leaf = false;
     } else {
-        p.node = dv.Np + div_fix(e - dv.leaf_base, dv.nx, dv.inv_nx, p.comp);
+        p.node = dv.Np + div_fix(e - dv.leaf_base, dv.nbl, dv.inv_nbl, p.comp);
         p.leaf = true;
     }
     return p;
@@ -120,25 +131,27 @@ template <class T>
 __device__ __forceinline__ void pos_next(const DualView<T> &dv, Pos &p) {
     ++p.comp;
     if (!p.leaf) {
-        if (p.comp == dv.nxu) {
+        if (p.comp == dv.nb) {
             p.comp = 0;
             ++p.node;
             p.leaf = p.node >= dv.Np;
         }
-    } else if (p.comp == dv.nx) {
+    } else if (p.comp == dv.nbl) {
         p.comp = 0;
         ++p.node;
     }
 }
 
-// Per-component constants of the dual layout in shared memory (dynamic, 9 (nx + nu) reals):
-// nonleaf [x; u] lo, hi, quadratic and linear cost weights; leaf quadratic and linear weights
-// (the leaf box is the x part of the nonleaf box); rho, delta and kind of the term g.
+// Per-component constants of the dual layout in shared memory (dynamic, 9 tab_n reals): lo, hi,
+// quadratic and linear cost weights of nonleaf entries and of leaf entries, rho, delta and kind of
+// the term g.  Selection layout: nonleaf [x; u] components, the leaves the x part with the
+// terminal weights; general maps: the z components of nonleaf blocks, then those of leaf blocks,
+// no cost weights.
 template <class T>
 struct CompTab {
     T *lo, *hi, *w, *l, *wl, *ll, *rh, *dl, *kd;
     __device__ void load(const DualView<T> &dv, T *sm) {
-        const int n = dv.nxu;
+        const int n = dv.tab_n;
         lo = sm;
         hi = sm + n;
         w = sm + 2 * n;
@@ -149,18 +162,19 @@ struct CompTab {
         dl = sm + 7 * n;
         kd = sm + 8 * n;
         nx_ = dv.nx;
+        leaf_off_ = dv.leaf_off;
+        root_free_ = dv.root_free;
         for (int c = threadIdx.x; c < n; c += blockDim.x) {
             lo[c] = dv.box[c];
             hi[c] = dv.box[n + c];
             rh[c] = dv.box[2 * n + c];
             dl[c] = dv.box[3 * n + c];
             kd[c] = dv.box[4 * n + c];
-            w[c] = dv.Wc[c];
-            l[c] = dv.Wc[2 * dv.nx + dv.nu + c];
-            if (c < dv.nx) {
-                wl[c] = dv.Wc[n + c];
-                ll[c] = dv.Wc[2 * dv.nx + dv.nu + n + c];
-            }
+            const int nxu = dv.nx + dv.nu;
+            w[c] = dv.has_cost && c < nxu ? dv.Wc[c] : T(0);
+            l[c] = dv.has_cost && c < nxu ? dv.Wc[2 * dv.nx + dv.nu + c] : T(0);
+            wl[c] = dv.has_cost && c < dv.nx ? dv.Wc[nxu + c] : T(0);
+            ll[c] = dv.has_cost && c < dv.nx ? dv.Wc[2 * dv.nx + dv.nu + nxu + c] : T(0);
         }
         __syncthreads();
     }
@@ -171,26 +185,27 @@ struct CompTab {
         typename DualView<T>::Meta M;
         M.sq = sq;
         const int c = p.comp;
-        if (!p.leaf && p.node == 0 && c < nx_) {  // the root state is the parameter: unboxed
+        const int bi = p.leaf ? leaf_off_ + c : c;
+        if (root_free_ && !p.leaf && p.node == 0 && c < nx_) {  // the root state is the parameter: unboxed
             M.lo = -INFINITY;
             M.hi = INFINITY;
             M.kind = 0;
         } else {
-            M.lo = sq * lo[c];
-            M.hi = sq * hi[c];
-            M.kind = G ? (int)kd[c] : 0;
+            M.lo = sq * lo[bi];
+            M.hi = sq * hi[bi];
+            M.kind = G ? (int)kd[bi] : 0;
         }
-        M.rho = G ? rh[c] : T(0);
-        M.delta = G ? dl[c] : T(1);
+        M.rho = G ? rh[bi] : T(0);
+        M.delta = G ? dl[bi] : T(1);
         M.w = p.leaf ? wl[c] : w[c];
         M.l = sq * (p.leaf ? ll[c] : l[c]);
         return M;
     }
-    int nx_;
+    int nx_, leaf_off_, root_free_;
 };
 template <class T>
 size_t comp_tab_bytes(const DualView<T> &dv) {
-    return (size_t)9 * dv.nxu * sizeof(T);
+    return (size_t)9 * dv.tab_n * sizeof(T);
 }
 
 template <class T>
@@ -461,7 +476,7 @@ __global__ void __launch_bounds__(kThreads) k_point(DualView<T> dv, const T *__r
     if constexpr (BT == 2) sums[5] = r2;
     T maxs[1] = {rmax};
     if (reduce_last<T, NS, 1>(sums, maxs, partials, &sc->red_counter, tot) && threadIdx.x == 0) {
-        sc->phi = -tot[0];
+        sc->phi = -(tot[0] + sc->f_pt);  // f(x) from the primal with general maps (else 0)
         sc->res_inf = tot[NS];
         if constexpr (BT == 1) {
             sc->bt_a = tot[5];
@@ -767,8 +782,11 @@ __global__ void __launch_bounds__(kThreads) k_ls(DualView<T> dv, const T *__rest
     if (reduce_last<T, J, 0>(sums, maxs, partials, &sc->red_counter, tot) && threadIdx.x == 0) {
         // FBE(w) - FBE(ybar) = -sum_e (term(w) - term(ybar))
         for (int j = 0; j < nc; ++j) {
-            sc->cand[e0 + j] = -tot[j];
-            if (-tot[j] <= 0.0) {
+            // with general maps f(x(w(tau))) - f(x(ybar)) from the primal (else 0)
+            const double t = ldexp(1.0, -(e0 + j));
+            const double dphi = -(tot[j] + sc->f_ls[0] + t * (sc->f_ls[1] + t * sc->f_ls[2]));
+            sc->cand[e0 + j] = dphi;
+            if (dphi <= 0.0) {
                 sc->tau = ldexp(1.0, -(e0 + j));
                 sc->ls_done = 1;
                 return;
@@ -902,7 +920,7 @@ __global__ void __launch_bounds__(kThreads) k_gpad(DualView<T> dv, const T *__re
     T sums[2] = {fsum, (T)nan};
     T maxs[1] = {rmax};
     if (reduce_last<T, 2, 1>(sums, maxs, partials, &sc->red_counter, tot) && threadIdx.x == 0) {
-        sc->phi = -tot[0];
+        sc->phi = -(tot[0] + sc->f_pt);  // f(x) from the primal with general maps (else 0)
         sc->res_inf = tot[2];
         if (tot[1] > 0.0 || !(tot[0] == tot[0])) sc->nan_flag = 1;
         // stop: converged at w, NaN, or the iteration cap (the host returns w of this step)
@@ -947,30 +965,92 @@ __global__ void k_scale_in(DualView<T> dv, const T *y, T *yb) {
 }
 
 template <class T>
-__global__ void k_finish_out(DualView<T> dv, const T *yb, const T *h, const SolverScalars *sc, T *y, T *z, T *x,
-                             T *u) {
+__global__ void k_finish_out(DualView<T> dv, const T *yb, const T *h, const SolverScalars *sc, T *y, T *z) {
     const T lam = (T)sc->lambda, ilam = T(1) / lam;
     for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < dv.m; e += gridDim.x * blockDim.x) {
         const auto M = dv.meta(e);
         const T ye = yb[e], he = h[e];
         y[e] = M.sq * ye;
         if (z) z[e] = prox_el<T, true>(he + ye * ilam, lam, M) / M.sq;
-        if (x) {
-            int node, k;
-            if (e < dv.leaf_base) {
-                node = e / dv.nxu;
-                k = e - node * dv.nxu;
-                if (k < dv.nx)
-                    x[(size_t)node * dv.nx + k] = he / M.sq;
-                else
-                    u[(size_t)node * dv.nu + (k - dv.nx)] = he / M.sq;
-            } else {
-                const int e2 = e - dv.leaf_base;
-                node = dv.Np + e2 / dv.nx;
-                k = e2 - (node - dv.Np) * dv.nx;
-                x[(size_t)node * dv.nx + k] = he / M.sq;
-            }
+    }
+}
+
+// x [Nn][nx], u [Np][nu] from a primal vector in the [x; u] layout scaled by sqrt(pi) per node (sv:
+// the selection layout's view): Hx itself for the selection maps, the primal output of the
+// solve round for general maps.
+template <class T>
+__global__ void k_primal_out(DualView<T> sv, const T *p, T *x, T *u) {
+    for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < sv.m; e += gridDim.x * blockDim.x) {
+        int node, k;
+        if (e < sv.leaf_base) {
+            node = e / sv.nb;
+            k = e - node * sv.nb;
+            const T v = p[e] / sv.sqp[node];
+            if (k < sv.nx)
+                x[(size_t)node * sv.nx + k] = v;
+            else
+                u[(size_t)node * sv.nu + (k - sv.nx)] = v;
+        } else {
+            const int e2 = e - sv.leaf_base;
+            node = sv.Np + e2 / sv.nbl;
+            k = e2 - (node - sv.Np) * sv.nbl;
+            x[(size_t)node * sv.nx + k] = p[e] / sv.sqp[node];
         }
+    }
+}
+
+// The cost f(x) of Section II-B for general maps, from the primal vectors of the solve rounds in
+// the [x; u] layout scaled by sqrt(pi) (p = sqrt(pi) [x; u], so pi x'Qx = p'Qp, pi q'x =
+// sqrt(pi) q'p), summed in FP64 over blocks:
+//   k_fcost: f(p0) -> sc->f_pt (the FBE at a point adds it to the dual terms);
+//   k_fquad: for the line search's affine primal p(tau) = pa + tau pb with pa = p0 - lam pr,
+//   pb = pd + lam pr (NAMA) or pa = p0, pb = pd (MINFBE): f(pa) - f(p0), the linear and the
+//   quadratic coefficient of f(p(tau)) in tau -> sc->f_ls[0..2].
+template <class T>
+__global__ void __launch_bounds__(kThreads) k_fcost(DualView<T> sv, const T *__restrict__ p0, SolverScalars *sc,
+                                                    double *partials) {
+    extern __shared__ __align__(16) unsigned char tab_raw[];
+    CompTab<T> tab;
+    tab.load(sv, reinterpret_cast<T *>(tab_raw));
+    T acc = T(0);
+    for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < sv.m; e += gridDim.x * blockDim.x) {
+        const Pos ps = pos_of(sv, e);
+        const auto M = tab.meta(ps, sv.sqp[ps.node]);
+        const T v = p0[e];
+        acc += v * (M.w * v + M.l);
+    }
+    T sums[1] = {acc};
+    T maxs[1];
+    __shared__ double tot[1];
+    if (reduce_last<T, 1, 0>(sums, maxs, partials, &sc->red_counter, tot) && threadIdx.x == 0) sc->f_pt = tot[0];
+}
+
+template <class T>
+__global__ void __launch_bounds__(kThreads) k_fquad(DualView<T> sv, const T *__restrict__ p0, const T *__restrict__ pr,
+                                                    const T *__restrict__ pd, int nama, SolverScalars *sc,
+                                                    double *partials) {
+    extern __shared__ __align__(16) unsigned char tab_raw[];
+    CompTab<T> tab;
+    tab.load(sv, reinterpret_cast<T *>(tab_raw));
+    const T lam = (T)sc->lambda;
+    T s0 = T(0), s1 = T(0), s2 = T(0);
+    for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < sv.m; e += gridDim.x * blockDim.x) {
+        const Pos ps = pos_of(sv, e);
+        const auto M = tab.meta(ps, sv.sqp[ps.node]);
+        const T v0 = p0[e];
+        const T pa = nama ? v0 - lam * pr[e] : v0;
+        const T pb = nama ? pd[e] + lam * pr[e] : pd[e];
+        s0 += (pa - v0) * (M.w * (pa + v0) + M.l);
+        s1 += pb * (T(2) * M.w * pa + M.l);
+        s2 += M.w * pb * pb;
+    }
+    T sums[3] = {s0, s1, s2};
+    T maxs[1];
+    __shared__ double tot[3];
+    if (reduce_last<T, 3, 0>(sums, maxs, partials, &sc->red_counter, tot) && threadIdx.x == 0) {
+        sc->f_ls[0] = tot[0];
+        sc->f_ls[1] = tot[1];
+        sc->f_ls[2] = tot[2];
     }
 }
 
@@ -1022,20 +1102,47 @@ int red_grid(int64_t m) {
     return (int)(b < kRedBlocks ? (b > 0 ? b : 1) : kRedBlocks);
 }
 
+// The selection layout ([x; u] per nonleaf node, x per leaf) with the box and cost of the x and u
+// components: the dual of the selection maps, and the primal of every problem.
 template <class T>
-DualView<T> make_view(stotree_t h) {
+DualView<T> make_sel_view(stotree_t h) {
     DualView<T> dv;
-    dv.m = (int)h->m;
     dv.Np = h->Np;
     dv.nx = h->nx;
     dv.nu = h->nu;
-    dv.nxu = h->nx + h->nu;
-    dv.leaf_base = h->Np * (h->nx + h->nu);
-    dv.inv_nxu = 1.0f / (float)dv.nxu;
-    dv.inv_nx = 1.0f / (float)dv.nx;
+    dv.nb = h->nx + h->nu;
+    dv.nbl = h->nx;
+    dv.m = (int)((int64_t)h->Np * dv.nb + (int64_t)h->Nl * dv.nbl);
+    dv.leaf_base = h->Np * dv.nb;
+    dv.inv_nb = 1.0f / (float)dv.nb;
+    dv.inv_nbl = 1.0f / (float)dv.nbl;
+    dv.tab_n = dv.nb;
+    dv.leaf_off = 0;
+    dv.root_free = 1;
+    dv.has_cost = 1;
     dv.sqp = h->at<T>(h->L.sqp);
     dv.box = h->at<T>(h->L.box);
     dv.Wc = h->at<T>(h->L.cost);
+    return dv;
+}
+
+// The dual layout: the selection layout, or the z blocks of general maps (nc per nonleaf node, ncN
+// per leaf) with their box and no cost weights (f(x) then comes from the primal).
+template <class T>
+DualView<T> make_view(stotree_t h) {
+    DualView<T> dv = make_sel_view<T>(h);
+    if (!h->fg) return dv;
+    dv.m = (int)h->m;
+    dv.nb = h->nc;
+    dv.nbl = h->ncN;
+    dv.leaf_base = h->Np * h->nc;
+    dv.inv_nb = 1.0f / (float)dv.nb;
+    dv.inv_nbl = 1.0f / (float)dv.nbl;
+    dv.tab_n = h->nc + h->ncN;
+    dv.leaf_off = h->nc;
+    dv.root_free = 0;
+    dv.has_cost = 0;
+    dv.box = h->at<T>(h->L.zbox);
     return dv;
 }
 
@@ -1060,6 +1167,16 @@ sto_status solver_impl(stotree_t h, int method, const sto_opts *o, const void *x
     const int grid = red_grid(m);
     const bool nama = method == 0;
     const size_t tabb = comp_tab_bytes(dv);
+    // general maps: the primal vectors ([x; u] layout) of x(ybar), x_lin(r), x_lin(d), and a copy of
+    // the first (the original backtracking rule restores it); f(x) is evaluated from them
+    const bool fg = h->fg;
+    const DualView<T> sv = make_sel_view<T>(h);
+    const int sgrid = red_grid(sv.m);
+    const size_t stabb = comp_tab_bytes(sv);
+    const long long ps = (long long)((h->msel + 63) / 64 * 64);
+    T *P = fg ? h->at<T>(h->L.pvec) : nullptr;
+    T *pvh = fg ? P : nullptr, *pvr = fg ? P + ps : nullptr, *pvd = fg ? P + 2 * ps : nullptr;
+    T *psave = fg ? P + 3 * ps : nullptr;
 
     cudaEvent_t e0, e1;
     STO_CUDA(h, cudaEventCreate(&e0));
@@ -1098,21 +1215,28 @@ sto_status solver_impl(stotree_t h, int method, const sto_opts *o, const void *x
     auto full_solve = [&]() -> sto_status {
         const void *ys[1] = {yb};
         void *hs_[1] = {hv};
-        return solve_round(h, ys, x0v, hs_, 1, false, true, st);
+        void *po[1] = {pvh};
+        return solve_round(h, ys, x0v, hs_, 1, false, true, st, nullptr, fg ? po : nullptr);
     };
-    auto lin_solve = [&](T *in, T *out) -> sto_status {
+    auto lin_solve = [&](T *in, T *out, T *pout) -> sto_status {
         const void *ys[1] = {in};
         void *hs_[1] = {out};
-        return solve_round(h, ys, nullptr, hs_, 1, true, true, st);
+        void *po[1] = {pout};
+        return solve_round(h, ys, nullptr, hs_, 1, true, true, st, nullptr, fg ? po : nullptr);
     };
 
     k_scale_in<T><<<grid, kThreads, 0, st>>>(dv, static_cast<const T *>(yv), yb);
     h->launches += 1;
     sto_status s = full_solve();
     if (s != STO_OK) return s;
-    // k_point with the backtracking reductions the rule needs
+    // k_point with the backtracking reductions the rule needs (with general maps, f(x) at the
+    // point from its primal first)
     const bool gen = h->general;  // some element's term is not the box indicator
     auto point = [&](int pair, const T *rwp, const T *hwp) {
+        if (fg) {
+            k_fcost<T><<<sgrid, kThreads, stabb, st>>>(sv, pvh, sc, part);
+            h->launches += 1;
+        }
 #define STO_POINT(BT, G) \
     k_point<T, BT, G><<<grid, kThreads, tabb, st>>>(dv, yb, hv, r, ringS, ringY, vs, pair, sc, part, rwp, hwp)
         if (bt == 1) {
@@ -1127,7 +1251,7 @@ sto_status solver_impl(stotree_t h, int method, const sto_opts *o, const void *x
     point(0, hv, hv);  // (with BT = 1 the w terms of this call are not used)
     h->launches += 1;
     if (!nama) {
-        if ((s = lin_solve(r, hr)) != STO_OK) return s;
+        if ((s = lin_solve(r, hr, pvr)) != STO_OK) return s;
         k_grad<T><<<grid, kThreads, 0, st>>>(m, r, hr, g, ringS, ringY, vs, sc, part);
         h->launches += 1;
     }
@@ -1143,7 +1267,7 @@ sto_status solver_impl(stotree_t h, int method, const sto_opts *o, const void *x
         point(0, hv, hv);
         h->launches += 2;
         if (!nama) {
-            const sto_status e = lin_solve(r, hr);
+            const sto_status e = lin_solve(r, hr, pvr);
             if (e != STO_OK) return e;
             k_grad<T><<<grid, kThreads, 0, st>>>(m, r, hr, g, ringS, ringY, vs, sc, part);
             h->launches += 1;
@@ -1182,7 +1306,9 @@ sto_status solver_impl(stotree_t h, int method, const sto_opts *o, const void *x
         if (nama) {
             const void *ys[2] = {r, d};
             void *outs[2] = {hr, hd};
-            if ((s = solve_round(h, ys, nullptr, outs, 2, true, true, st)) != STO_OK) return s;
+            void *po[2] = {pvr, pvd};
+            if ((s = solve_round(h, ys, nullptr, outs, 2, true, true, st, nullptr, fg ? po : nullptr)) != STO_OK)
+                return s;
             if (bt == 2) {  // NAMA: the test needs x_lin(r) of this round
                 k_norm2<T><<<grid, kThreads, 0, st>>>(m, hr, sc, part);
                 h->launches += 1;
@@ -1193,7 +1319,11 @@ sto_status solver_impl(stotree_t h, int method, const sto_opts *o, const void *x
                 }
             }
         } else {
-            if ((s = lin_solve(d, hd)) != STO_OK) return s;
+            if ((s = lin_solve(d, hd, pvd)) != STO_OK) return s;
+        }
+        if (fg) {  // f along the line search's affine primal
+            k_fquad<T><<<sgrid, kThreads, stabb, st>>>(sv, pvh, pvr, pvd, nama ? 1 : 0, sc, part);
+            h->launches += 1;
         }
         for (int k = 0; k < ng; ++k) {
             const int last = k == ng - 1;
@@ -1211,6 +1341,7 @@ sto_status solver_impl(stotree_t h, int method, const sto_opts *o, const void *x
         if (bt == 1) {
             STO_CUDA(h, cudaMemcpyAsync(ysave, yb, (size_t)m * sizeof(T), cudaMemcpyDeviceToDevice, st));
             STO_CUDA(h, cudaMemcpyAsync(hsave, hv, (size_t)m * sizeof(T), cudaMemcpyDeviceToDevice, st));
+            if (fg) STO_CUDA(h, cudaMemcpyAsync(psave, pvh, (size_t)sv.m * sizeof(T), cudaMemcpyDeviceToDevice, st));
         }
         if (gen)
             k_fbstep<T, true><<<grid, kThreads, tabb, st>>>(dv, yb, hv, r, d, hr, hd, nama, ringS, vs, sc, rw_arg, hw_arg);
@@ -1225,12 +1356,14 @@ sto_status solver_impl(stotree_t h, int method, const sto_opts *o, const void *x
             if (hs->nan_flag == 0 && hs->bt_a > (1.0 - o->bt_param) * hs->bt_b) {
                 STO_CUDA(h, cudaMemcpyAsync(yb, ysave, (size_t)m * sizeof(T), cudaMemcpyDeviceToDevice, st));
                 STO_CUDA(h, cudaMemcpyAsync(hv, hsave, (size_t)m * sizeof(T), cudaMemcpyDeviceToDevice, st));
+                if (fg)
+                    STO_CUDA(h, cudaMemcpyAsync(pvh, psave, (size_t)sv.m * sizeof(T), cudaMemcpyDeviceToDevice, st));
                 if ((s = halve()) != STO_OK) return s;
                 continue;
             }
         }
         if (!nama) {
-            if ((s = lin_solve(r, hr)) != STO_OK) return s;
+            if ((s = lin_solve(r, hr, pvr)) != STO_OK) return s;
             k_grad<T><<<grid, kThreads, 0, st>>>(m, r, hr, g, ringS, ringY, vs, sc, part);
             h->launches += 1;
         }
@@ -1238,9 +1371,10 @@ sto_status solver_impl(stotree_t h, int method, const sto_opts *o, const void *x
         STO_CUDA(h, cudaGetLastError());
     }
     h->launches += 1;
-    k_finish_out<T><<<grid, kThreads, 0, st>>>(dv, yb, hv, sc, static_cast<T *>(yv), static_cast<T *>(zv),
-                                               static_cast<T *>(xv), static_cast<T *>(uv));
+    k_finish_out<T><<<grid, kThreads, 0, st>>>(dv, yb, hv, sc, static_cast<T *>(yv), static_cast<T *>(zv));
     if (xv) {
+        k_primal_out<T><<<sgrid, kThreads, 0, st>>>(sv, fg ? pvh : hv, static_cast<T *>(xv), static_cast<T *>(uv));
+        h->launches += 1;
         // the root state is the parameter p
         STO_CUDA(h, cudaMemcpyAsync(xv, x0v, h->nx * sizeof(T), cudaMemcpyDeviceToDevice, st));
     }
@@ -1310,6 +1444,12 @@ sto_status gpad_impl(stotree_t h, const sto_opts *o, const void *x0v, void *yv, 
     // buffers; once a step stops the run (device flag), the look-ahead step leaves the
     // buffers of the stopped step alone.
     T *wb[2] = {w, wn}, *hb[2] = {hv, V + 11 * vs};
+    // general maps: the primal of each buffer's solve, for f(x) and the returned x, u
+    const bool fg = h->fg;
+    const DualView<T> sv = make_sel_view<T>(h);
+    const int sgrid = red_grid(sv.m);
+    const long long ps = (long long)((h->msel + 63) / 64 * 64);
+    T *pb[2] = {fg ? h->at<T>(h->L.pvec) : nullptr, fg ? h->at<T>(h->L.pvec) + ps : nullptr};
     SolverScalars *hbuf[2] = {hs, h->host_scal2};
     cudaEvent_t ev[2];
     STO_CUDA(h, cudaEventCreateWithFlags(&ev[0], cudaEventDisableTiming));
@@ -1321,8 +1461,13 @@ sto_status gpad_impl(stotree_t h, const sto_opts *o, const void *x0v, void *yv, 
         theta = theta_next;
         const void *ys[1] = {wb[k & 1]};
         void *hs_[1] = {hb[k & 1]};
-        const sto_status s = solve_round(h, ys, x0v, hs_, 1, false, true, st);
+        void *po[1] = {pb[k & 1]};
+        const sto_status s = solve_round(h, ys, x0v, hs_, 1, false, true, st, nullptr, fg ? po : nullptr);
         if (s != STO_OK) return s;
+        if (fg) {
+            k_fcost<T><<<sgrid, kThreads, comp_tab_bytes(sv), st>>>(sv, pb[k & 1], sc, part);
+            h->launches += 1;
+        }
         if (h->general)
             k_gpad<T, true><<<grid, kThreads, tabb, st>>>(dv, wb[k & 1], hb[k & 1], yb, wb[(k + 1) & 1], beta, k,
                                                           o->max_iter, sc, part);
@@ -1361,9 +1506,13 @@ sto_status gpad_impl(stotree_t h, const sto_opts *o, const void *x0v, void *yv, 
     w = wb[iters & 1];
     hv = hb[iters & 1];
     h->launches += 1;
-    k_finish_out<T><<<grid, kThreads, 0, st>>>(dv, w, hv, sc, static_cast<T *>(yv), static_cast<T *>(zv),
-                                               static_cast<T *>(xv), static_cast<T *>(uv));
-    if (xv) STO_CUDA(h, cudaMemcpyAsync(xv, x0v, h->nx * sizeof(T), cudaMemcpyDeviceToDevice, st));
+    k_finish_out<T><<<grid, kThreads, 0, st>>>(dv, w, hv, sc, static_cast<T *>(yv), static_cast<T *>(zv));
+    if (xv) {
+        k_primal_out<T><<<sgrid, kThreads, 0, st>>>(sv, fg ? pb[iters & 1] : hv, static_cast<T *>(xv),
+                                                   static_cast<T *>(uv));
+        h->launches += 1;
+        STO_CUDA(h, cudaMemcpyAsync(xv, x0v, h->nx * sizeof(T), cudaMemcpyDeviceToDevice, st));
+    }
     STO_CUDA(h, cudaEventRecord(e1, st));
     STO_CUDA(h, cudaMemcpyAsync(hs, sc, sizeof(SolverScalars), cudaMemcpyDeviceToHost, st));
     STO_CUDA(h, cudaStreamSynchronize(st));
@@ -1436,10 +1585,10 @@ __device__ void atomic_max_nonneg(double *addr, double v) {
     atomicMax(reinterpret_cast<unsigned long long *>(addr), (unsigned long long)__double_as_longlong(v));
 }
 
-template <class T>
+template <class T, class TY>
 __global__ void k_kkt_stage(int first, int nx, int nu, int Np, int ld64, const int *cbeg, const int *ccnt,
                             const double *prob, const double *G64, const double *cost64, const T *x, const T *u,
-                            const T *y, double *mu, double *out) {
+                            const TY *y, double *mu, double *out) {
     const int i = first + blockIdx.x;
     const int nxu = nx + nu;
     const long long oi = i < Np ? (long long)i * nxu : (long long)Np * nxu + (long long)(i - Np) * nx;
@@ -1471,7 +1620,7 @@ __global__ void k_kkt_stage(int first, int nx, int nu, int Np, int ld64, const i
 template <class T>
 __global__ void k_kkt_elem(int Nn, int nx, int nu, int Np, int ld64, const int *parent, const double *G64,
                            const double *box64, const T *x0, const T *x, const T *u, const T *y, double tol_act,
-                           double *out) {
+                           double *out, int box_terms) {
     const int nxu = nx + nu;
     // dynamics residual per node and state component
     for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < (long long)(Nn - 1) * nx;
@@ -1484,6 +1633,7 @@ __global__ void k_kkt_elem(int Nn, int nx, int nu, int Np, int ld64, const int *
         for (int k = 0; k < nu; ++k) acc += row[nx + k] * (double)u[(size_t)i * nu + k];
         atomic_max_nonneg(out + 0, fabs((double)x[(size_t)j * nx + rr] - acc));
     }
+    if (!box_terms) return;  // general maps: k_kkt_fg_box checks z
     // box feasibility, complementarity and multiplier signs per dual entry
     const long long m = (long long)Np * nxu + (long long)(Nn - Np) * nx;
     for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < m; e += (long long)gridDim.x * blockDim.x) {
@@ -1547,24 +1697,75 @@ __global__ void k_kkt_elem(int Nn, int nx, int nu, int Np, int ld64, const int *
     }
 }
 
+// General maps: feasibility, complementarity and multiplier signs of the box on z = F x + G u
+// (FN x at the leaves; the root's x is x0), z formed in FP64 from x and u.
+template <class T>
+__global__ void k_kkt_fg_box(int Nn, int nx, int nu, int Np, int nc, int ncN, const double *FG64, const double *zbox64,
+                             const T *x0, const T *x, const T *u, const T *y, double tol_act, double *out) {
+    const double *F = FG64, *G = FG64 + (size_t)nc * nx, *FN = G + (size_t)nc * nu;
+    const int nb = nc + ncN;
+    const long long m = (long long)Np * nc + (long long)(Nn - Np) * ncN;
+    for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < m; e += (long long)gridDim.x * blockDim.x) {
+        double z = 0.0;
+        int bi;
+        if (e < (long long)Np * nc) {
+            const int i = (int)(e / nc), c = (int)(e - (long long)i * nc);
+            const T *xi = i == 0 ? x0 : x + (size_t)i * nx;
+            for (int k = 0; k < nx; ++k) z += F[(size_t)c * nx + k] * (double)xi[k];
+            for (int a = 0; a < nu; ++a) z += G[(size_t)c * nu + a] * (double)u[(size_t)i * nu + a];
+            bi = c;
+        } else {
+            const long long e2 = e - (long long)Np * nc;
+            const int l = Np + (int)(e2 / ncN), c = (int)(e2 - (long long)(l - Np) * ncN);
+            for (int k = 0; k < nx; ++k) z += FN[(size_t)c * nx + k] * (double)x[(size_t)l * nx + k];
+            bi = nc + c;
+        }
+        const double lo = zbox64[bi], hi = zbox64[nb + bi], ye = (double)y[e];
+        atomic_max_nonneg(out + 2, fmax(0.0, fmax(lo - z, z - hi)));
+        const bool at_hi = z >= hi - tol_act, at_lo = z <= lo + tol_act;
+        if (!at_hi && !at_lo) atomic_max_nonneg(out + 3, fabs(ye));
+        double sgn = 0.0;
+        if (at_hi && !at_lo) sgn = fmax(0.0, -ye);
+        if (at_lo && !at_hi) sgn = fmax(0.0, ye);
+        atomic_max_nonneg(out + 4, sgn);
+    }
+}
+
 template <class T>
 sto_status kkt_impl(stotree_t h, const void *x0, const void *x, const void *u, const void *y, double tol_act,
                     double *out, cudaStream_t st) {
     const Layout &L = h->L;
     double *mu = h->at<double>(L.kkt);
     double *dout = mu + (size_t)h->Nn * h->nx + (size_t)h->Np * h->nu;
+    double *hty = dout + 64;  // general maps: H'y in FP64, laid out like [x; u]
     STO_CUDA(h, cudaMemsetAsync(dout, 0, 8 * sizeof(double), st));
+    if (h->fg) {
+        const sto_status s = fg_ht(h, y, hty, true, st);
+        if (s != STO_OK) return s;
+    }
     for (int t = h->N; t >= 0; --t) {
         const int first = h->soff[t], count = h->soff[t + 1] - first;
-        k_kkt_stage<T><<<count, 128, 0, st>>>(first, h->nx, h->nu, h->Np, h->ld64, h->at<int>(L.cbeg),
-                                              h->at<int>(L.ccnt), h->at<double>(L.prob64), h->at<double>(L.G64),
-                                              h->at<double>(L.cost64), static_cast<const T *>(x),
-                                              static_cast<const T *>(u), static_cast<const T *>(y), mu, dout);
+        if (h->fg)
+            k_kkt_stage<T, double><<<count, 128, 0, st>>>(first, h->nx, h->nu, h->Np, h->ld64, h->at<int>(L.cbeg),
+                                                          h->at<int>(L.ccnt), h->at<double>(L.prob64),
+                                                          h->at<double>(L.G64), h->at<double>(L.cost64),
+                                                          static_cast<const T *>(x), static_cast<const T *>(u), hty,
+                                                          mu, dout);
+        else
+            k_kkt_stage<T, T><<<count, 128, 0, st>>>(first, h->nx, h->nu, h->Np, h->ld64, h->at<int>(L.cbeg),
+                                                     h->at<int>(L.ccnt), h->at<double>(L.prob64), h->at<double>(L.G64),
+                                                     h->at<double>(L.cost64), static_cast<const T *>(x),
+                                                     static_cast<const T *>(u), static_cast<const T *>(y), mu, dout);
     }
     k_kkt_elem<T><<<592, 256, 0, st>>>(h->Nn, h->nx, h->nu, h->Np, h->ld64, h->at<int>(L.parent),
                                        h->at<double>(L.G64), h->at<double>(L.box64), static_cast<const T *>(x0),
                                        static_cast<const T *>(x), static_cast<const T *>(u),
-                                       static_cast<const T *>(y), tol_act, dout);
+                                       static_cast<const T *>(y), tol_act, dout, h->fg ? 0 : 1);
+    if (h->fg)
+        k_kkt_fg_box<T><<<592, 256, 0, st>>>(h->Nn, h->nx, h->nu, h->Np, h->nc, h->ncN, h->at<double>(L.FG64),
+                                             h->at<double>(L.zbox64), static_cast<const T *>(x0),
+                                             static_cast<const T *>(x), static_cast<const T *>(u),
+                                             static_cast<const T *>(y), tol_act, dout);
     STO_CUDA(h, cudaMemcpyAsync(out, dout, 5 * sizeof(double), cudaMemcpyDeviceToHost, st));
     STO_CUDA(h, cudaStreamSynchronize(st));
     STO_CUDA(h, cudaGetLastError());

@@ -74,6 +74,8 @@ def lib():
             "stotree_solve_step_noalloc": [vp, vp, vp, vp, i32, i32, vp],
             "stotree_last_primal": [vp, vp, vp, vp],
             "stotree_set_wait_limit": [vp, dbl],
+            "stotree_set_constraint_maps": [vp, i32, i32, vp, vp, vp],
+            "stotree_set_zbox": [vp, vp, vp, vp, vp, vp],
             "stotree_round_status": [vp, vp],
             "stotree_estimate_lambda": [vp, vp, i32, dbl, vp, vp, vp],
             "stotree_nama_solve": [vp, vp, vp, vp, vp, vp, vp, vp, vp],
@@ -144,7 +146,8 @@ def lib():
 
 
 def exported_symbols():
-    return [n for n in ("stotree_create", "stotree_destroy", "stotree_sizes", "stotree_workspace_size",
+    return [n for n in ("stotree_create", "stotree_destroy", "stotree_set_constraint_maps", "stotree_set_zbox",
+                        "stotree_sizes", "stotree_workspace_size",
                         "stotree_bind_workspace", "stotree_set_dynamics", "stotree_set_costs", "stotree_set_box", "stotree_set_penalty",
                         "stotree_factor", "stotree_solve_step", "stotree_solve_step_noalloc", "stotree_set_wait_limit",
                         "stotree_round_status", "stotree_last_primal", "stotree_estimate_lambda",
@@ -189,6 +192,11 @@ class StoTree:
         h = ctypes.c_void_p()
         self._check(L.stotree_create(ctypes.byref(desc), self.prec, ctypes.byref(h)), "stotree_create", handle=False)
         self.h = h
+        self.general = bool(getattr(problem, "general", False))
+        if self.general:  # general constraint maps: before the sizes and the workspace
+            self._maps = [np.ascontiguousarray(a, dtype=np.float64) for a in (problem.F, problem.G, problem.FN)]
+            self._check(L.stotree_set_constraint_maps(h, problem.F.shape[0], problem.FN.shape[0],
+                                                      *[_np_ptr(a) for a in self._maps]), "set_constraint_maps")
         m, n = ctypes.c_int64(), ctypes.c_int64()
         npl, nl = ctypes.c_int32(), ctypes.c_int32()
         L.stotree_sizes(h, ctypes.byref(m), ctypes.byref(n), ctypes.byref(npl), ctypes.byref(nl))
@@ -209,7 +217,10 @@ class StoTree:
                 cc = np.ascontiguousarray(problem.c[f:f + c], dtype=np.float64)
                 self._check(L.stotree_set_dynamics(h, f, c, _np_ptr(A), _np_ptr(B), _np_ptr(cc), st), "set_dynamics")
             self.set_costs(problem.Q, problem.R, problem.PN, problem.q, problem.r, problem.pN)
-            self.set_box(problem.xlo, problem.xhi, problem.ulo, problem.uhi)
+            if self.general:
+                self.set_zbox(problem.zlo, problem.zhi, problem.zNlo, problem.zNhi)
+            else:
+                self.set_box(problem.xlo, problem.xhi, problem.ulo, problem.uhi)
             if getattr(problem, "pen_kind", None) is not None:
                 self.set_penalty(problem.pen_kind, problem.pen_rho, problem.pen_delta)
 
@@ -253,6 +264,11 @@ class StoTree:
         d = np.ascontiguousarray(np.broadcast_to(np.asarray(delta, dtype=np.float64), (n,)))
         self._check(lib().stotree_set_penalty(self.h, k.ctypes.data_as(ctypes.c_void_p), _np_ptr(r), _np_ptr(d),
                                               _stream()), "set_penalty")
+
+    def set_zbox(self, zlo, zhi, zNlo, zNhi):
+        """stotree_set_zbox: the box on z of the general constraint maps."""
+        arr = [np.ascontiguousarray(v, dtype=np.float64) for v in (zlo, zhi, zNlo, zNhi)]
+        self._check(lib().stotree_set_zbox(self.h, *[_np_ptr(a) for a in arr], _stream()), "set_zbox")
 
     def set_box(self, xlo, xhi, ulo, uhi):
         arr = [np.ascontiguousarray(v, dtype=np.float64) for v in (xlo, xhi, ulo, uhi)]

@@ -192,3 +192,59 @@ def test_soft_terms_by_hand():
     assert abs(res(-1.2, 0.0, 1)["complementarity"] - 0.6) <= 1e-12
     # beyond delta the derivative saturates at rho delta = 1.5
     assert abs(res(2.0, 1.0, 1)["complementarity"] - 0.5) <= 1e-12
+
+
+FG_PROBS = [dict(seed=81, horizon=3, nx=3, nu=2, nc=4, ncN=2), dict(seed=85, horizon=4, nx=4, nu=2, nc=3, ncN=4)]
+
+
+@pytest.mark.parametrize("kw", FG_PROBS, ids=lambda k: f"fg{k['seed']}")
+def test_general_maps_zero_at_the_certified_solution_and_planted_violations(kw):
+    """With general constraint maps: all five vanish at the certified QP solution; a multiplier of
+    a z component strictly inside its box and a z component pushed past its bound are reported
+    by their amounts; the stationarity residual is the reduced gradient (central differences)."""
+    from oracle import oracle as O
+    kw = dict(kw)
+    seed = kw.pop("seed")
+    p = D.constrained_boxed_problem(seed, **kw)
+    o = O.LQOracle(p)
+    lam, _ = O.power_lambda(o, np.random.default_rng(0).standard_normal(o.m))
+    res = O.nama(o, lam, tol=1e-11, max_iter=5000)
+    x, u, y, ok = D.active_set_qp(p, res["y"], thresh=1e-7)
+    assert ok and np.count_nonzero(np.abs(y) > 1e-7) > 0
+    r = KC.kkt_residuals(p, p.x0, x, u, y, tol_active=1e-8)
+    scale = max(1.0, np.max(np.abs(y)), np.max(np.abs(x)))
+    for k, v in r.items():
+        assert v <= 1e-10 * scale, (k, v)
+    h = o.stack(x, u)
+    lo, hi = D.box_vectors(p)
+    inside = np.nonzero((h < hi - 1e-3) & (h > lo + 1e-3))[0]
+    y2 = y.copy()
+    y2[int(inside[0])] = 0.04
+    assert abs(KC.kkt_residuals(p, p.x0, x, u, y2, tol_active=1e-8)["complementarity"] - 0.04) <= 1e-14
+    act = np.nonzero(np.abs(y) > 1e-6)[0]
+    y3 = y.copy()
+    y3[int(act[0])] = -y[int(act[0])]
+    assert abs(KC.kkt_residuals(p, p.x0, x, u, y3, tol_active=1e-8)["sign"] - abs(y[int(act[0])])) <= 1e-12 * scale
+    # stationarity at a rolled-out trajectory equals the reduced gradient of f + <y, Hx>
+    rng = np.random.default_rng(seed)
+    npl = p.tree.num_nonleaf
+    uu = rng.standard_normal((npl, p.nu))
+    yy = W.random_dual(p, seed + 1)
+    xx = _rollout(p, uu)
+
+    def lag(u_):
+        xr = _rollout(p, u_)
+        pr = p.tree.prob
+        f = sum(pr[i] * (xr[i] @ (p.Q * xr[i]) + u_[i] @ (p.R * u_[i]) + p.q @ xr[i] + p.r @ u_[i]) for i in range(npl))
+        f += sum(pr[l] * (xr[l] @ (p.PN * xr[l]) + p.pN @ xr[l]) for l in range(npl, p.tree.num_nodes))
+        return f + yy @ o.stack(xr, u_)
+
+    grad = np.zeros_like(uu)
+    for i in range(npl):
+        for a in range(p.nu):
+            up, dn = uu.copy(), uu.copy()
+            up[i, a] += 1e-3
+            dn[i, a] -= 1e-3
+            grad[i, a] = (lag(up) - lag(dn)) / 2e-3
+    g = float(np.max(np.abs(grad)))
+    assert abs(KC.kkt_residuals(p, p.x0, xx, uu, yy, tol_active=1e-8)["stationarity"] - g) <= 1e-8 * g

@@ -225,6 +225,13 @@ KKT_MUTANTS = [
      "rho[k] if hk >= hi[k] - tol_active else 0.0", "0.0"),
     ("kkt_huber_unsaturated", "Huber derivative rho d without the cap at delta",
      "gd = rho[k] * min(d, delta[k])", "gd = rho[k] * d"),
+    ("kkt_fg_no_G_in_u_equation", "general maps: the u equations without G'y",
+     "= p.G.T @ yi", "= 0.0 * (p.G.T @ yi)"),
+    ("kkt_fg_leaf_dual_dropped", "general maps: the leaves' FN'y left out of the costates",
+     "= p.FN.T @ y[o:o + ncn]", "= 0.0 * (p.FN.T @ y[o:o + ncn])"),
+    ("kkt_fg_sign_at_upper_bound", "general maps: multiplier of z at its upper bound required to be <= 0",
+     "elif at_hi and not at_lo:\n                sign = max(sign, -yk)",
+     "elif at_hi and not at_lo:\n                sign = max(sign, yk)"),
 ]
 
 INPUT_MUTANTS = [
