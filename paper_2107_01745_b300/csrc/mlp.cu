@@ -601,15 +601,27 @@ __device__ __forceinline__ void write_bf16_copies(const NetDev &n, long long p, 
 }
 
 // mode 0: gradient out (unpadded order, grad may be null), loss out; mode 1: Adam step.
-__global__ void k_adam(NetDev n, int mode, float lr, float *grad, float *loss, float *loss_hist, int t0) {
+__global__ void __launch_bounds__(256) k_adam(NetDev n, int mode, float lr, float *grad, float *loss,
+                                              float *loss_hist, int t0) {
     const long long p = (long long)blockIdx.x * blockDim.x + threadIdx.x;
     const int t = *n.tstep;
-    if (p == 0 && (loss || loss_hist)) {
+    if (blockIdx.x == 0 && (loss || loss_hist)) {
+        // the loss partials (one per warp of the output-layer product) summed by the first block
+        // in a fixed order: strided per thread, a shuffle tree per warp, the warps in order
+        __shared__ float red[8];
         float s = 0.f;
-        for (int k = 0; k < (n.B / kBM) * 8; ++k) s += n.loss_part[k];
-        const float l = s / (float)max(1, *n.count);
-        if (loss) *loss = l;
-        if (loss_hist) loss_hist[t - t0] = l;
+        for (int k = threadIdx.x; k < (n.B / kBM) * 8; k += 256) s += n.loss_part[k];
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+        if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = s;
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            float tot = 0.f;
+            for (int w = 0; w < 8; ++w) tot += red[w];
+            const float l = tot / (float)max(1, *n.count);
+            if (loss) *loss = l;
+            if (loss_hist) loss_hist[t - t0] = l;
+        }
     }
     if (p >= nparam_padded(n)) return;
     const float g = param_grad(n, p);
