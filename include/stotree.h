@@ -303,7 +303,13 @@ STO_API sto_status stotree_gpad_solve(stotree_t h, const sto_opts *opts, const v
  *            g_k at Hx where g_k is differentiable there
  *   out[4] = max of -y_k at upper bounds / +y_k at lower bounds (sign of the multipliers);
  *            for soft terms the distance of y_k to the subdifferential at a kink
- * Synchronises.  out is host double[5]. */
+ *   out[5] = sum over the components of g_k(h_k) + g_k*(y_k) - y_k h_k, h = Hx (the
+ *            Fenchel-Young gap: >= 0, zero exactly at y in the subdifferential; with x = x(y) it is
+ *            the duality gap of the primal and dual objectives of Section II-D).  For the box,
+ *            g_k = 0 and g_k*(y) = hi y (y > 0) or lo y (y < 0); the soft terms add rho dist or
+ *            rho Huber(dist), and y^2 / (2 rho) for Huber, without imposing the conjugates'
+ *            domains (out[3], out[4] measure those).  Summed in FP64 in a fixed order.
+ * Synchronises.  out is host double[6]. */
 STO_API sto_status stotree_kkt_check(stotree_t h, const void *x0, const void *x, const void *u, const void *y,
                              double tol_active, double *out, sto_stream_t stream);
 

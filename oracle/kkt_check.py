@@ -28,11 +28,14 @@ hold with H'y in place of y in the costates and u equations (per nonleaf node F'
 part and G'y^i for the input part, FN'y^l at a leaf) and with the box on z, the root's block
 included (x^0 = x0).
 
-kkt_residuals returns the five numbers that stotree_kkt_check defines (largest violations, with
+kkt_residuals returns the six numbers that stotree_kkt_check defines (largest violations, with
 points within tol_active of a bound counted as lying on it):
   dynamics, stationarity, feasibility (hard components), complementarity (hard components
   strictly inside; soft components whose subdifferential is one value: distance of y to it),
-  sign (hard components at one bound; soft components at a kink: distance of y to the interval).
+  sign (hard components at one bound; soft components at a kink: distance of y to the interval),
+  gap: the sum over the components of the Fenchel-Young gap g_k(h) + g_k*(y_k) - y_k h >= 0 (Section
+  II-D: with x = x(y) it is the primal objective f(x) + g(Hx) minus the dual objective at y), with
+  the box's g taken as 0 (feasibility is reported apart) and the conjugates' domains not imposed.
 """
 from __future__ import annotations
 
@@ -65,6 +68,25 @@ def _ht_blocks(p, y):
             o = npn * nc + (i - npn) * ncn
             out[npn * (nx + nu) + (i - npn) * nx:npn * (nx + nu) + (i - npn + 1) * nx] = p.FN.T @ y[o:o + ncn]
     return out
+
+
+def _fy_gap(h, y, lo, hi, kind, rho, delta):
+    """g(h) + g*(y) - y h for one component (see the module docstring).  The support function of
+    [lo, hi] is hi y for y > 0 and lo y for y < 0; g is 0 (box), rho d (kind 1) or rho Huber_delta(d)
+    (kind 2) with d the distance of h to the box; g* adds y^2 / (2 rho) for Huber."""
+    if y > 0:
+        t = y * (hi - h)
+    elif y < 0:
+        t = y * (lo - h)
+    else:
+        t = 0.0
+    if kind != 0:
+        d = max(lo - h, 0.0) + max(h - hi, 0.0)
+        if kind == 1:
+            t += rho * d
+        else:
+            t += rho * (0.5 * d * d if d <= delta else delta * (d - 0.5 * delta)) + y * y / (2.0 * rho)
+    return t
 
 
 def _component_terms(p):
@@ -124,7 +146,7 @@ def kkt_residuals(p, x0, x, u, y, tol_active):
         return {"dynamics": dyn, "stationarity": stat, **_box_on_z(p, x0, x, u, y_dual, tol_active)}
     # the nonsmooth term, component by component
     lo, hi, kind, rho, delta = _component_terms(p)
-    feas = comp = sign = 0.0
+    feas = comp = sign = gap = 0.0
     for i in range(nn):
         o, n = _dual_block(p, i)
         h = np.concatenate([xstate(i), u[i]]) if i < npn else x[i]
@@ -133,6 +155,7 @@ def kkt_residuals(p, x0, x, u, y, tol_active):
             if i == 0 and k < nx:  # the parameter: no term, so y must vanish
                 comp = max(comp, abs(yk))
                 continue
+            gap += _fy_gap(hk, yk, lo[k], hi[k], kind[k], rho[k], delta[k])
             if kind[k] == 0:
                 feas = max(feas, lo[k] - hk, hk - hi[k], 0.0)
                 at_hi, at_lo = hk >= hi[k] - tol_active, hk <= lo[k] + tol_active
@@ -161,7 +184,8 @@ def kkt_residuals(p, x0, x, u, y, tol_active):
                 comp = max(comp, viol)
             else:
                 sign = max(sign, viol)
-    return {"dynamics": dyn, "stationarity": stat, "feasibility": feas, "complementarity": comp, "sign": sign}
+    return {"dynamics": dyn, "stationarity": stat, "feasibility": feas, "complementarity": comp, "sign": sign,
+            "gap": gap}
 
 
 def _box_on_z(p, x0, x, u, y, tol_active):
@@ -169,7 +193,7 @@ def _box_on_z(p, x0, x, u, y, tol_active):
     t = p.tree
     npn, nn = t.num_nonleaf, t.num_nodes
     nc, ncn = p.F.shape[0], p.FN.shape[0]
-    feas = comp = sign = 0.0
+    feas = comp = sign = gap = 0.0
     for i in range(nn):
         if i < npn:
             z = p.F @ (x0 if i == 0 else x[i]) + p.G @ u[i]
@@ -180,6 +204,7 @@ def _box_on_z(p, x0, x, u, y, tol_active):
             yi, lo, hi = y[o:o + ncn], p.zNlo, p.zNhi
         for k in range(len(z)):
             zk, yk = float(z[k]), float(yi[k])
+            gap += _fy_gap(zk, yk, lo[k], hi[k], 0, 0.0, 1.0)
             feas = max(feas, lo[k] - zk, zk - hi[k], 0.0)
             at_hi, at_lo = zk >= hi[k] - tol_active, zk <= lo[k] + tol_active
             if not at_hi and not at_lo:
@@ -188,5 +213,5 @@ def _box_on_z(p, x0, x, u, y, tol_active):
                 sign = max(sign, -yk)
             elif at_lo and not at_hi:
                 sign = max(sign, yk)
-    return {"feasibility": feas, "complementarity": comp, "sign": sign}
+    return {"feasibility": feas, "complementarity": comp, "sign": sign, "gap": gap}
 

@@ -1617,10 +1617,41 @@ __global__ void k_kkt_stage(int first, int nx, int nu, int Np, int ld64, const i
     }
 }
 
+// One component's Fenchel-Young gap g(h) + g*(y) - y h (>= 0, zero exactly when y is in the
+// subdifferential of g at h): g the indicator of [lo, hi] (kind 0, taken as 0: feasibility is
+// out[2]), rho dist (kind 1) or rho Huber_delta(dist) (kind 2); g*(y) = sigma_[lo,hi](y), plus
+// y^2 / (2 rho) for kind 2 (the conjugates' domains |y| <= rho, |y| <= rho delta are not imposed
+// here: outputs 3 and 4 measure y against the subdifferential).  sigma(y) - y h is formed as
+// y (hi - h) or y (lo - h), so no large terms cancel.
+__device__ __forceinline__ double gap_term(double hv, double ye, double lo, double hi, int kind, double rho,
+                                           double dl) {
+    double t = ye > 0.0 ? ye * (hi - hv) : (ye < 0.0 ? ye * (lo - hv) : 0.0);
+    if (kind != 0) {
+        const double d = fmax(lo - hv, 0.0) + fmax(hv - hi, 0.0);
+        t += kind == 1 ? rho * d : rho * (d <= dl ? 0.5 * d * d : dl * (d - 0.5 * dl)) + ye * ye / (2.0 * rho);
+    }
+    return t;
+}
+// Sum of the gap terms of a block into partial[blockIdx.x] (fixed order inside the block; the host
+// adds the blocks' partials in order).
+__device__ __forceinline__ void block_gap_partial(double v, double *partial) {
+    __shared__ double red[8];
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = v;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double s = 0.0;
+        for (int w = 0; w < (int)(blockDim.x >> 5); ++w) s += red[w];
+        partial[blockIdx.x] = s;
+    }
+}
+
 template <class T>
-__global__ void k_kkt_elem(int Nn, int nx, int nu, int Np, int ld64, const int *parent, const double *G64,
-                           const double *box64, const T *x0, const T *x, const T *u, const T *y, double tol_act,
-                           double *out, int box_terms) {
+__global__ void __launch_bounds__(256) k_kkt_elem(int Nn, int nx, int nu, int Np, int ld64, const int *parent,
+                                                  const double *G64, const double *box64, const T *x0, const T *x,
+                                                  const T *u, const T *y, double tol_act, double *out,
+                                                  double *gap_part, int box_terms) {
     const int nxu = nx + nu;
     // dynamics residual per node and state component
     for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < (long long)(Nn - 1) * nx;
@@ -1634,8 +1665,9 @@ __global__ void k_kkt_elem(int Nn, int nx, int nu, int Np, int ld64, const int *
         atomic_max_nonneg(out + 0, fabs((double)x[(size_t)j * nx + rr] - acc));
     }
     if (!box_terms) return;  // general maps: k_kkt_fg_box checks z
-    // box feasibility, complementarity and multiplier signs per dual entry
+    // box feasibility, complementarity, multiplier signs and the gap per dual entry
     const long long m = (long long)Np * nxu + (long long)(Nn - Np) * nx;
+    double gap = 0.0;
     for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < m; e += (long long)gridDim.x * blockDim.x) {
         int node, k, bi;
         double hv;
@@ -1659,12 +1691,14 @@ __global__ void k_kkt_elem(int Nn, int nx, int nu, int Np, int ld64, const int *
         double lo = box64[bi], hi = box64[nxu + bi];
         const double rho = box64[2 * nxu + bi], dl = box64[3 * nxu + bi];
         int kind = (int)box64[4 * nxu + bi];
-        if (node == 0 && k < nx) {
+        const bool param = node == 0 && k < nx;  // the root state is the parameter: no term
+        if (param) {
             lo = -INFINITY;
             hi = INFINITY;
             kind = 0;
         }
         const double ye = (double)y[e];
+        if (!param) gap += gap_term(hv, ye, lo, hi, kind, rho, dl);
         if (kind == 0) {
             atomic_max_nonneg(out + 2, fmax(0.0, fmax(lo - hv, hv - hi)));
             const bool at_hi = hv >= hi - tol_act, at_lo = hv <= lo + tol_act;
@@ -1695,16 +1729,20 @@ __global__ void k_kkt_elem(int Nn, int nx, int nu, int Np, int ld64, const int *
             atomic_max_nonneg(out + (slo == shi ? 3 : 4), res);
         }
     }
+    block_gap_partial(gap, gap_part);
 }
 
 // General maps: feasibility, complementarity and multiplier signs of the box on z = F x + G u
 // (FN x at the leaves; the root's x is x0), z formed in FP64 from x and u.
 template <class T>
-__global__ void k_kkt_fg_box(int Nn, int nx, int nu, int Np, int nc, int ncN, const double *FG64, const double *zbox64,
-                             const T *x0, const T *x, const T *u, const T *y, double tol_act, double *out) {
+__global__ void __launch_bounds__(256) k_kkt_fg_box(int Nn, int nx, int nu, int Np, int nc, int ncN,
+                                                    const double *FG64, const double *zbox64, const T *x0,
+                                                    const T *x, const T *u, const T *y, double tol_act, double *out,
+                                                    double *gap_part) {
     const double *F = FG64, *G = FG64 + (size_t)nc * nx, *FN = G + (size_t)nc * nu;
     const int nb = nc + ncN;
     const long long m = (long long)Np * nc + (long long)(Nn - Np) * ncN;
+    double gap = 0.0;
     for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < m; e += (long long)gridDim.x * blockDim.x) {
         double z = 0.0;
         int bi;
@@ -1721,6 +1759,7 @@ __global__ void k_kkt_fg_box(int Nn, int nx, int nu, int Np, int nc, int ncN, co
             bi = nc + c;
         }
         const double lo = zbox64[bi], hi = zbox64[nb + bi], ye = (double)y[e];
+        gap += gap_term(z, ye, lo, hi, 0, 0.0, 1.0);
         atomic_max_nonneg(out + 2, fmax(0.0, fmax(lo - z, z - hi)));
         const bool at_hi = z >= hi - tol_act, at_lo = z <= lo + tol_act;
         if (!at_hi && !at_lo) atomic_max_nonneg(out + 3, fabs(ye));
@@ -1729,6 +1768,7 @@ __global__ void k_kkt_fg_box(int Nn, int nx, int nu, int Np, int nc, int ncN, co
         if (at_lo && !at_hi) sgn = fmax(0.0, ye);
         atomic_max_nonneg(out + 4, sgn);
     }
+    block_gap_partial(gap, gap_part);
 }
 
 template <class T>
@@ -1738,6 +1778,8 @@ sto_status kkt_impl(stotree_t h, const void *x0, const void *x, const void *u, c
     double *mu = h->at<double>(L.kkt);
     double *dout = mu + (size_t)h->Nn * h->nx + (size_t)h->Np * h->nu;
     double *hty = dout + 64;  // general maps: H'y in FP64, laid out like [x; u]
+    constexpr int kGapBlocks = 592;
+    double *gap_part = h->at<double>(L.partials);  // the gap's per-block sums (the solvers' scratch)
     STO_CUDA(h, cudaMemsetAsync(dout, 0, 8 * sizeof(double), st));
     if (h->fg) {
         const sto_status s = fg_ht(h, y, hty, true, st);
@@ -1757,18 +1799,25 @@ sto_status kkt_impl(stotree_t h, const void *x0, const void *x, const void *u, c
                                                      h->at<double>(L.cost64), static_cast<const T *>(x),
                                                      static_cast<const T *>(u), static_cast<const T *>(y), mu, dout);
     }
-    k_kkt_elem<T><<<592, 256, 0, st>>>(h->Nn, h->nx, h->nu, h->Np, h->ld64, h->at<int>(L.parent),
-                                       h->at<double>(L.G64), h->at<double>(L.box64), static_cast<const T *>(x0),
-                                       static_cast<const T *>(x), static_cast<const T *>(u),
-                                       static_cast<const T *>(y), tol_act, dout, h->fg ? 0 : 1);
+    k_kkt_elem<T><<<kGapBlocks, 256, 0, st>>>(h->Nn, h->nx, h->nu, h->Np, h->ld64, h->at<int>(L.parent),
+                                              h->at<double>(L.G64), h->at<double>(L.box64),
+                                              static_cast<const T *>(x0), static_cast<const T *>(x),
+                                              static_cast<const T *>(u), static_cast<const T *>(y), tol_act, dout,
+                                              gap_part, h->fg ? 0 : 1);
     if (h->fg)
-        k_kkt_fg_box<T><<<592, 256, 0, st>>>(h->Nn, h->nx, h->nu, h->Np, h->nc, h->ncN, h->at<double>(L.FG64),
-                                             h->at<double>(L.zbox64), static_cast<const T *>(x0),
-                                             static_cast<const T *>(x), static_cast<const T *>(u),
-                                             static_cast<const T *>(y), tol_act, dout);
+        k_kkt_fg_box<T><<<kGapBlocks, 256, 0, st>>>(h->Nn, h->nx, h->nu, h->Np, h->nc, h->ncN,
+                                                    h->at<double>(L.FG64), h->at<double>(L.zbox64),
+                                                    static_cast<const T *>(x0), static_cast<const T *>(x),
+                                                    static_cast<const T *>(u), static_cast<const T *>(y), tol_act,
+                                                    dout, gap_part);
+    std::vector<double> parts(kGapBlocks);
     STO_CUDA(h, cudaMemcpyAsync(out, dout, 5 * sizeof(double), cudaMemcpyDeviceToHost, st));
+    STO_CUDA(h, cudaMemcpyAsync(parts.data(), gap_part, kGapBlocks * sizeof(double), cudaMemcpyDeviceToHost, st));
     STO_CUDA(h, cudaStreamSynchronize(st));
     STO_CUDA(h, cudaGetLastError());
+    double gap = 0.0;
+    for (double v : parts) gap += v;  // blocks in order
+    out[5] = gap;
     return STO_OK;
 }
 

@@ -349,11 +349,11 @@ class StoTree:
         return dict(y=y, x=x, u=u, z=z, info=info.as_dict())
 
     def kkt_check(self, x0, x, u, y, tol_active=1e-6):
-        out = (ctypes.c_double * 5)()
+        out = (ctypes.c_double * 6)()
         self._check(lib().stotree_kkt_check(self.h, _t_ptr(x0), _t_ptr(x), _t_ptr(u), _t_ptr(y), tol_active, out,
                                             _stream()), "kkt_check")
         return dict(dynamics=out[0], stationarity=out[1], feasibility=out[2], complementarity=out[3],
-                    sign=out[4])
+                    sign=out[4], gap=out[5])
 
     # -- measurement ----------------------------------------------------------------------
     def set_timing(self, on=True):

@@ -18,7 +18,7 @@ from tests import dense_kkt as D
 
 pytestmark = pytest.mark.gpu
 
-KEYS = ("dynamics", "stationarity", "feasibility", "complementarity", "sign")
+KEYS = ("dynamics", "stationarity", "feasibility", "complementarity", "sign", "gap")
 BOXED = [D.boxed_problem(12, horizon=3, nx=3, nu=2), D.boxed_problem(17, horizon=4, nx=4, nu=2, frac=0.9),
          D.boxed_problem(16, horizon=3, nx=5, nu=3, frac=0.9)]
 

@@ -248,3 +248,45 @@ def test_general_maps_zero_at_the_certified_solution_and_planted_violations(kw):
             grad[i, a] = (lag(up) - lag(dn)) / 2e-3
     g = float(np.max(np.abs(grad)))
     assert abs(KC.kkt_residuals(p, p.x0, xx, uu, yy, tol_active=1e-8)["stationarity"] - g) <= 1e-8 * g
+
+
+def test_gap_of_a_planted_interior_multiplier(solved):
+    """A multiplier y_k < 0 on a component strictly inside its box adds y_k (lo_k - h_k) to the
+    gap (the support function's lo y against y h); at the solution the gap is zero."""
+    p, x, u, y = solved
+    h = np.concatenate([np.concatenate([x[i], u[i]]) if i < p.tree.num_nonleaf else x[i]
+                        for i in range(p.tree.num_nodes)])
+    lo, hi = D.box_vectors(p)
+    inside = np.nonzero((h < hi - 1e-3) & (h > lo + 1e-3))[0]
+    inside = inside[inside >= p.nx]
+    k = int(inside[0])
+    y2 = y.copy()
+    y2[k] = -0.0375
+    base = KC.kkt_residuals(p, p.x0, x, u, y, tol_active=1e-8)["gap"]
+    r = KC.kkt_residuals(p, p.x0, x, u, y2, tol_active=1e-8)
+    assert abs(r["gap"] - base - 0.0375 * (h[k] - lo[k])) <= 1e-13
+
+
+@pytest.mark.parametrize("soft", [False, True], ids=["box", "soft"])
+def test_gap_is_primal_minus_dual_objective(soft):
+    """At x = x(y) the gap equals the primal objective f(x) + g(Hx) minus the dual objective
+    -fhat(y) - g*(y) of Section II-D, both taken from the oracle's solve step and its g, g*
+    (a different route from the per-component formula); y is inside the conjugates' domains."""
+    from oracle import oracle as O
+    p = D.boxed_problem(17, horizon=4, nx=4, nu=2, frac=0.9)
+    if soft:
+        n = p.nx + p.nu
+        W.with_penalty(p, np.array([1, 2] * (n // 2) + [0] * (n % 2)), 5.0 * np.ones(n), 0.4 * np.ones(n))
+    o = O.LQOracle(p)
+    rng = np.random.default_rng(11)
+    for trial in range(3):
+        y = 0.3 * W.random_dual(p, 20 + trial)
+        x, u = o.solve(y)
+        r = KC.kkt_residuals(p, p.x0, x, u, y, tol_active=1e-8)
+        yb = y / o.sq
+        h = o.hx(y)
+        primal = o.cost(x, u) + (O.g_val(o, o.sq * h) if soft else 0.0)
+        dual = -O.fhat(o, yb) - O.g_conj(o, yb)
+        assert np.isfinite(dual)
+        assert abs(r["gap"] - (primal - dual)) <= 1e-9 * max(1.0, abs(primal)), (trial, r["gap"], primal - dual)
+        assert r["gap"] >= -1e-12

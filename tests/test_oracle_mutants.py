@@ -229,6 +229,10 @@ KKT_MUTANTS = [
      "= p.G.T @ yi", "= 0.0 * (p.G.T @ yi)"),
     ("kkt_fg_leaf_dual_dropped", "general maps: the leaves' FN'y left out of the costates",
      "= p.FN.T @ y[o:o + ncn]", "= 0.0 * (p.FN.T @ y[o:o + ncn])"),
+    ("kkt_gap_support_bound", "gap: the support function takes lo for a positive multiplier",
+     "t = y * (hi - h)", "t = y * (lo - h)"),
+    ("kkt_gap_huber_conjugate", "gap: Huber's conjugate without y^2 / (2 rho)",
+     "+ y * y / (2.0 * rho)", ""),
     ("kkt_fg_sign_at_upper_bound", "general maps: multiplier of z at its upper bound required to be <= 0",
      "elif at_hi and not at_lo:\n                sign = max(sign, -yk)",
      "elif at_hi and not at_lo:\n                sign = max(sign, yk)"),
