@@ -258,6 +258,11 @@ def run_ours(args):
     e2e_ms = _max_over_ranks(pg, e2e_ms, dev)
     h2d = 4 * (st.nx + st.m)
     d2h = 4 * (st.m + st.Nn * st.nx + st.Np * st.nu)
+    # the last e2e solution through the library's FP64 optimality check (untimed)
+    kkt = st.kkt_check(x0, res["x"], res["u"], res["y"], tol_active=1e-3)
+    kkt = {k: float(f"{v:.4g}") for k, v in kkt.items()}
+    kkt["note"] = ("FP64 residuals of the returned (x, u, y) (stotree_kkt_check; tol_active 1e-3): max "
+                   "violations, and the Fenchel-Young duality gap summed over the 1.79 M duals")
 
     batched = run_batched(dev, max(1, min(args.steps, 3)))
     warm = run_warm(dev, args.warm_train_draws, args.warm_eval_draws) if args.warm_train_draws > 0 else None
@@ -284,6 +289,7 @@ def run_ours(args):
             "solve_step_gbs": round(achieved, 1),
             "e2e": {"value": round(e2e_ms, 4), "unit": "ms", "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
             "gpu_launches": launches,
+            "kkt": kkt,
             "factor": factor,
             "gpad": gpad,
             "backtracking": backtrack,
