@@ -174,11 +174,20 @@ __device__ __forceinline__ bool mbar_wait(uint64_t *b, unsigned parity, int *err
     atomicExch(err, 2);
     return false;
 }
-__device__ __forceinline__ void bulk_load(void *dst, const void *src, unsigned bytes, uint64_t *bar) {
-    asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
-                     sm_addr(dst)),
-                 "l"(src), "r"(bytes), "r"(sm_addr(bar))
-                 : "memory");
+// The node matrices are streamed once per round and do not fit in L2, so their bulk copies carry
+// an evict-first L2 policy: they then displace the solver's vectors (read by the elementwise
+// passes between rounds) as little as possible.
+__device__ __forceinline__ uint64_t evict_first_policy() {
+    uint64_t pol;
+    asm volatile("createpolicy.fractional.L2::evict_first.b64 %0, 1.0;" : "=l"(pol));
+    return pol;
+}
+__device__ __forceinline__ void bulk_load(void *dst, const void *src, unsigned bytes, uint64_t *bar, uint64_t pol) {
+    asm volatile(
+        "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes.L2::cache_hint [%0], [%1], %2, [%3], %4;" ::"r"(
+            sm_addr(dst)),
+        "l"(src), "r"(bytes), "r"(sm_addr(bar)), "l"(pol)
+        : "memory");
 }
 __device__ __forceinline__ unsigned ld_acquire(const unsigned *p) {
     unsigned v;
@@ -254,8 +263,10 @@ struct Producer {
     uint64_t *full, *empty;
     unsigned long long n = 0;
 
+    uint64_t pol;  // L2 policy of the matrix copies
+
     __device__ Producer(const TreeArgs<T> &a_, unsigned char *r, Meta *m, uint64_t *f, uint64_t *e)
-        : a(a_), ring(r), meta(m), full(f), empty(e) {}
+        : a(a_), ring(r), meta(m), full(f), empty(e), pol(evict_first_policy()) {}
 
     // false when a slot never came free (the error flag is then raised): stop issuing copies
     __device__ bool slot_acquire(int &slot) {
@@ -282,7 +293,7 @@ struct Producer {
         meta[slot] = md;
         const unsigned bytes = (unsigned)(nrows * ld * sizeof(T));
         mbar_expect_tx(&full[slot], bytes);
-        bulk_load(ring + (size_t)slot * kChunk, src + (size_t)row0 * ld, bytes, &full[slot]);
+        bulk_load(ring + (size_t)slot * kChunk, src + (size_t)row0 * ld, bytes, &full[slot], pol);
         ++n;
     }
     __device__ void emit_end() {
