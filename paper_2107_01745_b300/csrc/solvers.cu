@@ -553,7 +553,7 @@ __global__ void __launch_bounds__(kThreads) k_grad(int m, const T *__restrict__ 
 // L-BFGS, compact representation (Byrd, Nocedal, Schnabel 1994): one pass for S'g, Y'g and the
 // Gram column of a newly committed pair, then the small solve in the last block.  MEM >= mem.
 template <class T, int MEM>
-__global__ void __launch_bounds__(kThreads) k_lb_dots(int m, const T *__restrict__ g, const T *ringS,
+__global__ void __launch_bounds__(kThreads, 4) k_lb_dots(int m, const T *__restrict__ g, const T *ringS,
                                                       const T *ringY, long long vstride, SolverScalars *sc,
                                                       double *partials) {
     __shared__ double tot[4 * MEM];
@@ -652,7 +652,7 @@ __global__ void __launch_bounds__(kThreads) k_lb_dots(int m, const T *__restrict
 
 // d = -(gamma g + sum_i coef_s[i] s_i + sum_i coef_y[i] y_i)
 template <class T, int MEM>
-__global__ void __launch_bounds__(kThreads) k_lb_dir(int m, const T *__restrict__ g, const T *ringS, const T *ringY,
+__global__ void __launch_bounds__(kThreads, 4) k_lb_dir(int m, const T *__restrict__ g, const T *ringS, const T *ringY,
                                                      long long vstride, const SolverScalars *sc, T *dvec) {
     const int cnt = sc->lb_count, head = sc->lb_head, M1 = sc->mem + 1;
     const T gamma = (T)sc->gamma;
