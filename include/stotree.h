@@ -169,8 +169,10 @@ STO_API sto_status stotree_bind_workspace(stotree_t h, void *dev_ptr, size_t byt
 
 /* Upload the dynamics of nodes [first, first+count) (eq. system_dynamics_tree): host
  * FP64 A [count][nx][nx], B [count][nx][nu], c [count][nx], row-major, where entry k
- * belongs to node first+k.  Node 0's data is ignored.  May be called in chunks.
- * Invalidates the factor. */
+ * belongs to node first+k.  Node 0's data is ignored.  May be called in chunks.  A and B may
+ * both be NULL to replace only the disturbances c of nodes that already have their matrices
+ * (a new scenario draw of the same system; STO_ERR_NOT_READY otherwise).  Invalidates the
+ * factor. */
 STO_API sto_status stotree_set_dynamics(stotree_t h, int32_t first, int32_t count, const double *A,
                                 const double *B, const double *c, sto_stream_t stream);
 

@@ -470,13 +470,20 @@ sto_status stotree_bind_workspace(stotree_t h, void *dev, size_t bytes, sto_stre
 
 sto_status stotree_set_dynamics(stotree_t h, int32_t first, int32_t count, const double *A,
                                 const double *B, const double *c, sto_stream_t stream) {
-    if (!h || !A || !B || !c || first < 0 || count < 1 || first + count > h->Nn) return STO_ERR_INVALID_ARG;
+    if (!h || !c || (A == nullptr) != (B == nullptr) || first < 0 || count < 1 || first + count > h->Nn)
+        return STO_ERR_INVALID_ARG;
     if (!h->ws) return STO_ERR_NOT_READY;
+    if (!A)  // the disturbances only: the nodes keep their matrices
+        for (int i = first; i < first + count; ++i)
+            if (!h->have_dyn[i]) return STO_ERR_NOT_READY;
     cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
     const size_t nx = h->nx, nu = h->nu, ld = h->ld64;
     double *dst = h->at<double>(h->L.G64) + (size_t)first * nx * ld;
-    STO_CUDA(h, cudaMemcpy2DAsync(dst, ld * 8, A, nx * 8, nx * 8, (size_t)count * nx, cudaMemcpyHostToDevice, st));
-    STO_CUDA(h, cudaMemcpy2DAsync(dst + nx, ld * 8, B, nu * 8, nu * 8, (size_t)count * nx, cudaMemcpyHostToDevice, st));
+    if (A) {
+        STO_CUDA(h, cudaMemcpy2DAsync(dst, ld * 8, A, nx * 8, nx * 8, (size_t)count * nx, cudaMemcpyHostToDevice, st));
+        STO_CUDA(h, cudaMemcpy2DAsync(dst + nx, ld * 8, B, nu * 8, nu * 8, (size_t)count * nx, cudaMemcpyHostToDevice,
+                                      st));
+    }
     STO_CUDA(h, cudaMemcpy2DAsync(dst + nx + nu, ld * 8, c, 8, 8, (size_t)count * nx, cudaMemcpyHostToDevice, st));
     STO_CUDA(h, cudaStreamSynchronize(st));  // host arrays may be released on return
     for (int i = first; i < first + count; ++i) h->have_dyn[i] = 1;

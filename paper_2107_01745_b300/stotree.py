@@ -209,13 +209,8 @@ class StoTree:
             self.ws = torch.empty(self.workspace_bytes, dtype=torch.uint8, device=self.device)
             st = _stream()
             self._check(L.stotree_bind_workspace(h, _t_ptr(self.ws), self.workspace_bytes, st), "bind_workspace")
-            nn = t.num_nodes
-            for f in range(0, nn, chunk_nodes):
-                c = min(chunk_nodes, nn - f)
-                A = np.ascontiguousarray(problem.A[f:f + c], dtype=np.float64)
-                B = np.ascontiguousarray(problem.B[f:f + c], dtype=np.float64)
-                cc = np.ascontiguousarray(problem.c[f:f + c], dtype=np.float64)
-                self._check(L.stotree_set_dynamics(h, f, c, _np_ptr(A), _np_ptr(B), _np_ptr(cc), st), "set_dynamics")
+            self._chunk = chunk_nodes
+            self.set_dynamics(problem.A, problem.B, problem.c)
             self.set_costs(problem.Q, problem.R, problem.PN, problem.q, problem.r, problem.pN)
             if self.general:
                 self.set_zbox(problem.zlo, problem.zhi, problem.zNlo, problem.zNhi)
@@ -250,6 +245,20 @@ class StoTree:
         return torch.as_tensor(np.asarray(a), dtype=self.dtype).to(self.device).contiguous()
 
     # -- set-up ---------------------------------------------------------------------------
+    def set_dynamics(self, A, B, c):
+        """stotree_set_dynamics for every node, in chunks (A [Nn][nx][nx], B [Nn][nx][nu],
+        c [Nn][nx]; A = B = None keeps the matrices and replaces the disturbances); the handle
+        needs stotree_factor again before its next solve."""
+        nn = self.p.tree.num_nodes
+        for f in range(0, nn, self._chunk):
+            n = min(self._chunk, nn - f)
+            Af = None if A is None else np.ascontiguousarray(A[f:f + n], dtype=np.float64)
+            Bf = None if B is None else np.ascontiguousarray(B[f:f + n], dtype=np.float64)
+            cf = np.ascontiguousarray(c[f:f + n], dtype=np.float64)
+            self._check(lib().stotree_set_dynamics(self.h, f, n, _np_ptr(Af) if Af is not None else None,
+                                                   _np_ptr(Bf) if Bf is not None else None, _np_ptr(cf), _stream()),
+                        "set_dynamics")
+
     def set_costs(self, Q, R, PN, q=None, r=None, pN=None):
         arr = [np.ascontiguousarray(v, dtype=np.float64) if v is not None else None for v in (Q, R, PN, q, r, pN)]
         self._keep_cost = arr

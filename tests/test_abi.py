@@ -264,3 +264,32 @@ def test_wait_limit_and_round_status_refusals_need_no_device(libso):
         assert L.stotree_round_status(h, None) == 3  # no workspace bound
     finally:
         L.stotree_destroy(h)
+
+
+def test_set_dynamics_argument_checks_need_no_device(libso):
+    """stotree_set_dynamics: c is required, A and B are given together or both NULL (NULL keeps
+    the nodes' matrices and is refused for nodes that have none), the node range must lie in the
+    tree; the checks answer before any device work (no workspace bound here: NOT_READY)."""
+    L = libso
+    vp = ctypes.c_void_p
+    L.stotree_set_dynamics.argtypes = [vp, ctypes.c_int32, ctypes.c_int32, vp, vp, vp, vp]
+    L.stotree_destroy.argtypes = [vp]
+    parent = np.array([-1, 0, 0], dtype=np.int32)
+    prob = np.array([1.0, 0.5, 0.5])
+    d = _Desc(3, 1, 2, 1, parent.ctypes.data, prob.ctypes.data)
+    h = ctypes.c_void_p()
+    assert L.stotree_create(ctypes.byref(d), 1, ctypes.byref(h)) == 0
+    A = np.zeros((3, 2, 2))
+    B = np.zeros((3, 2, 1))
+    c = np.zeros((3, 2))
+    p = lambda a: a.ctypes.data
+    try:
+        assert L.stotree_set_dynamics(h, 0, 3, p(A), p(B), None, None) == 1   # no c
+        assert L.stotree_set_dynamics(h, 0, 3, p(A), None, p(c), None) == 1   # B without A
+        assert L.stotree_set_dynamics(h, 0, 3, None, p(B), p(c), None) == 1   # A without B
+        assert L.stotree_set_dynamics(h, 1, 3, p(A), p(B), p(c), None) == 1   # past the last node
+        assert L.stotree_set_dynamics(h, 0, 0, p(A), p(B), p(c), None) == 1   # empty range
+        assert L.stotree_set_dynamics(h, 0, 3, p(A), p(B), p(c), None) == 3   # no workspace yet
+        assert L.stotree_set_dynamics(h, 0, 3, None, None, p(c), None) == 3
+    finally:
+        L.stotree_destroy(h)

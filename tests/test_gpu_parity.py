@@ -439,3 +439,25 @@ def test_paper_scale_gpad_warm_start(cuda_device, paper_scale):
     assert abs(g["info"]["res_inf"] - ref["res_inf"]) <= 1e-3 * ref["res_inf"]
     res = st.solve("nama", lam, y0=g["y"], tol=1e-4, max_iter=300)
     assert res["info"]["status"] == 0 and res["info"]["res_inf"] <= 1e-4
+
+
+def test_new_disturbances_on_a_factored_handle(cuda_device):
+    """stotree_set_dynamics with A = B = NULL replaces only the disturbances: after a new factor
+    the handle solves another scenario draw of the same system exactly as a handle built for that
+    draw (the same data, so the same bits), and the oracle agrees."""
+    rng = np.random.default_rng(36)
+    g = W.make_group(rng, 4, 2, 3, 6, 3, 3)
+    st = _st()(g.instance(0), precision="fp32")
+    for k in (1, 2):
+        pk = g.instance(k)
+        st.set_dynamics(None, None, g.c[k])
+        st.factor()
+        fresh = _st()(pk, precision="fp32")
+        fresh.factor()
+        y = st.to_dev(W.random_dual(pk, 40 + k))
+        x0 = st.to_dev(g.x0[k])
+        h1 = st.solve_step(y, x0=x0).cpu().numpy()
+        h2 = fresh.solve_step(y, x0=x0).cpu().numpy()
+        assert np.array_equal(h1, h2)
+        assert _rel2(h1, O.LQOracle(pk).hx(W.random_dual(pk, 40 + k))) < 1e-5
+        fresh.close()
