@@ -226,6 +226,7 @@ def run_ours(args):
     backtrack = run_backtrack(st, Lhat, x0)
     soft = run_soft(st, lam, x0)
     spring = run_spring_mass(dev) if args.spring_mass else None
+    largest = run_largest(dev, max(1, min(args.steps, 3))) if args.largest else None
 
     mat_bytes, vec_bytes = st.solve_bytes()
     alg_bytes = rounds * mat_bytes + rhs * vec_bytes
@@ -295,6 +296,7 @@ def run_ours(args):
             "backtracking": backtrack,
             "soft_states": soft,
             "spring_mass": spring,
+            "largest": largest,
             "batched": batched,
             "warm_start": warm,
             "clocks": clk.summary(),
@@ -399,6 +401,61 @@ def run_soft(st, lam, x0):
         st.set_penalty([0] * n, 0.0, 1.0)
     return {"rho": 1.0, "ms": round(i["ms"], 3), "iters": i["iters"], "solve_calls": i["solve_calls"],
             "res_inf": i["res_inf"], "converged": i["status"] == 0}
+
+
+def run_largest(dev, steps):
+    """The largest single instance (horizon 24, binary for 12 stages, 57,343 nodes, nx = 200,
+    nu = 100: 16.8 M primal variables; per-node data generated in seeded 512-node blocks): NAMA to
+    the tolerance, one warm-up solve and `steps` timed ones, the solve rounds' HBM roofline (the
+    library's algorithmic bytes over the rounds' CUDA-event time), and the FP64 optimality check
+    of the result.  Set-up (data generation, upload, FP64 factor, lambda) is untimed."""
+    import time
+    import torch
+    from paper_2107_01745_b300 import workloads as W
+    from paper_2107_01745_b300.stotree import StoTree
+    t0 = time.time()
+    p = W.largest(5)
+    st = StoTree(p, precision="fp32", device=dev, chunk_nodes=4096)
+    st.factor()
+    r0 = torch.as_tensor(np.random.default_rng(7).standard_normal(st.m), dtype=torch.float32, device=dev)
+    lam, _ = st.estimate_lambda(r0, iters=50, safety=0.9)
+    x0 = st.to_dev(p.x0)
+    st.solve("nama", lam, x0=x0, tol=TOL, max_iter=1000, outputs=False)
+    setup_s = time.time() - t0
+    stream = torch.cuda.current_stream()
+    st.set_timing(True)
+    st.get_timing()
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(steps):
+        res = st.solve("nama", lam, x0=x0, tol=TOL, max_iter=1000)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    solve_ms, rounds, rhs = st.get_timing()
+    st.set_timing(False)
+    info = res["info"]
+    if info["status"] != 0 or info["res_inf"] > TOL:
+        raise RuntimeError(f"largest instance: NAMA stopped at residual {info['res_inf']}")
+    mat_bytes, vec_bytes = st.solve_bytes()
+    gbs = (rounds * mat_bytes + rhs * vec_bytes) / (solve_ms * 1e-3) / 1e9
+    peak, peak_kind = _peaks()
+    kkt = st.kkt_check(x0, res["x"], res["u"], res["y"], tol_active=1e-3)
+    del res, r0, x0
+    out = {"workload": "largest: horizon 24, binary for stages 0-11 then one child (4096 scenarios, 57,343 nodes), "
+                       "nx=200, nu=100 (16.8 M primal variables), A_j = A + 0.02 N(0,1) with rho(A)=0.98, "
+                       "B_j ~ N(0,1/nx), c ~ N(0,0.05^2), Q=I, R=0.1I, P_N=I, stored input box; seed 5; NAMA to 1e-4",
+           "ms": round(e0.elapsed_time(e1) / steps, 3), "steps": steps, "iters": info["iters"],
+           "solve_calls": info["solve_calls"], "res_inf": info["res_inf"],
+           "roofline": {"kernel": "k_tree solve rounds", "bound": "hbm", "achieved": round(gbs, 1), "peak": peak,
+                        "unit": "GB/s", "frac": round(gbs / peak, 4), "peak_source": peak_kind,
+                        "algorithmic_bytes_per_round": mat_bytes, "avg_round_ms": round(solve_ms / max(rounds, 1), 4)},
+           "kkt": {k: float(f"{v:.4g}") for k, v in kkt.items()},
+           "setup_s": round(setup_s, 1)}
+    st.close()
+    del st
+    torch.cuda.empty_cache()  # about 70 GB of workspace, returned before the later sections
+    return out
 
 
 def run_spring_mass(dev):
@@ -810,6 +867,8 @@ def main():
                     help="training draws of the learned warm start (0 skips it)")
     ap.add_argument("--warm-eval-draws", type=int, default=5000,
                     help="held-out draws the learned warm start is evaluated on")
+    ap.add_argument("--largest", type=int, default=1,
+                    help="1: also solve the largest single instance (about a minute of set-up)")
     ap.add_argument("--spring-mass", type=int, default=1,
                     help="run the 300-problem spring-mass experiment of Section IV-A (0 skips it)")
     ap.add_argument("--profile", choices=["nama", "minfbe", "batched", "warm", "infer", "warm_round", "warm_round_full",
