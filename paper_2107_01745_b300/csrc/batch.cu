@@ -315,6 +315,15 @@ __device__ void wait_count(const unsigned *c, unsigned need, int *err) {
     atomicCAS(err, 0, 1);
 }
 
+// Staging copies of the stage matrices: one 4-byte asynchronous global-to-shared copy per entry, so
+// that a thread's copies are all in flight at once (a plain load-then-store loop waits out the
+// L2 latency once per entry); cp_wait() before the barrier that publishes them.
+__device__ __forceinline__ void cp4(float *dst, const float *src) {
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 4;" ::"r"((unsigned)__cvta_generic_to_shared(dst)), "l"(src)
+                 : "memory");
+}
+__device__ __forceinline__ void cp_wait() { asm volatile("cp.async.wait_all;" ::: "memory"); }
+
 // Backward tile: parents of stage t.  S = sum_children s, o = [A | B]' S, v = y_u/2 + o_B + gu,
 // ubar = -(1/pi_t) R~^-1 v, s = y_x/2 + o_A + K_t' v + gx.  Every global read of the tile (the
 // children's s, or the leaves' y, and the column's y and gamma block) is issued in one gather.
@@ -339,9 +348,9 @@ __device__ __forceinline__ void bwd_tile(const RoundArgs<NR> &a, const RTask &tk
     if (!__syncthreads_or(threadIdx.x < TC ? ci.ok[threadIdx.x] : 0)) return;
     const int key = 2 * (tk.group * (kMaxStages + 1) + t);
     if (staged != key) {
-        for (int e = threadIdx.x; e < nx * nxu; e += NT) Gs[e] = q.G[e];
-        for (int e = threadIdx.x; e < nu * nx; e += NT) Ks[e] = q.Kt[(size_t)t * nu * nx + e];
-        for (int e = threadIdx.x; e < nu * nu; e += NT) Rs[e] = q.Ri[(size_t)t * nu * nu + e];
+        for (int e = threadIdx.x; e < nx * nxu; e += NT) cp4(Gs + e, q.G + e);
+        for (int e = threadIdx.x; e < nu * nx; e += NT) cp4(Ks + e, q.Kt + (size_t)t * nu * nx + e);
+        for (int e = threadIdx.x; e < nu * nu; e += NT) cp4(Rs + e, q.Ri + (size_t)t * nu * nu + e);
         staged = key;
     }
     {
@@ -370,6 +379,7 @@ __device__ __forceinline__ void bwd_tile(const RoundArgs<NR> &a, const RTask &tk
                     Wb[(k * XU + r - nx) * C::TP + col] = v;
             });
     }
+    cp_wait();
     __syncthreads();
     const int cg = threadIdx.x % C::CG, rg = threadIdx.x / C::CG;
     const int mr = (nxu + C::RG - 1) / C::RG, r0 = rg * mr;
@@ -492,9 +502,9 @@ __device__ __forceinline__ void fwd_tile(const RoundArgs<NR> &a, const RTask &tk
     if (!__syncthreads_or(threadIdx.x < TC ? ci.ok[threadIdx.x] : 0)) return;
     const int key = 2 * (tk.group * (kMaxStages + 1) + t) + 1;
     if (staged != key) {
-        for (int e = threadIdx.x; e < nx * nxu; e += NT) Gs[e] = q.G[e];
+        for (int e = threadIdx.x; e < nx * nxu; e += NT) cp4(Gs + e, q.G + e);
         if (!leaf)
-            for (int e = threadIdx.x; e < nu * nx; e += NT) Ks[e] = q.Kt[(size_t)t * nu * nx + e];
+            for (int e = threadIdx.x; e < nu * nx; e += NT) cp4(Ks + e, q.Kt + (size_t)t * nu * nx + e);
         staged = key;
     }
     {
@@ -525,6 +535,7 @@ __device__ __forceinline__ void fwd_tile(const RoundArgs<NR> &a, const RTask &tk
                     CB[(k * C::NXM + r - nxu) * C::TP + col] = v;
             });
     }
+    cp_wait();
     __syncthreads();
     const int cg = threadIdx.x % C::CG, rg = threadIdx.x / C::CG;
     const float sc = a.scaled ? q.sq_t : 1.f;
@@ -742,24 +753,26 @@ __device__ __forceinline__ void col_stage(const Geo &q, int t, bool leaf, float 
     const int nx = q.nx, nu = q.nu, nxu = q.nxu;
     for (int e = threadIdx.x; e < NXP * (NXP + NUP); e += NT) {
         const int r = e / (NXP + NUP), c = e - r * (NXP + NUP);
-        float v = 0.f;
-        if (r < nx) {
-            if (c < NXP) {
-                if (c < nx) v = q.G[r * nxu + c];
-            } else if (c - NXP < nu) {
-                v = q.G[r * nxu + nx + c - NXP];
-            }
-        }
-        Gp[e] = v;
+        const int gc = c < NXP ? (c < nx ? c : -1) : (c - NXP < nu ? nx + c - NXP : -1);
+        if (r < nx && gc >= 0)
+            cp4(Gp + e, q.G + r * nxu + gc);
+        else
+            Gp[e] = 0.f;
     }
     if (!leaf) {
         for (int e = threadIdx.x; e < NUP * NXP; e += NT) {
             const int aa = e / NXP, c = e - aa * NXP;
-            Kp[e] = (aa < nu && c < nx) ? q.Kt[(size_t)t * nu * nx + aa * nx + c] : 0.f;
+            if (aa < nu && c < nx)
+                cp4(Kp + e, q.Kt + (size_t)t * nu * nx + aa * nx + c);
+            else
+                Kp[e] = 0.f;
         }
         for (int e = threadIdx.x; e < NUP * NUP; e += NT) {
             const int aa = e / NUP, bb = e - aa * NUP;
-            Rp[e] = (aa < nu && bb < nu) ? q.Ri[(size_t)t * nu * nu + aa * nu + bb] : 0.f;
+            if (aa < nu && bb < nu)
+                cp4(Rp + e, q.Ri + (size_t)t * nu * nu + aa * nu + bb);
+            else
+                Rp[e] = 0.f;
         }
     }
 }
@@ -985,6 +998,7 @@ __global__ void __launch_bounds__(NT, 4) k_bcol(RoundArgs<NR> a) {
             col_stage<NXP, NUP>(q, t, q.s0 >= q.Np, Gp, Kp, Rp, NT);
             staged = key;
         }
+        cp_wait();
         __syncthreads();  // the matrices, the next ticket and the dependency wait
         const int col = threadIdx.x;
         if (col < tk.ncols) {
