@@ -90,12 +90,15 @@ __device__ __forceinline__ long long doff(const GroupDev &g, int i) {
 // column c of a stage with n nodes is instance c / n, node soff_t + c % n.  A round is one
 // persistent launch (one wave of CTAs) that hands the tiles out in ticket order: the backward
 // tiles by height (stage N_g - 1 - p of every group g, for p = 0, 1, ...), then the forward tiles
-// by depth.  A tile first waits (bounded) until every tile of the (group, stage, pass) it reads
-// is done: backward (g, t) on backward (g, t + 1) (the leaves' s comes from y), forward (g, t) on
-// forward (g, t - 1), forward (g, 0) on backward (g, 0).  Those tiles hold earlier tickets and
-// every CTA is resident, so every wait ends; a wait that gives up raises an error word, and the
-// round runs to its end without that input.  Data other CTAs write during the round (s, ubar,
-// x) is read through L2.
+// by depth.  Each tile raises its own done flag, and first waits (bounded) for the flags of the
+// tiles that hold the columns it reads: column c of stage t has children c b_t + j at stage t + 1
+// and parent floor(c / b_{t-1}) at stage t - 1 (instances stay contiguous), so backward (g, t)
+// waits on the backward tiles of (g, t + 1) covering its children (the leaves' s comes from y),
+// forward (g, t) on the forward tiles of (g, t - 1) covering its parents, forward (g, 0) on the
+// backward tile of (g, 0) with its columns (which, transitively, covers every backward tile of
+// its instances).  Those tiles hold earlier tickets and every CTA is resident, so every wait
+// ends; a wait that gives up raises an error word, and the round runs to its end without that
+// input.  Data other CTAs write during the round (s, ubar, x) is read through L2.
 // ---------------------------------------------------------------------------------------------
 struct Task {  // set-up passes (gamma): a tile of kGC columns of one (group, stage)
     int group, stage, col0, ncols;
@@ -105,9 +108,8 @@ constexpr int kGC = 64;
 struct RTask {
     int group, stage, col0, ncols;
     int pass;       // 0 backward, 1 forward
-    int wait_ctr;   // counter to wait on (-1: none)
-    int wait_need;  // tiles that counter must reach
-    int done_ctr;   // counter this tile increments when done
+    int dep0, ndep; // the tiles (ticket indices dep0 .. dep0 + ndep - 1) whose flags it waits on
+    int pad;
 };
 
 template <int NR>
@@ -124,7 +126,7 @@ struct RoundArgs {
     float *s, *ubar, *xs;  // scratch; second right-hand side at +stride
     long long s_stride, u_stride;
     const int *active;    // per instance (null: all active)
-    unsigned *ctrs;       // tiles done per (group, stage, pass)
+    unsigned *ctrs;       // done flag per tile (ticket index)
     unsigned *ticket;     // next tile to hand out
     int *err;             // raised by a dependency wait that gave up
     int homog, scaled;
@@ -313,6 +315,12 @@ __device__ void wait_count(const unsigned *c, unsigned need, int *err) {
         if (*(volatile int *)err) return;
     }
     atomicCAS(err, 0, 1);
+}
+
+// The first warp waits for a tile's dependencies, one flag per lane at a time.
+template <int NR>
+__device__ __forceinline__ void wait_deps(const RoundArgs<NR> &a, const RTask &tk) {
+    for (int d = threadIdx.x; d < tk.ndep; d += 32) wait_count(a.ctrs + tk.dep0 + d, 1u, a.err);
 }
 
 // Staging copies of the stage matrices: one 4-byte asynchronous global-to-shared copy per entry, so
@@ -678,9 +686,9 @@ __global__ void __launch_bounds__(NT) k_bround(RoundArgs<NR> a) {
         const int k = s_tick[it & 1];
         if (k >= a.ntasks) return;
         const RTask tk = a.tasks[k];
-        if (threadIdx.x == 0) {
-            s_tick[(it + 1) & 1] = (int)atomicAdd(a.ticket, 1u);
-            if (tk.wait_ctr >= 0) wait_count(a.ctrs + tk.wait_ctr, (unsigned)tk.wait_need, a.err);
+        if (threadIdx.x < 32) {
+            if (threadIdx.x == 0) s_tick[(it + 1) & 1] = (int)atomicAdd(a.ticket, 1u);
+            wait_deps(a, tk);
         }
         __syncthreads();
         if (tk.pass == 0)
@@ -691,7 +699,7 @@ __global__ void __launch_bounds__(NT) k_bround(RoundArgs<NR> a) {
         __syncthreads();
         if (threadIdx.x == 0) {
             __threadfence();
-            atomicAdd(a.ctrs + tk.done_ctr, 1u);
+            atomicAdd(a.ctrs + k, 1u);
         }
     }
 }
@@ -986,9 +994,9 @@ __global__ void __launch_bounds__(NT, 4) k_bcol(RoundArgs<NR> a) {
         const int k = s_tick[it & 1];
         if (k >= a.ntasks) return;
         const RTask tk = a.tasks[k];
-        if (threadIdx.x == 0) {
-            s_tick[(it + 1) & 1] = (int)atomicAdd(a.ticket, 1u);
-            if (tk.wait_ctr >= 0) wait_count(a.ctrs + tk.wait_ctr, (unsigned)tk.wait_need, a.err);
+        if (threadIdx.x < 32) {
+            if (threadIdx.x == 0) s_tick[(it + 1) & 1] = (int)atomicAdd(a.ticket, 1u);
+            wait_deps(a, tk);
         }
         const int t = tk.stage;
         const Geo q = load_geo(a.groups[tk.group], t);
@@ -1013,7 +1021,7 @@ __global__ void __launch_bounds__(NT, 4) k_bcol(RoundArgs<NR> a) {
         __syncthreads();
         if (threadIdx.x == 0) {
             __threadfence();
-            atomicAdd(a.ctrs + tk.done_ctr, 1u);
+            atomicAdd(a.ctrs + k, 1u);
         }
     }
 }
@@ -1729,52 +1737,67 @@ STO_API sto_status stobatch_create(const sto_group_desc *groups, int32_t ngroups
         for (int c0 = 0; c0 < cols; c0 += kGC) b->tasks.push_back(Task{gi, t, c0, std::min(kGC, cols - c0)});
     };
     // solve-round tiles in ticket order, per tile variant: backward by height, then forward by
-    // depth; counter (g, t, pass) = cbase[g] + pass (N_g + 1) + t
+    // depth; first[cbase[g] + pass (N_g + 1) + t] = ticket of the first tile of (g, t, pass)
     std::vector<int> cbase(ngroups);
-    b->nctr = 0;
+    int nsets = 0;
     b->xu = 48;
     int maxnx = 0, maxnu = 0;
     for (int gi = 0; gi < ngroups; ++gi) {
-        cbase[gi] = b->nctr;
-        b->nctr += 2 * (b->groups[gi].N + 1);
+        cbase[gi] = nsets;
+        nsets += 2 * (b->groups[gi].N + 1);
         if (b->groups[gi].nx > 32 || b->groups[gi].nu > 16) b->xu = 96;
         maxnx = std::max(maxnx, b->groups[gi].nx);
         maxnu = std::max(maxnu, b->groups[gi].nu);
     }
     b->nxp = maxnx <= 16 ? 16 : (maxnx <= 24 ? 24 : 32);
     b->nup = maxnu <= 8 ? 8 : 16;
+    b->nctr = 0;
     for (int v = 0; v < kTileVars; ++v) {
         const int tc = kTileCols[v];
-        auto ntiles = [&](int gi, int t) {
-            const GroupDev &g = b->groups[gi];
-            return ((g.soff[t + 1] - g.soff[t]) * g.I + tc - 1) / tc;
-        };
-        auto add = [&](int gi, int t, int pass, int wctr, int wneed) {
+        std::vector<int> first(nsets, -1);
+        auto bt_of = [&](const GroupDev &g, int t) { return t < g.s ? g.b : 1; };  // children per node of stage t
+        // tiles of (gi, t, pass) columns [c0, c0 + ncols); dep(c0, ncols) -> the dependency range
+        auto add = [&](int gi, int t, int pass, auto dep) {
             const GroupDev &g = b->groups[gi];
             const int cols = (g.soff[t + 1] - g.soff[t]) * g.I;
-            const int done = cbase[gi] + pass * (g.N + 1) + t;
-            for (int c0 = 0; c0 < cols; c0 += tc)
-                b->rtasks[v].push_back(RTask{gi, t, c0, std::min(tc, cols - c0), pass, wctr, wneed, done});
+            first[cbase[gi] + pass * (g.N + 1) + t] = (int)b->rtasks[v].size();
+            for (int c0 = 0; c0 < cols; c0 += tc) {
+                const int nc = std::min(tc, cols - c0);
+                int d0 = -1, nd = 0;
+                dep(c0, nc, d0, nd);
+                b->rtasks[v].push_back(RTask{gi, t, c0, nc, pass, d0, nd, 0});
+            }
         };
         for (int p = 0; p < b->maxN; ++p)
             for (int gi = 0; gi < ngroups; ++gi) {
                 const GroupDev &g = b->groups[gi];
                 if (g.N <= p) continue;
                 const int t = g.N - 1 - p;
-                if (t + 1 < g.N)
-                    add(gi, t, 0, cbase[gi] + t + 1, ntiles(gi, t + 1));
-                else
-                    add(gi, t, 0, -1, 0);
+                add(gi, t, 0, [&](int c0, int nc, int &d0, int &nd) {
+                    if (t + 1 >= g.N) return;  // children are leaves: s from y
+                    const int bt = bt_of(g, t), f = first[cbase[gi] + t + 1];
+                    const int lo = c0 * bt / tc, hi = ((c0 + nc) * bt - 1) / tc;
+                    d0 = f + lo;
+                    nd = hi - lo + 1;
+                });
             }
         for (int p = 0; p <= b->maxN; ++p)
             for (int gi = 0; gi < ngroups; ++gi) {
                 const GroupDev &g = b->groups[gi];
                 if (g.N < p) continue;
-                if (p == 0)
-                    add(gi, 0, 1, cbase[gi] + 0, ntiles(gi, 0));  // the backward pass of stage 0
-                else
-                    add(gi, p, 1, cbase[gi] + (g.N + 1) + p - 1, ntiles(gi, p - 1));
+                add(gi, p, 1, [&](int c0, int nc, int &d0, int &nd) {
+                    if (p == 0) {  // the backward tile of stage 0 with the same columns
+                        d0 = first[cbase[gi] + 0] + c0 / tc;
+                        nd = 1;
+                        return;
+                    }
+                    const int bp = bt_of(g, p - 1), f = first[cbase[gi] + (g.N + 1) + p - 1];
+                    const int lo = c0 / bp / tc, hi = (c0 + nc - 1) / bp / tc;
+                    d0 = f + lo;
+                    nd = hi - lo + 1;
+                });
             }
+        b->nctr = std::max(b->nctr, (int)b->rtasks[v].size());
     }
     for (int p = 0; p < b->maxN; ++p) {
         b->bwd_phase.push_back((int)b->tasks.size());
@@ -1801,7 +1824,7 @@ STO_API sto_status stobatch_create(const sto_group_desc *groups, int32_t ngroups
     b->o_blk = add(b->nblocks * 4);
     b->o_tasks = add(b->tasks.size() * sizeof(Task));
     for (int v = 0; v < kTileVars; ++v) b->o_rtask[v] = add(b->rtasks[v].size() * sizeof(RTask));
-    b->o_ctr = add((size_t)(b->nctr + 1) * 4);  // the counters, then the ticket
+    b->o_ctr = add((size_t)(b->nctr + 1) * 4);  // the tiles' done flags, then the ticket
     size_t gsz = 0, ksz = 0, rsz = 0, absz = 0, psz = 0, scsz = 0;
     for (auto &g : b->groups) {
         gsz += (size_t)g.nx * g.nxu;
