@@ -229,9 +229,10 @@ STO_API sto_status stotree_solve_step(stotree_t h, const void *y, const void *x0
  * timing (stotree_set_timing) does not cover this call.
  *   y, x0, hx, homogeneous, scaled: as stotree_solve_step with nrhs = 1.
  * Limit: with esz = sizeof(real) and a256(v) = v rounded up to a multiple of 256, the call
- * needs 2 (a256(Nn nx esz) + a256(Np nu esz)) + a256(8 Nn) + 256 bytes of scratch (s, ubar,
- * x, u, the round's dependency flags and its work counter), at most 33554432 (32 MiB); larger
- * problems get STO_ERR_INVALID_ARG and a message in stotree_last_error.  The first call on a
+ * needs a256(Np nu esz) + 2 a256(2 Nn nx esz) + a256(2 Np nu esz) + a256(8 Nn) + 256 bytes of
+ * scratch (ubar; s, x and u as tagged words, 8 bytes per 4 bytes of a value; the round's
+ * dependency flags and its work counter), at most 33554432 (32 MiB); larger problems get
+ * STO_ERR_INVALID_ARG and a message in stotree_last_error.  The first call on a
  * device looks the array's address up (cudaGetSymbolAddress) with that device current; make
  * that first call before any stream capture.  All calls share the one array: calls that
  * overlap on the GPU (other streams, other handles) race and give wrong results.  The

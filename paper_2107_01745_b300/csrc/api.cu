@@ -115,10 +115,13 @@ static void compute_layout(stotree_t h) {
     L.c = add(Nn * nx * es);
     L.cost = add(2 * (2 * nx + nu) * es);
     L.box = add(5 * (nx + nu) * es);
-    L.s = add(kMaxRhs * Nn * nx * es);
     L.ubar = add(kMaxRhs * Np * nu * es);
     L.xs = add(kMaxRhs * Nn * nx * es);
     L.us = add(kMaxRhs * Np * nu * es);
+    L.ts = add(kMaxRhs * Nn * nx * 2 * es);  // one 8-byte word per 4 bytes of a value
+    L.txs = add(kMaxRhs * Nn * nx * 2 * es);
+    L.tus = add(kMaxRhs * Np * nu * 2 * es);
+    L.tus_end = L.tus + kMaxRhs * Np * nu * 2 * es;
     L.vec = add(kNumVec * mpad * es);
     L.ringS = add((kMaxMem + 1) * mpad * es);
     L.ringY = add((kMaxMem + 1) * mpad * es);

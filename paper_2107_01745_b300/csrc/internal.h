@@ -68,8 +68,10 @@ struct Layout {
     size_t G, RK, gu, gx, c;     // RK = [-Rbar^-1 | K] per nonleaf node (nu rows of ldrk)
     size_t Gt, Kt;               // forward pass: [A | B]' per node (nx+nu rows of ldk), K' (nx rows of ldr)
     size_t cost, box;            // real copies: W (Q|R|PN), ell (q|r|pN), lo/hi/rho/delta/kind (x|u)
-    // solve scratch (real)
-    size_t s, ubar, xs, us;
+    // solve scratch: ubar, x, u (real); tagged s, x, u (64-bit words, sizeof(real) / 4 per
+    // value; [ts, tus_end) is one range)
+    size_t ubar, xs, us;
+    size_t ts, txs, tus, tus_end;
     // solver
     size_t vec;                  // kNumVec vectors of m reals
     size_t ringS, ringY;         // (kMaxMem+1) vectors of m reals each
@@ -172,9 +174,11 @@ sto_status factor_run(stotree_t h, cudaStream_t st);
 // or caller memory).  scaled: input is ybar and output S Hx.  With `scratch`, the round
 // (one right-hand side) keeps its intermediate vectors there instead of in the workspace.
 struct SolveScratch {
-    void *s, *ubar, *xs, *us;  // real [Nn][nx], [Np][nu], [Nn][nx], [Np][nu]
+    void *ubar;                // real [Np][nu]
+    void *ts, *txs, *tus;      // tagged words, sizeof(real) / 4 per value: [Nn][nx], [Nn][nx], [Np][nu]
     void *flags;               // unsigned [2][Nn] (cleared by the round)
     void *ticket;              // unsigned long long (cleared by the round)
+    unsigned epoch;            // the round's epoch: never used before with these tagged words
 };
 // With general maps the round computes H'y, runs Algorithm 3/4 in the [x; u] layout into the
 // primal vectors pout[k] (the workspace's when pout is null; msel reals, scaled like hx) and

@@ -16,10 +16,10 @@
 // Scheduling.  "For k = N-1..0, in parallel over nodes(k)" needs a grid-wide barrier per
 // stage; instead the round is a dataflow over work items, each a path segment of up to
 // kSegMax nodes (api.cu: build_segments).  A ticket counter hands the items out in an order in
-// which every item depends only on earlier ones; an item waits (bounded) on per-node epoch
-// flags of the segments it depends on, so a CTA holding a ticket never waits on a later one
-// and all CTAs are resident (grid = occupancy): no deadlock.  Inside a segment the recursion's
-// vector stays in shared memory.
+// which every item depends only on earlier ones; an item waits (bounded) for the vectors of the
+// segments it depends on, so a CTA holding a ticket never waits on a later one and all CTAs are
+// resident (grid = occupancy): no deadlock.  Inside a segment the recursion's vector stays in
+// shared memory; between segments it travels as tagged words (below).
 //
 // Data movement.  The node matrices are independent of the solve, so one producer warp per
 // CTA streams the matrices of its items with cp.async.bulk (TMA bulk copies) into a ring of
@@ -212,6 +212,65 @@ __device__ __forceinline__ void wait_flag(const unsigned *f, unsigned epoch, int
     }
     atomicCAS(err, 0, 1);
 }
+// Tagged hand-off of a vector between work items (a segment's last s in the backward pass, its
+// last [x; u] in the forward pass).  Each 32 bits of a value travel as one 64-bit word
+// {bits, epoch}, written with a relaxed store by the thread that computed the value and polled
+// by the thread that needs it: a word carrying the round's epoch is that value (a 64-bit
+// aligned access is single-copy atomic), so the writer needs no release fence and the reader no
+// flag and no second load.  On the paper-scale tree the binary top stages form the round's
+// serial path, and this hand-off is the largest part of each of their steps.
+__device__ __forceinline__ void st_relaxed_u64(unsigned long long *p, unsigned long long v) {
+    asm volatile("st.relaxed.gpu.global.u64 [%0], %1;" ::"l"(p), "l"(v) : "memory");
+}
+__device__ __forceinline__ unsigned long long ld_relaxed_u64(const unsigned long long *p) {
+    unsigned long long v;
+    asm volatile("ld.relaxed.gpu.global.u64 %0, [%1];" : "=l"(v) : "l"(p) : "memory");
+    return v;
+}
+// Bounded poll of one tagged word, with the limits and the error reporting of wait_flag.
+__device__ __forceinline__ unsigned poll_word(const unsigned long long *w, unsigned epoch, int *err,
+                                              unsigned long long limit) {
+    unsigned long long v = ld_relaxed_u64(w);
+    if ((unsigned)(v >> 32) == epoch) return (unsigned)v;
+    const unsigned long long t0 = now_ns();
+    while (now_ns() - t0 < limit) {
+        for (int it = 0; it < 32; ++it) {
+            v = ld_relaxed_u64(w);
+            if ((unsigned)(v >> 32) == epoch) return (unsigned)v;
+            __nanosleep(32);
+        }
+        if (*(volatile int *)err) return (unsigned)v;
+    }
+    atomicCAS(err, 0, 1);
+    return (unsigned)v;
+}
+template <class T>
+struct Tagged;
+template <>
+struct Tagged<float> {
+    static constexpr int W = 1;  // words per value
+    __device__ static void put(unsigned long long *w, float v, unsigned epoch) {
+        st_relaxed_u64(w, ((unsigned long long)epoch << 32) | __float_as_uint(v));
+    }
+    __device__ static float get(const unsigned long long *w, unsigned epoch, int *err, unsigned long long limit) {
+        return __uint_as_float(poll_word(w, epoch, err, limit));
+    }
+};
+template <>
+struct Tagged<double> {
+    static constexpr int W = 2;
+    __device__ static void put(unsigned long long *w, double v, unsigned epoch) {
+        const unsigned long long b = (unsigned long long)__double_as_longlong(v);
+        st_relaxed_u64(w, ((unsigned long long)epoch << 32) | (b & 0xffffffffull));
+        st_relaxed_u64(w + 1, ((unsigned long long)epoch << 32) | (b >> 32));
+    }
+    __device__ static double get(const unsigned long long *w, unsigned epoch, int *err, unsigned long long limit) {
+        const unsigned lo = poll_word(w, epoch, err, limit);
+        const unsigned hi = poll_word(w + 1, epoch, err, limit);
+        return __longlong_as_double((long long)(((unsigned long long)hi << 32) | lo));
+    }
+};
+
 // Asynchronous element copies global -> shared (the small per-node vectors); the issuing thread
 // waits for its own copies with cp_async_wait, a named barrier then publishes them.
 template <int B>
@@ -240,9 +299,10 @@ struct TreeArgs {
     const T *y[kMaxRhs];
     T *h[kMaxRhs];
     const T *x0;
-    T *s, *ubar, *xs, *us;  // scratch, [kMaxRhs][Nn][nx] and [kMaxRhs][Np][nu]
+    T *ubar, *xs, *us;      // scratch, [kMaxRhs][Np][nu], [kMaxRhs][Nn][nx], [kMaxRhs][Np][nu] (xs, us may be null)
+    unsigned long long *ts, *txs, *tus;  // tagged s, x, u of the segments' last nodes (Tagged<T>::W words per value)
     long long s_stride, u_stride;
-    unsigned *flags;        // [2][Nn]
+    unsigned *flags;        // [2][Nn]: flags[0] = the root's backward step is done
     unsigned long long *ticket;
     int *err;
     unsigned long long wait_ns;  // limit of each dependency wait
@@ -493,11 +553,10 @@ struct Consumer {
                             s_in[e] = T(0.5) * scj * a.y[k][o + r] + cj * a.pN[r];
                         }
                     } else {
-                        if (tid == 0) wait_flag(a.flags + j, epoch, a.err, a.wait_ns);
-                        cbar();
                         for (int e = tid; e < NR * nx; e += kCW * 32) {
                             const int k = e / nx, r = e - k * nx;
-                            s_in[e] = __ldcg(a.s + k * a.s_stride + (long long)j * nx + r);
+                            s_in[e] = Tagged<T>::get(a.ts + (k * a.s_stride + (long long)j * nx + r) * Tagged<T>::W,
+                                                     epoch, a.err, a.wait_ns);
                         }
                     }
                     cbar();
@@ -537,13 +596,15 @@ struct Consumer {
                         const T val = T(0.5) * sci * pre[k * a.nxu + cc] + accs[k * a.lda + cc] +
                                       xu[k * a.lda + a.ldr + cc] + (a.homog ? T(0) : pre[NR * a.nxu + nu + cc]);
                         s_out[e] = val;
-                        if (f & F_END_ITEM) a.s[k * a.s_stride + (long long)i * nx + cc] = val;
+                        if (f & F_END_ITEM)
+                            Tagged<T>::put(a.ts + (k * a.s_stride + (long long)i * nx + cc) * Tagged<T>::W, val, epoch);
                     }
                     zero_acc();
                     cbar();
-                    // the named barrier above orders every consumer's stores before thread 0's
-                    // release store (release is cumulative), so no separate fence is needed
-                    if ((f & F_END_ITEM) && tid == 0) st_release(a.flags + i, epoch);
+                    // the forward launch's root step starts from this flag; the named barrier above
+                    // orders every consumer's stores before thread 0's release store (release is
+                    // cumulative), so no separate fence is needed
+                    if (i == 0 && tid == 0) st_release(a.flags, epoch);
                 }
             }
             } else {
@@ -560,21 +621,20 @@ struct Consumer {
                         }
                     } else {
                         const int i = a.parent[j];
-                        if (tid == 0) wait_flag(a.flags + a.Nn + i, epoch, a.err, a.wait_ns);
-                        cbar();
                         for (int e = tid; e < NR * a.ldg; e += kCW * 32) {
                             const int k = e / a.ldg, cc = e - k * a.ldg;
                             T val = T(0);
                             if (cc < nx)
-                                val = __ldcg(a.xs + k * a.s_stride + (long long)i * nx + cc);
+                                val = Tagged<T>::get(a.txs + (k * a.s_stride + (long long)i * nx + cc) * Tagged<T>::W,
+                                                     epoch, a.err, a.wait_ns);
                             else if (cc < nx + nu)
-                                val = __ldcg(a.us + k * a.u_stride + (long long)i * nu + cc - nx);
+                                val = Tagged<T>::get(a.tus + (k * a.u_stride + (long long)i * nu + cc - nx) * Tagged<T>::W,
+                                                     epoch, a.err, a.wait_ns);
                             xu[e] = val;
                         }
                     }
-                    // c^j and ubar^j, consumed at the end of the node's G and K runs.  ubar^j comes
-                    // from the backward pass: read only after this item's dependency wait, which
-                    // (through the forward chain from the root) follows the whole backward pass.
+                    // c^j and ubar^j, consumed at the end of the node's G and K runs (ubar^j was
+                    // written by the backward launch, which ended before this one started)
                     if (!a.homog) prefetch(0, a.c + (size_t)j * nx, nx);
                     if (j < a.Np)
                         for (int k = 0; k < NR; ++k)
@@ -603,7 +663,7 @@ struct Consumer {
                         const int k = e / nx, r = e - k * nx;
                         const T val = xj[k * a.ldk + r];
                         a.h[k][oj + r] = scj * val;
-                        a.xs[k * a.s_stride + (long long)j * nx + r] = val;
+                        if (a.xs) a.xs[k * a.s_stride + (long long)j * nx + r] = val;
                     }
                 }
             } else if (md.kind == KIND_FK) {
@@ -638,13 +698,17 @@ struct Consumer {
                         const int k = e / (nx + nu), r = e - k * (nx + nu);
                         const T val = r < nx ? xj[k * a.ldk + r] : uj[k * a.ldr + r - nx];
                         a.h[k][oj + r] = scj * val;
-                        if (r < nx)
-                            a.xs[k * a.s_stride + (long long)j * nx + r] = val;
-                        else
-                            a.us[k * a.u_stride + (long long)j * nu + r - nx] = val;
+                        if (r < nx) {
+                            const long long o = k * a.s_stride + (long long)j * nx + r;
+                            if (a.xs) a.xs[o] = val;
+                            if (f & F_END_ITEM) Tagged<T>::put(a.txs + o * Tagged<T>::W, val, epoch);
+                        } else {
+                            const long long o = k * a.u_stride + (long long)j * nu + r - nx;
+                            if (a.us) a.us[o] = val;
+                            if (f & F_END_ITEM) Tagged<T>::put(a.tus + o * Tagged<T>::W, val, epoch);
+                        }
                     }
                     cbar();
-                    if ((f & F_END_ITEM) && tid == 0) st_release(a.flags + a.Nn + j, epoch);
                 }
             }
             }
@@ -845,25 +909,29 @@ sto_status solve_impl(stotree_t h, const void *const *y, const void *x0, void *c
         }
     }
     if (scratch) {  // caller scratch for one right-hand side: its flags and counter are cleared first
-        a.s = static_cast<T *>(scratch->s);
         a.ubar = static_cast<T *>(scratch->ubar);
-        a.xs = static_cast<T *>(scratch->xs);
-        a.us = static_cast<T *>(scratch->us);
+        a.xs = a.us = nullptr;  // the trajectory is not kept
+        a.ts = static_cast<unsigned long long *>(scratch->ts);
+        a.txs = static_cast<unsigned long long *>(scratch->txs);
+        a.tus = static_cast<unsigned long long *>(scratch->tus);
         a.flags = static_cast<unsigned *>(scratch->flags);
         a.ticket = static_cast<unsigned long long *>(scratch->ticket);
         STO_CUDA(h, cudaMemsetAsync(scratch->flags, 0, (size_t)2 * h->Nn * sizeof(unsigned), st));
         STO_CUDA(h, cudaMemsetAsync(scratch->ticket, 0, sizeof(unsigned long long), st));
-        epoch = 1;
+        epoch = scratch->epoch;  // unique per call on the device: stale tagged words never match
         tbase = 0;
     } else {
-        a.s = h->at<T>(L.s);
         a.ubar = h->at<T>(L.ubar);
         a.xs = h->at<T>(L.xs);
         a.us = h->at<T>(L.us);
+        a.ts = h->at<unsigned long long>(L.ts);
+        a.txs = h->at<unsigned long long>(L.txs);
+        a.tus = h->at<unsigned long long>(L.tus);
         a.flags = h->at<unsigned>(L.flags);
         a.ticket = h->at<unsigned long long>(L.ticket);
-        if (h->epoch == 0xffffffffu) {  // epochs wrapped: start the flags over
+        if (h->epoch == 0xffffffffu) {  // epochs wrapped: start the flags and tagged words over
             STO_CUDA(h, cudaMemsetAsync(a.flags, 0, (size_t)2 * h->Nn * sizeof(unsigned), st));
+            STO_CUDA(h, cudaMemsetAsync(h->ws + L.ts, 0, L.tus_end - L.ts, st));
             h->epoch = 0;
         }
         epoch = ++h->epoch;
@@ -940,8 +1008,7 @@ sto_status check_round_error(stotree_t h, cudaStream_t st) {
     STO_CUDA(h, cudaMemsetAsync(h->ws + h->L.ticket, 0, 64, st));
     STO_CUDA(h, cudaMemsetAsync(dev_err, 0, sizeof(int), st));
     STO_CUDA(h, cudaStreamSynchronize(st));
-    h->epoch = 0;
-    h->ticket_base = 0;
+    h->ticket_base = 0;  // the epoch keeps counting: tagged words of the failed round never match again
     h->err = err == 1 ? "a solve round gave up waiting for a dependency" : "a solve round gave up waiting for a copy";
     return STO_ERR_TIMEOUT;
 }

@@ -167,7 +167,7 @@ def test_noalloc_refusals_need_no_device(libso):
 
     def need(k):
         nn = k + 1
-        return 2 * (a256(4 * nn * nx) + a256(4 * nu)) + a256(8 * nn) + 256
+        return a256(4 * nu) + 2 * a256(8 * nn * nx) + a256(8 * nu) + a256(8 * nn) + 256
 
     kmax = 1
     while need(kmax + 1) <= 32 << 20:

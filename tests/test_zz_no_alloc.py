@@ -81,7 +81,7 @@ def test_noalloc_paper_scale_and_limit(cuda_device):
         assert _rel2(out, ref) < 1e-5
     # a tree needing more scratch than the fixed array: refused before any device work
     from paper_2107_01745_b300.stotree import _TreeDesc, lib
-    t = W.tree_from_branching([2] * 13)  # 16383 nodes; with nx=400, nu=100: about 59 MB of scratch
+    t = W.tree_from_branching([2] * 13)  # 16383 nodes; with nx=400, nu=100: about 115 MB of scratch
     parent = np.ascontiguousarray(t.parent, dtype=np.int32)
     prob = np.ascontiguousarray(t.prob)
     desc = _TreeDesc(t.num_nodes, t.horizon, 400, 100, parent.ctypes.data, prob.ctypes.data)
