@@ -50,7 +50,8 @@ enum : int {
     F_INSEG = 8,        // the child (backward) / parent (forward) is the previous node of the segment
     F_END_NODE = 16,    // last chunk of the node's step
     F_END_ITEM = 32,    // last chunk of the work item (segment)
-    F_ROOT = 64         // forward root step
+    F_ROOT = 64,        // forward root step
+    F_PUB_X = 128       // forward: the node's x is published (tagged) as soon as it is known
 };
 
 struct Meta {
@@ -411,12 +412,14 @@ struct Producer {
                     const bool last_node = k == f1 - 1;
                     const int endf = F_END_NODE | (last_node ? F_END_ITEM : 0);
                     const bool nonleaf = j < a.Np;
+                    // a segment's last nonleaf node hands x^j to its children before its K step
+                    const int pubx = nonleaf && last_node ? F_PUB_X : 0;
                     if (j != 0)
                         matrix(KIND_FG, j, -1, a.Gt + (size_t)j * (nx + nu) * a.ldk, nx + nu, a.ldk, a.rpcGt,
-                               k > f0 ? F_INSEG : 0, nonleaf ? 0 : endf);
+                               k > f0 ? F_INSEG : 0, nonleaf ? pubx : endf);
                     if (nonleaf)
-                        matrix(KIND_FK, j, -1, a.Kt + (size_t)j * nx * a.ldr, nx, a.ldr, a.rpcKt, j == 0 ? F_ROOT : 0,
-                               endf);
+                        matrix(KIND_FK, j, -1, a.Kt + (size_t)j * nx * a.ldr, nx, a.ldr, a.rpcKt,
+                               j == 0 ? F_ROOT | pubx : 0, endf);
                 }
             }
         }
@@ -513,6 +516,7 @@ struct Consumer {
     __device__ void run() {
         const int nx = a.nx, nu = a.nu;
         unsigned long long n = 0;
+        int upend = -1;  // forward: parent whose u^i this node's [x; u] still waits for
         zero_acc();
         for (;;) {
             const int slot = (int)(n % kSlots);
@@ -620,18 +624,18 @@ struct Consumer {
                             xu[e] = cc < nx ? xj[k * a.ldk + cc] : (cc < nx + nu ? uj[k * a.ldr + cc - nx] : T(0));
                         }
                     } else {
+                        // the parent's x^i now; its u^i (published after the parent's K step)
+                        // only before the first chunk that reaches the u rows of G^j'
                         const int i = a.parent[j];
                         for (int e = tid; e < NR * a.ldg; e += kCW * 32) {
                             const int k = e / a.ldg, cc = e - k * a.ldg;
-                            T val = T(0);
                             if (cc < nx)
-                                val = Tagged<T>::get(a.txs + (k * a.s_stride + (long long)i * nx + cc) * Tagged<T>::W,
-                                                     epoch, a.err, a.wait_ns);
-                            else if (cc < nx + nu)
-                                val = Tagged<T>::get(a.tus + (k * a.u_stride + (long long)i * nu + cc - nx) * Tagged<T>::W,
-                                                     epoch, a.err, a.wait_ns);
-                            xu[e] = val;
+                                xu[e] = Tagged<T>::get(a.txs + (k * a.s_stride + (long long)i * nx + cc) * Tagged<T>::W,
+                                                       epoch, a.err, a.wait_ns);
+                            else if (cc >= nx + nu)
+                                xu[e] = T(0);
                         }
+                        upend = i;
                     }
                     // c^j and ubar^j, consumed at the end of the node's G and K runs (ubar^j was
                     // written by the backward launch, which ended before this one started)
@@ -640,6 +644,16 @@ struct Consumer {
                         for (int k = 0; k < NR; ++k)
                             prefetch(nx + k * nu, a.ubar + k * a.u_stride + (long long)j * nu, nu);
                     cp_async_commit();
+                    cbar();
+                }
+                if (upend >= 0 && md.row0 + md.nrows > nx) {
+                    for (int e = tid; e < NR * nu; e += kCW * 32) {
+                        const int k = e / nu, cc = e - k * nu;
+                        xu[k * a.ldg + nx + cc] =
+                            Tagged<T>::get(a.tus + (k * a.u_stride + (long long)upend * nu + cc) * Tagged<T>::W, epoch,
+                                           a.err, a.wait_ns);
+                    }
+                    upend = -1;
                     cbar();
                 }
                 axpy_rows(M, a.ldk, md.nrows, xu, a.ldg, md.row0);
@@ -655,6 +669,12 @@ struct Consumer {
                         }
                     zero_acc();
                     cbar();
+                    if (f & F_PUB_X)
+                        for (int e = tid; e < NR * nx; e += kCW * 32) {
+                            const int k = e / nx, r = e - k * nx;
+                            Tagged<T>::put(a.txs + (k * a.s_stride + (long long)j * nx + r) * Tagged<T>::W,
+                                           xj[k * a.ldk + r], epoch);
+                        }
                 }
                 if (f & F_END_NODE) {  // leaf: no K step
                     const long long oj = dual_off(j, a.Np, a.nxu, nx);
@@ -679,6 +699,11 @@ struct Consumer {
                         xj[e] = (r < nx && !a.homog) ? a.x0[r] : T(0);
                     }
                     cbar();
+                    if (f & F_PUB_X)
+                        for (int e = tid; e < NR * nx; e += kCW * 32) {
+                            const int k = e / nx, r = e - k * nx;
+                            Tagged<T>::put(a.txs + (k * a.s_stride + r) * Tagged<T>::W, xj[k * a.ldk + r], epoch);
+                        }
                 }
                 axpy_rows(M, a.ldr, md.nrows, xj, a.ldk, md.row0);
                 __syncwarp();
@@ -698,10 +723,8 @@ struct Consumer {
                         const int k = e / (nx + nu), r = e - k * (nx + nu);
                         const T val = r < nx ? xj[k * a.ldk + r] : uj[k * a.ldr + r - nx];
                         a.h[k][oj + r] = scj * val;
-                        if (r < nx) {
-                            const long long o = k * a.s_stride + (long long)j * nx + r;
-                            if (a.xs) a.xs[o] = val;
-                            if (f & F_END_ITEM) Tagged<T>::put(a.txs + o * Tagged<T>::W, val, epoch);
+                        if (r < nx) {  // x^j was handed on after the G step
+                            if (a.xs) a.xs[k * a.s_stride + (long long)j * nx + r] = val;
                         } else {
                             const long long o = k * a.u_stride + (long long)j * nu + r - nx;
                             if (a.us) a.us[o] = val;
