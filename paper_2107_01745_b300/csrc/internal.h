@@ -48,6 +48,10 @@ struct SolverScalars {
     // reduction bookkeeping
     unsigned int red_counter;
     unsigned int pad2;
+    // look-ahead (an iteration is enqueued before the host reads the previous one's result):
+    // with `lookahead` set, the residual pass sets `stop` once the run has converged or met a
+    // NaN, and every kernel of a later iteration (solve rounds included) then does nothing
+    int lookahead, stop;
 };
 constexpr size_t kScalHead = 112;
 
@@ -185,7 +189,7 @@ struct SolveScratch {
 // writes hx = H p.
 sto_status solve_round(stotree_t h, const void *const *y, const void *x0, void *const *hx, int nrhs,
                        bool homogeneous, bool scaled, cudaStream_t st, const SolveScratch *scratch = nullptr,
-                       void *const *pout = nullptr);
+                       void *const *pout = nullptr, const int *stop = nullptr);
 
 // Grid and shared-memory caps of the one-right-hand-side round, set up ahead of its first launch
 // (called when the factor is computed, so that later rounds do no host-side set-up work).

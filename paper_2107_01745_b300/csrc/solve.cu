@@ -309,6 +309,7 @@ struct TreeArgs {
     unsigned long long wait_ns;  // limit of each dependency wait
     int homog, scaled;
     int rpcG, rpcRK, rpcGt, rpcKt;  // rows per ring slot
+    const int *stop;                // a solver's stop flag (null: always run)
 };
 
 __device__ __forceinline__ long long dual_off(int i, int Np, int nxu, int nx) {
@@ -385,6 +386,13 @@ struct Producer {
     __device__ void run(unsigned long long tbase, int phase) {
         const int nx = a.nx, nu = a.nu;
         const int total = phase == 0 ? a.Tb : a.Tf;
+        if (a.stop && *(volatile const int *)a.stop) {
+            // a look-ahead round of a solver that has stopped: no work, but the tickets of the
+            // launch are drawn all the same (the host's count of the ticket counter stays right)
+            if (blockIdx.x == 0) atomicAdd(a.ticket, (unsigned long long)(total + gridDim.x));
+            emit_end();
+            return;
+        }
         for (;;) {
             if (dead) return;
             const unsigned long long tk = atomicAdd(a.ticket, 1ull) - tbase;
@@ -875,7 +883,7 @@ sto_status prepare_impl(stotree_t h) {
 
 template <class T>
 sto_status solve_impl(stotree_t h, const void *const *y, const void *x0, void *const *hx, int nrhs, bool homog,
-                      bool scaled, cudaStream_t st, const SolveScratch *scratch) {
+                      bool scaled, cudaStream_t st, const SolveScratch *scratch, const int *stop) {
     const Layout &L = h->L;
     TreeArgs<T> a;
     tree_dims(h, a);
@@ -916,6 +924,7 @@ sto_status solve_impl(stotree_t h, const void *const *y, const void *x0, void *c
     a.rpcKt = kChunk / (h->ldr * (int)sizeof(T));
     a.err = h->at<int>(L.fstatus) + 8;
     a.wait_ns = h->wait_ns;
+    a.stop = stop;
     unsigned epoch;
     unsigned long long tbase;
     int &grid = h->grid_ctas[nrhs];
@@ -985,11 +994,11 @@ sto_status prepare_round(stotree_t h) {
 }
 
 sto_status solve_round(stotree_t h, const void *const *y, const void *x0, void *const *hx, int nrhs, bool homog,
-                       bool scaled, cudaStream_t st, const SolveScratch *scratch, void *const *pout) {
+                       bool scaled, cudaStream_t st, const SolveScratch *scratch, void *const *pout, const int *stop) {
     if (scratch && nrhs != 1) return STO_ERR_INVALID_ARG;
     if (!h->fg)
-        return h->prec == STO_FP64 ? solve_impl<double>(h, y, x0, hx, nrhs, homog, scaled, st, scratch)
-                                   : solve_impl<float>(h, y, x0, hx, nrhs, homog, scaled, st, scratch);
+        return h->prec == STO_FP64 ? solve_impl<double>(h, y, x0, hx, nrhs, homog, scaled, st, scratch, stop)
+                                   : solve_impl<float>(h, y, x0, hx, nrhs, homog, scaled, st, scratch, stop);
     // general maps: H'y -> the round in the [x; u] layout -> Hx = H p
     if (scratch) {
         h->err = "the no-allocation solve step takes the selection maps only";
@@ -1005,8 +1014,8 @@ sto_status solve_round(stotree_t h, const void *const *y, const void *x0, void *
         ys[k] = ht;
         ps[k] = pout ? pout[k] : h->ws + h->L.pv + k * spad;
     }
-    const sto_status s = h->prec == STO_FP64 ? solve_impl<double>(h, ys, x0, ps, nrhs, homog, scaled, st, nullptr)
-                                             : solve_impl<float>(h, ys, x0, ps, nrhs, homog, scaled, st, nullptr);
+    const sto_status s = h->prec == STO_FP64 ? solve_impl<double>(h, ys, x0, ps, nrhs, homog, scaled, st, nullptr, stop)
+                                             : solve_impl<float>(h, ys, x0, ps, nrhs, homog, scaled, st, nullptr, stop);
     if (s != STO_OK) return s;
     for (int k = 0; k < nrhs; ++k) {
         const sto_status e = fg_hx(h, ps[k], hx[k], st);

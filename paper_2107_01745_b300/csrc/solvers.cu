@@ -405,6 +405,7 @@ __global__ void __launch_bounds__(kThreads) k_point(DualView<T> dv, const T *__r
                                                     SolverScalars *sc, double *partials, const T *__restrict__ rw,
                                                     const T *__restrict__ hw) {
     __shared__ double tot[9];
+    if (sc->stop) return;  // a look-ahead iteration after the run stopped
     extern __shared__ __align__(16) unsigned char tab_raw[];
     CompTab<T> tab;
     tab.load(dv, reinterpret_cast<T *>(tab_raw));
@@ -484,6 +485,7 @@ __global__ void __launch_bounds__(kThreads) k_point(DualView<T> dv, const T *__r
         }
         if constexpr (BT == 2) sc->r2 = tot[5];
         if (tot[4] > 0.0 || !(tot[0] == tot[0])) sc->nan_flag = 1;
+        if (sc->lookahead && (sc->nan_flag || sc->res_inf <= sc->tol)) sc->stop = 1;
         if (pair && sc->lb_pending_valid) {
             if (tot[1] > sc->eps_curv * tot[2] * tot[3]) {
                 if (sc->lb_count < sc->mem)
@@ -504,6 +506,7 @@ __global__ void __launch_bounds__(kThreads) k_grad(int m, const T *__restrict__ 
                                                    T *ringS, T *ringY, long long vstride, SolverScalars *sc,
                                                    double *partials) {
     __shared__ double tot[8];
+    if (sc->stop) return;
     constexpr int VN = Vec16<T>::n;
     const T lam = (T)sc->lambda;
     const int pair = sc->lb_pending_valid;
@@ -557,6 +560,7 @@ __global__ void __launch_bounds__(kThreads, 4) k_lb_dots(int m, const T *__restr
                                                       const T *ringY, long long vstride, SolverScalars *sc,
                                                       double *partials) {
     __shared__ double tot[4 * MEM];
+    if (sc->stop) return;
     const int cnt = sc->lb_count, head = sc->lb_head, M1 = sc->mem + 1, newp = sc->lb_new_pair;
     if (cnt == 0) {
         if (blockIdx.x == 0 && threadIdx.x == 0) {
@@ -654,6 +658,7 @@ __global__ void __launch_bounds__(kThreads, 4) k_lb_dots(int m, const T *__restr
 template <class T, int MEM>
 __global__ void __launch_bounds__(kThreads, 4) k_lb_dir(int m, const T *__restrict__ g, const T *ringS, const T *ringY,
                                                      long long vstride, const SolverScalars *sc, T *dvec) {
+    if (sc->stop) return;
     const int cnt = sc->lb_count, head = sc->lb_head, M1 = sc->mem + 1;
     const T gamma = (T)sc->gamma;
     T cs[MEM], cy[MEM];
@@ -720,7 +725,7 @@ __global__ void __launch_bounds__(kThreads) k_ls(DualView<T> dv, const T *__rest
                                                  const T *__restrict__ hr, const T *__restrict__ hd, int nama, int e0,
                                                  int nc, int last_group, SolverScalars *sc, double *partials) {
     __shared__ double tot[J];
-    if (sc->ls_done) return;
+    if (sc->ls_done || sc->stop) return;
     const T lam = (T)sc->lambda, ilam = T(1) / lam;
     T tau[J];
 #pragma unroll
@@ -808,6 +813,7 @@ __global__ void __launch_bounds__(kThreads) k_fbstep(DualView<T> dv, T *yb, cons
                                                      const T *__restrict__ hr, const T *__restrict__ hd, int nama,
                                                      T *ringS, long long vstride, SolverScalars *sc, T *rw_out,
                                                      T *hw_out) {
+    if (sc->stop) return;
     const T lam = (T)sc->lambda, ilam = T(1) / lam;
     const T tau = (T)sc->tau;
     const int p = (sc->lb_head + sc->lb_count) % (sc->mem + 1);
@@ -1193,6 +1199,10 @@ sto_status solver_impl(stotree_t h, int method, const sto_opts *o, const void *x
     hs->mem = o->lbfgs_mem;
     hs->max_ls = o->max_ls;
     hs->method = method;
+    // look-ahead needs an iteration whose kernels the host does not have to inspect: a fixed
+    // step (no backtracking test between the kernels) and the selection maps
+    const bool ahead = bt == 0 && !fg;
+    hs->lookahead = ahead ? 1 : 0;
     STO_CUDA(h, cudaMemcpyAsync(sc, hs, sizeof(SolverScalars), cudaMemcpyHostToDevice, st));
     // the host mirror is rewritten below; make sure the upload has consumed it
     STO_CUDA(h, cudaStreamSynchronize(st));
@@ -1216,13 +1226,13 @@ sto_status solver_impl(stotree_t h, int method, const sto_opts *o, const void *x
         const void *ys[1] = {yb};
         void *hs_[1] = {hv};
         void *po[1] = {pvh};
-        return solve_round(h, ys, x0v, hs_, 1, false, true, st, nullptr, fg ? po : nullptr);
+        return solve_round(h, ys, x0v, hs_, 1, false, true, st, nullptr, fg ? po : nullptr, &sc->stop);
     };
     auto lin_solve = [&](T *in, T *out, T *pout) -> sto_status {
         const void *ys[1] = {in};
         void *hs_[1] = {out};
         void *po[1] = {pout};
-        return solve_round(h, ys, nullptr, hs_, 1, true, true, st, nullptr, fg ? po : nullptr);
+        return solve_round(h, ys, nullptr, hs_, 1, true, true, st, nullptr, fg ? po : nullptr, &sc->stop);
     };
 
     k_scale_in<T><<<grid, kThreads, 0, st>>>(dv, static_cast<const T *>(yv), yb);
@@ -1282,24 +1292,11 @@ sto_status solver_impl(stotree_t h, int method, const sto_opts *o, const void *x
     // lambda ||S H x_lin(r)|| > eps'' ||r||, i.e. eq. (simple-backtracking) with
     // T(y) - y = -lambda r and grad fhat(T(y)) - grad fhat(y) = lambda S H x_lin(r)
     auto simple_fails = [&]() { return lam * lam * hs->hr2 > o->bt_param * o->bt_param * hs->r2; };
-    sto_status result = STO_OK;
-    int iters = 0;
-    while (true) {
-        if ((s = read_head()) != STO_OK) return s;
-        if (hs->nan_flag) {
-            result = STO_ERR_NUMERICAL;
-            h->err = "NaN or Inf in the residual";
-            break;
-        }
-        if (hs->res_inf <= o->tol) break;
-        if (iters >= o->max_iter || halvings > o->max_halvings) {
-            result = STO_NOT_CONVERGED;
-            break;
-        }
-        if (bt == 2 && !nama && simple_fails()) {  // MINFBE: ||hr||^2 came with the FBE gradient
-            if ((s = halve()) != STO_OK) return s;
-            continue;
-        }
+    // One iteration (the FB step and the L-BFGS update around it); restart = the iteration was
+    // abandoned for a step-size halving (backtracking rules), to be tried again.
+    auto body = [&](bool &restart) -> sto_status {
+        sto_status s;
+        restart = false;
         T *gdir = nama ? r : g;
         lb_direction<T>(o->lbfgs_mem, grid, st, m, gdir, ringS, ringY, vs, sc, part, d);
         h->launches += 2 + ng + 2;  // L-BFGS pair, line-search groups, FB step, residual pass
@@ -1307,7 +1304,8 @@ sto_status solver_impl(stotree_t h, int method, const sto_opts *o, const void *x
             const void *ys[2] = {r, d};
             void *outs[2] = {hr, hd};
             void *po[2] = {pvr, pvd};
-            if ((s = solve_round(h, ys, nullptr, outs, 2, true, true, st, nullptr, fg ? po : nullptr)) != STO_OK)
+            if ((s = solve_round(h, ys, nullptr, outs, 2, true, true, st, nullptr, fg ? po : nullptr, &sc->stop)) !=
+                STO_OK)
                 return s;
             if (bt == 2) {  // NAMA: the test needs x_lin(r) of this round
                 k_norm2<T><<<grid, kThreads, 0, st>>>(m, hr, sc, part);
@@ -1315,7 +1313,7 @@ sto_status solver_impl(stotree_t h, int method, const sto_opts *o, const void *x
                 if ((s = read_head()) != STO_OK) return s;
                 if (simple_fails()) {
                     if ((s = halve()) != STO_OK) return s;
-                    continue;
+                    { restart = true; return STO_OK; }
                 }
             }
         } else {
@@ -1359,7 +1357,7 @@ sto_status solver_impl(stotree_t h, int method, const sto_opts *o, const void *x
                 if (fg)
                     STO_CUDA(h, cudaMemcpyAsync(pvh, psave, (size_t)sv.m * sizeof(T), cudaMemcpyDeviceToDevice, st));
                 if ((s = halve()) != STO_OK) return s;
-                continue;
+                { restart = true; return STO_OK; }
             }
         }
         if (!nama) {
@@ -1367,8 +1365,87 @@ sto_status solver_impl(stotree_t h, int method, const sto_opts *o, const void *x
             k_grad<T><<<grid, kThreads, 0, st>>>(m, r, hr, g, ringS, ringY, vs, sc, part);
             h->launches += 1;
         }
-        ++iters;
         STO_CUDA(h, cudaGetLastError());
+        return STO_OK;
+    };
+    sto_status result = STO_OK;
+    int iters = 0;
+    if (ahead) {
+        // One iteration of look-ahead: iteration k + 1 is enqueued before the host reads the
+        // result of iteration k, so the GPU does not idle on the host's decision.  Once a
+        // residual pass finds the run converged (or a NaN), it sets the device's stop flag and
+        // the look-ahead iteration's kernels and solve rounds do nothing; its counts are taken
+        // back below.
+        SolverScalars *hb[2] = {hs, h->host_scal2};
+        cudaEvent_t ev[2];
+        STO_CUDA(h, cudaEventCreateWithFlags(&ev[0], cudaEventDisableTiming));
+        STO_CUDA(h, cudaEventCreateWithFlags(&ev[1], cudaEventDisableTiming));
+        auto head_to = [&](int k) -> sto_status {
+            STO_CUDA(h, cudaMemcpyAsync(hb[k & 1], sc, kScalHead, cudaMemcpyDeviceToHost, st));
+            STO_CUDA(h, cudaEventRecord(ev[k & 1], st));
+            return STO_OK;
+        };
+        const int64_t *cnt[4] = {&h->solve_calls, &h->launches, &h->solve_launches, &h->solve_rhs};
+        int64_t saved[4] = {0, 0, 0, 0};
+        size_t saved_ev = 0;
+        bool pending = false;
+        if ((s = head_to(0)) != STO_OK) return s;
+        while (true) {
+            pending = false;
+            if (iters < o->max_iter) {
+                for (int q = 0; q < 4; ++q) saved[q] = *cnt[q];
+                saved_ev = h->ev_used;
+                bool restart;
+                if ((s = body(restart)) != STO_OK) return s;
+                if ((s = head_to(iters + 1)) != STO_OK) return s;
+                pending = true;
+            }
+            STO_CUDA(h, cudaEventSynchronize(ev[iters & 1]));
+            const SolverScalars *hk = hb[iters & 1];
+            if (hk->nan_flag) {
+                result = STO_ERR_NUMERICAL;
+                h->err = "NaN or Inf in the residual";
+                break;
+            }
+            if (hk->res_inf <= o->tol) break;
+            if (iters >= o->max_iter) {
+                result = STO_NOT_CONVERGED;
+                break;
+            }
+            ++iters;
+        }
+        if (pending) {  // the look-ahead iteration did nothing on the device
+            h->solve_calls = saved[0];
+            h->launches = saved[1];
+            h->solve_launches = saved[2];
+            h->solve_rhs = saved[3];
+            h->ev_used = saved_ev;
+        }
+        STO_CUDA(h, cudaStreamSynchronize(st));
+        cudaEventDestroy(ev[0]);
+        cudaEventDestroy(ev[1]);
+    } else {
+    while (true) {
+        if ((s = read_head()) != STO_OK) return s;
+        if (hs->nan_flag) {
+            result = STO_ERR_NUMERICAL;
+            h->err = "NaN or Inf in the residual";
+            break;
+        }
+        if (hs->res_inf <= o->tol) break;
+        if (iters >= o->max_iter || halvings > o->max_halvings) {
+            result = STO_NOT_CONVERGED;
+            break;
+        }
+        if (bt == 2 && !nama && simple_fails()) {  // MINFBE: ||hr||^2 came with the FBE gradient
+            if ((s = halve()) != STO_OK) return s;
+            continue;
+        }
+        bool restart;
+        if ((s = body(restart)) != STO_OK) return s;
+        if (restart) continue;
+        ++iters;
+    }
     }
     h->launches += 1;
     k_finish_out<T><<<grid, kThreads, 0, st>>>(dv, yb, hv, sc, static_cast<T *>(yv), static_cast<T *>(zv));
