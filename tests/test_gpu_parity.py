@@ -114,6 +114,32 @@ def test_solver_fp64_matches_oracle(cuda_device, p, method):
     assert kkt["feasibility"] < 1e-9 and kkt["sign"] < 1e-12
 
 
+@pytest.mark.parametrize("method", ["nama", "minfbe"])
+@pytest.mark.parametrize("prec", ["fp64", "fp32"])
+def test_lookahead_iteration_is_not_counted(cuda_device, method, prec):
+    """With a fixed step the solvers enqueue iteration k + 1 before reading iteration k's
+    residual; the iteration enqueued after the last one does no work on the device, and its
+    rounds, solve calls and round timings must not be counted: NAMA runs 1 + 2 k rounds (one
+    right-hand side, then two and one per iteration), MINFBE 2 + 3 k, the right-hand sides equal
+    the reported solve calls, and a run stopped by the iteration limit counts the same way."""
+    p = BT_BOXED[1]
+    o = O.LQOracle(p)
+    lam, _ = O.power_lambda(o, np.random.default_rng(0).standard_normal(o.m))
+    st = _st()(p, precision=prec)
+    st.factor()
+    st.set_timing(True)
+    for tol, max_iter in ((1e-8 if prec == "fp64" else 1e-5, 500), (1e-300, 3)):
+        st.get_timing()  # reset
+        res = st.solve(method, lam, tol=tol, max_iter=max_iter, allow_not_converged=True)
+        ms, rounds, rhs = st.get_timing()
+        k = res["info"]["iters"]
+        assert k >= 3
+        assert rounds == (1 + 2 * k if method == "nama" else 2 + 3 * k), (tol, k, rounds)
+        assert rhs == res["info"]["solve_calls"] == (1 + 3 * k if method == "nama" else 2 + 3 * k)
+        assert ms > 0.0
+    st.set_timing(False)
+
+
 FP32_CASES = BOXED[1:] + [D.boxed_problem(12, horizon=3, nx=3, nu=2), D.boxed_problem(17, horizon=4, nx=4, nu=2, frac=0.9),
                           D.boxed_problem(16, horizon=3, nx=5, nu=3, frac=0.9)]
 
