@@ -697,6 +697,17 @@ struct stowarm_s {
     const float *x0 = nullptr, *c = nullptr, *y = nullptr;
     long long tstep_host = 0;
     std::string err;
+    // the backward pass's side branches (weight-gradient products) run on three streams of
+    // their own, forked from and joined back into the caller's stream by events
+    cudaStream_t side[3] = {nullptr, nullptr, nullptr};
+    cudaEvent_t fork[3] = {nullptr, nullptr, nullptr}, join[3] = {nullptr, nullptr, nullptr};
+    ~stowarm_s() {
+        for (int k = 0; k < 3; ++k) {
+            if (side[k]) cudaStreamDestroy(side[k]);
+            if (fork[k]) cudaEventDestroy(fork[k]);
+            if (join[k]) cudaEventDestroy(join[k]);
+        }
+    }
 };
 
 namespace {
@@ -841,6 +852,25 @@ sto_status run_net(stowarm_t h, bool train, bool predict, float *yout, cudaStrea
     e.ldat = n.B;
     WCUDA(h, run_gemm<EPI_OUT>(h->g_l3, e, st));
     if (!train) return STO_OK;
+    // Backward.  The data products dZ2 -> dZ1 are the chain; each weight-gradient product only
+    // needs the transposed copies of one layer, so it runs on a side stream as soon as they are
+    // written (dW3 beside dZ2, dW2 beside dZ1, dW1 beside the bias gradients) and joins the
+    // caller's stream before the optimiser step.  Each writes its own split-K partials, so the
+    // step is the same as when they run one after another.
+    for (int k = 0; k < 3; ++k) {
+        if (!h->side[k]) WCUDA(h, cudaStreamCreateWithFlags(&h->side[k], cudaStreamNonBlocking));
+        if (!h->fork[k]) WCUDA(h, cudaEventCreateWithFlags(&h->fork[k], cudaEventDisableTiming));
+        if (!h->join[k]) WCUDA(h, cudaEventCreateWithFlags(&h->join[k], cudaEventDisableTiming));
+    }
+    // dW3 = dY' A2 (dY' and A2' written by the output layer's epilogue)
+    WCUDA(h, cudaEventRecord(h->fork[0], st));
+    WCUDA(h, cudaStreamWaitEvent(h->side[0], h->fork[0], 0));
+    EpiArgs w = epi0(h);
+    w.C = n.P3;
+    w.ldc = n.DO;
+    w.split_stride = (long long)n.H * n.DO;
+    WCUDA(h, run_gemm<EPI_PART>(h->g_dw3, w, h->side[0]));
+    WCUDA(h, cudaEventRecord(h->join[0], h->side[0]));
     e = epi0(h);
     e.Zin = n.Z2;
     e.ldzin = n.H;
@@ -849,26 +879,32 @@ sto_status run_net(stowarm_t h, bool train, bool predict, float *yout, cudaStrea
     e.AT = n.dZ2T;
     e.ldat = n.B;
     WCUDA(h, run_gemm<EPI_DGELU>(h->g_da2, e, st));
+    // dW2 = dZ2' A1
+    WCUDA(h, cudaEventRecord(h->fork[1], st));
+    WCUDA(h, cudaStreamWaitEvent(h->side[1], h->fork[1], 0));
+    w = epi0(h);
+    w.C = n.P2;
+    w.ldc = n.H;
+    w.split_stride = (long long)n.H * n.H;
+    WCUDA(h, run_gemm<EPI_PART>(h->g_dw2, w, h->side[1]));
+    WCUDA(h, cudaEventRecord(h->join[1], h->side[1]));
     e.Zin = n.Z1;
     e.A = nullptr;
     e.AT = n.dZ1T;
     WCUDA(h, run_gemm<EPI_DGELU>(h->g_da1, e, st));
-    e = epi0(h);
-    e.C = n.P3;
-    e.ldc = n.DO;
-    e.split_stride = (long long)n.H * n.DO;
-    WCUDA(h, run_gemm<EPI_PART>(h->g_dw3, e, st));
-    e.C = n.P2;
-    e.ldc = n.H;
-    e.split_stride = (long long)n.H * n.H;
-    WCUDA(h, run_gemm<EPI_PART>(h->g_dw2, e, st));
-    e.C = n.P1;
-    e.ldc = n.D0;
-    e.split_stride = (long long)n.H * n.D0;
-    WCUDA(h, run_gemm<EPI_PART>(h->g_dw1, e, st));
+    // dW1 = dZ1' X
+    WCUDA(h, cudaEventRecord(h->fork[2], st));
+    WCUDA(h, cudaStreamWaitEvent(h->side[2], h->fork[2], 0));
+    w = epi0(h);
+    w.C = n.P1;
+    w.ldc = n.D0;
+    w.split_stride = (long long)n.H * n.D0;
+    WCUDA(h, run_gemm<EPI_PART>(h->g_dw1, w, h->side[2]));
+    WCUDA(h, cudaEventRecord(h->join[2], h->side[2]));
     const int rows = n.DO + 2 * n.H;
     k_bias_grad<<<(rows + 7) / 8, 256, 0, st>>>(n);
     WCUDA(h, cudaGetLastError());
+    for (int k = 0; k < 3; ++k) WCUDA(h, cudaStreamWaitEvent(st, h->join[k], 0));
     return STO_OK;
 }
 
