@@ -1374,8 +1374,8 @@ sto_status solver_impl(stotree_t h, int method, const sto_opts *o, const void *x
         // One iteration of look-ahead: iteration k + 1 is enqueued before the host reads the
         // result of iteration k, so the GPU does not idle on the host's decision.  Once a
         // residual pass finds the run converged (or a NaN), it sets the device's stop flag and
-        // the look-ahead iteration's kernels and solve rounds do nothing; its counts are taken
-        // back below.
+        // the look-ahead iteration's kernels and solve rounds do nothing; its solve calls and
+        // round timings are taken back below (its launches did happen and stay counted).
         SolverScalars *hb[2] = {hs, h->host_scal2};
         cudaEvent_t ev[2];
         STO_CUDA(h, cudaEventCreateWithFlags(&ev[0], cudaEventDisableTiming));
@@ -1385,15 +1385,15 @@ sto_status solver_impl(stotree_t h, int method, const sto_opts *o, const void *x
             STO_CUDA(h, cudaEventRecord(ev[k & 1], st));
             return STO_OK;
         };
-        const int64_t *cnt[4] = {&h->solve_calls, &h->launches, &h->solve_launches, &h->solve_rhs};
-        int64_t saved[4] = {0, 0, 0, 0};
+        const int64_t *cnt[3] = {&h->solve_calls, &h->solve_launches, &h->solve_rhs};
+        int64_t saved[3] = {0, 0, 0};
         size_t saved_ev = 0;
         bool pending = false;
         if ((s = head_to(0)) != STO_OK) return s;
         while (true) {
             pending = false;
             if (iters < o->max_iter) {
-                for (int q = 0; q < 4; ++q) saved[q] = *cnt[q];
+                for (int q = 0; q < 3; ++q) saved[q] = *cnt[q];
                 saved_ev = h->ev_used;
                 bool restart;
                 if ((s = body(restart)) != STO_OK) return s;
@@ -1416,9 +1416,8 @@ sto_status solver_impl(stotree_t h, int method, const sto_opts *o, const void *x
         }
         if (pending) {  // the look-ahead iteration did nothing on the device
             h->solve_calls = saved[0];
-            h->launches = saved[1];
-            h->solve_launches = saved[2];
-            h->solve_rhs = saved[3];
+            h->solve_launches = saved[1];
+            h->solve_rhs = saved[2];
             h->ev_used = saved_ev;
         }
         STO_CUDA(h, cudaStreamSynchronize(st));
